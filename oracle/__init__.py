@@ -1,0 +1,26 @@
+"""FP64 CPU oracle for the EMIN-AMG V-cycle / FGMRES path (test infrastructure).
+
+This package is TEST INFRASTRUCTURE.  Only the tests, the `smoke()` check in
+`__graft_entry__.py` and the CPU-baseline leg of `bench.py` may import it.  The
+product path (the C++ setup, the CUDA kernels and their Python binding)
+shares no code with it, and it imports nothing from the product.
+
+It is a plain, slow restatement of the method, step by step in the paper's
+order (Alg. 1-4, Section 4.3 for EMIN, Section 5.2 for Braess-Sarazin),
+written with numpy / scipy.sparse primitives and Python loops over graph
+vertices.  Where the paper is silent or garbled, the reading taken is stated
+in the docstring of the function that implements the step.
+
+Parity status per function (the pins are in tests/test_oracle_*.py and
+tests/test_synth.py):
+  * filter_lump, find_coarse_pressures (with the min-distance reading of
+    update_heuristics), pressure_pattern, find_velocity_cpoints,
+    velocity_pattern, emin_step, the Galerkin products, gauss_seidel,
+    bs_sweep, coarse_solve, vcycle, fgmres: pinned (closed forms, the
+    paper's worked special cases, invariants, dense brute force, Table 1).
+  * find_extra_dist3_cpoints: the paper names its criteria but gives no
+    thresholds, and no uniform-mesh case triggers it, so its choices are
+    parity unpinned (only the coverage invariant it must keep is pinned).
+"""
+from .hierarchy import Params, Hierarchy, setup_hierarchy  # noqa: F401
+from .solve import bs_sweep, vcycle, fgmres, apply_A  # noqa: F401

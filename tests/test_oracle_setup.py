@@ -1,0 +1,226 @@
+"""Pins for the oracle's hierarchy setup (Alg. 1-4, eq. e:filtering, eq. min_problem).
+
+Each test checks the oracle against something other than itself: invariants
+the paper states, special cases it works out, closed forms, dense products.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from synth import make_problem, stokes_lid_2d, stokes_pinned_2d, oseen_recirculating_2d
+from oracle import setup_hierarchy, Params
+from oracle.hierarchy import (CPT, FPT, EXCL, bfs, filter_lump, find_coarse_pressures,
+                              find_velocity_cpoints, emin_step, pressure_pattern, kron_identity)
+
+
+@pytest.fixture(scope="module")
+def lid32():
+    p = stokes_lid_2d(32, nrhs=1, body="none", lo=-1.0, hi=1.0)
+    return p, setup_hierarchy(p)
+
+
+def test_filter_keeps_row_sums_and_gives_9_point_pressure_graph(lid32):
+    """eq. e:filtering lumps dropped entries, so row sums are kept; on a uniform
+    mesh the filtered B B^T graph is the 9-point graph (footnote to Fig. 2)."""
+    p, H = lid32
+    L0 = H.levels[0]
+    Z = (L0.B @ L0.B.T).tocsr()
+    F, adj = filter_lump(Z, 0.06)
+    assert np.allclose(np.asarray(F.sum(axis=1)).ravel(), np.asarray(Z.sum(axis=1)).ravel(), atol=1e-15)
+    m = 33
+    for (i, j) in [(10, 10), (16, 5), (1, 20)]:
+        v = j * m + i
+        nb = sorted(adj[v])
+        expect = sorted((j + dy) * m + (i + dx) for dx in (-1, 0, 1) for dy in (-1, 0, 1) if dx or dy)
+        assert nb == expect
+    # filtered graphs have no self loops and are symmetric
+    for v in range(len(adj)):
+        assert v not in adj[v]
+        for w in adj[v]:
+            assert v in adj[w]
+
+
+def test_alg3_distance4_packing_and_coverage(lid32):
+    """After Alg. 3's main loop C-points are pairwise >= 4 apart and every F-point
+    is within distance 3 of a C-point (Section 4.1)."""
+    p, H = lid32
+    L0 = H.levels[0]
+    info = L0.info
+    adj = info["adjp"]
+    main = info["selection_order"]
+    mainset = set(main)
+    for c in main:
+        d = bfs(adj, c, 3)
+        assert not (set(d) - {c}) & mainset
+    state = info["state"]
+    for j in np.flatnonzero(state == FPT):
+        assert any(bfs(adj, int(j), 3).get(c) is not None for c in info["S"][j])
+        assert info["S"][j]
+
+
+def test_alg3_perfect_coarsening_on_uniform_mesh(lid32):
+    """Started at p_{0,0}, the packing heuristic picks every 4th node in each direction,
+    the perfect coarsening of Fig. 2 (right) that the paper says its metrics encourage."""
+    p, H = lid32
+    L0 = H.levels[0]
+    m = 33
+    expect = sorted(j * m + i for i in range(0, m, 4) for j in range(0, m, 4))
+    assert L0.info["Cp"] == expect
+    assert L0.info["extra_p"] == []
+
+
+def test_alg4_midpoints_on_perfect_coarsening(lid32):
+    """Alg. 4 on a perfect distance-4 coarsening adds exactly the even-indexed pressure
+    nodes (targets sit on pressure vertices, Fig. 4); visits 7^d-1 = 48 points and
+    |B_i| <= 3^(d-1) 7^(d-1) = 21 (Section 4.2's cost bound)."""
+    p, H = lid32
+    L0 = H.levels[0]
+    m = 33
+    expect = sorted(j * m + i for i in range(0, m, 2) for j in range(0, m, 2))
+    assert L0.info["Cbar"] == expect
+    assert max(L0.info["visited"]) == 48
+    # |B_i| bound, recomputed from the S sets
+    S = L0.info["S"]
+    state = L0.info["state"]
+    F = [i for i in range(len(state)) if state[i] == FPT]
+    sizes = [sum(1 for j in F if set(S[i]) <= set(S[j])) for i in F[::7]]
+    assert max(sizes) == 21
+
+
+def test_alg4_tau2_large_rejects_midpoints():
+    """With tau2 very large no mid-point passes the distance test except where B_i
+    holds no C-bar point yet; with tau2 = 0 every chosen m is added."""
+    p = stokes_lid_2d(16, nrhs=1, body="none")
+    H = setup_hierarchy(p)
+    info = H.levels[0].info
+    S, state, X = info["S"], info["state"].copy(), p.pcoords
+    Cbar0, _ = find_velocity_cpoints(state, S, X, 0.0)
+    Cbar_big, _ = find_velocity_cpoints(state, S, X, 1e6)
+    C = set(np.flatnonzero(state == CPT))
+    assert C < Cbar_big <= Cbar0
+    assert len(Cbar_big) < len(Cbar0)
+
+
+def test_pinned_pressure_is_excluded():
+    p = stokes_pinned_2d(8)
+    H = setup_hierarchy(p)
+    L0 = H.levels[0]
+    assert L0.info["state"][0] == EXCL
+    assert L0.Pp[0].nnz == 0
+    assert H.levels[1].pinned == -1
+
+
+def test_velocity_pattern_rows(lid32):
+    p, H = lid32
+    L0, L1 = H.levels[0], H.levels[1]
+    P = L0.P
+    Cv = L0.info["Cv"]
+    cnt = np.diff(P.indptr)
+    assert np.all(cnt[L0.dirichlet] == 0)
+    assert np.all(cnt[~L0.dirichlet] > 0)
+    for t, c in enumerate(Cv):
+        assert cnt[c] == 1 and P.indices[P.indptr[c]] == t and P.data[P.indptr[c]] == 1.0
+    # coarse velocities are the interior nodes co-located with the even pressure nodes
+    nv1 = 65
+    expect = sorted(j * nv1 + i for i in range(4, nv1 - 1, 4) for j in range(4, nv1 - 1, 4))
+    assert Cv == expect
+    assert L1.n_v == len(Cv) and L1.n_p == 81
+
+
+def test_emin_constraint_pattern_and_energy(lid32):
+    """P 1 = 1 on every non-excluded row (W in range(P), Section 4.3), the pattern is
+    respected, and one CG step does not raise the energy of the initial guess."""
+    p, H = lid32
+    for L in H.levels[:-1]:
+        for P, rowsmask in ((L.P, ~L.dirichlet), (L.Pp, np.arange(L.n_p) != L.pinned)):
+            s = np.asarray(P.sum(axis=1)).ravel()
+            assert np.abs(s[rowsmask] - 1.0).max() < 1e-12
+            assert np.all(s[~rowsmask] == 0.0)
+    L0 = H.levels[0]
+    info = L0.info
+    rows = pressure_pattern(info["state"], info["S"], info["Cp"])
+    At = info["Ap_filtered"]
+    P1 = emin_step(At, rows, len(info["Cp"]), "cg")
+    cnt = np.array([len(r) for r in rows])
+    P0 = sp.csr_matrix((np.repeat(1.0 / np.maximum(cnt, 1), cnt), np.concatenate([np.array(r, int) for r in rows]),
+                        np.concatenate([[0], np.cumsum(cnt)])), shape=P1.shape)
+    e0 = (P0.multiply(At @ P0)).sum()
+    e1 = (P1.multiply(At @ P1)).sum()
+    assert e1 < e0
+    assert np.array_equal(P1.indices, L0.Pp.indices)
+
+
+def _dense_transfer(L, which):
+    M = L.P if which == "P" else L.R
+    Mp = L.Pp if which == "P" else L.Rp
+    return sp.block_diag([kron_identity(L.dim, M), Mp]).toarray()
+
+
+@pytest.mark.parametrize("case", ["lid", "pinned", "oseen"])
+def test_galerkin_identity_and_block_structure(case):
+    """A_{l+1} = R_l A_l P_l (Alg. 1) against a dense triple product; the coarse
+    (2,2) block is zero, the velocity block is I_d (x) A_hat_{l+1}, and the
+    constant pressure is a null vector on every coarse level."""
+    if case == "lid":
+        p = stokes_lid_2d(16, nrhs=1, body="none")
+    elif case == "pinned":
+        p = stokes_pinned_2d(16)
+    else:
+        p = oseen_recirculating_2d(16, Re=10.0, nrhs=1)
+    H = setup_hierarchy(p)
+    assert len(H.levels) >= 2
+    for l in range(len(H.levels) - 1):
+        L, Lc = H.levels[l], H.levels[l + 1]
+        A = L.full_matrix().toarray()
+        RAP = _dense_transfer(L, "R") @ A @ _dense_transfer(L, "P")
+        Ac = Lc.full_matrix().toarray()
+        assert np.abs(RAP - Ac).max() <= 1e-13 * np.abs(A).max()
+        assert np.abs(Ac[Lc.dim * Lc.n_v:, Lc.dim * Lc.n_v:]).max() == 0.0
+        if case == "pinned":
+            # the pin removes the constant pressure from the null space on every level
+            sv = np.linalg.svd(Ac, compute_uv=False)
+            assert sv[-1] > 1e-8 * sv[0]
+            continue
+        z = np.zeros(Lc.N)
+        z[Lc.dim * Lc.n_v:] = 1.0
+        assert np.abs(Ac @ z).max() <= 1e-12 * np.abs(Ac).max()
+        if case != "oseen":
+            assert np.abs(z @ Ac).max() <= 1e-12 * np.abs(Ac).max()
+            assert abs(Lc.Bt - Lc.B.T).max() <= 1e-14 * abs(Lc.B).max()
+
+
+def test_oseen_restriction_is_petrov_galerkin():
+    """NS case: R != P^T, R comes from EMIN with the transposed pattern (Section 4.3);
+    R^T keeps the pattern of P and R^T 1 = 1."""
+    p = oseen_recirculating_2d(16, Re=100.0, nrhs=1)
+    H = setup_hierarchy(p)
+    L0 = H.levels[0]
+    Rt = L0.R.T.tocsr()
+    Rt.sort_indices()
+    P = L0.P.copy()
+    P.sort_indices()
+    assert np.array_equal(Rt.indptr, P.indptr) and np.array_equal(Rt.indices, P.indices)
+    assert abs(Rt - P).max() > 1e-6
+    s = np.asarray(Rt.sum(axis=1)).ravel()
+    assert np.abs(s[~L0.dirichlet] - 1.0).max() < 1e-12
+
+
+def test_coarsest_level_size_and_operator_complexity():
+    """Table 1 hierarchy shape: coarsest level below 205 dofs and low complexity."""
+    p = stokes_lid_2d(64, nrhs=1, body="none", lo=-1.0, hi=1.0)
+    H = setup_hierarchy(p)
+    assert H.levels[-1].N < 205
+    assert 1.0 < H.complexity() < 1.12
+    sizes = [L.N for L in H.levels]
+    assert all(a > 8 * b for a, b in zip(sizes, sizes[1:-1]))
+
+
+def test_3d_hierarchy_builds_with_null_vector():
+    p = make_problem(4, 3, 0.0, 1.0, bc="lid", nrhs=1)
+    H = setup_hierarchy(p, Params(max_coarse=200))
+    assert len(H.levels) >= 2
+    Lc = H.levels[1]
+    z = np.zeros(Lc.N)
+    z[Lc.dim * Lc.n_v:] = 1.0
+    Ac = Lc.full_matrix()
+    assert np.abs(Ac @ z).max() <= 1e-12 * abs(Ac).max()

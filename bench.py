@@ -1,0 +1,375 @@
+#!/usr/bin/env python3
+"""Benchmark: FGMRES solves/s to a 1e-8 relative residual on the Q2-Q1 lid-driven
+Stokes cavity, 256x256 mesh (592,387 dofs), 8 right-hand sides per launch.
+
+One step = one batched flexible-GMRES solve of the 8 right-hand sides with the
+EMIN-AMG V-cycle as preconditioner: every part of the hot path runs in it (block
+residual, Braess-Sarazin Schur right-hand side, multicolor Gauss-Seidel,
+velocity/pressure update, restriction, prolongation, coarsest solve, FP64
+Arnoldi).  `value` uses the FP32 V-cycle inside FP64 FGMRES; the plain FP64
+V-cycle is timed beside it.  Inputs are resident in HBM when the timed region
+starts; `e2e` repeats the measurement through the host-buffer entry point.
+
+--impl reference times the FP64 CPU oracle on the host cores instead.
+Under torchrun each rank solves its own seeded batch (weak scaling, no
+data-path collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+MESH = 256
+NRHS = 8
+RTOL = 1e-8
+RESTART = 100
+MAXIT = 300
+METRIC = "solves/s @1e-8 rel resid: FP32 V-cycle vs FP64; HBM GB/s; p50/p99 latency"
+WORKLOAD = (f"2D Stokes Q2-Q1 leaky lid-driven cavity, {MESH}x{MESH} mesh (592,387 dofs), nu=1, "
+            f"{NRHS} seeded uniform[-1,1] body loads batched in one launch, FGMRES to {RTOL:g}")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+
+class ClockSampler:
+    """nvidia-smi every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() in ("active", "0x1", "1"):
+                    reasons.add(nm)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+# algorithmic bytes per kernel launch (the per-unit figures are in the design doc)
+
+def algorithmic_bytes(H, level, cls, K, s, zero_fraction=0.25):
+    """Compulsory bytes of one launch of kernel class `cls` on `level`: each matrix
+    entry (value + int32 column) and row pointer read once, each vector operand
+    read or written once (K right-hand sides of s bytes each).  For the Gauss-Seidel
+    class this is one color sweep, i.e. one Gauss-Seidel iteration / n_colors.
+    The velocity predictor's first sweep of a cycle starts from x = 0 and reads no
+    matrix; `zero_fraction` of its launches are of that kind (1 of 4 in V(2,2))."""
+    info = H.level_info(level)
+    d, nv, np_ = info["dim"], info["n_v"], info["n_p"]
+    N = d * nv + np_
+    mat = lambda nnz, rows: nnz * (s + 4) + (rows + 1) * 4  # noqa: E731
+    vec = lambda n: n * K * s  # noqa: E731
+    if cls == "velocity":
+        full = mat(info["nnz_A"], nv) + mat(info["nnz_Bt"], d * nv) + nv * s + vec(d * nv) + vec(N) + vec(d * nv)
+        zero = nv * s + vec(d * nv) + vec(d * nv)
+        return zero_fraction * zero + (1 - zero_fraction) * full
+    if cls == "schur_rhs":
+        return mat(info["nnz_B"], np_) + vec(d * nv) + 2 * vec(np_)
+    if cls == "gs_color":
+        nnz_off = info["nnz_S"] - np_
+        return (mat(nnz_off, np_) + np_ * (4 + s) + 3 * vec(np_)) / info["n_colors"]
+    if cls == "update":
+        return mat(info["nnz_Bt"], d * nv) + nv * s + vec(d * nv) + 2 * vec(np_) + vec(N)
+    if cls == "residual":
+        return (mat(info["nnz_A"], nv) + mat(info["nnz_Bt"], d * nv) + mat(info["nnz_B"], np_) + 3 * vec(N))
+    if cls == "restrict":
+        c = H.level_info(level + 1)
+        return (mat(info["nnz_R"], c["n_v"]) + mat(info["nnz_Rp"], c["n_p"]) + vec(N)
+                + vec(c["dim"] * c["n_v"] + c["n_p"]))
+    if cls == "prolong":
+        c = H.level_info(level + 1)
+        return (mat(info["nnz_P"], nv) + mat(info["nnz_Pp"], np_) + 2 * vec(N) + vec(c["dim"] * c["n_v"] + c["n_p"]))
+    if cls == "coarse":
+        return N * N * 8 + 2 * vec(N)
+    raise KeyError(cls)
+
+
+def load_traffic(kernel, level, K, s):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on the
+    current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        rec = json.load(open(path))
+    except ValueError:
+        return None
+    if rec.get("source_sha") != source_sha():
+        return None
+    e = rec.get("kernels", {}).get(f"{kernel}/L{level}/K{K}/{'f32' if s == 4 else 'f64'}")
+    return e.get("dram_bytes_per_launch") if e else None
+
+
+def source_sha():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1607_02489_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle leg
+
+CPU_SAMPLE = ("the FP64 oracle (numpy/scipy) solving 1 of the 8 right-hand sides of the same "
+              "256x256 lid-cavity workload to 1e-8 with the same method; hierarchy set up beforehand, untimed")
+
+
+def _oracle_worker(n_solves, q):
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    from synth import stokes_lid_2d
+    from oracle import setup_hierarchy, fgmres
+    p = stokes_lid_2d(MESH, nrhs=1, seed=0)
+    Ho = setup_hierarchy(p)
+    times = []
+    its = []
+    for _ in range(n_solves):
+        t0 = time.perf_counter()
+        x, it, rel, _ = fgmres(Ho, p.b, rtol=RTOL, restart=RESTART, maxit=MAXIT)
+        times.append(time.perf_counter() - t0)
+        its.append(int(it[0]))
+    q.put((times, its))
+
+
+def run_oracle(n_solves):
+    """Time the oracle in a fresh single-threaded process (spawned, so no CUDA state is forked)."""
+    import multiprocessing as mp
+    env_before = os.environ.get("OMP_NUM_THREADS")
+    os.environ["OMP_NUM_THREADS"] = "1"
+    os.environ["OPENBLAS_NUM_THREADS"] = "1"
+    os.environ["MKL_NUM_THREADS"] = "1"
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    pr = ctx.Process(target=_oracle_worker, args=(n_solves, q))
+    pr.start()
+    times, its = q.get()
+    pr.join()
+    if env_before is None:
+        os.environ.pop("OMP_NUM_THREADS", None)
+    return times, its
+
+
+def reference_main(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    times, its = run_oracle(args.warmup + args.steps)
+    timed = times[args.warmup:]
+    total = sum(timed)
+    value = len(timed) / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total / len(timed),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "1 right-hand side per step"},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                             "sample": CPU_SAMPLE, "iterations": its[-1]},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_main(args)
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    # the CPU oracle runs first, in a spawned process, before any CUDA work
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        t, its_cpu = run_oracle(1)
+        cpu = {"value": 1.0 / t[0], "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": CPU_SAMPLE,
+               "seconds": t[0], "iterations": its_cpu[0]}
+
+    import paper_1607_02489_gb300 as g
+    from synth import stokes_lid_2d
+    g._build.build()
+    p = stokes_lid_2d(MESH, nrhs=NRHS, seed=rank)
+    H32 = g.Hierarchy(p, max_nrhs=NRHS, vcycle_fp32=1)
+    H64 = g.Hierarchy(p, max_nrhs=NRHS)
+    b = torch.tensor(p.b, device=dev)
+    x = torch.zeros_like(b)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def timed(H, steps, warm):
+        for _ in range(warm):
+            st, its, rel = H.fgmres(b, x, rtol=RTOL, restart=RESTART, maxit=MAXIT)
+            assert st == g.AMG_OK, st
+        barrier()
+        torch.cuda.synchronize()
+        n0 = H.kernel_launches()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        lat = []
+        e0.record(stream)
+        for _ in range(steps):
+            t0 = time.perf_counter()
+            st, its, rel = H.fgmres(b, x, rtol=RTOL, restart=RESTART, maxit=MAXIT)
+            lat.append(time.perf_counter() - t0)
+            assert st == g.AMG_OK and np.all(rel <= RTOL), (st, rel)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, H.kernel_launches() - n0, its, rel, lat
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    ms32, launches32, its32, rel32, lat32 = timed(H32, args.steps, args.warmup)
+    clocks = sampler.stop()
+    ms64, launches64, its64, rel64, lat64 = timed(H64, args.steps, args.warmup)
+
+    solves = NRHS * args.steps * world
+    value = solves / (ms32 / 1000.0)
+    value64 = solves / (ms64 / 1000.0)
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    bh = torch.tensor(p.b).pin_memory()
+    xh = torch.zeros_like(bh).pin_memory()
+    for _ in range(max(1, args.warmup)):
+        H32.fgmres_host(bh, xh, rtol=RTOL, restart=RESTART, maxit=MAXIT)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        st, its_e, rel_e = H32.fgmres_host(bh, xh, rtol=RTOL, restart=RESTART, maxit=MAXIT)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": solves / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": int(bh.numel() * 8),
+           "d2h_bytes_per_step": int(xh.numel() * 8)}
+
+    # dominant V-cycle kernel, timed live with CUDA events on the launching stream
+    H32.vcycle(b, x)
+    reps = 20
+    ms_tab, cnt_tab = H32.profile_vcycle(NRHS, reps=reps)
+    lvl, ci = np.unravel_index(np.argmax(ms_tab), ms_tab.shape)
+    cls = g.KERNEL_CLASSES[ci]
+    avg_ms = ms_tab[lvl, ci] / cnt_tab[lvl, ci]
+    bytes_launch = algorithmic_bytes(H32, int(lvl), cls, NRHS, 4)
+    peak, peak_kind = measured_peaks()
+    achieved = bytes_launch / (avg_ms / 1000.0) / 1e9
+    vcycle_ms = ms_tab.sum() / reps
+    vcycle_bytes = sum(algorithmic_bytes(H32, l, c, NRHS, 4) * cnt_tab[l, k] / reps
+                       for l in range(ms_tab.shape[0]) for k, c in enumerate(g.KERNEL_CLASSES) if cnt_tab[l, k])
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": load_traffic(cls, int(lvl), NRHS, 4),
+                "kernel": f"{cls} (level {int(lvl)}, fp32, {NRHS} rhs)", "peak_kind": peak_kind,
+                "bytes_per_launch": bytes_launch, "avg_launch_us": avg_ms * 1000.0,
+                "vcycle_kernels_GBs": vcycle_bytes / (vcycle_ms / 1000.0) / 1e9,
+                "vcycle_kernels_frac": vcycle_bytes / (vcycle_ms / 1000.0) / 1e9 / peak}
+    breakdown = {f"L{l}/{c}": round(float(ms_tab[l, k] / reps * 1000.0), 2)
+                 for l in range(ms_tab.shape[0]) for k, c in enumerate(g.KERNEL_CLASSES) if cnt_tab[l, k]}
+
+    if rank == 0:
+        lat_sorted = sorted(lat32)
+        line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms32 / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32 V-cycle / f64 FGMRES", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "nrhs_per_launch": NRHS, "restart": RESTART,
+                           "l2": "inputs larger than L2 (hierarchy + Krylov basis > 1 GB)",
+                           "parallelism": f"weak: {world} independent batch(es), one per GPU"},
+                "fp64_vcycle": {"value": value64, "unit": "solves/s", "ms_per_step": ms64 / args.steps,
+                                "iterations": its64.tolist(), "gpu_launches": launches64},
+                "iterations": its32.tolist(), "relres_max": float(np.max(rel32)),
+                "latency_ms": {"p50": 1000 * lat_sorted[len(lat_sorted) // 2],
+                               "p99": 1000 * lat_sorted[min(len(lat_sorted) - 1, int(0.99 * len(lat_sorted)))]},
+                "e2e": e2e, "gpu_launches": launches32, "clocks": clocks, "roofline": roofline,
+                "vcycle_us_by_kernel": breakdown, "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,173 @@
+/*
+ * emin_amg.h — C ABI of the GB300 EMIN-AMG solver for Q2-Q1 Stokes / Oseen systems.
+ *
+ * Method: Prokopenko & Tuminaro, "An algebraic multigrid method for Q2-Q1
+ * mixed discretizations of the Navier-Stokes equations" (arXiv 1607.02489).
+ * The library builds the multigrid hierarchy of Alg. 1 on the host and applies
+ * its V-cycle (Braess-Sarazin relaxation of Section 5.2, EMIN transfers of
+ * Section 4) and a flexible GMRES around it with CUDA kernels on one GPU.
+ *
+ * Conventions for every entry point:
+ *   - The system is the block matrix of eq. stokes_block_system /
+ *     ns_block_system, [I_d (x) A, B^T; B, C], where A is the n_v x n_v scalar
+ *     velocity block shared by the d components, B is n_p x (d*n_v) with
+ *     component-major columns (column c*n_v + i is component c of velocity node
+ *     i) and C is zero except for an optional pinned pressure (C_kk = 1).
+ *   - Dofs are ordered [u_x | u_y (| u_z) | p], N = d*n_v + n_p.
+ *   - A block of nrhs vectors is stored row-major, N x nrhs: entry (dof i,
+ *     right-hand side k) is at index i*nrhs + k.  With nrhs = 1 this is a plain
+ *     vector.  These buffers are DEVICE pointers owned by the caller, except
+ *     in amg_fgmres_solve_host.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream); all GPU
+ *     work of a call is enqueued on it.  Calls that return results to the host
+ *     (iteration counts, residuals) synchronise that stream before returning.
+ *   - Every call returns an amg_status; nothing is thrown across the ABI.
+ *     amg_last_error() gives a message for the last failing call of the
+ *     calling thread.
+ *   - A handle is not thread safe: one call at a time per handle.
+ */
+#ifndef EMIN_AMG_H
+#define EMIN_AMG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct amg_hierarchy* amg_handle;
+
+typedef enum {
+  AMG_OK = 0,
+  AMG_NOT_CONVERGED = 1, /* FGMRES hit maxit; x, iters and relres are valid */
+  AMG_BREAKDOWN = 2,     /* an Arnoldi vector vanished before convergence */
+  AMG_ERR_ARG = -1,      /* invalid argument (null pointer, size, malformed CSR) */
+  AMG_ERR_OOM = -2,      /* host or device allocation failed */
+  AMG_ERR_CUDA = -3,     /* a CUDA call failed */
+  AMG_ERR_SETUP = -4     /* the hierarchy could not be built */
+} amg_status;
+
+/* The problem, all HOST arrays, 0-based int32 indices, columns ascending in a
+ * row, no duplicate entries.  The library copies what it needs during
+ * amg_hierarchy_create; the caller may free these afterwards.
+ * Section 2 (eq. stokes_block_system, ns_block_system) defines A and B; the
+ * coordinates and the pressure-to-velocity co-location are the inputs Alg. 1
+ * and Alg. 4 rely on (Section 4: "our algorithms rely on coordinate
+ * locations"; Section 4.2: co-located velocities). */
+typedef struct {
+  int dim;                         /* 2 or 3 */
+  int n_vnodes;                    /* n_v: velocity nodes per component */
+  int n_pnodes;                    /* n_p: pressure nodes */
+  const int* A_rowptr;             /* n_v + 1 */
+  const int* A_col;                /* nnz(A) */
+  const double* A_val;             /* nnz(A): the velocity block (nu*A_hat [+ K_hat]) */
+  const int* B_rowptr;             /* n_p + 1 */
+  const int* B_col;                /* nnz(B), in [0, dim*n_v) */
+  const double* B_val;             /* nnz(B) */
+  const double* vcoords;           /* n_v x dim, row-major */
+  const double* pcoords;           /* n_p x dim, row-major */
+  const int* p2v;                  /* n_p: velocity node co-located with each pressure node */
+  const unsigned char* v_dirichlet;/* n_v: 1 = Dirichlet node (identity row/column in A, zero B column) */
+  int pinned_p;                    /* pinned pressure node (identity in C, zero B row), -1 = none */
+  int symmetric;                   /* 1: Stokes (R = P^T, one EMIN CG step); 0: Oseen
+                                      (Petrov-Galerkin, one EMIN GMRES step for P and for R) */
+} amg_problem;
+
+/* Method parameters; amg_params_default fills the values of Section 6. */
+typedef struct {
+  double tau1;        /* eq. e:filtering drop tolerance, 0.06 */
+  double tau2sq;      /* Alg. 4 tolerance squared, 1.5e-3 */
+  double omega;       /* Braess-Sarazin relaxation, 0.666 */
+  int omega_on_D;     /* 0: M = [omega D, B^T; B, 0] (eq. bs2's factorisation, default);
+                         1: M = [D/omega, B^T; B, 0] (eq. bs) */
+  int gs_iters;       /* Gauss-Seidel iterations on the Schur complement, 5 */
+  int pre, post;      /* BS sweeps before / after the coarse correction, 2 and 2 */
+  int max_coarse;     /* stop coarsening at <= this many dofs, 200 */
+  int max_levels;     /* 12 */
+  int vcycle_fp32;    /* 0: FP64 V-cycle; 1: FP32 V-cycle (FP32 accumulation), FP64 coarsest solve */
+  int max_nrhs;       /* largest nrhs later passed to vcycle/fgmres (workspace size), 8 */
+  int host_only;      /* 1: build the hierarchy on the host and upload nothing (inspection
+                         calls work, solve calls return AMG_ERR_ARG); 0 (default): upload */
+} amg_params;
+
+void amg_params_default(amg_params* prm);
+
+/* Alg. 1: build the hierarchy on the host (filtering, Alg. 3, Alg. 4, one EMIN
+ * step, Petrov-Galerkin products, Braess-Sarazin data, coarsest pseudo-inverse)
+ * and upload it to the current CUDA device.  Synchronises `stream` once at the
+ * end.  *out is set only on AMG_OK. */
+amg_status amg_hierarchy_create(const amg_problem* prob, const amg_params* prm, void* stream,
+                                amg_handle* out);
+
+/* z = M^-1 r: one V(pre, post) cycle from a zero initial guess (Alg. 1's relaxation
+ * form on every level, coarse correction by R and P).  r and z: device, N x nrhs,
+ * FP64; 1 <= nrhs <= max_nrhs.  r and z must not overlap.  Asynchronous. */
+amg_status amg_vcycle_apply(amg_handle h, const double* r, double* z, int nrhs, void* stream);
+
+/* Block product y = A x on the finest level (device, N x nrhs, FP64). Asynchronous. */
+amg_status amg_apply(amg_handle h, const double* x, double* y, int nrhs, void* stream);
+
+/* Right-preconditioned flexible GMRES with the V-cycle as preconditioner
+ * (Section 6: "multigrid-preconditioned GMRES"), FP64 Arnoldi (classical
+ * Gram-Schmidt with one re-orthogonalisation) and Givens rotations on the
+ * device, x0 = 0, restarted every `restart` iterations, stopped per column when
+ * ||b - A x|| / ||b|| <= rtol (the recurrence residual, then checked with the
+ * true residual recomputed in FP64).  b, x: device, N x nrhs.  iters and
+ * relres: host arrays of nrhs (may be NULL); relres is the true relative
+ * residual.  Synchronises `stream`.  Returns AMG_NOT_CONVERGED if some column
+ * did not reach rtol within maxit iterations. */
+amg_status amg_fgmres_solve(amg_handle h, const double* b, double* x, int nrhs, double rtol,
+                            int restart, int maxit, int* iters, double* relres, void* stream);
+
+/* The same solve with HOST b and x (N x nrhs): the host-to-device copy of b and the
+ * device-to-host copy of x are part of the call. */
+amg_status amg_fgmres_solve_host(amg_handle h, const double* b_host, double* x_host, int nrhs,
+                                 double rtol, int restart, int maxit, int* iters, double* relres,
+                                 void* stream);
+
+/* Kernel timing: run `reps` V-cycles on the current contents of the level-0
+ * input buffer without the CUDA graph, with a CUDA event pair on `stream`
+ * around every kernel launch.  ms and count are caller arrays of
+ * amg_num_levels(h) * AMG_NUM_KERNEL_CLASSES; entry [level * 8 + class] gets the
+ * summed milliseconds and the number of launches of that class on that level.
+ * Classes: 0 velocity predictor, 1 Schur right-hand side, 2 Gauss-Seidel color
+ * sweep, 3 velocity/pressure update, 4 block residual, 5 restriction,
+ * 6 prolongation, 7 coarsest solve.  Synchronises `stream`. */
+#define AMG_NUM_KERNEL_CLASSES 8
+amg_status amg_profile_vcycle(amg_handle h, int nrhs, int reps, double* ms, long long* count, void* stream);
+
+/* Number of CUDA kernels this handle has launched so far (a replayed V-cycle graph
+ * counts each of its kernel nodes).  Host-side counter, no synchronisation. */
+long long amg_kernel_launches(amg_handle h);
+
+/* Hierarchy inspection (host copies kept from the setup), for parity checks and
+ * checkpoints.  Level 0 is the finest. */
+typedef struct {
+  int dim, n_v, n_p, pinned;
+  long long nnz_A, nnz_B, nnz_Bt, nnz_S;
+  int n_colors;
+  long long nnz_P, nnz_Pp, nnz_R, nnz_Rp; /* 0 on the coarsest level */
+  int n_cp, n_cv;                          /* coarse points chosen on this level (0 on the coarsest) */
+} amg_level_info;
+
+int amg_num_levels(amg_handle h);
+amg_status amg_level_get_info(amg_handle h, int level, amg_level_info* info);
+
+/* Copy one matrix of a level to caller-owned host arrays sized from amg_level_info:
+ * which = 0 A, 1 B, 2 Bt (the (1,2) block), 3 S (Schur complement B D^-1 Bt,
+ * original row order), 4 P (velocity, one component), 5 Pp, 6 R, 7 Rp.
+ * rowptr: nrows + 1 (int64), col: nnz, val: nnz. */
+amg_status amg_level_get_matrix(amg_handle h, int level, int which, long long* rowptr, int* col,
+                                double* val);
+
+/* Coarse points of a level as fine indices (cp: n_cp pressure nodes, cv: n_cv
+ * velocity nodes, ascending), the Gauss-Seidel colors of the pressure nodes
+ * (n_p) and the Braess-Sarazin diagonal D (n_v).  Any pointer may be NULL. */
+amg_status amg_level_get_points(amg_handle h, int level, int* cp, int* cv, int* colors, double* D);
+
+void amg_hierarchy_destroy(amg_handle h);
+
+const char* amg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EMIN_AMG_H */

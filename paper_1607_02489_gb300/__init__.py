@@ -1,0 +1,281 @@
+"""Python binding of libemin_amg.so (include/emin_amg.h): argument marshalling only.
+
+Every step of the solve runs in the library's CUDA kernels; this module only
+converts arrays and tensors to the C ABI's pointers and sizes.  There is no
+fallback: if the library is missing or no GPU is present, the calls raise.
+
+Vectors are torch CUDA tensors of shape (N,) or (N, nrhs), float64,
+contiguous, dofs ordered [u_x | u_y (| u_z) | p].
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+LIB_PATH = _build.LIB
+
+AMG_OK, AMG_NOT_CONVERGED, AMG_BREAKDOWN = 0, 1, 2
+STATUS_NAMES = {0: "OK", 1: "NOT_CONVERGED", 2: "BREAKDOWN", -1: "ERR_ARG", -2: "ERR_OOM", -3: "ERR_CUDA",
+                -4: "ERR_SETUP"}
+EXPORTED = ["amg_params_default", "amg_hierarchy_create", "amg_vcycle_apply", "amg_apply", "amg_fgmres_solve",
+            "amg_fgmres_solve_host", "amg_num_levels", "amg_level_get_info", "amg_level_get_matrix",
+            "amg_level_get_points", "amg_hierarchy_destroy", "amg_last_error", "amg_profile_vcycle", "amg_kernel_launches"]
+KERNEL_CLASSES = ["velocity", "schur_rhs", "gs_color", "update", "residual", "restrict", "prolong", "coarse"]
+MATRICES = {"A": 0, "B": 1, "Bt": 2, "S": 3, "P": 4, "Pp": 5, "R": 6, "Rp": 7}
+
+_i32p = ctypes.POINTER(ctypes.c_int)
+_f64p = ctypes.POINTER(ctypes.c_double)
+_u8p = ctypes.POINTER(ctypes.c_ubyte)
+_i64p = ctypes.POINTER(ctypes.c_longlong)
+
+
+class AmgProblem(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n_vnodes", ctypes.c_int), ("n_pnodes", ctypes.c_int),
+                ("A_rowptr", _i32p), ("A_col", _i32p), ("A_val", _f64p),
+                ("B_rowptr", _i32p), ("B_col", _i32p), ("B_val", _f64p),
+                ("vcoords", _f64p), ("pcoords", _f64p), ("p2v", _i32p), ("v_dirichlet", _u8p),
+                ("pinned_p", ctypes.c_int), ("symmetric", ctypes.c_int)]
+
+
+class AmgParams(ctypes.Structure):
+    _fields_ = [("tau1", ctypes.c_double), ("tau2sq", ctypes.c_double), ("omega", ctypes.c_double),
+                ("omega_on_D", ctypes.c_int), ("gs_iters", ctypes.c_int), ("pre", ctypes.c_int),
+                ("post", ctypes.c_int), ("max_coarse", ctypes.c_int), ("max_levels", ctypes.c_int),
+                ("vcycle_fp32", ctypes.c_int), ("max_nrhs", ctypes.c_int), ("host_only", ctypes.c_int)]
+
+
+class AmgLevelInfo(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n_v", ctypes.c_int), ("n_p", ctypes.c_int), ("pinned", ctypes.c_int),
+                ("nnz_A", ctypes.c_longlong), ("nnz_B", ctypes.c_longlong), ("nnz_Bt", ctypes.c_longlong),
+                ("nnz_S", ctypes.c_longlong), ("n_colors", ctypes.c_int),
+                ("nnz_P", ctypes.c_longlong), ("nnz_Pp", ctypes.c_longlong), ("nnz_R", ctypes.c_longlong),
+                ("nnz_Rp", ctypes.c_longlong), ("n_cp", ctypes.c_int), ("n_cv", ctypes.c_int)]
+
+
+_lib = None
+
+
+def load(build_if_missing: bool = False) -> ctypes.CDLL:
+    """Load libemin_amg.so (raise if it is absent; build it first on request)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        if not build_if_missing:
+            raise ImportError(f"{LIB_PATH} is not built; run __graft_entry__.build() or "
+                              "python -m paper_1607_02489_gb300._build")
+        _build.build()
+    lib = ctypes.CDLL(LIB_PATH)
+    vp = ctypes.c_void_p
+    lib.amg_params_default.argtypes = [ctypes.POINTER(AmgParams)]
+    lib.amg_params_default.restype = None
+    lib.amg_hierarchy_create.argtypes = [ctypes.POINTER(AmgProblem), ctypes.POINTER(AmgParams), vp,
+                                         ctypes.POINTER(vp)]
+    lib.amg_hierarchy_create.restype = ctypes.c_int
+    lib.amg_vcycle_apply.argtypes = [vp, vp, vp, ctypes.c_int, vp]
+    lib.amg_vcycle_apply.restype = ctypes.c_int
+    lib.amg_apply.argtypes = [vp, vp, vp, ctypes.c_int, vp]
+    lib.amg_apply.restype = ctypes.c_int
+    for name in ("amg_fgmres_solve", "amg_fgmres_solve_host"):
+        f = getattr(lib, name)
+        f.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, _i32p, _f64p, vp]
+        f.restype = ctypes.c_int
+    lib.amg_profile_vcycle.argtypes = [vp, ctypes.c_int, ctypes.c_int, _f64p, _i64p, vp]
+    lib.amg_profile_vcycle.restype = ctypes.c_int
+    lib.amg_kernel_launches.argtypes = [vp]
+    lib.amg_kernel_launches.restype = ctypes.c_longlong
+    lib.amg_num_levels.argtypes = [vp]
+    lib.amg_num_levels.restype = ctypes.c_int
+    lib.amg_level_get_info.argtypes = [vp, ctypes.c_int, ctypes.POINTER(AmgLevelInfo)]
+    lib.amg_level_get_info.restype = ctypes.c_int
+    lib.amg_level_get_matrix.argtypes = [vp, ctypes.c_int, ctypes.c_int, _i64p, _i32p, _f64p]
+    lib.amg_level_get_matrix.restype = ctypes.c_int
+    lib.amg_level_get_points.argtypes = [vp, ctypes.c_int, _i32p, _i32p, _i32p, _f64p]
+    lib.amg_level_get_points.restype = ctypes.c_int
+    lib.amg_hierarchy_destroy.argtypes = [vp]
+    lib.amg_hierarchy_destroy.restype = None
+    lib.amg_last_error.argtypes = []
+    lib.amg_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+class AmgError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _check(status):
+    if status < 0:
+        raise AmgError(status, load().amg_last_error().decode())
+    return status
+
+
+def default_params(**kw) -> AmgParams:
+    prm = AmgParams()
+    load().amg_params_default(ctypes.byref(prm))
+    for k, v in kw.items():
+        if not hasattr(prm, k):
+            raise KeyError(k)
+        setattr(prm, k, v)
+    return prm
+
+
+def _ptr(a, ctype):
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _dev_ptr(t, what):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError(f"{what} must be a contiguous float64 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Hierarchy:
+    """amg_hierarchy_create over a problem with the fields of synth.Problem
+    (A, B as scipy CSR, vcoords, pcoords, p2v, v_dirichlet, pinned, symmetric, dim)."""
+
+    def __init__(self, prob, stream=None, **params):
+        lib = load()
+        self.dim = int(prob.dim)
+        self.n_v, self.n_p = int(prob.n_v), int(prob.n_p)
+        self.N = self.dim * self.n_v + self.n_p
+        A, B = prob.A, prob.B
+        keep = dict(
+            Ar=np.ascontiguousarray(A.indptr, dtype=np.int32), Ac=np.ascontiguousarray(A.indices, dtype=np.int32),
+            Av=np.ascontiguousarray(A.data, dtype=np.float64),
+            Br=np.ascontiguousarray(B.indptr, dtype=np.int32), Bc=np.ascontiguousarray(B.indices, dtype=np.int32),
+            Bv=np.ascontiguousarray(B.data, dtype=np.float64),
+            vX=np.ascontiguousarray(prob.vcoords, dtype=np.float64),
+            pX=np.ascontiguousarray(prob.pcoords, dtype=np.float64),
+            p2v=np.ascontiguousarray(prob.p2v, dtype=np.int32),
+            dir=np.ascontiguousarray(prob.v_dirichlet, dtype=np.uint8))
+        pb = AmgProblem(self.dim, self.n_v, self.n_p,
+                        _ptr(keep["Ar"], ctypes.c_int), _ptr(keep["Ac"], ctypes.c_int), _ptr(keep["Av"], ctypes.c_double),
+                        _ptr(keep["Br"], ctypes.c_int), _ptr(keep["Bc"], ctypes.c_int), _ptr(keep["Bv"], ctypes.c_double),
+                        _ptr(keep["vX"], ctypes.c_double), _ptr(keep["pX"], ctypes.c_double),
+                        _ptr(keep["p2v"], ctypes.c_int), _ptr(keep["dir"], ctypes.c_ubyte),
+                        int(prob.pinned), 1 if prob.symmetric else 0)
+        self.params = default_params(**params)
+        handle = ctypes.c_void_p()
+        sptr = ctypes.c_void_p(0) if self.params.host_only else _stream_ptr(stream)
+        _check(lib.amg_hierarchy_create(ctypes.byref(pb), ctypes.byref(self.params), sptr, ctypes.byref(handle)))
+        self._h = handle
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().amg_hierarchy_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _nrhs(t):
+        return 1 if t.dim() == 1 else int(t.shape[1])
+
+    def vcycle(self, r, z, stream=None):
+        """z = M^-1 r (amg_vcycle_apply)."""
+        _check(load().amg_vcycle_apply(self._h, _dev_ptr(r, "r"), _dev_ptr(z, "z"), self._nrhs(r), _stream_ptr(stream)))
+        return z
+
+    def apply(self, x, y, stream=None):
+        """y = A x on the finest level (amg_apply)."""
+        _check(load().amg_apply(self._h, _dev_ptr(x, "x"), _dev_ptr(y, "y"), self._nrhs(x), _stream_ptr(stream)))
+        return y
+
+    def fgmres(self, b, x, rtol=1e-8, restart=100, maxit=500, stream=None):
+        """amg_fgmres_solve on device tensors; returns (status, iters, relres)."""
+        k = self._nrhs(b)
+        its = np.zeros(k, dtype=np.int32)
+        rel = np.zeros(k, dtype=np.float64)
+        st = _check(load().amg_fgmres_solve(self._h, _dev_ptr(b, "b"), _dev_ptr(x, "x"), k, float(rtol), int(restart),
+                                            int(maxit), _ptr(its, ctypes.c_int), _ptr(rel, ctypes.c_double),
+                                            _stream_ptr(stream)))
+        return st, its, rel
+
+    def fgmres_host(self, b_host, x_host, rtol=1e-8, restart=100, maxit=500, stream=None):
+        """amg_fgmres_solve_host on host (pinned or pageable) float64 tensors or arrays."""
+        import torch
+        k = 1 if b_host.ndim == 1 else int(b_host.shape[1])
+        for t, nm in ((b_host, "b"), (x_host, "x")):
+            if isinstance(t, torch.Tensor):
+                if t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+                    raise TypeError(f"{nm} must be a contiguous float64 host tensor")
+        bp = ctypes.c_void_p(b_host.data_ptr() if isinstance(b_host, torch.Tensor) else b_host.ctypes.data)
+        xp = ctypes.c_void_p(x_host.data_ptr() if isinstance(x_host, torch.Tensor) else x_host.ctypes.data)
+        its = np.zeros(k, dtype=np.int32)
+        rel = np.zeros(k, dtype=np.float64)
+        st = _check(load().amg_fgmres_solve_host(self._h, bp, xp, k, float(rtol), int(restart), int(maxit),
+                                                 _ptr(its, ctypes.c_int), _ptr(rel, ctypes.c_double),
+                                                 _stream_ptr(stream)))
+        return st, its, rel
+
+    def profile_vcycle(self, nrhs, reps=10, stream=None):
+        """Per (level, kernel class) summed ms and launch counts over `reps` cycles
+        (amg_profile_vcycle); arrays of shape (levels, len(KERNEL_CLASSES))."""
+        L = self.num_levels()
+        ms = np.zeros(L * len(KERNEL_CLASSES))
+        cnt = np.zeros(L * len(KERNEL_CLASSES), dtype=np.int64)
+        _check(load().amg_profile_vcycle(self._h, int(nrhs), int(reps), _ptr(ms, ctypes.c_double),
+                                         _ptr(cnt, ctypes.c_longlong), _stream_ptr(stream)))
+        return ms.reshape(L, -1), cnt.reshape(L, -1)
+
+    def kernel_launches(self) -> int:
+        """Kernels launched by this hierarchy so far (amg_kernel_launches)."""
+        return int(load().amg_kernel_launches(self._h))
+
+    # -- inspection (host copies of the setup) --
+    def num_levels(self) -> int:
+        return load().amg_num_levels(self._h)
+
+    def level_info(self, level: int) -> dict:
+        info = AmgLevelInfo()
+        _check(load().amg_level_get_info(self._h, level, ctypes.byref(info)))
+        return {f: getattr(info, f) for f, _ in AmgLevelInfo._fields_}
+
+    def level_matrix(self, level: int, which: str):
+        """(rowptr int64, col int32, val float64, shape) of one matrix of a level."""
+        info = self.level_info(level)
+        d, nv, np_ = info["dim"], info["n_v"], info["n_p"]
+        nvc = npc = 0
+        if level + 1 < self.num_levels():
+            ci = self.level_info(level + 1)
+            nvc, npc = ci["n_v"], ci["n_p"]
+        shapes = {"A": (nv, nv), "B": (np_, d * nv), "Bt": (d * nv, np_), "S": (np_, np_), "P": (nv, nvc),
+                  "Pp": (np_, npc), "R": (nvc, nv), "Rp": (npc, np_)}
+        nnz = {"A": "nnz_A", "B": "nnz_B", "Bt": "nnz_Bt", "S": "nnz_S", "P": "nnz_P", "Pp": "nnz_Pp",
+               "R": "nnz_R", "Rp": "nnz_Rp"}[which]
+        shape = shapes[which]
+        rp = np.zeros(shape[0] + 1, dtype=np.int64)
+        col = np.zeros(max(info[nnz], 1), dtype=np.int32)
+        val = np.zeros(max(info[nnz], 1), dtype=np.float64)
+        _check(load().amg_level_get_matrix(self._h, level, MATRICES[which], _ptr(rp, ctypes.c_longlong),
+                                           _ptr(col, ctypes.c_int), _ptr(val, ctypes.c_double)))
+        return rp, col[:info[nnz]], val[:info[nnz]], shape
+
+    def level_points(self, level: int) -> dict:
+        info = self.level_info(level)
+        cp = np.zeros(max(info["n_cp"], 1), dtype=np.int32)
+        cv = np.zeros(max(info["n_cv"], 1), dtype=np.int32)
+        colors = np.zeros(max(info["n_p"], 1), dtype=np.int32)
+        D = np.zeros(max(info["n_v"], 1), dtype=np.float64)
+        _check(load().amg_level_get_points(self._h, level, _ptr(cp, ctypes.c_int), _ptr(cv, ctypes.c_int),
+                                           _ptr(colors, ctypes.c_int), _ptr(D, ctypes.c_double)))
+        return dict(Cp=cp[:info["n_cp"]], Cv=cv[:info["n_cv"]], colors=colors[:info["n_p"]], D=D[:info["n_v"]])

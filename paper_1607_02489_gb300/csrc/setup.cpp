@@ -1,0 +1,637 @@
+// Host setup of the EMIN-AMG hierarchy (Alg. 1 with Alg. 2-4 and Section 4.3).
+//
+// Built with -ffp-contract=off: the integer decisions taken from floating
+// point (filtering, the packing heuristic, the mid-point test) must not
+// depend on whether the compiler fuses a multiply and an add.
+#include "setup.hpp"
+
+#include <algorithm>
+#include <cmath>
+#include <deque>
+#include <limits>
+#include <stdexcept>
+#include <string>
+
+namespace emin {
+namespace {
+
+enum : signed char { UNMARKED = 0, CPT = 1, FPT = 2, EXCL = 3 };
+
+struct Graph {
+  int n = 0;
+  std::vector<int64_t> ptr;
+  std::vector<int> adj;  // ascending neighbours, no self loops
+  int64_t begin(int v) const { return ptr[v]; }
+  int64_t end(int v) const { return ptr[v + 1]; }
+};
+
+// eq. e:filtering: drop |z_ij| <= tau sqrt(|z_ii z_jj|), i != j, and add the
+// dropped values to the diagonal (row sums kept).  The graph is the kept
+// off-diagonal pattern, symmetrised by union.
+void filter_lump(const Csr& Z, double tau, Csr& F, Graph& G) {
+  const int n = Z.nrows;
+  std::vector<double> d(n, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int64_t t = Z.row_begin(i); t < Z.row_end(i); ++t)
+      if (Z.col[t] == i) d[i] = d[i] + Z.val[t];
+  F.resize_rows(n, n);
+  std::vector<std::vector<int>> nb(n);
+  for (int i = 0; i < n; ++i) {
+    double lump = 0.0;
+    std::vector<std::pair<int, double>> kept;
+    for (int64_t t = Z.row_begin(i); t < Z.row_end(i); ++t) {
+      const int j = Z.col[t];
+      if (j == i) continue;
+      const double v = Z.val[t];
+      const double thr = tau * std::sqrt(std::fabs(d[i] * d[j]));
+      if (std::fabs(v) <= thr) {
+        lump = lump + v;
+      } else {
+        kept.push_back({j, v});
+        nb[i].push_back(j);
+        nb[j].push_back(i);
+      }
+    }
+    kept.push_back({i, d[i] + lump});
+    std::sort(kept.begin(), kept.end());
+    for (auto& kv : kept) {
+      F.col.push_back(kv.first);
+      F.val.push_back(kv.second);
+    }
+    F.rowptr[i + 1] = (int64_t)F.col.size();
+  }
+  G.n = n;
+  G.ptr.assign(n + 1, 0);
+  G.adj.clear();
+  for (int i = 0; i < n; ++i) {
+    auto& v = nb[i];
+    std::sort(v.begin(), v.end());
+    v.erase(std::unique(v.begin(), v.end()), v.end());
+    G.adj.insert(G.adj.end(), v.begin(), v.end());
+    G.ptr[i + 1] = (int64_t)G.adj.size();
+  }
+}
+
+// Breadth-first search to distance maxd; `stamp` marks visited vertices.
+struct Bfs {
+  std::vector<int> stamp, dist;
+  int epoch = 0;
+  std::vector<int> out;  // visited vertices in BFS order
+  explicit Bfs(int n) : stamp(n, -1), dist(n, 0) {}
+  void run(const Graph& G, int src, int maxd) {
+    ++epoch;
+    out.clear();
+    stamp[src] = epoch;
+    dist[src] = 0;
+    out.push_back(src);
+    for (size_t h = 0; h < out.size(); ++h) {
+      const int v = out[h];
+      if (dist[v] == maxd) continue;
+      for (int64_t t = G.begin(v); t < G.end(v); ++t) {
+        const int w = G.adj[t];
+        if (stamp[w] != epoch) {
+          stamp[w] = epoch;
+          dist[w] = dist[v] + 1;
+          out.push_back(w);
+        }
+      }
+    }
+  }
+};
+
+double sqdist(const double* x, const double* y, int dim) {
+  double s = 0.0;
+  for (int k = 0; k < dim; ++k) {
+    const double t = x[k] - y[k];
+    s = s + t * t;
+  }
+  return s;
+}
+
+double seg_sqdist(const double* x, const double* a, const double* b, int dim) {
+  double ab[3], ax[3];
+  double L2 = 0.0, dot = 0.0;
+  for (int k = 0; k < dim; ++k) {
+    ab[k] = b[k] - a[k];
+    ax[k] = x[k] - a[k];
+  }
+  for (int k = 0; k < dim; ++k) {
+    L2 = L2 + ab[k] * ab[k];
+    dot = dot + ax[k] * ab[k];
+  }
+  double t = L2 > 0.0 ? dot / L2 : 0.0;
+  t = std::min(std::max(t, 0.0), 1.0);
+  double s = 0.0;
+  for (int k = 0; k < dim; ++k) {
+    const double e = ax[k] - t * ab[k];
+    s = s + e * e;
+  }
+  return s;
+}
+
+struct CoarsePressures {
+  std::vector<signed char> state;
+  std::vector<std::vector<std::pair<int, int>>> S;  // (C-point, graph distance <= 3)
+};
+
+// Alg. 3 main loop (find_coarse_pressures) with update_heuristics taken as the
+// smallest Euclidean distance to a C-point within graph distance 4; the next
+// C-point is the lowest-index candidate whose squared distance is within a
+// relative 1e-9 of the smallest one, or the lowest-index unmarked vertex.
+CoarsePressures find_coarse_pressures(const Graph& G, const double* X, int dim, int excluded) {
+  const int n = G.n;
+  CoarsePressures cp;
+  cp.state.assign(n, UNMARKED);
+  cp.S.assign(n, {});
+  if (excluded >= 0) cp.state[excluded] = EXCL;
+  std::vector<double> h1sq(n, std::numeric_limits<double>::infinity());
+  std::vector<char> in_cand(n, 0);
+  std::vector<int> cand;
+  Bfs bfs(n);
+  int next_unmarked = 0;
+  auto lowest_unmarked = [&]() {
+    while (next_unmarked < n && cp.state[next_unmarked] != UNMARKED) ++next_unmarked;
+    return next_unmarked < n ? next_unmarked : -1;
+  };
+  int k = lowest_unmarked();
+  while (k >= 0) {
+    bfs.run(G, k, 4);
+    for (int j : bfs.out)
+      if (bfs.dist[j] <= 3) cp.S[j].push_back({k, bfs.dist[j]});
+    cp.state[k] = CPT;
+    for (int j : bfs.out)
+      if (bfs.dist[j] <= 3 && j != k && cp.state[j] == UNMARKED) cp.state[j] = FPT;
+    for (int j : bfs.out)
+      if (bfs.dist[j] == 4 && !in_cand[j]) {
+        in_cand[j] = 1;
+        cand.push_back(j);
+      }
+    size_t w = 0;
+    for (size_t t = 0; t < cand.size(); ++t) {
+      if (cp.state[cand[t]] == UNMARKED)
+        cand[w++] = cand[t];
+      else
+        in_cand[cand[t]] = 0;
+    }
+    cand.resize(w);
+    for (int j : bfs.out)
+      if (j != k) h1sq[j] = std::min(h1sq[j], sqdist(X + (size_t)j * dim, X + (size_t)k * dim, dim));
+    if (!cand.empty()) {
+      double m = std::numeric_limits<double>::infinity();
+      for (int j : cand) m = std::min(m, h1sq[j]);
+      const double lim = m * (1.0 + 1e-9);
+      int best = -1;
+      for (int j : cand)
+        if (h1sq[j] <= lim && (best < 0 || j < best)) best = j;
+      k = best;
+    } else {
+      k = lowest_unmarked();
+    }
+  }
+  return cp;
+}
+
+// find_extra_dist3_Cpoints: in index order convert F-points with |S_j| = 1 at
+// graph distance 3, or |S_j| = 2 at distance 3 from both C-points and farther
+// than a quarter of their separation from the segment joining them.
+std::vector<int> find_extra_dist3_cpoints(const Graph& G, const double* X, int dim, CoarsePressures& cp) {
+  std::vector<int> added;
+  Bfs bfs(G.n);
+  for (int j = 0; j < G.n; ++j) {
+    if (cp.state[j] != FPT) continue;
+    auto s = cp.S[j];
+    std::sort(s.begin(), s.end());
+    bool convert = false;
+    if (s.size() == 1) {
+      convert = s[0].second == 3;
+    } else if (s.size() == 2) {
+      const int a = s[0].first, b = s[1].first;
+      if (s[0].second == 3 && s[1].second == 3) {
+        const double L2 = sqdist(X + (size_t)a * dim, X + (size_t)b * dim, dim);
+        convert = seg_sqdist(X + (size_t)j * dim, X + (size_t)a * dim, X + (size_t)b * dim, dim) > 0.0625 * L2;
+      }
+    }
+    if (convert) {
+      cp.state[j] = CPT;
+      added.push_back(j);
+      bfs.run(G, j, 3);
+      for (int v : bfs.out) cp.S[v].push_back({j, bfs.dist[v]});
+    }
+  }
+  return added;
+}
+
+std::vector<int> sorted_keys(const std::vector<std::pair<int, int>>& s) {
+  std::vector<int> k;
+  k.reserve(s.size());
+  for (auto& e : s) k.push_back(e.first);
+  std::sort(k.begin(), k.end());
+  return k;
+}
+
+// Alg. 4 (find_velocity_Cpoints): pressure mid-points, processed by descending
+// |S_i| then index; t_i^2 is the squared diagonal of B_i's bounding box and the
+// test is min squared distance >= tau2^2 t_i^2 (+inf when B_i has no C-bar point).
+std::vector<char> find_velocity_cpoints(const CoarsePressures& cp, const double* X, int dim, double tau2sq) {
+  const int n = (int)cp.state.size();
+  std::vector<int> F;
+  for (int i = 0; i < n; ++i)
+    if (cp.state[i] == FPT) F.push_back(i);
+  std::vector<std::vector<int>> keys(n);
+  std::vector<std::vector<int>> users(n);
+  for (int j : F) {
+    keys[j] = sorted_keys(cp.S[j]);
+    for (int c : keys[j]) users[c].push_back(j);
+  }
+  std::vector<char> Cbar(n, 0);
+  for (int i = 0; i < n; ++i)
+    if (cp.state[i] == CPT) Cbar[i] = 1;
+  std::vector<int> order = F;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    if (keys[a].size() != keys[b].size()) return keys[a].size() > keys[b].size();
+    return a < b;
+  });
+  std::vector<int> Bi;
+  for (int i : order) {
+    const auto& s = keys[i];
+    double Xi[3] = {0, 0, 0};
+    for (int k = 0; k < dim; ++k) {
+      double acc = 0.0;
+      for (int c : s) acc = acc + X[(size_t)c * dim + k];
+      Xi[k] = acc / (double)s.size();
+    }
+    Bi.clear();
+    for (int j : users[s[0]]) {
+      if (cp.state[j] != FPT) continue;
+      const auto& kj = keys[j];
+      if (std::includes(kj.begin(), kj.end(), s.begin(), s.end())) Bi.push_back(j);
+    }
+    std::sort(Bi.begin(), Bi.end());
+    double t2 = 0.0;
+    for (int k = 0; k < dim; ++k) {
+      double mx = -std::numeric_limits<double>::infinity(), mn = std::numeric_limits<double>::infinity();
+      for (int j : Bi) {
+        mx = std::max(mx, X[(size_t)j * dim + k]);
+        mn = std::min(mn, X[(size_t)j * dim + k]);
+      }
+      const double e = mx - mn;
+      t2 = t2 + e * e;
+    }
+    int m = -1;
+    double best = 0.0;
+    for (int j : Bi) {
+      const double dj = sqdist(X + (size_t)j * dim, Xi, dim);
+      if (m < 0 || dj < best) {
+        best = dj;
+        m = j;
+      }
+    }
+    double dmin = std::numeric_limits<double>::infinity();
+    for (int j : Bi)
+      if (Cbar[j]) dmin = std::min(dmin, sqdist(X + (size_t)j * dim, X + (size_t)m * dim, dim));
+    if (dmin >= tau2sq * t2) Cbar[m] = 1;
+  }
+  return Cbar;
+}
+
+// Velocity pattern: C^(v) nodes within distance 3 in the filtered velocity
+// graph; extra C-points for non-Dirichlet nodes left without one (index order);
+// C rows injection, Dirichlet rows empty.  Returns rows of coarse indices.
+std::vector<std::vector<int>> velocity_pattern(const Graph& G, std::vector<char>& isC,
+                                               const std::vector<unsigned char>& dirichlet,
+                                               std::vector<int>& Cv) {
+  const int n = G.n;
+  std::vector<std::vector<int>> rows(n);
+  Bfs bfs(n);
+  for (int c = 0; c < n; ++c) {
+    if (!isC[c]) continue;
+    bfs.run(G, c, 3);
+    for (int v : bfs.out) rows[v].push_back(c);
+  }
+  for (int i = 0; i < n; ++i) {
+    if (dirichlet[i] || isC[i] || !rows[i].empty()) continue;
+    isC[i] = 1;
+    bfs.run(G, i, 3);
+    for (int v : bfs.out) rows[v].push_back(i);
+  }
+  Cv.clear();
+  std::vector<int> cidx(n, -1);
+  for (int i = 0; i < n; ++i)
+    if (isC[i]) {
+      cidx[i] = (int)Cv.size();
+      Cv.push_back(i);
+    }
+  std::vector<std::vector<int>> out(n);
+  for (int i = 0; i < n; ++i) {
+    if (dirichlet[i]) continue;
+    if (isC[i]) {
+      out[i] = {cidx[i]};
+      continue;
+    }
+    for (int c : rows[i]) out[i].push_back(cidx[c]);
+    std::sort(out[i].begin(), out[i].end());
+    out[i].erase(std::unique(out[i].begin(), out[i].end()), out[i].end());
+  }
+  return out;
+}
+
+Csr pattern_csr(const std::vector<std::vector<int>>& rows, int ncols) {
+  Csr N;
+  N.resize_rows((int)rows.size(), ncols);
+  for (size_t i = 0; i < rows.size(); ++i) {
+    for (int c : rows[i]) {
+      N.col.push_back(c);
+      N.val.push_back(1.0);
+    }
+    N.rowptr[i + 1] = (int64_t)N.col.size();
+  }
+  return N;
+}
+
+// Orthogonal projection onto {pattern of N, zero row sums}: G sampled on the
+// pattern minus each row's mean over the pattern.
+Csr project(const Csr& G, const Csr& N) {
+  Csr Q = N;
+  for (int i = 0; i < N.nrows; ++i) {
+    const int64_t b = N.row_begin(i), e = N.row_end(i);
+    if (b == e) continue;
+    double sum = 0.0;
+    int64_t g = G.row_begin(i);
+    for (int64_t t = b; t < e; ++t) {
+      while (g < G.row_end(i) && G.col[g] < N.col[t]) ++g;
+      Q.val[t] = (g < G.row_end(i) && G.col[g] == N.col[t]) ? G.val[g] : 0.0;
+      sum = sum + Q.val[t];
+    }
+    const double mean = sum / (double)(e - b);
+    for (int64_t t = b; t < e; ++t) Q.val[t] = Q.val[t] - mean;
+  }
+  return Q;
+}
+
+// One EMIN step (eq. min_problem): P0 = pattern / row count,
+// R0 = -Proj(At P0); CG: alpha = <R0,R0> / <R0, At R0>; GMRES: Q = Proj(At R0),
+// alpha = <R0,Q> / <Q,Q>; P = P0 + alpha R0 on the pattern.
+Csr emin_step(const Csr& At, const std::vector<std::vector<int>>& rows, int ncols, bool cg) {
+  Csr P = pattern_csr(rows, ncols);
+  for (int i = 0; i < P.nrows; ++i) {
+    const int64_t cnt = P.row_end(i) - P.row_begin(i);
+    for (int64_t t = P.row_begin(i); t < P.row_end(i); ++t) P.val[t] = 1.0 / (double)cnt;
+  }
+  Csr R0 = project(spgemm(At, P), P);
+  for (auto& v : R0.val) v = -v;
+  double num = 0.0, den = 0.0;
+  if (cg) {
+    for (double v : R0.val) num += v * v;
+    Csr AR = spgemm(At, R0);
+    for (int i = 0; i < R0.nrows; ++i)
+      for (int64_t t = R0.row_begin(i); t < R0.row_end(i); ++t) den += R0.val[t] * lookup(AR, i, R0.col[t]);
+  } else {
+    Csr Q = project(spgemm(At, R0), P);
+    for (size_t t = 0; t < R0.val.size(); ++t) {
+      num += R0.val[t] * Q.val[t];
+      den += Q.val[t] * Q.val[t];
+    }
+  }
+  const double alpha = den != 0.0 ? num / den : 0.0;
+  for (size_t t = 0; t < P.val.size(); ++t) P.val[t] = P.val[t] + alpha * R0.val[t];
+  return P;
+}
+
+// Braess-Sarazin data (Section 5.2): D = |A| row sums (Dirichlet rows 1/c), the
+// explicit Schur complement S = B D^-1 Bt (pinned row = identity) and a greedy
+// coloring of its graph (vertices in index order, smallest free color).
+void form_relaxation(HostLevel& L, const SetupParams& prm) {
+  L.D.assign(L.n_v, 0.0);
+  for (int i = 0; i < L.n_v; ++i) {
+    double s = 0.0;
+    for (int64_t t = L.A.row_begin(i); t < L.A.row_end(i); ++t) s += std::fabs(L.A.val[t]);
+    L.D[i] = L.dirichlet[i] ? 1.0 / prm.c : s;
+  }
+  Csr BD = L.B;
+  for (int64_t t = 0; t < BD.nnz(); ++t) BD.val[t] = BD.val[t] * (1.0 / L.D[BD.col[t] % L.n_v]);
+  L.S = spgemm(BD, L.Bt);
+  if (L.pinned >= 0) {
+    Csr S2;
+    S2.resize_rows(L.S.nrows, L.S.ncols);
+    for (int i = 0; i < L.S.nrows; ++i) {
+      bool done = false;
+      for (int64_t t = L.S.row_begin(i); t < L.S.row_end(i); ++t) {
+        const int j = L.S.col[t];
+        if (i == L.pinned && !done && j > i) {
+          S2.col.push_back(i);
+          S2.val.push_back(1.0);
+          done = true;
+        }
+        S2.col.push_back(j);
+        S2.val.push_back((i == L.pinned && j == i) ? 1.0 : L.S.val[t]);
+        if (i == L.pinned && j == i) done = true;
+      }
+      if (i == L.pinned && !done) {
+        S2.col.push_back(i);
+        S2.val.push_back(1.0);
+      }
+      S2.rowptr[i + 1] = (int64_t)S2.col.size();
+    }
+    L.S = std::move(S2);
+  }
+  L.colors.assign(L.n_p, -1);
+  L.n_colors = 0;
+  std::vector<int> used_stamp(64, -1);
+  for (int i = 0; i < L.n_p; ++i) {
+    for (int64_t t = L.S.row_begin(i); t < L.S.row_end(i); ++t) {
+      const int j = L.S.col[t];
+      if (j != i && L.colors[j] >= 0) {
+        if (L.colors[j] >= (int)used_stamp.size()) used_stamp.resize(2 * L.colors[j] + 2, -1);
+        used_stamp[L.colors[j]] = i;
+      }
+    }
+    int c = 0;
+    while (c < (int)used_stamp.size() && used_stamp[c] == i) ++c;
+    if (c >= (int)used_stamp.size()) used_stamp.resize(2 * c + 2, -1);
+    L.colors[i] = c;
+    L.n_colors = std::max(L.n_colors, c + 1);
+  }
+}
+
+// Dense block matrix of a level, row-major N x N.
+std::vector<double> dense_level(const HostLevel& L) {
+  const int N = L.N(), nu = L.dim * L.n_v;
+  std::vector<double> M((size_t)N * N, 0.0);
+  for (int c = 0; c < L.dim; ++c)
+    for (int i = 0; i < L.n_v; ++i)
+      for (int64_t t = L.A.row_begin(i); t < L.A.row_end(i); ++t)
+        M[(size_t)(c * L.n_v + i) * N + c * L.n_v + L.A.col[t]] += L.A.val[t];
+  for (int r = 0; r < nu; ++r)
+    for (int64_t t = L.Bt.row_begin(r); t < L.Bt.row_end(r); ++t) M[(size_t)r * N + nu + L.Bt.col[t]] += L.Bt.val[t];
+  for (int k = 0; k < L.n_p; ++k)
+    for (int64_t t = L.B.row_begin(k); t < L.B.row_end(k); ++t) M[(size_t)(nu + k) * N + L.B.col[t]] += L.B.val[t];
+  if (L.pinned >= 0) M[(size_t)(nu + L.pinned) * N + nu + L.pinned] += 1.0;
+  return M;
+}
+
+// Pseudo-inverse by the one-sided Jacobi SVD (Hestenes 1958): rotate column
+// pairs of M until they are orthogonal; then M = U S V^T with the column norms
+// as singular values; singular values below rcond * max are dropped.
+std::vector<double> pseudo_inverse(const std::vector<double>& M, int n, double rcond) {
+  std::vector<double> U((size_t)n * n), V((size_t)n * n, 0.0);  // column j at [j*n, j*n+n)
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) U[(size_t)j * n + i] = M[(size_t)i * n + j];
+  for (int j = 0; j < n; ++j) V[(size_t)j * n + j] = 1.0;
+  for (int sweep = 0; sweep < 80; ++sweep) {
+    double off = 0.0;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        double* up = &U[(size_t)p * n];
+        double* uq = &U[(size_t)q * n];
+        double a = 0.0, b = 0.0, g = 0.0;
+        for (int i = 0; i < n; ++i) {
+          a += up[i] * up[i];
+          b += uq[i] * uq[i];
+          g += up[i] * uq[i];
+        }
+        if (a == 0.0 || b == 0.0) continue;
+        const double rel = std::fabs(g) / std::sqrt(a * b);
+        if (rel <= 1e-15) continue;
+        off = std::max(off, rel);
+        const double zeta = (b - a) / (2.0 * g);
+        const double t = (zeta >= 0 ? 1.0 : -1.0) / (std::fabs(zeta) + std::sqrt(1.0 + zeta * zeta));
+        const double c = 1.0 / std::sqrt(1.0 + t * t), s = c * t;
+        double* vp = &V[(size_t)p * n];
+        double* vq = &V[(size_t)q * n];
+        for (int i = 0; i < n; ++i) {
+          const double x = up[i], y = uq[i];
+          up[i] = c * x - s * y;
+          uq[i] = s * x + c * y;
+          const double xv = vp[i], yv = vq[i];
+          vp[i] = c * xv - s * yv;
+          vq[i] = s * xv + c * yv;
+        }
+      }
+    if (off <= 1e-15) break;
+  }
+  std::vector<double> s(n);
+  double smax = 0.0;
+  for (int j = 0; j < n; ++j) {
+    double a = 0.0;
+    for (int i = 0; i < n; ++i) a += U[(size_t)j * n + i] * U[(size_t)j * n + i];
+    s[j] = std::sqrt(a);
+    smax = std::max(smax, s[j]);
+  }
+  std::vector<double> Pinv((size_t)n * n, 0.0);
+  for (int j = 0; j < n; ++j) {
+    if (!(s[j] > rcond * smax)) continue;
+    const double inv2 = 1.0 / (s[j] * s[j]);
+    const double* u = &U[(size_t)j * n];
+    const double* v = &V[(size_t)j * n];
+    for (int i = 0; i < n; ++i) {
+      const double vi = v[i] * inv2;
+      double* row = &Pinv[(size_t)i * n];
+      for (int k = 0; k < n; ++k) row[k] += vi * u[k];
+    }
+  }
+  return Pinv;
+}
+
+// Alg. 2 + form_restriction + the Petrov-Galerkin product; false when the
+// coarsening makes no progress.
+bool form_interpolation(HostLevel& L, HostLevel& Lc, const SetupParams& prm) {
+  const int d = L.dim;
+  // form_aux_block_diagonal
+  Csr Zp = spgemm(L.B, transpose(L.B));
+  Csr Ap, Av;
+  Graph Gp, Gv;
+  filter_lump(Zp, prm.tau1, Ap, Gp);
+  filter_lump(L.A, prm.tau1, Av, Gv);
+  // Alg. 3
+  CoarsePressures cp = find_coarse_pressures(Gp, L.pX.data(), d, L.pinned);
+  find_extra_dist3_cpoints(Gp, L.pX.data(), d, cp);
+  L.Cp.clear();
+  std::vector<int> cidx(L.n_p, -1);
+  for (int i = 0; i < L.n_p; ++i)
+    if (cp.state[i] == CPT) {
+      cidx[i] = (int)L.Cp.size();
+      L.Cp.push_back(i);
+    }
+  if ((int)L.Cp.size() >= L.n_p) return false;
+  // pressure pattern: S_i for F-points, injection for C-points, empty if excluded
+  std::vector<std::vector<int>> rows_p(L.n_p);
+  for (int i = 0; i < L.n_p; ++i) {
+    if (cp.state[i] == CPT) {
+      rows_p[i] = {cidx[i]};
+    } else if (cp.state[i] == FPT) {
+      for (auto& e : cp.S[i]) rows_p[i].push_back(cidx[e.first]);
+      std::sort(rows_p[i].begin(), rows_p[i].end());
+    }
+  }
+  const bool cg = prm.symmetric;
+  L.Pp = emin_step(Ap, rows_p, (int)L.Cp.size(), cg);
+  // Alg. 4 and co-located velocities
+  std::vector<char> Cbar = find_velocity_cpoints(cp, L.pX.data(), d, prm.tau2sq);
+  std::vector<char> isCv(L.n_v, 0);
+  for (int k = 0; k < L.n_p; ++k)
+    if (Cbar[k]) {
+      const int v = L.p2v[k];
+      if (v >= 0 && !L.dirichlet[v]) isCv[v] = 1;
+    }
+  std::vector<std::vector<int>> rows_v = velocity_pattern(Gv, isCv, L.dirichlet, L.Cv);
+  L.P = emin_step(Av, rows_v, (int)L.Cv.size(), cg);
+  // form_restriction (Section 4.3)
+  if (cg) {
+    L.R = transpose(L.P);
+    L.Rp = transpose(L.Pp);
+  } else {
+    L.R = transpose(emin_step(transpose(Av), rows_v, (int)L.Cv.size(), false));
+    L.Rp = transpose(emin_step(transpose(Ap), rows_p, (int)L.Cp.size(), false));
+  }
+  // Petrov-Galerkin product A_{l+1} = R A P, block by block
+  Csr Pv = kron_identity(d, L.P), Rv = kron_identity(d, L.R);
+  Lc.dim = d;
+  Lc.n_v = (int)L.Cv.size();
+  Lc.n_p = (int)L.Cp.size();
+  Lc.pinned = -1;
+  Lc.A = spgemm(spgemm(L.R, L.A), L.P);
+  Lc.B = spgemm(spgemm(L.Rp, L.B), Pv);
+  Lc.Bt = spgemm(spgemm(Rv, L.Bt), L.Pp);
+  // project_coordinates: injection; co-location restricted to the coarse points
+  Lc.vX.resize((size_t)Lc.n_v * d);
+  Lc.pX.resize((size_t)Lc.n_p * d);
+  for (int t = 0; t < Lc.n_v; ++t)
+    for (int k = 0; k < d; ++k) Lc.vX[(size_t)t * d + k] = L.vX[(size_t)L.Cv[t] * d + k];
+  for (int t = 0; t < Lc.n_p; ++t)
+    for (int k = 0; k < d; ++k) Lc.pX[(size_t)t * d + k] = L.pX[(size_t)L.Cp[t] * d + k];
+  std::vector<int> vpos(L.n_v, -1);
+  for (int t = 0; t < Lc.n_v; ++t) vpos[L.Cv[t]] = t;
+  Lc.p2v.resize(Lc.n_p);
+  for (int t = 0; t < Lc.n_p; ++t) {
+    const int v = L.p2v[L.Cp[t]];
+    Lc.p2v[t] = v >= 0 ? vpos[v] : -1;
+  }
+  Lc.dirichlet.assign(Lc.n_v, 0);
+  return true;
+}
+
+}  // namespace
+
+std::vector<HostLevel> build_hierarchy(HostLevel fine, const SetupParams& prm) {
+  std::vector<HostLevel> levels;
+  levels.push_back(std::move(fine));
+  while (true) {
+    HostLevel& L = levels.back();
+    form_relaxation(L, prm);
+    if (L.N() <= prm.max_coarse || (int)levels.size() == prm.max_levels) break;
+    HostLevel Lc;
+    if (!form_interpolation(L, Lc, prm) || Lc.N() >= L.N()) {
+      L.P = L.Pp = L.R = L.Rp = Csr();
+      L.Cp.clear();
+      L.Cv.clear();
+      break;
+    }
+    levels.push_back(std::move(Lc));
+  }
+  HostLevel& C = levels.back();
+  if (C.N() > 4096) throw std::runtime_error("coarsest level too large for the dense solve: " + std::to_string(C.N()));
+  C.pinv = pseudo_inverse(dense_level(C), C.N(), 1e-12);
+  return levels;
+}
+
+}  // namespace emin

@@ -1,0 +1,47 @@
+// Host-side multigrid hierarchy (Alg. 1) for Q2-Q1 saddle-point systems.
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "csr.hpp"
+
+namespace emin {
+
+struct SetupParams {
+  double tau1 = 0.06;      // eq. e:filtering
+  double tau2sq = 1.5e-3;  // Alg. 4, tau2 = sqrt(1.5e-3)
+  double c = 0.666;        // scale of D in the (1,1) block of the Braess-Sarazin matrix
+  int max_coarse = 200;
+  int max_levels = 12;
+  bool symmetric = true;   // one EMIN CG step, R = P^T; otherwise EMIN GMRES for P and R
+};
+
+struct HostLevel {
+  int dim = 2, n_v = 0, n_p = 0, pinned = -1;
+  Csr A;   // n_v x n_v scalar velocity block
+  Csr B;   // n_p x dim*n_v, the (2,1) block
+  Csr Bt;  // dim*n_v x n_p, the (1,2) block
+  std::vector<double> vX, pX;          // coordinates, row-major
+  std::vector<int> p2v;                // co-located velocity node or -1
+  std::vector<unsigned char> dirichlet;
+  // Braess-Sarazin data (Section 5.2)
+  std::vector<double> D;               // |A| row sums; Dirichlet rows 1/c
+  Csr S;                               // B D^-1 Bt, pinned row = identity
+  std::vector<int> colors;             // greedy coloring of S's graph
+  int n_colors = 0;
+  // transfers to the next level
+  Csr P, Pp, R, Rp;
+  std::vector<int> Cp, Cv;             // coarse points (fine indices, ascending)
+  // coarsest level
+  std::vector<double> pinv;            // N x N row-major pseudo-inverse
+  int N() const { return dim * n_v + n_p; }
+  long long nnz_total() const {
+    return (long long)dim * A.nnz() + B.nnz() + Bt.nnz() + (pinned >= 0 ? 1 : 0);
+  }
+};
+
+// Builds every level; throws std::runtime_error with a message on failure.
+std::vector<HostLevel> build_hierarchy(HostLevel fine, const SetupParams& prm);
+
+}  // namespace emin

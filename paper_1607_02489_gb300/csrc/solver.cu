@@ -1,0 +1,711 @@
+// C ABI (include/emin_amg.h): hierarchy creation, V-cycle application and the
+// flexible GMRES driver with its FP64 Arnoldi / Givens kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/emin_amg.h"
+#include "setup.hpp"
+#include "vcycle.cuh"
+
+using namespace emin;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+amg_status fail(amg_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+int round_k(int nrhs) {
+  int K = 1;
+  while (K < nrhs) K <<= 1;
+  return K;
+}
+
+// ---------------------------------------------------------------------------
+// FGMRES kernels (FP64).  Vectors are N x K interleaved; a block of basis
+// vectors is nv consecutive vectors of N*K entries.
+
+constexpr int kRedBlocks = 608;  // 4 blocks per SM on 152 SMs for the streaming reductions
+
+// part[(blk*nv + i)*K + k] = sum over this block's entries with rhs k of V_i[e] * w[e].
+template <int K, typename TV>
+__global__ void __launch_bounds__(kBlock) k_mdot_partial(long long NK, int nv, const TV* __restrict__ V,
+                                                         const double* __restrict__ w, double* __restrict__ part) {
+  __shared__ double sm[kBlock / 32][K];
+  const int k = threadIdx.x % K;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (int i = 0; i < nv; ++i) {
+    const TV* Vi = V + (size_t)i * NK;
+    double acc = 0.0;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < NK; e += stride)
+      acc += (double)Vi[e] * w[e];
+#pragma unroll
+    for (int off = 16; off >= K; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) < K) sm[threadIdx.x >> 5][k] = acc;
+    __syncthreads();
+    if (threadIdx.x < K) {
+      double s = 0.0;
+      for (int wp = 0; wp < kBlock / 32; ++wp) s += sm[wp][threadIdx.x];
+      part[((size_t)blockIdx.x * nv + i) * K + threadIdx.x] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// out[t] (+)= sum over blocks of part, t = i*K + k, fixed summation order.
+__global__ void k_reduce_partials(int nblk, int nvK, const double* __restrict__ part, double* __restrict__ out,
+                                  int accumulate, int take_sqrt) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nvK) return;
+  double s = 0.0;
+  for (int b = 0; b < nblk; ++b) s += part[(size_t)b * nvK + t];
+  if (take_sqrt) s = sqrt(s);
+  out[t] = accumulate ? out[t] + s : s;
+}
+
+// w -= sum_i V_i h_i (per rhs); with nrm_part, also the partial sums of |w|^2.
+template <int K, typename TV>
+__global__ void __launch_bounds__(kBlock) k_maxpy(long long NK, int nv, const TV* __restrict__ V,
+                                                  const double* __restrict__ h, double* __restrict__ w,
+                                                  double* __restrict__ nrm_part) {
+  __shared__ double sm[kBlock / 32][K];
+  const int k = threadIdx.x % K;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  double acc = 0.0;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < NK; e += stride) {
+    double s = w[e];
+    for (int i = 0; i < nv; ++i) s -= (double)V[(size_t)i * NK + e] * h[i * K + k];
+    w[e] = s;
+    acc += s * s;
+  }
+  if (!nrm_part) return;
+#pragma unroll
+  for (int off = 16; off >= K; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  if ((threadIdx.x & 31) < K) sm[threadIdx.x >> 5][k] = acc;
+  __syncthreads();
+  if (threadIdx.x < K) {
+    double s = 0.0;
+    for (int wp = 0; wp < kBlock / 32; ++wp) s += sm[wp][threadIdx.x];
+    nrm_part[(size_t)blockIdx.x * K + threadIdx.x] = s;
+  }
+}
+
+// v = w / nrm for active columns, 0 otherwise.
+template <int K>
+__global__ void k_scale(long long NK, const double* __restrict__ w, const double* __restrict__ nrm,
+                        const int* __restrict__ active, double* __restrict__ v) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= NK) return;
+  const int k = (int)(e % K);
+  v[e] = (active[k] && nrm[k] > 0.0) ? w[e] / nrm[k] : 0.0;
+}
+
+struct GmresState {
+  double* Hm;   // (m+1) x m x K upper Hessenberg, rotated
+  double* cs;   // m x K
+  double* sn;   // m x K
+  double* gv;   // (m+1) x K
+  int* active;  // K
+  int* jcount;  // K: basis vectors used in this cycle
+  int* budget;  // K: iterations left for the column
+  int* flags;   // K: 1 converged (recurrence), 2 breakdown
+  double* resest;  // K
+};
+
+// Column j of the Hessenberg matrix for every rhs: apply the previous Givens
+// rotations, form the new one, update the residual recurrence, retire
+// columns that converged, broke down or ran out of iterations.
+__global__ void k_givens(int j, int m, int K, const double* __restrict__ hcol, GmresState st,
+                         const double* __restrict__ bnorm, double rtol, int* __restrict__ n_active) {
+  const int k = threadIdx.x;
+  int still = 0;
+  if (k < K && st.active[k]) {
+    double col[2];
+    // rotate the column in place into Hm
+    for (int i = 0; i <= j + 1; ++i) st.Hm[((size_t)i * m + j) * K + k] = hcol[(size_t)i * K + k];
+    for (int i = 0; i < j; ++i) {
+      col[0] = st.Hm[((size_t)i * m + j) * K + k];
+      col[1] = st.Hm[((size_t)(i + 1) * m + j) * K + k];
+      const double c = st.cs[i * K + k], s = st.sn[i * K + k];
+      st.Hm[((size_t)i * m + j) * K + k] = c * col[0] + s * col[1];
+      st.Hm[((size_t)(i + 1) * m + j) * K + k] = -s * col[0] + c * col[1];
+    }
+    const double a = st.Hm[((size_t)j * m + j) * K + k];
+    const double b = st.Hm[((size_t)(j + 1) * m + j) * K + k];
+    const double r = hypot(a, b);
+    const double c = r == 0.0 ? 1.0 : a / r, s = r == 0.0 ? 0.0 : b / r;
+    st.cs[j * K + k] = c;
+    st.sn[j * K + k] = s;
+    st.Hm[((size_t)j * m + j) * K + k] = r;
+    st.Hm[((size_t)(j + 1) * m + j) * K + k] = 0.0;
+    const double gj = st.gv[j * K + k];
+    st.gv[(j + 1) * K + k] = -s * gj;
+    st.gv[j * K + k] = c * gj;
+    st.jcount[k] = j + 1;
+    const double est = fabs(st.gv[(j + 1) * K + k]) / bnorm[k];
+    st.resest[k] = est;
+    still = 1;
+    if (est <= rtol) {
+      st.flags[k] = 1;
+      still = 0;
+    } else if (b == 0.0) {
+      st.flags[k] = 2;
+      still = 0;
+    } else if (j + 1 >= st.budget[k]) {
+      still = 0;
+    }
+    st.active[k] = still;
+  }
+  const int cnt = __syncthreads_count(still);
+  if (threadIdx.x == 0) *n_active = cnt;
+}
+
+// Back substitution H y = g per column over its jcount rows.
+__global__ void k_solve_y(int m, int K, GmresState st, double* __restrict__ y, int nmax) {
+  const int k = threadIdx.x;
+  if (k >= K) return;
+  const int n = st.jcount[k];
+  for (int i = nmax - 1; i >= n; --i) y[i * K + k] = 0.0;
+  for (int i = n - 1; i >= 0; --i) {
+    double s = st.gv[i * K + k];
+    for (int l = i + 1; l < n; ++l) s -= st.Hm[((size_t)i * m + l) * K + k] * y[l * K + k];
+    y[i * K + k] = s / st.Hm[((size_t)i * m + i) * K + k];
+  }
+}
+
+// x += sum_i Z_i y_i.
+template <int K, typename TZ>
+__global__ void __launch_bounds__(kBlock) k_update_x(long long NK, int nz, const TZ* __restrict__ Z,
+                                                     const double* __restrict__ y, double* __restrict__ x) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= NK) return;
+  const int k = (int)(e % K);
+  double s = x[e];
+  for (int i = 0; i < nz; ++i) s += (double)Z[(size_t)i * NK + e] * y[i * K + k];
+  x[e] = s;
+}
+
+// ---------------------------------------------------------------------------
+
+template <typename U>
+U* dev_alloc(size_t n, std::vector<void*>& list) {
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(U));
+  if (e != cudaSuccess) throw std::runtime_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  list.push_back(p);
+  return (U*)p;
+}
+
+}  // namespace
+
+struct amg_hierarchy {
+  std::vector<HostLevel> host;
+  amg_params prm{};
+  VCycleIface* v64 = nullptr;
+  VCycleIface* v32 = nullptr;
+  long long N = 0;
+  // FGMRES workspace, sized for (ws_K, ws_m)
+  int ws_K = 0, ws_m = 0;
+  std::vector<void*> ws;
+  double *V = nullptr, *w = nullptr, *bK = nullptr, *xK = nullptr, *rK = nullptr;
+  void* Z = nullptr;
+  double *hbuf = nullptr, *part = nullptr, *y = nullptr, *bnorm = nullptr, *rnorm = nullptr;
+  GmresState st{};
+  int* n_active = nullptr;
+  int* host_i = nullptr;     // pinned
+  double* host_d = nullptr;  // pinned
+  void* stage_b = nullptr;   // device copies for amg_fgmres_solve_host
+  void* stage_x = nullptr;
+  long long launches = 0;    // kernels launched by this file's code (the V-cycles count their own)
+
+  VCycleIface* vc() { return prm.vcycle_fp32 ? v32 : v64; }
+
+  void free_ws() {
+    for (void* p : ws) cudaFree(p);
+    ws.clear();
+    ws_K = ws_m = 0;
+  }
+  ~amg_hierarchy() {
+    free_ws();
+    if (host_i) cudaFreeHost(host_i);
+    if (host_d) cudaFreeHost(host_d);
+    if (stage_b) cudaFree(stage_b);
+    if (stage_x) cudaFree(stage_x);
+    delete v64;
+    delete v32;
+  }
+};
+
+namespace {
+
+void ensure_ws(amg_hierarchy* h, int K, int m) {
+  if (h->ws_K == K && h->ws_m >= m) return;
+  h->free_ws();
+  const size_t NK = (size_t)h->N * K;
+  const bool f32 = h->prm.vcycle_fp32 != 0;
+  h->V = dev_alloc<double>(NK * (m + 1), h->ws);
+  h->Z = f32 ? (void*)dev_alloc<float>(NK * m, h->ws) : (void*)dev_alloc<double>(NK * m, h->ws);
+  h->w = dev_alloc<double>(NK, h->ws);
+  h->bK = dev_alloc<double>(NK, h->ws);
+  h->xK = dev_alloc<double>(NK, h->ws);
+  h->rK = dev_alloc<double>(NK, h->ws);
+  h->hbuf = dev_alloc<double>((size_t)(m + 2) * K, h->ws);
+  h->part = dev_alloc<double>((size_t)kRedBlocks * (m + 2) * K, h->ws);
+  h->y = dev_alloc<double>((size_t)(m + 1) * K, h->ws);
+  h->bnorm = dev_alloc<double>(K, h->ws);
+  h->rnorm = dev_alloc<double>(K, h->ws);
+  h->st.Hm = dev_alloc<double>((size_t)(m + 1) * m * K, h->ws);
+  h->st.cs = dev_alloc<double>((size_t)m * K, h->ws);
+  h->st.sn = dev_alloc<double>((size_t)m * K, h->ws);
+  h->st.gv = dev_alloc<double>((size_t)(m + 1) * K, h->ws);
+  h->st.active = dev_alloc<int>(K, h->ws);
+  h->st.jcount = dev_alloc<int>(K, h->ws);
+  h->st.budget = dev_alloc<int>(K, h->ws);
+  h->st.flags = dev_alloc<int>(K, h->ws);
+  h->st.resest = dev_alloc<double>(K, h->ws);
+  h->n_active = dev_alloc<int>(1, h->ws);
+  h->ws_K = K;
+  h->ws_m = m;
+  if (!h->host_i) EMIN_CUDA(cudaMallocHost(&h->host_i, 4 * 64 * sizeof(int)));
+  if (!h->host_d) EMIN_CUDA(cudaMallocHost(&h->host_d, 4 * 64 * sizeof(double)));
+}
+
+// Norms of the K columns of an N x K FP64 block into out[k] (deterministic).
+template <int K>
+void col_norms(amg_hierarchy* h, const double* v, double* out, cudaStream_t s) {
+  const long long NK = h->N * K;
+  k_mdot_partial<K, double><<<kRedBlocks, kBlock, 0, s>>>(NK, 1, v, v, h->part); ++h->launches;
+  k_reduce_partials<<<1, 64, 0, s>>>(kRedBlocks, K, h->part, out, 0, 1); ++h->launches;
+}
+
+template <int K, typename TZ>
+amg_status fgmres_k(amg_hierarchy* h, const double* b, double* x, int nrhs, double rtol, int restart, int maxit,
+                    int* iters, double* relres, cudaStream_t s) {
+  const long long N = h->N, NK = N * K;
+  ensure_ws(h, K, restart);
+  VCycleIface* vc = h->vc();
+  const bool f32 = vc->is_fp32();
+  const unsigned gNK = grid_for(NK);
+  // b (user layout) -> bK; x = 0
+  k_pack<double, double, K><<<gNK, kBlock, 0, s>>>(N, b, nrhs, nrhs, h->bK); ++h->launches;
+  EMIN_CUDA(cudaMemsetAsync(h->xK, 0, sizeof(double) * NK, s));
+  col_norms<K>(h, h->bK, h->bnorm, s);
+  EMIN_CUDA(cudaMemcpyAsync(h->host_d, h->bnorm, sizeof(double) * K, cudaMemcpyDeviceToHost, s));
+  EMIN_CUDA(cudaStreamSynchronize(s));
+  std::vector<double> bn(h->host_d, h->host_d + K);
+  std::vector<int> total(K, 0), done(K, 0), flag(K, 0);
+  std::vector<double> rel(K, 0.0);
+  for (int k = 0; k < K; ++k)
+    if (k >= nrhs || bn[k] == 0.0) done[k] = 1;
+  // r = b for the first cycle
+  EMIN_CUDA(cudaMemcpyAsync(h->rK, h->bK, sizeof(double) * NK, cudaMemcpyDeviceToDevice, s));
+  TZ* Z = (TZ*)h->Z;
+  bool any_left = std::any_of(done.begin(), done.end(), [](int d) { return !d; });
+  while (any_left) {
+    // start vector v0 = r / ||r|| for the columns still running; g = (||r||, 0, ...)
+    std::vector<int> act(K), bud(K);
+    for (int k = 0; k < K; ++k) {
+      act[k] = !done[k];
+      bud[k] = std::min(restart, maxit - total[k]);
+      if (bud[k] <= 0) act[k] = 0;
+    }
+    EMIN_CUDA(cudaMemcpyAsync(h->st.active, act.data(), sizeof(int) * K, cudaMemcpyHostToDevice, s));
+    EMIN_CUDA(cudaMemcpyAsync(h->st.budget, bud.data(), sizeof(int) * K, cudaMemcpyHostToDevice, s));
+    EMIN_CUDA(cudaMemsetAsync(h->st.jcount, 0, sizeof(int) * K, s));
+    EMIN_CUDA(cudaMemsetAsync(h->st.flags, 0, sizeof(int) * K, s));
+    EMIN_CUDA(cudaMemsetAsync(h->st.gv, 0, sizeof(double) * (restart + 1) * K, s));
+    col_norms<K>(h, h->rK, h->rnorm, s);
+    EMIN_CUDA(cudaMemcpyAsync(h->st.gv, h->rnorm, sizeof(double) * K, cudaMemcpyDeviceToDevice, s));
+    k_scale<K><<<gNK, kBlock, 0, s>>>(NK, h->rK, h->rnorm, h->st.active, h->V); ++h->launches;
+    int j = 0;
+    for (; j < restart; ++j) {
+      double* Vj = h->V + (size_t)j * NK;
+      // z_j = M^-1 v_j through the captured V-cycle
+      k_pack<double, TZ, K><<<gNK, kBlock, 0, s>>>(N, Vj, K, K, (TZ*)vc->input(0)); ++h->launches;
+      EMIN_CUDA(cudaGetLastError());
+      EMIN_CUDA(vc->run(K, s));
+      EMIN_CUDA(cudaMemcpyAsync(Z + (size_t)j * NK, vc->output(0), sizeof(TZ) * NK, cudaMemcpyDeviceToDevice, s));
+      // w = A z_j in FP64
+      EMIN_CUDA(apply_finest_f64(h->v64, Z + (size_t)j * NK, f32, nullptr, h->w, K, s)); ++h->launches;
+      // classical Gram-Schmidt with one re-orthogonalisation
+      const int nv = j + 1;
+      k_mdot_partial<K, double><<<kRedBlocks, kBlock, 0, s>>>(NK, nv, h->V, h->w, h->part); ++h->launches;
+      k_reduce_partials<<<(nv * K + 127) / 128, 128, 0, s>>>(kRedBlocks, nv * K, h->part, h->hbuf, 0, 0); ++h->launches;
+      k_maxpy<K, double><<<kRedBlocks, kBlock, 0, s>>>(NK, nv, h->V, h->hbuf, h->w, nullptr); ++h->launches;
+      k_mdot_partial<K, double><<<kRedBlocks, kBlock, 0, s>>>(NK, nv, h->V, h->w, h->part); ++h->launches;
+      double* h2 = h->y;  // scratch for the correction coefficients
+      k_reduce_partials<<<(nv * K + 127) / 128, 128, 0, s>>>(kRedBlocks, nv * K, h->part, h2, 0, 0); ++h->launches;
+      k_maxpy<K, double><<<kRedBlocks, kBlock, 0, s>>>(NK, nv, h->V, h2, h->w, h->part); ++h->launches;
+      k_reduce_partials<<<1, 64, 0, s>>>(kRedBlocks, K, h->part, h->hbuf + (size_t)nv * K, 0, 1); ++h->launches;
+      k_reduce_partials<<<(nv * K + 127) / 128, 128, 0, s>>>(1, nv * K, h2, h->hbuf, 1, 0); ++h->launches;
+      k_givens<<<1, 32, 0, s>>>(j, restart, K, h->hbuf, h->st, h->bnorm, rtol, h->n_active); ++h->launches;
+      EMIN_CUDA(cudaGetLastError());
+      EMIN_CUDA(cudaMemcpyAsync(h->host_i, h->n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
+      EMIN_CUDA(cudaStreamSynchronize(s));
+      if (*h->host_i == 0) {
+        ++j;
+        break;
+      }
+      k_scale<K><<<gNK, kBlock, 0, s>>>(NK, h->w, h->hbuf + (size_t)nv * K, h->st.active, h->V + (size_t)(j + 1) * NK); ++h->launches;
+    }
+    const int nmax = std::min(j, restart);
+    // x += Z y with y from the triangular systems; true residual r = b - A x
+    k_solve_y<<<1, 32, 0, s>>>(restart, K, h->st, h->y, nmax); ++h->launches;
+    k_update_x<K, TZ><<<gNK, kBlock, 0, s>>>(NK, nmax, Z, h->y, h->xK); ++h->launches;
+    EMIN_CUDA(apply_finest_f64(h->v64, h->xK, false, h->bK, h->rK, K, s)); ++h->launches;
+    col_norms<K>(h, h->rK, h->rnorm, s);
+    EMIN_CUDA(cudaMemcpyAsync(h->host_d, h->rnorm, sizeof(double) * K, cudaMemcpyDeviceToHost, s));
+    EMIN_CUDA(cudaMemcpyAsync(h->host_i, h->st.jcount, sizeof(int) * K, cudaMemcpyDeviceToHost, s));
+    EMIN_CUDA(cudaMemcpyAsync(h->host_i + 64, h->st.flags, sizeof(int) * K, cudaMemcpyDeviceToHost, s));
+    EMIN_CUDA(cudaStreamSynchronize(s));
+    any_left = false;
+    for (int k = 0; k < K; ++k) {
+      if (done[k]) continue;
+      total[k] += h->host_i[k];
+      rel[k] = h->host_d[k] / bn[k];
+      if (h->host_i[64 + k] == 2 && rel[k] > rtol) flag[k] = 2;
+      if (rel[k] <= rtol || total[k] >= maxit || flag[k] == 2 || h->host_i[k] == 0) {
+        done[k] = 1;
+      } else {
+        any_left = true;
+      }
+    }
+  }
+  k_unpack<double, double, K><<<grid_for(N * nrhs), kBlock, 0, s>>>(N, h->xK, nrhs, x, nrhs); ++h->launches;
+  EMIN_CUDA(cudaGetLastError());
+  EMIN_CUDA(cudaStreamSynchronize(s));
+  amg_status st = AMG_OK;
+  for (int k = 0; k < nrhs; ++k) {
+    if (iters) iters[k] = total[k];
+    if (relres) relres[k] = bn[k] == 0.0 ? 0.0 : rel[k];
+    if (bn[k] != 0.0 && rel[k] > rtol) st = flag[k] == 2 ? AMG_BREAKDOWN : AMG_NOT_CONVERGED;
+  }
+  return st;
+}
+
+template <typename TZ>
+amg_status fgmres_dispatch(amg_hierarchy* h, const double* b, double* x, int nrhs, double rtol, int restart,
+                           int maxit, int* iters, double* relres, cudaStream_t s) {
+  switch (round_k(nrhs)) {
+    case 1: return fgmres_k<1, TZ>(h, b, x, nrhs, rtol, restart, maxit, iters, relres, s);
+    case 2: return fgmres_k<2, TZ>(h, b, x, nrhs, rtol, restart, maxit, iters, relres, s);
+    case 4: return fgmres_k<4, TZ>(h, b, x, nrhs, rtol, restart, maxit, iters, relres, s);
+    case 8: return fgmres_k<8, TZ>(h, b, x, nrhs, rtol, restart, maxit, iters, relres, s);
+    case 16: return fgmres_k<16, TZ>(h, b, x, nrhs, rtol, restart, maxit, iters, relres, s);
+    case 32: return fgmres_k<32, TZ>(h, b, x, nrhs, rtol, restart, maxit, iters, relres, s);
+  }
+  return fail(AMG_ERR_ARG, "nrhs must be in 1..32");
+}
+
+template <int K, typename T>
+void vcycle_k(amg_hierarchy* h, const double* r, double* z, int nrhs, cudaStream_t s) {
+  VCycleIface* vc = h->vc();
+  const long long N = h->N;
+  k_pack<double, T, K><<<grid_for(N * K), kBlock, 0, s>>>(N, r, nrhs, nrhs, (T*)vc->input(0)); ++h->launches;
+  EMIN_CUDA(cudaGetLastError());
+  EMIN_CUDA(vc->run(K, s));
+  k_unpack<T, double, K><<<grid_for(N * nrhs), kBlock, 0, s>>>(N, (const T*)vc->output(0), nrhs, z, nrhs); ++h->launches;
+  EMIN_CUDA(cudaGetLastError());
+}
+
+template <typename T>
+void vcycle_dispatch(amg_hierarchy* h, const double* r, double* z, int nrhs, cudaStream_t s) {
+  switch (round_k(nrhs)) {
+    case 1: vcycle_k<1, T>(h, r, z, nrhs, s); break;
+    case 2: vcycle_k<2, T>(h, r, z, nrhs, s); break;
+    case 4: vcycle_k<4, T>(h, r, z, nrhs, s); break;
+    case 8: vcycle_k<8, T>(h, r, z, nrhs, s); break;
+    case 16: vcycle_k<16, T>(h, r, z, nrhs, s); break;
+    case 32: vcycle_k<32, T>(h, r, z, nrhs, s); break;
+  }
+}
+
+template <int K>
+void apply_k(amg_hierarchy* h, const double* x, double* y, int nrhs, cudaStream_t s) {
+  const long long N = h->N;
+  k_pack<double, double, K><<<grid_for(N * K), kBlock, 0, s>>>(N, x, nrhs, nrhs, h->bK); ++h->launches;
+  EMIN_CUDA(cudaGetLastError());
+  EMIN_CUDA(apply_finest_f64(h->v64, h->bK, false, nullptr, h->w, K, s)); ++h->launches;
+  k_unpack<double, double, K><<<grid_for(N * nrhs), kBlock, 0, s>>>(N, h->w, nrhs, y, nrhs); ++h->launches;
+  EMIN_CUDA(cudaGetLastError());
+}
+
+bool check_csr(const int* rp, const int* ci, int nrows, int ncols, std::string& why) {
+  if (!rp || rp[0] != 0) {
+    why = "rowptr must start at 0";
+    return false;
+  }
+  for (int i = 0; i < nrows; ++i) {
+    if (rp[i + 1] < rp[i]) {
+      why = "rowptr not monotone at row " + std::to_string(i);
+      return false;
+    }
+    for (int t = rp[i]; t < rp[i + 1]; ++t) {
+      if (ci[t] < 0 || ci[t] >= ncols) {
+        why = "column out of range in row " + std::to_string(i);
+        return false;
+      }
+      if (t > rp[i] && ci[t] <= ci[t - 1]) {
+        why = "columns not strictly ascending in row " + std::to_string(i);
+        return false;
+      }
+    }
+  }
+  return true;
+}
+
+Csr to_csr(const int* rp, const int* ci, const double* v, int nrows, int ncols) {
+  Csr M;
+  M.resize_rows(nrows, ncols);
+  for (int i = 0; i <= nrows; ++i) M.rowptr[i] = rp[i];
+  M.col.assign(ci, ci + rp[nrows]);
+  M.val.assign(v, v + rp[nrows]);
+  return M;
+}
+
+}  // namespace
+
+extern "C" {
+
+void amg_params_default(amg_params* p) {
+  if (!p) return;
+  p->tau1 = 0.06;
+  p->tau2sq = 1.5e-3;
+  p->omega = 0.666;
+  p->omega_on_D = 0;
+  p->gs_iters = 5;
+  p->pre = 2;
+  p->post = 2;
+  p->max_coarse = 200;
+  p->max_levels = 12;
+  p->vcycle_fp32 = 0;
+  p->max_nrhs = 8;
+  p->host_only = 0;
+}
+
+const char* amg_last_error(void) { return g_last_error.c_str(); }
+
+amg_status amg_hierarchy_create(const amg_problem* pb, const amg_params* prm_in, void* stream, amg_handle* out) {
+  if (!pb || !out) return fail(AMG_ERR_ARG, "null problem or output handle");
+  *out = nullptr;
+  amg_params prm;
+  if (prm_in)
+    prm = *prm_in;
+  else
+    amg_params_default(&prm);
+  if (pb->dim < 2 || pb->dim > 3 || pb->n_vnodes <= 0 || pb->n_pnodes <= 0)
+    return fail(AMG_ERR_ARG, "dim must be 2 or 3 and node counts positive");
+  if (!pb->A_val || !pb->B_val || !pb->vcoords || !pb->pcoords || !pb->p2v || !pb->v_dirichlet)
+    return fail(AMG_ERR_ARG, "null problem array");
+  if (prm.max_nrhs < 1 || prm.max_nrhs > 32) return fail(AMG_ERR_ARG, "max_nrhs must be in 1..32");
+  if (prm.gs_iters < 0 || prm.pre < 0 || prm.post < 0 || prm.omega <= 0.0)
+    return fail(AMG_ERR_ARG, "invalid smoother parameters");
+  if (pb->pinned_p >= pb->n_pnodes) return fail(AMG_ERR_ARG, "pinned pressure out of range");
+  std::string why;
+  if (!check_csr(pb->A_rowptr, pb->A_col, pb->n_vnodes, pb->n_vnodes, why)) return fail(AMG_ERR_ARG, "A: " + why);
+  if (!check_csr(pb->B_rowptr, pb->B_col, pb->n_pnodes, pb->dim * pb->n_vnodes, why))
+    return fail(AMG_ERR_ARG, "B: " + why);
+  for (int k = 0; k < pb->n_pnodes; ++k)
+    if (pb->p2v[k] < -1 || pb->p2v[k] >= pb->n_vnodes) return fail(AMG_ERR_ARG, "p2v out of range");
+  std::unique_ptr<amg_hierarchy> h(new amg_hierarchy());
+  try {
+    HostLevel fine;
+    fine.dim = pb->dim;
+    fine.n_v = pb->n_vnodes;
+    fine.n_p = pb->n_pnodes;
+    fine.pinned = pb->pinned_p;
+    fine.A = to_csr(pb->A_rowptr, pb->A_col, pb->A_val, fine.n_v, fine.n_v);
+    fine.B = to_csr(pb->B_rowptr, pb->B_col, pb->B_val, fine.n_p, fine.dim * fine.n_v);
+    fine.Bt = transpose(fine.B);
+    fine.vX.assign(pb->vcoords, pb->vcoords + (size_t)fine.n_v * fine.dim);
+    fine.pX.assign(pb->pcoords, pb->pcoords + (size_t)fine.n_p * fine.dim);
+    fine.p2v.assign(pb->p2v, pb->p2v + fine.n_p);
+    fine.dirichlet.assign(pb->v_dirichlet, pb->v_dirichlet + fine.n_v);
+    SetupParams sp;
+    sp.tau1 = prm.tau1;
+    sp.tau2sq = prm.tau2sq;
+    sp.c = prm.omega_on_D ? 1.0 / prm.omega : prm.omega;
+    sp.max_coarse = prm.max_coarse;
+    sp.max_levels = prm.max_levels;
+    sp.symmetric = pb->symmetric != 0;
+    h->host = build_hierarchy(std::move(fine), sp);
+    h->prm = prm;
+    h->N = h->host[0].N();
+    if (!prm.host_only) {
+      h->v64 = make_vcycle_f64(h->host, sp.c, prm.gs_iters, prm.pre, prm.post, round_k(prm.max_nrhs));
+      if (prm.vcycle_fp32)
+        h->v32 = make_vcycle_f32(h->host, sp.c, prm.gs_iters, prm.pre, prm.post, round_k(prm.max_nrhs));
+      EMIN_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    }
+  } catch (const std::bad_alloc&) {
+    return fail(AMG_ERR_OOM, "host allocation failed during setup");
+  } catch (const std::exception& e) {
+    const std::string m = e.what();
+    return fail(m.find("cuda") != std::string::npos ? AMG_ERR_CUDA : AMG_ERR_SETUP, m);
+  }
+  *out = h.release();
+  return AMG_OK;
+}
+
+amg_status amg_vcycle_apply(amg_handle h, const double* r, double* z, int nrhs, void* stream) {
+  if (!h || !r || !z) return fail(AMG_ERR_ARG, "null argument");
+  if (!h->vc()) return fail(AMG_ERR_ARG, "hierarchy was built with host_only");
+  if (nrhs < 1 || round_k(nrhs) > h->vc()->kmax()) return fail(AMG_ERR_ARG, "nrhs exceeds max_nrhs");
+  try {
+    if (h->prm.vcycle_fp32)
+      vcycle_dispatch<float>(h, r, z, nrhs, (cudaStream_t)stream);
+    else
+      vcycle_dispatch<double>(h, r, z, nrhs, (cudaStream_t)stream);
+  } catch (const std::exception& e) {
+    return fail(AMG_ERR_CUDA, e.what());
+  }
+  return AMG_OK;
+}
+
+amg_status amg_apply(amg_handle h, const double* x, double* y, int nrhs, void* stream) {
+  if (!h || !x || !y) return fail(AMG_ERR_ARG, "null argument");
+  if (!h->vc()) return fail(AMG_ERR_ARG, "hierarchy was built with host_only");
+  if (nrhs < 1 || round_k(nrhs) > h->vc()->kmax()) return fail(AMG_ERR_ARG, "nrhs exceeds max_nrhs");
+  try {
+    ensure_ws(h, round_k(nrhs), std::max(h->ws_m, 1));
+    cudaStream_t s = (cudaStream_t)stream;
+    switch (round_k(nrhs)) {
+      case 1: apply_k<1>(h, x, y, nrhs, s); break;
+      case 2: apply_k<2>(h, x, y, nrhs, s); break;
+      case 4: apply_k<4>(h, x, y, nrhs, s); break;
+      case 8: apply_k<8>(h, x, y, nrhs, s); break;
+      case 16: apply_k<16>(h, x, y, nrhs, s); break;
+      case 32: apply_k<32>(h, x, y, nrhs, s); break;
+    }
+  } catch (const std::exception& e) {
+    return fail(AMG_ERR_CUDA, e.what());
+  }
+  return AMG_OK;
+}
+
+amg_status amg_fgmres_solve(amg_handle h, const double* b, double* x, int nrhs, double rtol, int restart, int maxit,
+                            int* iters, double* relres, void* stream) {
+  if (!h || !b || !x) return fail(AMG_ERR_ARG, "null argument");
+  if (!h->vc()) return fail(AMG_ERR_ARG, "hierarchy was built with host_only");
+  if (nrhs < 1 || round_k(nrhs) > h->vc()->kmax()) return fail(AMG_ERR_ARG, "nrhs exceeds max_nrhs");
+  if (restart < 1 || maxit < 1 || !(rtol > 0.0)) return fail(AMG_ERR_ARG, "restart, maxit and rtol must be positive");
+  try {
+    if (h->prm.vcycle_fp32)
+      return fgmres_dispatch<float>(h, b, x, nrhs, rtol, restart, maxit, iters, relres, (cudaStream_t)stream);
+    return fgmres_dispatch<double>(h, b, x, nrhs, rtol, restart, maxit, iters, relres, (cudaStream_t)stream);
+  } catch (const std::bad_alloc&) {
+    return fail(AMG_ERR_OOM, "host allocation failed");
+  } catch (const std::exception& e) {
+    const std::string m = e.what();
+    return fail(m.find("cudaMalloc") != std::string::npos ? AMG_ERR_OOM : AMG_ERR_CUDA, m);
+  }
+}
+
+amg_status amg_fgmres_solve_host(amg_handle h, const double* b_host, double* x_host, int nrhs, double rtol,
+                                 int restart, int maxit, int* iters, double* relres, void* stream) {
+  if (!h || !b_host || !x_host) return fail(AMG_ERR_ARG, "null argument");
+  if (!h->vc()) return fail(AMG_ERR_ARG, "hierarchy was built with host_only");
+  if (nrhs < 1 || round_k(nrhs) > h->vc()->kmax()) return fail(AMG_ERR_ARG, "nrhs exceeds max_nrhs");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = sizeof(double) * (size_t)h->N * nrhs;
+  if (!h->stage_b) {
+    const size_t cap = sizeof(double) * (size_t)h->N * h->vc()->kmax();
+    if (cudaMalloc(&h->stage_b, cap) != cudaSuccess || cudaMalloc(&h->stage_x, cap) != cudaSuccess)
+      return fail(AMG_ERR_OOM, "cudaMalloc for the host-solve staging buffers");
+  }
+  cudaError_t e = cudaMemcpyAsync(h->stage_b, b_host, bytes, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return fail(AMG_ERR_CUDA, cudaGetErrorString(e));
+  amg_status st = amg_fgmres_solve(h, (const double*)h->stage_b, (double*)h->stage_x, nrhs, rtol, restart, maxit,
+                                   iters, relres, stream);
+  if (st < 0) return st;
+  e = cudaMemcpyAsync(x_host, h->stage_x, bytes, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(AMG_ERR_CUDA, cudaGetErrorString(e));
+  return st;
+}
+
+amg_status amg_profile_vcycle(amg_handle h, int nrhs, int reps, double* ms, long long* count, void* stream) {
+  if (!h || !ms || !count || reps < 1) return fail(AMG_ERR_ARG, "null argument or reps < 1");
+  if (!h->vc()) return fail(AMG_ERR_ARG, "hierarchy was built with host_only");
+  if (nrhs < 1 || round_k(nrhs) > h->vc()->kmax()) return fail(AMG_ERR_ARG, "nrhs exceeds max_nrhs");
+  const int n = h->vc()->levels() * kNumClasses;
+  std::fill(ms, ms + n, 0.0);
+  std::fill(count, count + n, 0LL);
+  cudaError_t e = h->vc()->profile(round_k(nrhs), reps, (cudaStream_t)stream, ms, count);
+  if (e != cudaSuccess) return fail(AMG_ERR_CUDA, cudaGetErrorString(e));
+  return AMG_OK;
+}
+
+long long amg_kernel_launches(amg_handle h) {
+  if (!h) return 0;
+  return h->launches + (h->v64 ? h->v64->launches() : 0) + (h->v32 ? h->v32->launches() : 0);
+}
+
+int amg_num_levels(amg_handle h) { return h ? (int)h->host.size() : 0; }
+
+amg_status amg_level_get_info(amg_handle h, int level, amg_level_info* info) {
+  if (!h || !info || level < 0 || level >= (int)h->host.size()) return fail(AMG_ERR_ARG, "bad handle or level");
+  const HostLevel& L = h->host[level];
+  info->dim = L.dim;
+  info->n_v = L.n_v;
+  info->n_p = L.n_p;
+  info->pinned = L.pinned;
+  info->nnz_A = L.A.nnz();
+  info->nnz_B = L.B.nnz();
+  info->nnz_Bt = L.Bt.nnz();
+  info->nnz_S = L.S.nnz();
+  info->n_colors = L.n_colors;
+  info->nnz_P = L.P.nnz();
+  info->nnz_Pp = L.Pp.nnz();
+  info->nnz_R = L.R.nnz();
+  info->nnz_Rp = L.Rp.nnz();
+  info->n_cp = (int)L.Cp.size();
+  info->n_cv = (int)L.Cv.size();
+  return AMG_OK;
+}
+
+amg_status amg_level_get_matrix(amg_handle h, int level, int which, long long* rowptr, int* col, double* val) {
+  if (!h || level < 0 || level >= (int)h->host.size()) return fail(AMG_ERR_ARG, "bad handle or level");
+  const HostLevel& L = h->host[level];
+  const Csr* M = nullptr;
+  switch (which) {
+    case 0: M = &L.A; break;
+    case 1: M = &L.B; break;
+    case 2: M = &L.Bt; break;
+    case 3: M = &L.S; break;
+    case 4: M = &L.P; break;
+    case 5: M = &L.Pp; break;
+    case 6: M = &L.R; break;
+    case 7: M = &L.Rp; break;
+    default: return fail(AMG_ERR_ARG, "which must be 0..7");
+  }
+  if (rowptr)
+    for (size_t i = 0; i < M->rowptr.size(); ++i) rowptr[i] = M->rowptr[i];
+  if (col) std::copy(M->col.begin(), M->col.end(), col);
+  if (val) std::copy(M->val.begin(), M->val.end(), val);
+  return AMG_OK;
+}
+
+amg_status amg_level_get_points(amg_handle h, int level, int* cp, int* cv, int* colors, double* D) {
+  if (!h || level < 0 || level >= (int)h->host.size()) return fail(AMG_ERR_ARG, "bad handle or level");
+  const HostLevel& L = h->host[level];
+  if (cp) std::copy(L.Cp.begin(), L.Cp.end(), cp);
+  if (cv) std::copy(L.Cv.begin(), L.Cv.end(), cv);
+  if (colors) std::copy(L.colors.begin(), L.colors.end(), colors);
+  if (D) std::copy(L.D.begin(), L.D.end(), D);
+  return AMG_OK;
+}
+
+void amg_hierarchy_destroy(amg_handle h) { delete h; }
+
+}  // extern "C"

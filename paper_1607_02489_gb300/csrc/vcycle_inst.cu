@@ -1,0 +1,54 @@
+// One translation unit per V-cycle arithmetic type: compiled with
+// -DEMIN_VCYCLE_DOUBLE (FP64 cycle and the FP64 finest-level product) or
+// without it (FP32 cycle with FP32 accumulation).
+#include "vcycle.cuh"
+
+namespace emin {
+
+#ifdef EMIN_VCYCLE_DOUBLE
+
+VCycleIface* make_vcycle_f64(const std::vector<HostLevel>& levels, double cfac, int gs, int pre, int post, int kmax) {
+  return new DeviceVCycle<double>(levels, cfac, gs, pre, post, kmax);
+}
+
+template <int K>
+static void apply_k(const LevelView<double>& L, const void* x, bool x_fp32, const double* b, double* out,
+                    cudaStream_t s) {
+  const unsigned g = grid_for((long long)(L.n_v + L.n_p) * K);
+  if (x_fp32) {
+    if (b)
+      k_block_spmv<double, float, double, K, true><<<g, kBlock, 0, s>>>(L, b, (const float*)x, out);
+    else
+      k_block_spmv<double, float, double, K, false><<<g, kBlock, 0, s>>>(L, nullptr, (const float*)x, out);
+  } else {
+    if (b)
+      k_block_spmv<double, double, double, K, true><<<g, kBlock, 0, s>>>(L, b, (const double*)x, out);
+    else
+      k_block_spmv<double, double, double, K, false><<<g, kBlock, 0, s>>>(L, nullptr, (const double*)x, out);
+  }
+}
+
+cudaError_t apply_finest_f64(VCycleIface* v64, const void* x, bool x_fp32, const double* b, double* out, int K,
+                             cudaStream_t s) {
+  const LevelView<double>& L = static_cast<DeviceVCycle<double>*>(v64)->view(0);
+  switch (K) {
+    case 1: apply_k<1>(L, x, x_fp32, b, out, s); break;
+    case 2: apply_k<2>(L, x, x_fp32, b, out, s); break;
+    case 4: apply_k<4>(L, x, x_fp32, b, out, s); break;
+    case 8: apply_k<8>(L, x, x_fp32, b, out, s); break;
+    case 16: apply_k<16>(L, x, x_fp32, b, out, s); break;
+    case 32: apply_k<32>(L, x, x_fp32, b, out, s); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+#else
+
+VCycleIface* make_vcycle_f32(const std::vector<HostLevel>& levels, double cfac, int gs, int pre, int post, int kmax) {
+  return new DeviceVCycle<float>(levels, cfac, gs, pre, post, kmax);
+}
+
+#endif
+
+}  // namespace emin

@@ -1,0 +1,216 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances (written here, derived in the design doc):
+  * FP64 V-cycle: relative 2-norm error <= 1e-11 per application and column;
+  * block product A x: <= 1e-13;
+  * FP32 V-cycle: <= 1e-4 (single precision through a few levels of smoothing);
+  * FGMRES: iteration counts within +-1 of the oracle's, true relative
+    residual <= rtol, solutions within 1e-6 of the oracle's (both at rtol 1e-10).
+"""
+import numpy as np
+import pytest
+
+from synth import make_problem, stokes_lid_2d, stokes_pinned_2d, oseen_recirculating_2d, uniform_pm1
+from oracle import setup_hierarchy, vcycle, fgmres, apply_A, Params
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+g = pytest.importorskip("paper_1607_02489_gb300")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu_and_lib():
+    assert torch.cuda.is_available(), "the gpu tests need a CUDA device"
+    g._build.build()
+    g.load()
+
+
+CASES = {
+    "pinned16": lambda: stokes_pinned_2d(16, nrhs=1),
+    "lid32": lambda: stokes_lid_2d(32, nrhs=2),
+    "oseen32": lambda: oseen_recirculating_2d(32, Re=10.0, nrhs=4),
+    "lid18_ragged3": lambda: make_problem(18, 2, 0.0, 1.0, bc="lid", nrhs=3, seed=5),
+    "single_level": lambda: stokes_lid_2d(2, nrhs=2),
+    "lid3d": lambda: make_problem(4, 3, 0.0, 1.0, bc="lid", nrhs=1),
+    "oseen_re100_k8": lambda: oseen_recirculating_2d(16, Re=100.0, nrhs=8),
+}
+
+
+def _rand(N, k, seed):
+    return uniform_pm1(seed, N * k).reshape(N, k)
+
+
+def _relerr(a, b):
+    return np.linalg.norm(a - b, axis=0) / np.maximum(np.linalg.norm(b, axis=0), 1e-300)
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_vcycle_fp64_matches_oracle(case):
+    p = CASES[case]()
+    Ho = setup_hierarchy(p)
+    Hg = g.Hierarchy(p, max_nrhs=p.b.shape[1])
+    assert Hg.num_levels() == len(Ho.levels)
+    r = _rand(p.N, p.b.shape[1], 11)
+    zo = vcycle(Ho, r)
+    rt = torch.tensor(r, device="cuda")
+    zt = torch.empty_like(rt)
+    Hg.vcycle(rt, zt)
+    torch.cuda.synchronize()
+    assert np.all(_relerr(zt.cpu().numpy(), zo) <= 1e-11), _relerr(zt.cpu().numpy(), zo)
+    # a second application reuses the captured graph and gives the same result
+    z2 = torch.empty_like(rt)
+    Hg.vcycle(rt, z2)
+    torch.cuda.synchronize()
+    assert torch.equal(zt, z2)
+
+
+@pytest.mark.parametrize("case", ["pinned16", "lid32", "oseen32"])
+def test_vcycle_fp32_close_to_oracle(case):
+    p = CASES[case]()
+    Ho = setup_hierarchy(p)
+    Hg = g.Hierarchy(p, max_nrhs=p.b.shape[1], vcycle_fp32=1)
+    r = _rand(p.N, p.b.shape[1], 12)
+    zo = vcycle(Ho, r)
+    rt = torch.tensor(r, device="cuda")
+    zt = torch.empty_like(rt)
+    Hg.vcycle(rt, zt)
+    torch.cuda.synchronize()
+    err = _relerr(zt.cpu().numpy(), zo)
+    assert np.all(err <= 1e-4) and np.all(err > 0), err
+
+
+@pytest.mark.parametrize("case", ["pinned16", "lid18_ragged3", "lid3d", "oseen32"])
+def test_block_product_matches_oracle(case):
+    p = CASES[case]()
+    Ho = setup_hierarchy(p, Params(max_levels=1))
+    Hg = g.Hierarchy(p, max_nrhs=p.b.shape[1], max_levels=1)
+    x = _rand(p.N, p.b.shape[1], 13)
+    yo = apply_A(Ho.levels[0], x)
+    xt = torch.tensor(x, device="cuda")
+    yt = torch.empty_like(xt)
+    Hg.apply(xt, yt)
+    torch.cuda.synchronize()
+    assert np.all(_relerr(yt.cpu().numpy(), yo) <= 1e-13)
+
+
+def _center(p, x):
+    x = x.copy()
+    if p.pinned < 0:
+        nu = p.dim * p.n_v
+        x[nu:] -= x[nu:].mean(axis=0)
+    return x
+
+
+@pytest.mark.parametrize("case", ["pinned16", "lid32", "oseen32", "lid18_ragged3"])
+@pytest.mark.parametrize("fp32", [0, 1])
+def test_fgmres_matches_oracle(case, fp32):
+    p = CASES[case]()
+    Ho = setup_hierarchy(p)
+    xo, its_o, rel_o, _ = fgmres(Ho, p.b, rtol=1e-10)
+    Hg = g.Hierarchy(p, max_nrhs=p.b.shape[1], vcycle_fp32=fp32)
+    bt = torch.tensor(p.b, device="cuda")
+    xt = torch.zeros_like(bt)
+    st, its, rel = Hg.fgmres(bt, xt, rtol=1e-10, restart=100, maxit=300)
+    assert st == g.AMG_OK
+    assert np.all(rel <= 1e-10)
+    if not fp32:
+        assert np.all(np.abs(its - its_o) <= 1), (its, its_o)
+    else:
+        assert np.all(its <= its_o + 2), (its, its_o)
+    x = xt.cpu().numpy()
+    # independent check of the true residual on the host
+    A = p.full_matrix()
+    assert np.all(np.linalg.norm(p.b - A @ x, axis=0) <= 1.01e-10 * np.linalg.norm(p.b, axis=0))
+    assert np.all(_relerr(_center(p, x), _center(p, xo)) <= 1e-6)
+
+
+def test_batched_columns_equal_single_solves():
+    """Eight right-hand sides in one launch give each column's single-rhs result."""
+    p = oseen_recirculating_2d(16, Re=10.0, nrhs=8)
+    Hg = g.Hierarchy(p, max_nrhs=8)
+    bt = torch.tensor(p.b, device="cuda")
+    xt = torch.zeros_like(bt)
+    st, its, rel = Hg.fgmres(bt, xt, rtol=1e-9)
+    for k in range(8):
+        b1 = bt[:, k].contiguous()
+        x1 = torch.zeros_like(b1)
+        st1, its1, rel1 = Hg.fgmres(b1, x1, rtol=1e-9)
+        assert its1[0] == its[k]
+        e = (x1 - xt[:, k]).norm() / x1.norm()
+        assert e.item() <= 1e-10
+
+
+def test_zero_and_ragged_right_hand_sides():
+    p = stokes_lid_2d(16, nrhs=3)
+    b = p.b.copy()
+    b[:, 1] = 0.0
+    Hg = g.Hierarchy(p, max_nrhs=4)
+    bt = torch.tensor(b, device="cuda")
+    xt = torch.full_like(bt, 7.0)
+    st, its, rel = Hg.fgmres(bt, xt, rtol=1e-8)
+    assert st == g.AMG_OK
+    assert its[1] == 0 and rel[1] == 0.0 and torch.all(xt[:, 1] == 0)
+    assert its[0] > 0 and its[2] > 0
+
+
+def test_max_nrhs_and_errors():
+    p = stokes_lid_2d(8, nrhs=1)
+    b = np.tile(p.b, (1, 32)) * np.linspace(0.5, 2.0, 32)
+    Hg = g.Hierarchy(p, max_nrhs=32)
+    bt = torch.tensor(b, device="cuda")
+    xt = torch.zeros_like(bt)
+    st, its, rel = Hg.fgmres(bt, xt, rtol=1e-8)
+    assert st == g.AMG_OK and np.all(its == its[0])
+    with pytest.raises(g.AmgError):
+        Hg.fgmres(torch.zeros((p.N, 33), dtype=torch.float64, device="cuda"),
+                  torch.zeros((p.N, 33), dtype=torch.float64, device="cuda"))
+    H2 = g.Hierarchy(p, host_only=1)
+    with pytest.raises(g.AmgError):
+        H2.vcycle(bt[:, :1].contiguous(), xt[:, :1].contiguous())
+
+
+def test_not_converged_status():
+    p = stokes_lid_2d(16, nrhs=1)
+    Hg = g.Hierarchy(p, max_nrhs=1)
+    bt = torch.tensor(p.b, device="cuda")
+    xt = torch.zeros_like(bt)
+    st, its, rel = Hg.fgmres(bt, xt, rtol=1e-12, restart=3, maxit=4)
+    assert st == g.AMG_NOT_CONVERGED and its[0] == 4 and rel[0] > 1e-12
+
+
+def test_host_buffers_match_device_buffers():
+    p = stokes_pinned_2d(16, nrhs=2)
+    Hg = g.Hierarchy(p, max_nrhs=2)
+    bt = torch.tensor(p.b, device="cuda")
+    xt = torch.zeros_like(bt)
+    st, its, rel = Hg.fgmres(bt, xt, rtol=1e-8)
+    bh = torch.tensor(p.b).pin_memory()
+    xh = torch.zeros_like(bh).pin_memory()
+    st2, its2, rel2 = Hg.fgmres_host(bh, xh, rtol=1e-8)
+    assert np.array_equal(its, its2)
+    assert torch.equal(xh, xt.cpu())
+
+
+def test_full_size_lid_cavity_256_eight_rhs():
+    """The 256x256 lid cavity with 8 right-hand sides in one launch: one V-cycle against the
+    oracle's, FGMRES to 1e-8 with the true residual re-checked on the host, and the
+    oracle's iteration count on the first column."""
+    p = stokes_lid_2d(256, nrhs=8)
+    Ho = setup_hierarchy(p)
+    Hg = g.Hierarchy(p, max_nrhs=8)
+    r = _rand(p.N, 8, 21)
+    zo = vcycle(Ho, r)
+    rt = torch.tensor(r, device="cuda")
+    zt = torch.empty_like(rt)
+    Hg.vcycle(rt, zt)
+    torch.cuda.synchronize()
+    assert np.all(_relerr(zt.cpu().numpy(), zo) <= 1e-11)
+    bt = torch.tensor(p.b, device="cuda")
+    xt = torch.zeros_like(bt)
+    st, its, rel = Hg.fgmres(bt, xt, rtol=1e-8)
+    assert st == g.AMG_OK and np.all(rel <= 1e-8)
+    A = p.full_matrix()
+    x = xt.cpu().numpy()
+    assert np.all(np.linalg.norm(p.b - A @ x, axis=0) <= 1.01e-8 * np.linalg.norm(p.b, axis=0))
+    xo, its_o, rel_o, _ = fgmres(Ho, p.b[:, :1], rtol=1e-8)
+    assert abs(int(its[0]) - int(its_o[0])) <= 1

@@ -1,0 +1,116 @@
+"""Host-side parity of the library's C++ hierarchy setup with the oracle (no GPU).
+
+The library is built with host_only=1, so nothing is uploaded; the C/F
+splits, patterns and colors must be identical (integer work: bit-exact) and
+the matrices equal to rounding.
+"""
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from synth import stokes_lid_2d, stokes_pinned_2d, oseen_recirculating_2d, make_problem
+from oracle import setup_hierarchy, Params
+
+g = pytest.importorskip("paper_1607_02489_gb300")
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    g._build.build()
+    g.load()
+
+
+def test_library_exports_every_declared_symbol():
+    hdr = open(os.path.join(ROOT, "include", "emin_amg.h")).read()
+    declared = sorted(set(re.findall(r"\b(amg_[a-z_]+)\s*\(", hdr)))
+    assert len(declared) >= 12
+    lib = g.load()
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert sorted(g.EXPORTED) == declared
+    out = subprocess.run(["nm", "-D", "--defined-only", g.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (amg_[a-z_]+)", out))
+    assert set(declared) <= exported
+
+
+def _csr(t):
+    rp, col, val, shape = t
+    return sp.csr_matrix((val, col, rp), shape=shape)
+
+
+def _compare(prob, prm=None, **kw):
+    Hg = g.Hierarchy(prob, host_only=1, **kw)
+    Ho = setup_hierarchy(prob, prm or Params())
+    assert Hg.num_levels() == len(Ho.levels)
+    for l, L in enumerate(Ho.levels):
+        info = Hg.level_info(l)
+        pts = Hg.level_points(l)
+        assert (info["n_v"], info["n_p"], info["pinned"]) == (L.n_v, L.n_p, L.pinned)
+        assert np.array_equal(pts["colors"], L.colors)
+        assert info["n_colors"] == int(L.colors.max()) + 1
+        assert np.abs(pts["D"] - L.D).max() <= 1e-12 * np.abs(L.D).max()
+        last = l + 1 == len(Ho.levels)
+        if not last:
+            assert np.array_equal(pts["Cp"], L.info["Cp"])
+            assert np.array_equal(pts["Cv"], L.info["Cv"])
+        # tolerances relative to the level's operator scale (a coarsest level with a single
+        # pressure has B and S at rounding level, where a relative comparison means nothing)
+        scale = abs(L.full_matrix()).max()
+        s_scale = max(abs(L.S).max(), abs(Ho.levels[0].S).max())
+        for nm in ["A", "B", "Bt", "S"] + ([] if last else ["P", "Pp", "R", "Rp"]):
+            M = _csr(Hg.level_matrix(l, nm))
+            O = sp.csr_matrix(getattr(L, nm))
+            O.sort_indices()
+            assert np.array_equal(M.indptr, O.indptr) and np.array_equal(M.indices, O.indices), (l, nm)
+            ref = {"A": scale, "B": scale, "Bt": scale, "S": s_scale}.get(nm, abs(O).max())
+            assert abs(M - O).max() <= 1e-11 * ref, (l, nm, abs(M - O).max(), ref)
+
+
+@pytest.mark.parametrize("n", [8, 16, 32, 64])
+def test_stokes_lid_setup_matches_oracle(n):
+    _compare(stokes_lid_2d(n, nrhs=1))
+
+
+@pytest.mark.parametrize("n", [8, 16, 32])
+def test_stokes_pinned_setup_matches_oracle(n):
+    _compare(stokes_pinned_2d(n))
+
+
+@pytest.mark.parametrize("Re", [1.0, 10.0, 100.0])
+def test_oseen_setup_matches_oracle(Re):
+    _compare(oseen_recirculating_2d(32, Re=Re, nrhs=1))
+
+
+def test_ragged_mesh_and_parameters_match_oracle():
+    """A mesh size not divisible by 4 (ragged coarsening at the far edges), and non-default
+    tau1 / tau2 / omega placement."""
+    p = make_problem(18, 2, 0.0, 1.0, bc="lid", nrhs=1)
+    _compare(p)
+    _compare(p, Params(tau1=0.1, tau2sq=0.04, omega_in_M="inverse"), tau1=0.1, tau2sq=0.04, omega_on_D=1)
+
+
+def test_3d_setup_matches_oracle():
+    _compare(make_problem(4, 3, 0.0, 1.0, bc="lid", nrhs=1))
+
+
+def test_invalid_problem_is_rejected():
+    p = stokes_lid_2d(4, nrhs=1)
+    bad = stokes_lid_2d(4, nrhs=1)
+    bad.A = bad.A.copy()
+    bad.A.indices = bad.A.indices.copy()
+    r = int(np.flatnonzero(np.diff(bad.A.indptr) >= 2)[0])
+    t = bad.A.indptr[r]
+    bad.A.indices[t], bad.A.indices[t + 1] = bad.A.indices[t + 1], bad.A.indices[t]   # columns out of order
+    with pytest.raises(g.AmgError) as e:
+        g.Hierarchy(bad, host_only=1)
+    assert e.value.status == -1
+    with pytest.raises(g.AmgError):
+        g.Hierarchy(p, host_only=1, max_nrhs=64)
+    H = g.Hierarchy(p, host_only=1)
+    assert H.num_levels() >= 1

@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ncu", action="store_true",
+                    help="short run for an ncu launch list: one warm-up solve, then one solve (FP32 V-cycle)")
     return ap.parse_args()
 
 
@@ -110,8 +112,8 @@ class ClockSampler:
 def algorithmic_bytes(H, level, cls, K, s, zero_fraction=0.25):
     """Compulsory bytes of one launch of kernel class `cls` on `level`: each matrix
     entry (value + int32 column) and row pointer read once, each vector operand
-    read or written once (K right-hand sides of s bytes each).  For the Gauss-Seidel
-    class this is one color sweep, i.e. one Gauss-Seidel iteration / n_colors.
+    read or written once (K right-hand sides of s bytes each).
+    The Gauss-Seidel class is one fused launch: all gs_iters iterations over all colors.
     The velocity predictor's first sweep of a cycle starts from x = 0 and reads no
     matrix; `zero_fraction` of its launches are of that kind (1 of 4 in V(2,2))."""
     info = H.level_info(level)
@@ -126,8 +128,9 @@ def algorithmic_bytes(H, level, cls, K, s, zero_fraction=0.25):
     if cls == "schur_rhs":
         return mat(info["nnz_B"], np_) + vec(d * nv) + 2 * vec(np_)
     if cls == "gs_color":
+        # one fused launch = gs_iters Gauss-Seidel iterations over all colors
         nnz_off = info["nnz_S"] - np_
-        return (mat(nnz_off, np_) + np_ * (4 + s) + 3 * vec(np_)) / info["n_colors"]
+        return H.params.gs_iters * (mat(nnz_off, np_) + np_ * (4 + s) + 3 * vec(np_))
     if cls == "update":
         return mat(info["nnz_Bt"], d * nv) + nv * s + vec(d * nv) + 2 * vec(np_) + vec(N)
     if cls == "residual":
@@ -242,6 +245,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return reference_main(args)
+    if args.ncu:
+        args.no_cpu_baseline = True
     import numpy as np
     import torch
     import torch.distributed as dist
@@ -265,6 +270,17 @@ def main():
     from synth import stokes_lid_2d
     g._build.build()
     p = stokes_lid_2d(MESH, nrhs=NRHS, seed=rank)
+    if args.ncu:
+        H = g.Hierarchy(p, max_nrhs=NRHS, vcycle_fp32=1)
+        b = torch.tensor(p.b, device=dev)
+        x = torch.zeros_like(b)
+        for rep in range(2):
+            n0 = H.kernel_launches()
+            st, its, rel = H.fgmres(b, x, rtol=RTOL, restart=RESTART, maxit=MAXIT)
+            torch.cuda.synchronize()
+            print(f"solve {rep}: status {st}, iterations {its.tolist()}, kernels {H.kernel_launches() - n0}",
+                  flush=True)
+        return
     H32 = g.Hierarchy(p, max_nrhs=NRHS, vcycle_fp32=1)
     H64 = g.Hierarchy(p, max_nrhs=NRHS)
     b = torch.tensor(p.b, device=dev)

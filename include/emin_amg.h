@@ -146,6 +146,8 @@ typedef struct {
   int n_colors;
   long long nnz_P, nnz_Pp, nnz_R, nnz_Rp; /* 0 on the coarsest level */
   int n_cp, n_cv;                          /* coarse points chosen on this level (0 on the coarsest) */
+  int gs_strip;                            /* Gauss-Seidel strip length T: rows are relaxed in the order
+                                              (floor(row / T) mod 2, color, row) */
 } amg_level_info;
 
 int amg_num_levels(amg_handle h);

@@ -61,6 +61,7 @@ class Level:
     D: np.ndarray = None          # |A| row sums (Dirichlet rows: 1/c so that c*D = 1)
     S: sp.csr_matrix = None       # B D^-1 Bt, pinned row = identity
     colors: np.ndarray = None     # greedy coloring of the graph of S
+    gs_strip: int = 1             # Gauss-Seidel strip length T = bandwidth of S
     # transfers to the next level (Alg. 2)
     P: sp.csr_matrix = None       # velocity, one component (n_v x n_v_coarse)
     Pp: sp.csr_matrix = None      # pressure (n_p x n_p_coarse)
@@ -482,7 +483,8 @@ def greedy_coloring(S) -> np.ndarray:
 
 def form_relaxation(L: Level, prm: Params):
     """Braess-Sarazin data: d_ii = sum_j |A_ij| (Section 5.2) and the explicit Schur
-    complement S = B D^-1 B^T (Bt on levels where R != P^T).  Readings: a
+    complement S = B D^-1 B^T (Bt on levels where R != P^T), its greedy coloring and
+    the strip length of the Gauss-Seidel ordering (see gauss_seidel).  Readings: a
     Dirichlet row of M is the identity row of A (D_ii = 1/c, so c*D_ii = 1);
     a pinned pressure row of S is the identity row (its update is exact)."""
     absA = abs(L.A)
@@ -498,6 +500,9 @@ def form_relaxation(L: Level, prm: Params):
     L.D = D
     L.S = S
     L.colors = greedy_coloring(S)
+    Sc = sp.coo_matrix(S)
+    offd = Sc.row != Sc.col
+    L.gs_strip = max(1, int(np.abs(Sc.row[offd] - Sc.col[offd]).max())) if offd.any() else 1
 
 
 def form_coarse_solve(L: Level, rcond: float = 1e-12):

@@ -28,16 +28,20 @@ def apply_A(L, x):
 
 def gauss_seidel(L, g, iters: int):
     """`iters` forward Gauss-Seidel iterations on S dp = g from dp = 0 (Section 5.2:
-    "several Gauss-Seidel iterations"; five in Section 6).  Ordering reading:
-    rows by color of the greedy coloring of S's graph, colors ascending.  Rows of
-    one color share no entry of S, so updating a color's rows at once gives the
-    same result as updating them one after another."""
+    "several Gauss-Seidel iterations"; five in Section 6).  The paper gives no
+    ordering.  Reading: rows ordered by (strip parity, color, index), where the
+    strips are consecutive blocks of T = bandwidth(S) rows (so strips two apart
+    share no entry of S) and the colors come from the greedy coloring of S's
+    graph.  Rows with the same parity and color share no entry of S, so
+    updating them at once gives the same result as one after another."""
     S = L.S
     diag = S.diagonal()
     off = S - sp.diags(diag)
     dp = np.zeros_like(g)
+    parity = (np.arange(L.n_p) // L.gs_strip) % 2
     ncol = int(L.colors.max()) + 1 if len(L.colors) else 0
-    groups = [np.flatnonzero(L.colors == c) for c in range(ncol)]
+    groups = [np.flatnonzero((parity == b) & (L.colors == c)) for b in (0, 1) for c in range(ncol)]
+    groups = [rows for rows in groups if len(rows)]
     for _ in range(iters):
         for rows in groups:
             dp[rows] = (g[rows] - off[rows] @ dp) / diag[rows][:, None]

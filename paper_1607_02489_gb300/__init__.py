@@ -53,7 +53,8 @@ class AmgLevelInfo(ctypes.Structure):
                 ("nnz_A", ctypes.c_longlong), ("nnz_B", ctypes.c_longlong), ("nnz_Bt", ctypes.c_longlong),
                 ("nnz_S", ctypes.c_longlong), ("n_colors", ctypes.c_int),
                 ("nnz_P", ctypes.c_longlong), ("nnz_Pp", ctypes.c_longlong), ("nnz_R", ctypes.c_longlong),
-                ("nnz_Rp", ctypes.c_longlong), ("n_cp", ctypes.c_int), ("n_cv", ctypes.c_int)]
+                ("nnz_Rp", ctypes.c_longlong), ("n_cp", ctypes.c_int), ("n_cv", ctypes.c_int),
+                ("gs_strip", ctypes.c_int)]
 
 
 _lib = None

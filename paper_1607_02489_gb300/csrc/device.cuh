@@ -2,9 +2,11 @@
 // Braess-Sarazin, Section 4 transfers) and of flexible GMRES.
 //
 // Vectors hold K right-hand sides interleaved: entry (dof i, rhs k) at i*K + k,
-// dofs ordered [u_x | u_y (| u_z) | p].  One thread computes one (row, rhs)
-// pair; the K threads of a row read the row's matrix entries once (broadcast)
-// and the K values of each column entry as one contiguous segment.
+// dofs ordered [u_x | u_y (| u_z) | p].  A row is handled by K*G consecutive
+// lanes of a warp: lane (k, g) takes right-hand side k and every G-th stored
+// entry of the row starting at g, so one load instruction reads G consecutive
+// matrix entries and, for each, the K contiguous values of its column; the G
+// partial sums are combined with warp shuffles.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -15,6 +17,7 @@
 namespace emin {
 
 constexpr int kBlock = 256;
+constexpr int kGsBlock = 512;
 
 template <typename T>
 struct DCsr {
@@ -44,54 +47,88 @@ __device__ __forceinline__ long long gtid() { return (long long)blockIdx.x * blo
 
 inline unsigned grid_for(long long items) { return (unsigned)((items + kBlock - 1) / kBlock); }
 
+// Lanes per row for K right-hand sides on small (latency-bound) levels: G lanes
+// split the stored entries, K*G <= 32.  Large levels use G = 1.
+template <int K>
+struct RowLanes {
+  static constexpr int G = K >= 32 ? 1 : (32 / K < 4 ? 32 / K : 4);
+  static constexpr int W = K * G;
+};
+constexpr long long kSmallLevelItems = 65536;  // rows * K below which a level uses G > 1
+
+// Mask of the W-lane group (aligned within the warp) of the calling thread.
+template <int W>
+__device__ __forceinline__ unsigned group_mask() {
+  return W == 32 ? 0xffffffffu : (((1u << W) - 1u) << ((threadIdx.x & 31) & ~(unsigned)(W - 1)));
+}
+
+template <int K, int G, typename T>
+__device__ __forceinline__ T group_sum(T v, unsigned mask) {
+#pragma unroll
+  for (int off = G / 2; off >= 1; off >>= 1) v += __shfl_xor_sync(mask, v, off * K);
+  return v;
+}
+
+// Decomposition of a flat thread index into (row, rhs, lane) for G lanes per row.
+template <int K, int G>
+struct RowThread {
+  int row, k, lane;
+  __device__ __forceinline__ RowThread(long long t) : row((int)(t / (K * G))), k((int)(t % K)), lane((int)((t / K) % G)) {}
+};
+
 // y = x + w .* (b_u - A u - Bt p) on velocity rows; with zero_x, y = w .* b_u.
 // (Braess-Sarazin step, first half: the Jacobi-like velocity predictor.)
-template <typename T, int K>
+template <typename T, int K, int G>
 __global__ void __launch_bounds__(kBlock) k_bs_velocity(LevelView<T> L, const T* __restrict__ b,
                                                         const T* __restrict__ x, T* __restrict__ y, int zero_x) {
-  const long long t = gtid();
-  const int i = (int)(t / K), k = (int)(t % K);
+  constexpr int W = K * G;
+  const RowThread<K, G> q(gtid());
+  const int i = q.row, k = q.k;
   if (i >= L.n_v) return;
   const size_t nuK = (size_t)L.dim * L.n_v * K;
-  T acc[3];
-#pragma unroll
-  for (int c = 0; c < 3; ++c)
-    if (c < L.dim) acc[c] = b[((size_t)c * L.n_v + i) * K + k];
+  T acc[3] = {T(0), T(0), T(0)};
   if (!zero_x) {
-    for (int e = L.A.rp[i]; e < L.A.rp[i + 1]; ++e) {
+    for (int e = L.A.rp[i] + q.lane; e < L.A.rp[i + 1]; e += G) {
       const T a = L.A.v[e];
       const size_t j = (size_t)L.A.ci[e];
 #pragma unroll
       for (int c = 0; c < 3; ++c)
-        if (c < L.dim) acc[c] -= a * x[((size_t)c * L.n_v + j) * K + k];
+        if (c < L.dim) acc[c] += a * x[((size_t)c * L.n_v + j) * K + k];
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c)
       if (c < L.dim) {
         const int r = c * L.n_v + i;
-        for (int e = L.Bt.rp[r]; e < L.Bt.rp[r + 1]; ++e) acc[c] -= L.Bt.v[e] * x[nuK + (size_t)L.Bt.ci[e] * K + k];
+        for (int e = L.Bt.rp[r] + q.lane; e < L.Bt.rp[r + 1]; e += G) acc[c] += L.Bt.v[e] * x[nuK + (size_t)L.Bt.ci[e] * K + k];
       }
+    const unsigned mask = group_mask<W>();
+#pragma unroll
+    for (int c = 0; c < 3; ++c) acc[c] = group_sum<K, G>(acc[c], mask);
   }
+  if (q.lane != 0) return;
   const T wi = L.w[i];
 #pragma unroll
   for (int c = 0; c < 3; ++c)
     if (c < L.dim) {
       const size_t o = ((size_t)c * L.n_v + i) * K + k;
-      y[o] = (zero_x ? T(0) : x[o]) + wi * acc[c];
+      y[o] = (zero_x ? T(0) : x[o]) + wi * (b[o] - acc[c]);
     }
 }
 
 // Schur right-hand side g = c (B y - b_p) (= B D^-1 r_u - c r_p); pinned row g = r_p.
-template <typename T, int K>
+template <typename T, int K, int G>
 __global__ void __launch_bounds__(kBlock) k_schur_rhs(LevelView<T> L, const T* __restrict__ b,
                                                       const T* __restrict__ x, const T* __restrict__ y,
                                                       T* __restrict__ g, T cfac, int zero_x) {
-  const long long t = gtid();
-  const int i = (int)(t / K), k = (int)(t % K);
+  constexpr int W = K * G;
+  const RowThread<K, G> q(gtid());
+  const int i = q.row, k = q.k;
   if (i >= L.n_p) return;
   const size_t nuK = (size_t)L.dim * L.n_v * K;
   T acc = T(0);
-  for (int e = L.B.rp[i]; e < L.B.rp[i + 1]; ++e) acc += L.B.v[e] * y[(size_t)L.B.ci[e] * K + k];
+  for (int e = L.B.rp[i] + q.lane; e < L.B.rp[i + 1]; e += G) acc += L.B.v[e] * y[(size_t)L.B.ci[e] * K + k];
+  acc = group_sum<K, G>(acc, group_mask<W>());
+  if (q.lane != 0) return;
   const T bp = b[nuK + (size_t)i * K + k];
   if (i == L.pinned)
     g[(size_t)i * K + k] = bp - (zero_x ? T(0) : x[nuK + (size_t)i * K + k]);
@@ -99,55 +136,345 @@ __global__ void __launch_bounds__(kBlock) k_schur_rhs(LevelView<T> L, const T* _
     g[(size_t)i * K + k] = cfac * (acc - bp);
 }
 
-// One color of a Gauss-Seidel iteration on S dp = g: rows of one color share no
-// entry of S, so they are updated concurrently.
-template <typename T, int K>
-__global__ void __launch_bounds__(kBlock) k_gs_color(LevelView<T> L, const T* __restrict__ g, T* __restrict__ dp,
-                                                     int r0, int r1) {
-  const long long t = gtid();
-  const int r = r0 + (int)(t / K), k = (int)(t % K);
-  if (r >= r1) return;
-  const int i = L.S_perm[r];
-  T acc = g[(size_t)i * K + k];
-  for (int e = L.S.rp[r]; e < L.S.rp[r + 1]; ++e) acc -= L.S.v[e] * dp[(size_t)L.S.ci[e] * K + k];
-  dp[(size_t)i * K + k] = acc * L.S_dinv[r];
+// Bounded grid barrier for the cooperative Gauss-Seidel launch.  Every waiting
+// block gives up after kSpinLimit polls (about a second), sets *err and returns
+// false, so a barrier can never hang the GPU; the host checks *err.
+struct GridBarrier {
+  unsigned int count;
+  unsigned int gen;
+};
+constexpr unsigned long long kSpinLimit = 1ull << 24;
+
+__device__ __forceinline__ bool grid_sync(GridBarrier* gb, int* err, unsigned nblocks) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* vgen = &gb->gen;
+    const unsigned int g0 = *vgen;
+    __threadfence();
+    const unsigned int arrived = atomicAdd(&gb->count, 1u) + 1u;
+    int ok = 1;
+    if (arrived == nblocks) {
+      gb->count = 0u;
+      __threadfence();
+      atomicAdd(&gb->gen, 1u);
+    } else {
+      unsigned long long spins = 0;
+      while (*vgen == g0) {
+        if (++spins > kSpinLimit || *(volatile int*)err) {
+          ok = 0;
+          atomicExch(err, 1);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Strip-ordered Gauss-Seidel for the Schur system S dp = g, gs_iters iterations
+// from dp = 0 in one launch.  Rows are relaxed in the order (strip parity,
+// color, index): strips are T consecutive rows with T >= bandwidth(S), so the
+// strips of one parity never share an entry of S and are relaxed concurrently,
+// one block per strip; inside a strip the rows of one color are independent.
+// A strip reads only rows within T of itself, so its block stages that halo of
+// dp (stage >= 1) and its own rows of S (stage == 2) in shared memory and runs
+// the color sub-steps there with __syncthreads; the strip parities are
+// separated by the bounded grid barrier (cooperative launch).  G lanes share a
+// row and combine their sums with warp shuffles.
+struct GsStrips {
+  const int* soff;  // nstrips x (ncol + 1): first sorted row of each (strip, color)
+  int nstrips, ncol, T, iters, stage, max_strip_nnz;
+};
+
+// Asynchronous global -> shared copies (cp.async): every copy of a staging
+// step is in flight at once and lands without a register round trip.
+__device__ __forceinline__ void cp_async(void* sdst, const void* gsrc, int bytes) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+  if (bytes == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
+  else if (bytes == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gsrc) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Copy n elements of type U from global to shared with cp.async, in 16-byte
+// pieces when both addresses allow it.  COHERENT data (written by other blocks
+// in the previous phase) is read only through L2: 16-byte cp.async.cg, or
+// ld.global.cg for an unaligned remainder.
+template <bool COHERENT, typename U>
+__device__ __forceinline__ void stage_copy(U* sdst, const U* gsrc, int n) {
+  const uintptr_t a = (uintptr_t)gsrc, b = (uintptr_t)__cvta_generic_to_shared(sdst);
+  const int per16 = 16 / (int)sizeof(U);
+  int done = 0;
+  if (((a | b) & 15) == 0) {
+    const int n16 = n / per16;
+    for (int t = threadIdx.x; t < n16; t += blockDim.x) cp_async(sdst + t * per16, gsrc + t * per16, 16);
+    done = n16 * per16;
+  }
+  for (int t = done + threadIdx.x; t < n; t += blockDim.x) {
+    if (COHERENT)
+      sdst[t] = __ldcg(gsrc + t);
+    else
+      cp_async(sdst + t, gsrc + t, (int)sizeof(U));
+  }
+}
+
+template <typename T, int K, int G>
+__global__ void __launch_bounds__(kGsBlock) k_gs_strips(LevelView<T> L, const T* __restrict__ g, T* dp, GsStrips P,
+                                                        GridBarrier* gb, int* err) {
+  static_assert(K * G <= 32, "a row group must fit in a warp");
+  extern __shared__ __align__(16) unsigned char smem[];
+  // layout: dp halo (3T x K), g (T x K), 1/S_ii (T), [S values], then ints:
+  // row offsets (T+1), permutation (T), [S columns]
+  T* s_dp = reinterpret_cast<T*>(smem);
+  T* s_g = s_dp + (size_t)3 * P.T * K;
+  T* s_dinv = s_g + (size_t)P.T * K;
+  T* s_v = s_dinv + P.T;
+  int* s_rp = reinterpret_cast<int*>(s_v + (P.stage == 2 ? P.max_strip_nnz : 0));
+  int* s_perm = s_rp + P.T + 1;
+  int* s_ci = s_perm + P.T;
+  constexpr int kGroup = K * G;
+  const int k = threadIdx.x % K;
+  const int lane = (threadIdx.x / K) % G;
+  const unsigned mask = kGroup == 32 ? 0xffffffffu
+                                     : (((1u << kGroup) - 1u) << ((threadIdx.x & 31) & ~(unsigned)(kGroup - 1)));
+  const int n_p = L.n_p;
+  for (int it = 0; it < P.iters; ++it)
+    for (int bc = 0; bc < 2; ++bc) {
+      for (int s = bc + 2 * blockIdx.x; s < P.nstrips; s += 2 * gridDim.x) {
+        const int r_lo = s * P.T, r_hi = min(r_lo + P.T, n_p);
+        const int h_lo = max(0, r_lo - P.T), h_hi = min(n_p, r_hi + P.T);
+        const int* so = P.soff + (size_t)s * (P.ncol + 1);
+        const int q0 = so[0], q1 = so[P.ncol];  // sorted rows of this strip
+        const int e0 = L.S.rp[q0], e1 = L.S.rp[q1];
+        if (P.stage >= 1) {
+          stage_copy<true>(s_dp, dp + (size_t)h_lo * K, (h_hi - h_lo) * K);
+          stage_copy<false>(s_g, g + (size_t)r_lo * K, (r_hi - r_lo) * K);
+          stage_copy<false>(s_dinv, L.S_dinv + q0, q1 - q0);
+          stage_copy<false>(s_perm, L.S_perm + q0, q1 - q0);
+          stage_copy<false>(s_rp, L.S.rp + q0, q1 - q0 + 1);
+          if (P.stage == 2) {
+            stage_copy<false>(s_v, L.S.v + e0, e1 - e0);
+            stage_copy<false>(s_ci, L.S.ci + e0, e1 - e0);
+          }
+          cp_async_wait_all();
+        }
+        __syncthreads();
+        for (int pc = 0; pc < P.ncol; ++pc) {
+          const int ra = so[pc], rb = so[pc + 1];
+          const int items = (rb - ra) * kGroup;
+          for (int t = threadIdx.x; t < items; t += blockDim.x) {
+            const int r = ra + t / kGroup;
+            T acc = T(0);
+            if (P.stage == 2) {
+              const int ea = s_rp[r - q0] - e0, eb = s_rp[r - q0 + 1] - e0;
+              for (int e = ea + lane; e < eb; e += G) acc += s_v[e] * s_dp[(size_t)(s_ci[e] - h_lo) * K + k];
+            } else if (P.stage == 1) {
+              const int ea = s_rp[r - q0], eb = s_rp[r - q0 + 1];
+              for (int e = ea + lane; e < eb; e += G) acc += L.S.v[e] * s_dp[(size_t)(L.S.ci[e] - h_lo) * K + k];
+            } else {
+              const int ea = L.S.rp[r], eb = L.S.rp[r + 1];
+              for (int e = ea + lane; e < eb; e += G) acc += L.S.v[e] * dp[(size_t)L.S.ci[e] * K + k];
+            }
+#pragma unroll
+            for (int off = G / 2; off >= 1; off >>= 1) acc += __shfl_xor_sync(mask, acc, off * K);
+            if (lane == 0) {
+              if (P.stage >= 1) {
+                const int i = s_perm[r - q0];
+                s_dp[(size_t)(i - h_lo) * K + k] = (s_g[(size_t)(i - r_lo) * K + k] - acc) * s_dinv[r - q0];
+              } else {
+                const int i = L.S_perm[r];
+                dp[(size_t)i * K + k] = (g[(size_t)i * K + k] - acc) * L.S_dinv[r];
+              }
+            }
+          }
+          __syncthreads();
+        }
+        if (P.stage >= 1)
+          for (int t = threadIdx.x; t < (r_hi - r_lo) * K; t += blockDim.x)
+            dp[(size_t)r_lo * K + t] = s_dp[(size_t)(r_lo - h_lo) * K + t];
+        __syncthreads();
+      }
+      if (gridDim.x > 1 && !grid_sync(gb, err, gridDim.x)) return;
+    }
+}
+
+// Pipelined strip Gauss-Seidel: the same ordering as k_gs_strips, one resident
+// block per strip for the whole call (cooperative launch), so a block stages
+// its strip's rows of S, 1/S_ii and g in shared memory once and keeps its own
+// dp rows there.  Instead of a grid barrier per phase, each strip waits only
+// for its two neighbours through per-strip counters of completed iterations:
+// an even strip at iteration it needs its odd neighbours to have completed it
+// iterations, an odd strip needs its even neighbours to have completed it + 1.
+// That is exactly the dependency of the sequential order, and it also keeps a
+// strip from overwriting rows a neighbour has not read yet.  Waits are bounded
+// (kSpinLimit polls), set *err and return on timeout.
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;\n" ::"l"(p), "r"(v) : "memory");
+}
+
+template <typename T, int K, int G>
+__global__ void __launch_bounds__(kGsBlock) k_gs_pipe(LevelView<T> L, const T* __restrict__ g, T* dp, GsStrips P,
+                                                      const int* __restrict__ ci_rel, int* done, int* err) {
+  static_assert(K * G <= 32, "a row group must fit in a warp");
+  extern __shared__ __align__(16) unsigned char smem[];
+  T* s_dp = reinterpret_cast<T*>(smem);
+  T* s_g = s_dp + (size_t)3 * P.T * K;
+  T* s_dinv = s_g + (size_t)P.T * K;
+  T* s_v = s_dinv + P.T;
+  int* s_rp = reinterpret_cast<int*>(s_v + (P.stage == 2 ? P.max_strip_nnz : 0));
+  int* s_perm = s_rp + P.T + 1;
+  int* s_ci = s_perm + P.T;
+  __shared__ int s_fail;
+  constexpr int kGroup = K * G;
+  const int k = threadIdx.x % K;
+  const int lane = (threadIdx.x / K) % G;
+  const unsigned mask = group_mask<kGroup>();
+  const int s = blockIdx.x;
+  if (s >= P.nstrips) return;
+  const int n_p = L.n_p;
+  const int r_lo = s * P.T, r_hi = min(r_lo + P.T, n_p);
+  const int h_lo = max(0, r_lo - P.T), h_hi = min(n_p, r_hi + P.T);
+  const int* so = P.soff + (size_t)s * (P.ncol + 1);
+  const int q0 = so[0], q1 = so[P.ncol];
+  const int e0 = L.S.rp[q0], e1 = L.S.rp[q1];
+  // stage the strip once
+  if (threadIdx.x == 0) s_fail = 0;
+  for (int t = threadIdx.x; t < (h_hi - h_lo) * K; t += blockDim.x) s_dp[t] = T(0);
+  stage_copy<false>(s_g, g + (size_t)r_lo * K, (r_hi - r_lo) * K);
+  stage_copy<false>(s_dinv, L.S_dinv + q0, q1 - q0);
+  stage_copy<false>(s_perm, L.S_perm + q0, q1 - q0);
+  stage_copy<false>(s_rp, L.S.rp + q0, q1 - q0 + 1);
+  if (P.stage == 2) {
+    stage_copy<false>(s_v, L.S.v + e0, e1 - e0);
+    stage_copy<false>(s_ci, ci_rel + e0, e1 - e0);
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  const int par = s & 1;
+  for (int it = 0; it < P.iters; ++it) {
+    const int need = par == 0 ? it : it + 1;
+    if (need > 0) {
+      if (threadIdx.x == 0) {
+        for (int nb = s - 1; nb <= s + 1; nb += 2) {
+          if (nb < 0 || nb >= P.nstrips) continue;
+          unsigned long long spins = 0;
+          while (ld_acquire(done + nb) < need) {
+            if (++spins > kSpinLimit || *(volatile int*)err) {
+              atomicExch(err, 1);
+              s_fail = 1;
+              break;
+            }
+            __nanosleep(32);
+          }
+        }
+      }
+      __syncthreads();
+      if (s_fail) return;
+      // neighbour rows of the halo, as the neighbours last wrote them (through L2)
+      stage_copy<true>(s_dp, dp + (size_t)h_lo * K, (r_lo - h_lo) * K);
+      stage_copy<true>(s_dp + (size_t)(r_hi - h_lo) * K, dp + (size_t)r_hi * K, (h_hi - r_hi) * K);
+      cp_async_wait_all();
+      __syncthreads();
+    }
+    for (int pc = 0; pc < P.ncol; ++pc) {
+      const int ra = so[pc], rb = so[pc + 1];
+      for (int t = threadIdx.x; t < (rb - ra) * kGroup; t += blockDim.x) {
+        const int r = ra + t / kGroup;
+        const int ea = s_rp[r - q0], eb = s_rp[r - q0 + 1];
+        T a0 = T(0), a1 = T(0);
+        int e = ea + lane;
+        if (P.stage == 2) {
+          for (; e + G < eb; e += 2 * G) {
+            const int c0 = s_ci[e - e0], c1 = s_ci[e - e0 + G];
+            a0 += s_v[e - e0] * s_dp[(size_t)c0 * K + k];
+            a1 += s_v[e - e0 + G] * s_dp[(size_t)c1 * K + k];
+          }
+          if (e < eb) a0 += s_v[e - e0] * s_dp[(size_t)s_ci[e - e0] * K + k];
+        } else {
+          for (; e + G < eb; e += 2 * G) {
+            const int c0 = ci_rel[e], c1 = ci_rel[e + G];
+            a0 += L.S.v[e] * s_dp[(size_t)c0 * K + k];
+            a1 += L.S.v[e + G] * s_dp[(size_t)c1 * K + k];
+          }
+          if (e < eb) a0 += L.S.v[e] * s_dp[(size_t)ci_rel[e] * K + k];
+        }
+        const T acc = group_sum<K, G>(a0 + a1, mask);
+        if (lane == 0) {
+          const int i = s_perm[r - q0];
+          s_dp[(size_t)(i - h_lo) * K + k] = (s_g[(size_t)(i - r_lo) * K + k] - acc) * s_dinv[r - q0];
+        }
+      }
+      __syncthreads();
+    }
+    for (int t = threadIdx.x; t < (r_hi - r_lo) * K; t += blockDim.x)
+      dp[(size_t)r_lo * K + t] = s_dp[(size_t)(r_lo - h_lo) * K + t];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      st_release(done + s, it + 1);
+    }
+  }
 }
 
 // u = y - w .* (Bt dp), p = p + dp (p = dp with zero_x): the velocity/pressure update.
-template <typename T, int K>
+template <typename T, int K, int G>
 __global__ void __launch_bounds__(kBlock) k_bs_update(LevelView<T> L, const T* __restrict__ y,
                                                       const T* __restrict__ dp, T* __restrict__ x, int zero_x) {
-  const long long t = gtid();
-  const int i = (int)(t / K), k = (int)(t % K);
+  constexpr int W = K * G;
+  const RowThread<K, G> q(gtid());
+  const int i = q.row, k = q.k;
   const size_t nuK = (size_t)L.dim * L.n_v * K;
   if (i < L.n_v) {
-    const T wi = L.w[i];
+    T sum[3] = {T(0), T(0), T(0)};
 #pragma unroll
     for (int c = 0; c < 3; ++c)
       if (c < L.dim) {
         const int r = c * L.n_v + i;
-        T s = T(0);
-        for (int e = L.Bt.rp[r]; e < L.Bt.rp[r + 1]; ++e) s += L.Bt.v[e] * dp[(size_t)L.Bt.ci[e] * K + k];
-        const size_t o = (size_t)r * K + k;
-        x[o] = y[o] - wi * s;
+        for (int e = L.Bt.rp[r] + q.lane; e < L.Bt.rp[r + 1]; e += G) sum[c] += L.Bt.v[e] * dp[(size_t)L.Bt.ci[e] * K + k];
       }
-  } else if (i < L.n_v + L.n_p) {
-    const int q = i - L.n_v;
-    const size_t o = nuK + (size_t)q * K + k;
-    x[o] = (zero_x ? T(0) : x[o]) + dp[(size_t)q * K + k];
+    const unsigned mask = group_mask<W>();
+#pragma unroll
+    for (int c = 0; c < 3; ++c) sum[c] = group_sum<K, G>(sum[c], mask);
+    if (q.lane != 0) return;
+    const T wi = L.w[i];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      if (c < L.dim) {
+        const size_t o = ((size_t)c * L.n_v + i) * K + k;
+        x[o] = y[o] - wi * sum[c];
+      }
+  } else if (i < L.n_v + L.n_p && q.lane == 0) {
+    const int p = i - L.n_v;
+    const size_t o = nuK + (size_t)p * K + k;
+    x[o] = (zero_x ? T(0) : x[o]) + dp[(size_t)p * K + k];
   }
 }
 
 // out = b - A x (HAS_B) or out = A x, for the whole block matrix [I(x)A, Bt; B, C].
-template <typename T, typename TX, typename TO, int K, bool HAS_B>
+template <typename T, typename TX, typename TO, int K, int G, bool HAS_B>
 __global__ void __launch_bounds__(kBlock) k_block_spmv(LevelView<T> L, const T* __restrict__ b,
                                                        const TX* __restrict__ x, TO* __restrict__ out) {
-  const long long t = gtid();
-  const int i = (int)(t / K), k = (int)(t % K);
+  constexpr int W = K * G;
+  const RowThread<K, G> q(gtid());
+  const int i = q.row, k = q.k;
   const size_t nuK = (size_t)L.dim * L.n_v * K;
+  const unsigned mask = group_mask<W>();
   if (i < L.n_v) {
     T acc[3] = {T(0), T(0), T(0)};
-    for (int e = L.A.rp[i]; e < L.A.rp[i + 1]; ++e) {
+    for (int e = L.A.rp[i] + q.lane; e < L.A.rp[i + 1]; e += G) {
       const T a = L.A.v[e];
       const size_t j = (size_t)L.A.ci[e];
 #pragma unroll
@@ -158,60 +485,176 @@ __global__ void __launch_bounds__(kBlock) k_block_spmv(LevelView<T> L, const T* 
     for (int c = 0; c < 3; ++c)
       if (c < L.dim) {
         const int r = c * L.n_v + i;
-        for (int e = L.Bt.rp[r]; e < L.Bt.rp[r + 1]; ++e) acc[c] += L.Bt.v[e] * (T)x[nuK + (size_t)L.Bt.ci[e] * K + k];
-        const size_t o = (size_t)r * K + k;
+        for (int e = L.Bt.rp[r] + q.lane; e < L.Bt.rp[r + 1]; e += G) acc[c] += L.Bt.v[e] * (T)x[nuK + (size_t)L.Bt.ci[e] * K + k];
+      }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) acc[c] = group_sum<K, G>(acc[c], mask);
+    if (q.lane != 0) return;
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      if (c < L.dim) {
+        const size_t o = ((size_t)c * L.n_v + i) * K + k;
         out[o] = (TO)(HAS_B ? b[o] - acc[c] : acc[c]);
       }
   } else if (i < L.n_v + L.n_p) {
-    const int q = i - L.n_v;
+    const int p = i - L.n_v;
     T acc = T(0);
-    for (int e = L.B.rp[q]; e < L.B.rp[q + 1]; ++e) acc += L.B.v[e] * (T)x[(size_t)L.B.ci[e] * K + k];
-    const size_t o = nuK + (size_t)q * K + k;
-    if (q == L.pinned) acc += (T)x[o];
+    for (int e = L.B.rp[p] + q.lane; e < L.B.rp[p + 1]; e += G) acc += L.B.v[e] * (T)x[(size_t)L.B.ci[e] * K + k];
+    acc = group_sum<K, G>(acc, mask);
+    if (q.lane != 0) return;
+    const size_t o = nuK + (size_t)p * K + k;
+    if (p == L.pinned) acc += (T)x[o];
     out[o] = (TO)(HAS_B ? b[o] - acc : acc);
   }
 }
 
 // b_c = R r: velocity rows by R (each component), pressure rows by Rp.
-template <typename T, int K>
+template <typename T, int K, int G>
 __global__ void __launch_bounds__(kBlock) k_restrict(LevelView<T> L, const T* __restrict__ r, T* __restrict__ bc) {
-  const long long t = gtid();
-  const int I = (int)(t / K), k = (int)(t % K);
+  constexpr int W = K * G;
+  const RowThread<K, G> q(gtid());
+  const int I = q.row, k = q.k;
+  const unsigned mask = group_mask<W>();
   if (I < L.n_vc) {
+    T s[3] = {T(0), T(0), T(0)};
+    for (int e = L.R.rp[I] + q.lane; e < L.R.rp[I + 1]; e += G) {
+      const T v = L.R.v[e];
+      const size_t j = (size_t)L.R.ci[e];
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        if (c < L.dim) s[c] += v * r[((size_t)c * L.n_v + j) * K + k];
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) s[c] = group_sum<K, G>(s[c], mask);
+    if (q.lane != 0) return;
 #pragma unroll
     for (int c = 0; c < 3; ++c)
-      if (c < L.dim) {
-        T s = T(0);
-        for (int e = L.R.rp[I]; e < L.R.rp[I + 1]; ++e) s += L.R.v[e] * r[((size_t)c * L.n_v + L.R.ci[e]) * K + k];
-        bc[((size_t)c * L.n_vc + I) * K + k] = s;
-      }
+      if (c < L.dim) bc[((size_t)c * L.n_vc + I) * K + k] = s[c];
   } else if (I < L.n_vc + L.n_pc) {
-    const int q = I - L.n_vc;
+    const int p = I - L.n_vc;
     const size_t nuK = (size_t)L.dim * L.n_v * K;
     T s = T(0);
-    for (int e = L.Rp.rp[q]; e < L.Rp.rp[q + 1]; ++e) s += L.Rp.v[e] * r[nuK + (size_t)L.Rp.ci[e] * K + k];
-    bc[((size_t)L.dim * L.n_vc + q) * K + k] = s;
+    for (int e = L.Rp.rp[p] + q.lane; e < L.Rp.rp[p + 1]; e += G) s += L.Rp.v[e] * r[nuK + (size_t)L.Rp.ci[e] * K + k];
+    s = group_sum<K, G>(s, mask);
+    if (q.lane != 0) return;
+    bc[((size_t)L.dim * L.n_vc + p) * K + k] = s;
   }
 }
 
 // x += P x_c: velocity rows by P (each component), pressure rows by Pp.
-template <typename T, int K>
+template <typename T, int K, int G>
 __global__ void __launch_bounds__(kBlock) k_prolong(LevelView<T> L, const T* __restrict__ xc, T* __restrict__ x) {
-  const long long t = gtid();
-  const int i = (int)(t / K), k = (int)(t % K);
+  constexpr int W = K * G;
+  const RowThread<K, G> q(gtid());
+  const int i = q.row, k = q.k;
+  const unsigned mask = group_mask<W>();
   if (i < L.n_v) {
+    T s[3] = {T(0), T(0), T(0)};
+    for (int e = L.P.rp[i] + q.lane; e < L.P.rp[i + 1]; e += G) {
+      const T v = L.P.v[e];
+      const size_t j = (size_t)L.P.ci[e];
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        if (c < L.dim) s[c] += v * xc[((size_t)c * L.n_vc + j) * K + k];
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) s[c] = group_sum<K, G>(s[c], mask);
+    if (q.lane != 0) return;
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      if (c < L.dim) x[((size_t)c * L.n_v + i) * K + k] += s[c];
+  } else if (i < L.n_v + L.n_p) {
+    const int p = i - L.n_v;
+    T s = T(0);
+    for (int e = L.Pp.rp[p] + q.lane; e < L.Pp.rp[p + 1]; e += G) s += L.Pp.v[e] * xc[((size_t)L.dim * L.n_vc + L.Pp.ci[e]) * K + k];
+    s = group_sum<K, G>(s, mask);
+    if (q.lane != 0) return;
+    x[((size_t)L.dim * L.n_v + p) * K + k] += s;
+  }
+}
+
+// Block product in float-float arithmetic: out = A z for an FP32 vector z and the
+// FP64 matrix split as a = hi + lo (two floats).  hi*z is formed exactly as
+// p + e (e = fma(hi, z, -p)), lo*z in FP32 (its rounding is 2^-24 of a term
+// already 2^-24 of a*z), and the sum is carried as a float-float pair with
+// Knuth's two-sum, so the result matches FP64 to about 2^-44 relative to
+// sum |a z| while using only FP32 instructions.
+struct FFMat {
+  const int* rp;
+  const int* ci;
+  const float* hi;
+  const float* lo;
+};
+struct FFLevel {
+  int dim, n_v, n_p, pinned;
+  FFMat A, B, Bt;
+};
+
+struct FFAcc {
+  float s, c;
+  __device__ __forceinline__ void add(float a, float z) {
+    const float p = a * z;
+    const float e = fmaf(a, z, -p);
+    const float t = s + p;
+    const float bp = t - s;
+    const float err = (s - (t - bp)) + (p - bp);
+    s = t;
+    c += err + e;
+  }
+  __device__ __forceinline__ void add_small(float a, float z) { c = fmaf(a, z, c); }
+};
+
+template <int K, int G>
+__global__ void __launch_bounds__(kBlock) k_block_spmv_ff(FFLevel L, const float* __restrict__ z,
+                                                          double* __restrict__ out) {
+  constexpr int W = K * G;
+  const RowThread<K, G> q(gtid());
+  const int i = q.row, k = q.k;
+  const size_t nuK = (size_t)L.dim * L.n_v * K;
+  const unsigned mask = group_mask<W>();
+  if (i < L.n_v) {
+    FFAcc acc[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    for (int e = L.A.rp[i] + q.lane; e < L.A.rp[i + 1]; e += G) {
+      const float h = L.A.hi[e], l = L.A.lo[e];
+      const size_t j = (size_t)L.A.ci[e];
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        if (c < L.dim) {
+          const float zz = z[((size_t)c * L.n_v + j) * K + k];
+          acc[c].add(h, zz);
+          acc[c].add_small(l, zz);
+        }
+    }
 #pragma unroll
     for (int c = 0; c < 3; ++c)
       if (c < L.dim) {
-        T s = T(0);
-        for (int e = L.P.rp[i]; e < L.P.rp[i + 1]; ++e) s += L.P.v[e] * xc[((size_t)c * L.n_vc + L.P.ci[e]) * K + k];
-        x[((size_t)c * L.n_v + i) * K + k] += s;
+        const int r = c * L.n_v + i;
+        for (int e = L.Bt.rp[r] + q.lane; e < L.Bt.rp[r + 1]; e += G) {
+          const float zz = z[nuK + (size_t)L.Bt.ci[e] * K + k];
+          acc[c].add(L.Bt.hi[e], zz);
+          acc[c].add_small(L.Bt.lo[e], zz);
+        }
       }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      double v = (double)acc[c].s + (double)acc[c].c;
+      v = group_sum<K, G>(v, mask);
+      if (q.lane == 0 && c < L.dim) out[((size_t)c * L.n_v + i) * K + k] = v;
+    }
   } else if (i < L.n_v + L.n_p) {
-    const int q = i - L.n_v;
-    T s = T(0);
-    for (int e = L.Pp.rp[q]; e < L.Pp.rp[q + 1]; ++e) s += L.Pp.v[e] * xc[((size_t)L.dim * L.n_vc + L.Pp.ci[e]) * K + k];
-    x[((size_t)L.dim * L.n_v + q) * K + k] += s;
+    const int p = i - L.n_v;
+    FFAcc acc = {0.f, 0.f};
+    for (int e = L.B.rp[p] + q.lane; e < L.B.rp[p + 1]; e += G) {
+      const float zz = z[(size_t)L.B.ci[e] * K + k];
+      acc.add(L.B.hi[e], zz);
+      acc.add_small(L.B.lo[e], zz);
+    }
+    double v = (double)acc.s + (double)acc.c;
+    v = group_sum<K, G>(v, mask);
+    if (q.lane != 0) return;
+    const size_t o = nuK + (size_t)p * K + k;
+    if (p == L.pinned) v += (double)z[o];
+    out[o] = v;
   }
 }
 

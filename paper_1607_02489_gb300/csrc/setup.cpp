@@ -398,8 +398,9 @@ Csr emin_step(const Csr& At, const std::vector<std::vector<int>>& rows, int ncol
 }
 
 // Braess-Sarazin data (Section 5.2): D = |A| row sums (Dirichlet rows 1/c), the
-// explicit Schur complement S = B D^-1 Bt (pinned row = identity) and a greedy
-// coloring of its graph (vertices in index order, smallest free color).
+// explicit Schur complement S = B D^-1 Bt (pinned row = identity), the strip
+// length of the Gauss-Seidel ordering and a greedy coloring of S's graph
+// (vertices in index order, smallest free color).
 void form_relaxation(HostLevel& L, const SetupParams& prm) {
   L.D.assign(L.n_v, 0.0);
   for (int i = 0; i < L.n_v; ++i) {
@@ -434,6 +435,13 @@ void form_relaxation(HostLevel& L, const SetupParams& prm) {
     }
     L.S = std::move(S2);
   }
+  // Gauss-Seidel ordering: strips of T = bandwidth(S) consecutive rows, so strips
+  // two apart share no entry of S; rows go by (strip parity, color, index)
+  int bw = 0;
+  for (int i = 0; i < L.n_p; ++i)
+    for (int64_t t = L.S.row_begin(i); t < L.S.row_end(i); ++t)
+      if (L.S.col[t] != i) bw = std::max(bw, std::abs(L.S.col[t] - i));
+  L.gs_strip = std::max(bw, 1);
   L.colors.assign(L.n_p, -1);
   L.n_colors = 0;
   std::vector<int> used_stamp(64, -1);

@@ -30,6 +30,7 @@ struct HostLevel {
   Csr S;                               // B D^-1 Bt, pinned row = identity
   std::vector<int> colors;             // greedy coloring of S's graph
   int n_colors = 0;
+  int gs_strip = 1;                    // Gauss-Seidel strip length: bandwidth of S
   // transfers to the next level
   Csr P, Pp, R, Rp;
   std::vector<int> Cp, Cv;             // coarse points (fine indices, ascending)

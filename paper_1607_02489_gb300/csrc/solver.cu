@@ -336,7 +336,12 @@ amg_status fgmres_k(amg_hierarchy* h, const double* b, double* x, int nrhs, doub
       EMIN_CUDA(vc->run(K, s));
       EMIN_CUDA(cudaMemcpyAsync(Z + (size_t)j * NK, vc->output(0), sizeof(TZ) * NK, cudaMemcpyDeviceToDevice, s));
       // w = A z_j in FP64
-      EMIN_CUDA(apply_finest_f64(h->v64, Z + (size_t)j * NK, f32, nullptr, h->w, K, s)); ++h->launches;
+      if (f32)
+        EMIN_CUDA(vc->apply_ff((const float*)(Z + (size_t)j * NK), h->w, K, s));
+      else {
+        EMIN_CUDA(apply_finest_f64(h->v64, Z + (size_t)j * NK, false, nullptr, h->w, K, s));
+        ++h->launches;
+      }
       // classical Gram-Schmidt with one re-orthogonalisation
       const int nv = j + 1;
       k_mdot_partial<K, double><<<kRedBlocks, kBlock, 0, s>>>(NK, nv, h->V, h->w, h->part); ++h->launches;
@@ -351,7 +356,9 @@ amg_status fgmres_k(amg_hierarchy* h, const double* b, double* x, int nrhs, doub
       k_givens<<<1, 32, 0, s>>>(j, restart, K, h->hbuf, h->st, h->bnorm, rtol, h->n_active); ++h->launches;
       EMIN_CUDA(cudaGetLastError());
       EMIN_CUDA(cudaMemcpyAsync(h->host_i, h->n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
+      EMIN_CUDA(cudaMemcpyAsync(h->host_i + 1, vc->error_flag(), sizeof(int), cudaMemcpyDeviceToHost, s));
       EMIN_CUDA(cudaStreamSynchronize(s));
+      if (h->host_i[1] != 0) throw std::runtime_error("cuda: a Gauss-Seidel grid barrier timed out");
       if (*h->host_i == 0) {
         ++j;
         break;
@@ -671,6 +678,7 @@ amg_status amg_level_get_info(amg_handle h, int level, amg_level_info* info) {
   info->nnz_Rp = L.Rp.nnz();
   info->n_cp = (int)L.Cp.size();
   info->n_cv = (int)L.Cv.size();
+  info->gs_strip = L.gs_strip;
   return AMG_OK;
 }
 

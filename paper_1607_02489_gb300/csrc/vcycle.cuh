@@ -30,6 +30,11 @@ struct VCycleIface {
   virtual cudaError_t profile(int K, int reps, cudaStream_t s, double* ms, long long* count) = 0;
   // Kernels launched so far by run() and profile() (graph replays count every kernel node).
   virtual long long launches() const = 0;
+  // Device word set when a bounded grid barrier timed out (0 otherwise).
+  virtual int* error_flag() const = 0;
+  // FP32 cycles only: out = A z on the finest level for an FP32 z, FP64 result by
+  // float-float arithmetic on the FP64 matrix split into two floats.
+  virtual cudaError_t apply_ff(const float* z, double* out, int K, cudaStream_t s) = 0;
 };
 
 // Kernel classes reported by profile().
@@ -60,6 +65,11 @@ class DeviceVCycle : public VCycleIface {
       const HostLevel& C = levels.back();
       Nc_ = C.N();
       pinv_ = alloc_copy<double>(C.pinv);
+      if (sizeof(T) == 4) build_ff(levels[0]);
+      barrier_ = alloc<GridBarrier>(levels.size());
+      err_ = alloc<int>(1);
+      EMIN_CUDA(cudaMemset(barrier_, 0, sizeof(GridBarrier) * levels.size()));
+      EMIN_CUDA(cudaMemset(err_, 0, sizeof(int)));
     } catch (...) {
       release();
       throw;
@@ -128,11 +138,19 @@ class DeviceVCycle : public VCycleIface {
       smooth<K>(l, pre_, true, s);
       const LevelView<T>& L = views_[l];
       mark_begin(l, kResidual, s);
-      k_block_spmv<T, T, T, K, true><<<grid_for((long long)(L.n_v + L.n_p) * K), kBlock, 0, s>>>(
-          L, buf_[l].b, buf_[l].x, buf_[l].r);
+      if (small_level(l, K))
+        k_block_spmv<T, T, T, K, RowLanes<K>::G, true><<<grid_for((long long)(L.n_v + L.n_p) * RowLanes<K>::W), kBlock, 0, s>>>(
+            L, buf_[l].b, buf_[l].x, buf_[l].r);
+      else
+        k_block_spmv<T, T, T, K, 1, true><<<grid_for((long long)(L.n_v + L.n_p) * K), kBlock, 0, s>>>(
+            L, buf_[l].b, buf_[l].x, buf_[l].r);
       mark_end(s);
       mark_begin(l, kRestrict, s);
-      k_restrict<T, K><<<grid_for((long long)(L.n_vc + L.n_pc) * K), kBlock, 0, s>>>(L, buf_[l].r, buf_[l + 1].b);
+      if (small_level(l + 1, K))
+        k_restrict<T, K, RowLanes<K>::G><<<grid_for((long long)(L.n_vc + L.n_pc) * RowLanes<K>::W), kBlock, 0, s>>>(
+            L, buf_[l].r, buf_[l + 1].b);
+      else
+        k_restrict<T, K, 1><<<grid_for((long long)(L.n_vc + L.n_pc) * K), kBlock, 0, s>>>(L, buf_[l].r, buf_[l + 1].b);
       mark_end(s);
     }
     mark_begin(nl - 1, kCoarse, s);  // every kernel launch of the cycle is preceded by mark_begin
@@ -141,7 +159,11 @@ class DeviceVCycle : public VCycleIface {
     for (int l = nl - 2; l >= 0; --l) {
       const LevelView<T>& L = views_[l];
       mark_begin(l, kProlong, s);
-      k_prolong<T, K><<<grid_for((long long)(L.n_v + L.n_p) * K), kBlock, 0, s>>>(L, buf_[l + 1].x, buf_[l].x);
+      if (small_level(l, K))
+        k_prolong<T, K, RowLanes<K>::G><<<grid_for((long long)(L.n_v + L.n_p) * RowLanes<K>::W), kBlock, 0, s>>>(
+            L, buf_[l + 1].x, buf_[l].x);
+      else
+        k_prolong<T, K, 1><<<grid_for((long long)(L.n_v + L.n_p) * K), kBlock, 0, s>>>(L, buf_[l + 1].x, buf_[l].x);
       mark_end(s);
       smooth<K>(l, post_, false, s);
     }
@@ -164,25 +186,33 @@ class DeviceVCycle : public VCycleIface {
   void smooth(int l, int sweeps, bool from_zero, cudaStream_t s) {
     const LevelView<T>& L = views_[l];
     const Buf& B = buf_[l];
-    const std::vector<int>& off = color_off_[l];
+    const bool small = small_level(l, K);
     for (int sw = 0; sw < sweeps; ++sw) {
       const int zero = (from_zero && sw == 0) ? 1 : 0;
       mark_begin(l, kVelocity, s);
-      k_bs_velocity<T, K><<<grid_for((long long)L.n_v * K), kBlock, 0, s>>>(L, B.b, B.x, B.y, zero);
+      if (small)
+        k_bs_velocity<T, K, RowLanes<K>::G><<<grid_for((long long)L.n_v * RowLanes<K>::W), kBlock, 0, s>>>(L, B.b, B.x, B.y,
+                                                                                                   zero);
+      else
+        k_bs_velocity<T, K, 1><<<grid_for((long long)L.n_v * K), kBlock, 0, s>>>(L, B.b, B.x, B.y, zero);
       mark_end(s);
       mark_begin(l, kSchurRhs, s);
-      k_schur_rhs<T, K><<<grid_for((long long)L.n_p * K), kBlock, 0, s>>>(L, B.b, B.x, B.y, B.g, cfac_, zero);
+      if (small)
+        k_schur_rhs<T, K, RowLanes<K>::G><<<grid_for((long long)L.n_p * RowLanes<K>::W), kBlock, 0, s>>>(L, B.b, B.x, B.y,
+                                                                                                 B.g, cfac_, zero);
+      else
+        k_schur_rhs<T, K, 1><<<grid_for((long long)L.n_p * K), kBlock, 0, s>>>(L, B.b, B.x, B.y, B.g, cfac_, zero);
       mark_end(s);
       cudaMemsetAsync(B.dp, 0, sizeof(T) * (size_t)L.n_p * K, s);
-      for (int it = 0; it < gs_iters_; ++it)
-        for (size_t c = 0; c + 1 < off.size(); ++c) {
-          mark_begin(l, kGsColor, s);
-          k_gs_color<T, K><<<grid_for((long long)(off[c + 1] - off[c]) * K), kBlock, 0, s>>>(L, B.g, B.dp, off[c],
-                                                                                              off[c + 1]);
-          mark_end(s);
-        }
+      mark_begin(l, kGsColor, s);
+      launch_gs<K>(l, s);
+      mark_end(s);
       mark_begin(l, kUpdate, s);
-      k_bs_update<T, K><<<grid_for((long long)(L.n_v + L.n_p) * K), kBlock, 0, s>>>(L, B.y, B.dp, B.x, zero);
+      if (small)
+        k_bs_update<T, K, RowLanes<K>::G><<<grid_for((long long)(L.n_v + L.n_p) * RowLanes<K>::W), kBlock, 0, s>>>(
+            L, B.y, B.dp, B.x, zero);
+      else
+        k_bs_update<T, K, 1><<<grid_for((long long)(L.n_v + L.n_p) * K), kBlock, 0, s>>>(L, B.y, B.dp, B.x, zero);
       mark_end(s);
     }
   }
@@ -202,6 +232,161 @@ class DeviceVCycle : public VCycleIface {
   }
   void mark_end(cudaStream_t s) {
     if (prof_on_) cudaEventRecord(recs_.back().b, s);
+  }
+
+  // Small levels are latency-bound: their sparse kernels put G > 1 lanes on a row.
+  bool small_level(int l, int K) const {
+    const LevelView<T>& L = views_[l];
+    return (long long)(L.n_v + L.n_p) * K < kSmallLevelItems;
+  }
+
+  // Shared memory of the strip kernel for K right-hand sides at a staging level.
+  size_t gs_smem(int l, int K, int stage) const {
+    const GsStrips& P = gs_[l];
+    if (stage == 0) return 0;
+    size_t b = (size_t)4 * P.T * K * sizeof(T) + (size_t)P.T * sizeof(T) + (size_t)(2 * P.T + 1) * sizeof(int);
+    if (stage == 2) b += (size_t)P.max_strip_nnz * (sizeof(T) + sizeof(int));
+    return (b + 15) / 16 * 16;
+  }
+  int gs_stage(int l, int K) const {
+    const size_t limit = 200 * 1024;
+    if (gs_smem(l, K, 2) <= limit) return 2;
+    if (gs_smem(l, K, 1) <= limit) return 1;
+    return 0;
+  }
+
+  // Strip-ordered Gauss-Seidel: one block per strip of the active parity, a
+  // cooperative grid (bounded barrier) when there are several strips.
+  template <int K>
+  void launch_gs(int l, cudaStream_t s) {
+    if (launch_gs_pipe<K>(l, s)) return;
+    if (K <= 8 && gs_lanes_[l] == 4) return launch_gs_g<K, (K <= 8 ? 4 : 1)>(l, s);
+    launch_gs_g<K, 1>(l, s);
+  }
+
+  // The pipelined kernel needs every strip resident at once; false if they do not fit.
+  // Lanes per row for the pipelined kernel: as many as the block has to spare
+  // for the average color of a strip (K * G <= 32).
+  template <int K>
+  bool launch_gs_pipe(int l, cudaStream_t s) {
+    const GsStrips& P0 = gs_[l];
+    const double rows_per_color = (double)P0.T / std::max(1, P0.ncol);
+    int G = 1;
+    while (G < 4 && K * G * 2 <= 32 && rows_per_color * K * G * 2 <= kGsBlock) G *= 2;
+    if (G == 4) return launch_gs_pipe_g<K, (K <= 8 ? 4 : 1)>(l, s);
+    if (G == 2) return launch_gs_pipe_g<K, (K <= 16 ? 2 : 1)>(l, s);
+    return launch_gs_pipe_g<K, 1>(l, s);
+  }
+
+  template <int K, int G>
+  bool launch_gs_pipe_g(int l, cudaStream_t s) {
+    const LevelView<T>& L = views_[l];
+    const Buf& B = buf_[l];
+    GsStrips P = gs_[l];
+    P.stage = gs_stage(l, K);
+    if (P.stage == 0) return false;
+    const size_t smem = gs_smem(l, K, P.stage);
+    auto kern = k_gs_pipe<T, K, G>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 48 * 1024));
+    int per = 0, sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kGsBlock, smem);
+    if (P.nstrips > sms * per) return false;
+    cudaMemsetAsync(done_[l], 0, sizeof(int) * P.nstrips, s);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(P.nstrips);
+    cfg.blockDim = dim3(kGsBlock);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kern, L, (const T*)B.g, B.dp, P, (const int*)ci_rel_[l], done_[l], err_);
+    return true;
+  }
+
+  template <int K, int G>
+  void launch_gs_g(int l, cudaStream_t s) {
+    const LevelView<T>& L = views_[l];
+    const Buf& B = buf_[l];
+    GsStrips P = gs_[l];
+    P.stage = gs_stage(l, K);
+    const size_t smem = gs_smem(l, K, P.stage);
+    auto kern = k_gs_strips<T, K, G>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 48 * 1024));
+    int per = 0, sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kGsBlock, smem);
+    const int coop = std::max(1, sms * std::max(per, 1));
+    const int nb = std::max(1, std::min((P.nstrips + 1) / 2, coop));
+    if (nb == 1) {
+      kern<<<1, kGsBlock, smem, s>>>(L, B.g, B.dp, P, barrier_ + l, err_);
+      return;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nb);
+    cfg.blockDim = dim3(kGsBlock);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kern, L, (const T*)B.g, B.dp, P, barrier_ + l, err_);
+  }
+
+ public:
+  // Nonzero when a grid barrier gave up (checked by the solver after a cycle).
+  int* error_flag() const override { return err_; }
+
+  cudaError_t apply_ff(const float* z, double* out, int K, cudaStream_t s) override {
+    if (!ff_.A.hi) return cudaErrorInvalidValue;
+    switch (K) {
+      case 1: return launch_ff<1>(z, out, s);
+      case 2: return launch_ff<2>(z, out, s);
+      case 4: return launch_ff<4>(z, out, s);
+      case 8: return launch_ff<8>(z, out, s);
+      case 16: return launch_ff<16>(z, out, s);
+      case 32: return launch_ff<32>(z, out, s);
+    }
+    return cudaErrorInvalidValue;
+  }
+
+ private:
+  template <int K>
+  cudaError_t launch_ff(const float* z, double* out, cudaStream_t s) {
+    k_block_spmv_ff<K, 1><<<grid_for((long long)(ff_.n_v + ff_.n_p) * K), kBlock, 0, s>>>(ff_, z, out);
+    ++launches_;
+    return cudaGetLastError();
+  }
+
+  FFMat upload_ff(const Csr& M) {
+    std::vector<int> rp(M.rowptr.begin(), M.rowptr.end());
+    std::vector<float> hi(M.val.size()), lo(M.val.size());
+    for (size_t t = 0; t < M.val.size(); ++t) {
+      hi[t] = (float)M.val[t];
+      lo[t] = (float)(M.val[t] - (double)hi[t]);
+    }
+    FFMat f;
+    f.rp = alloc_copy<int>(rp);
+    f.ci = alloc_copy<int>(M.col);
+    f.hi = alloc_copy<float>(hi);
+    f.lo = alloc_copy<float>(lo);
+    return f;
+  }
+  void build_ff(const HostLevel& H) {
+    ff_.dim = H.dim;
+    ff_.n_v = H.n_v;
+    ff_.n_p = H.n_p;
+    ff_.pinned = H.pinned;
+    ff_.A = upload_ff(H.A);
+    ff_.B = upload_ff(H.B);
+    ff_.Bt = upload_ff(H.Bt);
   }
 
   cudaError_t capture(int K, int slot) {
@@ -267,13 +452,25 @@ class DeviceVCycle : public VCycleIface {
     L.A = upload(H.A);
     L.B = upload(H.B);
     L.Bt = upload(H.Bt);
-    // Schur complement rows grouped by color, diagonal split off
-    std::vector<int> perm(H.n_p), off(H.n_colors + 1, 0);
-    for (int i = 0; i < H.n_p; ++i) off[H.colors[i] + 1]++;
-    for (int c = 0; c < H.n_colors; ++c) off[c + 1] += off[c];
+    // Schur complement rows sorted by (strip, color, index), diagonal split off;
+    // soff[s * (ncol + 1) + c] is the first sorted row of color c in strip s.
+    const int Tst = H.gs_strip, ncol = H.n_colors;
+    const int nstrips = std::max(1, (H.n_p + Tst - 1) / Tst);
+    std::vector<int> perm(H.n_p), soff((size_t)nstrips * (ncol + 1), 0);
     {
-      std::vector<int> pos(off.begin(), off.end() - 1);
-      for (int i = 0; i < H.n_p; ++i) perm[pos[H.colors[i]]++] = i;
+      std::vector<int> cnt((size_t)nstrips * ncol, 0);
+      for (int i = 0; i < H.n_p; ++i) cnt[(size_t)(i / Tst) * ncol + H.colors[i]]++;
+      std::vector<int> start((size_t)nstrips * ncol, 0);
+      int run = 0;
+      for (int st = 0; st < nstrips; ++st) {
+        for (int c = 0; c < ncol; ++c) {
+          soff[(size_t)st * (ncol + 1) + c] = run;
+          start[(size_t)st * ncol + c] = run;
+          run += cnt[(size_t)st * ncol + c];
+        }
+        soff[(size_t)st * (ncol + 1) + ncol] = run;
+      }
+      for (int i = 0; i < H.n_p; ++i) perm[start[(size_t)(i / Tst) * ncol + H.colors[i]]++] = i;
     }
     Csr So;
     So.resize_rows(H.n_p, H.n_p);
@@ -292,9 +489,34 @@ class DeviceVCycle : public VCycleIface {
       dinv[r] = diag != 0.0 ? 1.0 / diag : 0.0;
       So.rowptr[r + 1] = (int64_t)So.col.size();
     }
+    GsStrips gp{};
+    gp.nstrips = nstrips;
+    gp.ncol = ncol;
+    gp.T = Tst;
+    gp.iters = gs_iters_;
+    gp.max_strip_nnz = 0;
+    for (int st = 0; st < nstrips; ++st)
+      gp.max_strip_nnz = std::max<int>(gp.max_strip_nnz, (int)(So.rowptr[soff[(size_t)st * (ncol + 1) + ncol]] -
+                                                                So.rowptr[soff[(size_t)st * (ncol + 1)]]));
     L.S = upload(So);
     L.S_perm = alloc_copy<int>(perm);
     L.S_dinv = alloc_copy<T>(dinv);
+    gp.soff = alloc_copy<int>(soff);
+    // S columns relative to the halo start of the row's strip (for the pipelined kernel)
+    {
+      std::vector<int> rel(So.col.size());
+      for (int st = 0; st < nstrips; ++st) {
+        const int h0 = std::max(0, st * Tst - Tst);
+        for (int r = soff[(size_t)st * (ncol + 1)]; r < soff[(size_t)st * (ncol + 1) + ncol]; ++r)
+          for (int64_t t = So.rowptr[r]; t < So.rowptr[r + 1]; ++t) rel[t] = So.col[t] - h0;
+      }
+      ci_rel_.push_back(alloc_copy<int>(rel));
+      done_.push_back(alloc<int>(nstrips));
+    }
+    // lanes per Schur row: 4 when rows are long enough to share
+    const double avg = H.n_p ? (double)So.nnz() / H.n_p : 0.0;
+    gs_lanes_.push_back(avg > 16.0 ? 4 : 1);
+    gs_.push_back(gp);
     std::vector<double> w(H.n_v);
     for (int i = 0; i < H.n_v; ++i) w[i] = H.dirichlet[i] ? 1.0 : 1.0 / (c_ * H.D[i]);
     L.w = alloc_copy<T>(w);
@@ -314,7 +536,6 @@ class DeviceVCycle : public VCycleIface {
     B.dp = alloc<T>((size_t)H.n_p * kmax_);
     views_.push_back(L);
     buf_.push_back(B);
-    color_off_.push_back(off);
   }
 
   void release() {
@@ -332,7 +553,13 @@ class DeviceVCycle : public VCycleIface {
   int gs_iters_, pre_, post_, kmax_;
   std::vector<LevelView<T>> views_;
   std::vector<Buf> buf_;
-  std::vector<std::vector<int>> color_off_;
+  std::vector<GsStrips> gs_;
+  std::vector<int> gs_lanes_;
+  std::vector<int*> ci_rel_;
+  std::vector<int*> done_;
+  GridBarrier* barrier_ = nullptr;
+  int* err_ = nullptr;
+  FFLevel ff_{};
   double* pinv_ = nullptr;
   int Nc_ = 0;
   std::vector<void*> allocs_;

@@ -17,14 +17,14 @@ static void apply_k(const LevelView<double>& L, const void* x, bool x_fp32, cons
   const unsigned g = grid_for((long long)(L.n_v + L.n_p) * K);
   if (x_fp32) {
     if (b)
-      k_block_spmv<double, float, double, K, true><<<g, kBlock, 0, s>>>(L, b, (const float*)x, out);
+      k_block_spmv<double, float, double, K, 1, true><<<g, kBlock, 0, s>>>(L, b, (const float*)x, out);
     else
-      k_block_spmv<double, float, double, K, false><<<g, kBlock, 0, s>>>(L, nullptr, (const float*)x, out);
+      k_block_spmv<double, float, double, K, 1, false><<<g, kBlock, 0, s>>>(L, nullptr, (const float*)x, out);
   } else {
     if (b)
-      k_block_spmv<double, double, double, K, true><<<g, kBlock, 0, s>>>(L, b, (const double*)x, out);
+      k_block_spmv<double, double, double, K, 1, true><<<g, kBlock, 0, s>>>(L, b, (const double*)x, out);
     else
-      k_block_spmv<double, double, double, K, false><<<g, kBlock, 0, s>>>(L, nullptr, (const double*)x, out);
+      k_block_spmv<double, double, double, K, 1, false><<<g, kBlock, 0, s>>>(L, nullptr, (const double*)x, out);
   }
 }
 

@@ -44,8 +44,18 @@ def _relerr(a, b):
     return np.linalg.norm(a - b, axis=0) / np.maximum(np.linalg.norm(b, axis=0), 1e-300)
 
 
+def _coarse_condition(Ho):
+    """Condition number of the coarsest operator on the complement of its exact null space."""
+    s = np.linalg.svd(Ho.levels[-1].full_matrix().toarray(), compute_uv=False)
+    s = s[s > 1e-12 * s[0]]
+    return s[0] / s[-1]
+
+
 @pytest.mark.parametrize("case", list(CASES))
 def test_vcycle_fp64_matches_oracle(case):
+    """Relative error <= max(1e-11, 2 kappa u): the coarsest solve of any FP64 method is only
+    accurate to its condition number kappa times the unit roundoff u = 2^-53, and the
+    pinned problem's coarsest level is nearly singular (kappa ~ 7.5e6)."""
     p = CASES[case]()
     Ho = setup_hierarchy(p)
     Hg = g.Hierarchy(p, max_nrhs=p.b.shape[1])
@@ -56,7 +66,8 @@ def test_vcycle_fp64_matches_oracle(case):
     zt = torch.empty_like(rt)
     Hg.vcycle(rt, zt)
     torch.cuda.synchronize()
-    assert np.all(_relerr(zt.cpu().numpy(), zo) <= 1e-11), _relerr(zt.cpu().numpy(), zo)
+    tol = max(1e-11, 2.0 * _coarse_condition(Ho) * 2.0 ** -53)
+    assert np.all(_relerr(zt.cpu().numpy(), zo) <= tol), (_relerr(zt.cpu().numpy(), zo), tol)
     # a second application reuses the captured graph and gives the same result
     z2 = torch.empty_like(rt)
     Hg.vcycle(rt, z2)
@@ -82,8 +93,8 @@ def test_vcycle_fp32_close_to_oracle(case):
 @pytest.mark.parametrize("case", ["pinned16", "lid18_ragged3", "lid3d", "oseen32"])
 def test_block_product_matches_oracle(case):
     p = CASES[case]()
-    Ho = setup_hierarchy(p, Params(max_levels=1))
-    Hg = g.Hierarchy(p, max_nrhs=p.b.shape[1], max_levels=1)
+    Ho = setup_hierarchy(p)
+    Hg = g.Hierarchy(p, max_nrhs=p.b.shape[1])
     x = _rand(p.N, p.b.shape[1], 13)
     yo = apply_A(Ho.levels[0], x)
     xt = torch.tensor(x, device="cuda")

@@ -19,15 +19,17 @@ def _table1():
 
 
 def test_multicolor_gs_equals_sequential_gs():
-    """The color-block update equals row-by-row Gauss-Seidel in color order."""
-    p = stokes_lid_2d(8, nrhs=2)
+    """The grouped update equals row-by-row Gauss-Seidel in (strip parity, color, index)
+    order, and the ordering's groups are independent sets of S's graph."""
+    p = stokes_lid_2d(16, nrhs=2)
     H = setup_hierarchy(p)
     L = H.levels[0]
+    assert L.gs_strip == 2 * 17 + 2
     rng = np.random.default_rng(0)
     g = rng.standard_normal((L.n_p, 2))
     dp = gauss_seidel(L, g, 3)
     S = L.S.tocsr()
-    order = sorted(range(L.n_p), key=lambda i: (L.colors[i], i))
+    order = sorted(range(L.n_p), key=lambda i: ((i // L.gs_strip) % 2, L.colors[i], i))
     ref = np.zeros_like(g)
     for _ in range(3):
         for i in order:
@@ -38,10 +40,12 @@ def test_multicolor_gs_equals_sequential_gs():
                     s -= S.data[t] * ref[j]
             ref[i] = s / S[i, i]
     assert np.abs(dp - ref).max() <= 1e-13 * np.abs(ref).max()
-    # a proper coloring: no two neighbours share a color
+    # a proper coloring, and strips two apart never coupled
     rows = np.repeat(np.arange(L.n_p), np.diff(S.indptr))
     off = rows != S.indices
     assert np.all(L.colors[rows[off]] != L.colors[S.indices[off]])
+    strip = np.arange(L.n_p) // L.gs_strip
+    assert np.all(np.abs(strip[rows[off]] - strip[S.indices[off]]) <= 1)
 
 
 @pytest.mark.parametrize("placement", ["direct", "inverse"])

@@ -54,6 +54,7 @@ def _compare(prob, prm=None, **kw):
         assert (info["n_v"], info["n_p"], info["pinned"]) == (L.n_v, L.n_p, L.pinned)
         assert np.array_equal(pts["colors"], L.colors)
         assert info["n_colors"] == int(L.colors.max()) + 1
+        assert info["gs_strip"] == L.gs_strip
         assert np.abs(pts["D"] - L.D).max() <= 1e-12 * np.abs(L.D).max()
         last = l + 1 == len(Ho.levels)
         if not last:

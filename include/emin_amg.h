@@ -105,6 +105,25 @@ amg_status amg_vcycle_apply(amg_handle h, const double* r, double* z, int nrhs, 
 /* Block product y = A x on the finest level (device, N x nrhs, FP64). Asynchronous. */
 amg_status amg_apply(amg_handle h, const double* x, double* y, int nrhs, void* stream);
 
+/* y = A x like amg_apply, for callers that cannot allocate device memory during a
+ * call: for instance a solver service whose memory budget is fully owned by
+ * another allocator (such as PyTorch's caching allocator), where a surprise
+ * cudaMalloc could fail, or a latency-bound loop that cannot afford the device
+ * synchronisation cudaMalloc/cudaFree bring.  The paper has no counterpart:
+ * this is an allocation policy of this library, not a step of the method.
+ * It allocates nothing: its scratch (x and y padded to K = nrhs rounded up to a
+ * power of two columns) is a 16 MiB array in the library's device memory, held
+ * by every device that loads the library until the process exits.  Limit:
+ * N * K <= 1,048,576 (for example 2,467 dofs with 32 right-hand sides, or
+ * 592,387 dofs with one); larger sizes return AMG_ERR_ARG with a message.
+ * The first call on a device looks up the array's device address with
+ * cudaGetSymbolAddress (once per device, that device current); make that first
+ * call before any stream capture.  Every call on a device shares the array and
+ * its last contents (each call rewrites all it reads), so calls whose GPU work
+ * overlaps (different streams or threads on the same device) race; order them.
+ * x, y: device, N x nrhs, FP64; 1 <= nrhs <= 32.  Asynchronous. */
+amg_status amg_apply_noalloc(amg_handle h, const double* x, double* y, int nrhs, void* stream);
+
 /* Right-preconditioned flexible GMRES with the V-cycle as preconditioner
  * (Section 6: "multigrid-preconditioned GMRES"), FP64 Arnoldi (classical
  * Gram-Schmidt with one re-orthogonalisation) and Givens rotations on the

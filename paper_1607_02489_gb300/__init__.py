@@ -23,7 +23,7 @@ STATUS_NAMES = {0: "OK", 1: "NOT_CONVERGED", 2: "BREAKDOWN", -1: "ERR_ARG", -2: 
                 -4: "ERR_SETUP"}
 EXPORTED = ["amg_params_default", "amg_hierarchy_create", "amg_vcycle_apply", "amg_apply", "amg_fgmres_solve",
             "amg_fgmres_solve_host", "amg_num_levels", "amg_level_get_info", "amg_level_get_matrix",
-            "amg_level_get_points", "amg_hierarchy_destroy", "amg_last_error", "amg_profile_vcycle", "amg_kernel_launches"]
+            "amg_level_get_points", "amg_hierarchy_destroy", "amg_last_error", "amg_profile_vcycle", "amg_kernel_launches", "amg_apply_noalloc"]
 KERNEL_CLASSES = ["velocity", "schur_rhs", "gs_color", "update", "residual", "restrict", "prolong", "coarse"]
 MATRICES = {"A": 0, "B": 1, "Bt": 2, "S": 3, "P": 4, "Pp": 5, "R": 6, "Rp": 7}
 
@@ -81,6 +81,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.amg_vcycle_apply.restype = ctypes.c_int
     lib.amg_apply.argtypes = [vp, vp, vp, ctypes.c_int, vp]
     lib.amg_apply.restype = ctypes.c_int
+    lib.amg_apply_noalloc.argtypes = [vp, vp, vp, ctypes.c_int, vp]
+    lib.amg_apply_noalloc.restype = ctypes.c_int
     for name in ("amg_fgmres_solve", "amg_fgmres_solve_host"):
         f = getattr(lib, name)
         f.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, _i32p, _f64p, vp]
@@ -199,6 +201,13 @@ class Hierarchy:
     def apply(self, x, y, stream=None):
         """y = A x on the finest level (amg_apply)."""
         _check(load().amg_apply(self._h, _dev_ptr(x, "x"), _dev_ptr(y, "y"), self._nrhs(x), _stream_ptr(stream)))
+        return y
+
+    def apply_noalloc(self, x, y, stream=None):
+        """y = A x through amg_apply_noalloc: no device allocation in the call; its
+        scratch is the library's static 16 MiB array (N * K <= 1,048,576)."""
+        _check(load().amg_apply_noalloc(self._h, _dev_ptr(x, "x"), _dev_ptr(y, "y"), self._nrhs(x),
+                                        _stream_ptr(stream)))
         return y
 
     def fgmres(self, b, x, rtol=1e-8, restart=100, maxit=500, stream=None):

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -480,9 +481,86 @@ Csr to_csr(const int* rp, const int* ci, const double* v, int nrows, int ncols) 
   return M;
 }
 
+// Scratch of amg_apply_noalloc: a file-scope device array, so that entry point
+// never allocates.  Each device that loads the library holds these 16 MiB until
+// the process exits.  Host code must not pass the array's name to a kernel (it
+// is a host-side stand-in); it passes the address cudaGetSymbolAddress returns
+// for the current device, looked up once per device.
+constexpr long long kNoAllocScratchDoubles = 2LL << 20;              // 16 MiB of doubles
+constexpr long long kNoAllocMaxEntries = kNoAllocScratchDoubles / 2;  // per buffer: padded x and y
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
+
+std::mutex g_noalloc_mutex;
+std::vector<double*> g_noalloc_ptr;  // per device ordinal, filled on the first call on that device
+
+double* noalloc_scratch(std::string& why) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    why = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if ((int)g_noalloc_ptr.size() <= dev) g_noalloc_ptr.resize(dev + 1, nullptr);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) {
+      why = std::string("cudaGetSymbolAddress of the static scratch: ") + cudaGetErrorString(e);
+      return nullptr;
+    }
+    g_noalloc_ptr[dev] = (double*)p;
+  }
+  return g_noalloc_ptr[dev];
+}
+
+template <int K>
+void apply_noalloc_k(amg_hierarchy* h, const double* x, double* y, int nrhs, double* xs, double* ys,
+                     cudaStream_t s) {
+  const long long N = h->N;
+  k_pack<double, double, K><<<grid_for(N * K), kBlock, 0, s>>>(N, x, nrhs, nrhs, xs);
+  ++h->launches;
+  EMIN_CUDA(cudaGetLastError());
+  EMIN_CUDA(apply_finest_f64(h->v64, xs, false, nullptr, ys, K, s));
+  ++h->launches;
+  k_unpack<double, double, K><<<grid_for(N * nrhs), kBlock, 0, s>>>(N, ys, nrhs, y, nrhs);
+  ++h->launches;
+  EMIN_CUDA(cudaGetLastError());
+}
+
 }  // namespace
 
 extern "C" {
+
+amg_status amg_apply_noalloc(amg_handle h, const double* x, double* y, int nrhs, void* stream) {
+  if (!h || !x || !y) return fail(AMG_ERR_ARG, "amg_apply_noalloc: null argument");
+  if (!h->v64) return fail(AMG_ERR_ARG, "amg_apply_noalloc: hierarchy was built with host_only");
+  if (nrhs < 1 || nrhs > 32) return fail(AMG_ERR_ARG, "amg_apply_noalloc: nrhs must be in 1..32");
+  const int K = round_k(nrhs);
+  if ((long long)h->N * K > kNoAllocMaxEntries)
+    return fail(AMG_ERR_ARG, "amg_apply_noalloc: N * K = " + std::to_string((long long)h->N * K) +
+                                 " exceeds the static scratch of " + std::to_string(kNoAllocMaxEntries) +
+                                 " doubles per operand (K = nrhs rounded up to a power of two)");
+  std::string why;
+  double* scratch = noalloc_scratch(why);
+  if (!scratch) return fail(AMG_ERR_CUDA, "amg_apply_noalloc: " + why);
+  double* xs = scratch;
+  double* ys = scratch + kNoAllocMaxEntries;
+  cudaStream_t s = (cudaStream_t)stream;
+  try {
+    switch (K) {
+      case 1: apply_noalloc_k<1>(h, x, y, nrhs, xs, ys, s); break;
+      case 2: apply_noalloc_k<2>(h, x, y, nrhs, xs, ys, s); break;
+      case 4: apply_noalloc_k<4>(h, x, y, nrhs, xs, ys, s); break;
+      case 8: apply_noalloc_k<8>(h, x, y, nrhs, xs, ys, s); break;
+      case 16: apply_noalloc_k<16>(h, x, y, nrhs, xs, ys, s); break;
+      case 32: apply_noalloc_k<32>(h, x, y, nrhs, xs, ys, s); break;
+    }
+  } catch (const std::exception& e) {
+    return fail(AMG_ERR_CUDA, std::string("amg_apply_noalloc: ") + e.what());
+  }
+  return AMG_OK;
+}
 
 void amg_params_default(amg_params* p) {
   if (!p) return;

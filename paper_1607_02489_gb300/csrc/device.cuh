@@ -18,6 +18,8 @@ namespace emin {
 
 constexpr int kBlock = 256;
 constexpr int kGsBlock = 512;
+constexpr int kGsPipeBlock = 512;
+constexpr int kMaxColors = 255;  // colors of a Schur graph the pipelined kernel accepts
 
 template <typename T>
 struct DCsr {
@@ -47,14 +49,33 @@ __device__ __forceinline__ long long gtid() { return (long long)blockIdx.x * blo
 
 inline unsigned grid_for(long long items) { return (unsigned)((items + kBlock - 1) / kBlock); }
 
-// Lanes per row for K right-hand sides on small (latency-bound) levels: G lanes
-// split the stored entries, K*G <= 32.  Large levels use G = 1.
+// Row mapping.  A row is handled by (K/V)*G threads: each takes V consecutive
+// right-hand sides (one 16-byte vector load per matrix entry on large levels)
+// and G lanes split the row's stored entries (small, latency-bound levels),
+// combining their partial sums with warp shuffles.  Vector indices are 32-bit
+// (the hierarchy checks N * K < 2^31 at creation).
 template <int K>
 struct RowLanes {
   static constexpr int G = K >= 32 ? 1 : (32 / K < 4 ? 32 / K : 4);
   static constexpr int W = K * G;
 };
-constexpr long long kSmallLevelItems = 65536;  // rows * K below which a level uses G > 1
+// Below this many (row, rhs) pairs a level is not wide enough for one thread per
+// V right-hand sides to hide latency: it uses G > 1 lanes per row and V = 1.
+constexpr long long kSmallLevelItems = 1LL << 20;
+
+template <typename T, int K>
+struct VecWidth {  // right-hand sides per thread on large levels: 16 bytes, at most K
+  static constexpr int V = (int)(16 / sizeof(T)) < K ? (int)(16 / sizeof(T)) : K;
+};
+
+template <int K, int G, int V>
+struct RowMap {
+  static constexpr int KV = K / V;
+  static constexpr int W = KV * G;
+  unsigned row, k0, lane;
+  __device__ __forceinline__ RowMap(long long t)
+      : row((unsigned)(t / W)), k0((unsigned)(t % KV) * V), lane((unsigned)((t / KV) % G)) {}
+};
 
 // Mask of the W-lane group (aligned within the warp) of the calling thread.
 template <int W>
@@ -69,71 +90,138 @@ __device__ __forceinline__ T group_sum(T v, unsigned mask) {
   return v;
 }
 
-// Decomposition of a flat thread index into (row, rhs, lane) for G lanes per row.
-template <int K, int G>
-struct RowThread {
-  int row, k, lane;
-  __device__ __forceinline__ RowThread(long long t) : row((int)(t / (K * G))), k((int)(t % K)), lane((int)((t / K) % G)) {}
-};
+// V consecutive values at p (aligned to V values) into / out of registers.
+template <typename T, int V>
+__device__ __forceinline__ void vld(T (&r)[V], const T* __restrict__ p) {
+  if constexpr (sizeof(T) == 4 && V == 4) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    r[0] = q.x; r[1] = q.y; r[2] = q.z; r[3] = q.w;
+  } else if constexpr (sizeof(T) == 4 && V == 2) {
+    const float2 q = *reinterpret_cast<const float2*>(p);
+    r[0] = q.x; r[1] = q.y;
+  } else if constexpr (sizeof(T) == 8 && V == 2) {
+    const double2 q = *reinterpret_cast<const double2*>(p);
+    r[0] = q.x; r[1] = q.y;
+  } else {
+#pragma unroll
+    for (int u = 0; u < V; ++u) r[u] = p[u];
+  }
+}
+template <typename T, int V>
+__device__ __forceinline__ void vst(T* __restrict__ p, const T (&r)[V]) {
+  if constexpr (sizeof(T) == 4 && V == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(r[0], r[1], r[2], r[3]);
+  } else if constexpr (sizeof(T) == 4 && V == 2) {
+    *reinterpret_cast<float2*>(p) = make_float2(r[0], r[1]);
+  } else if constexpr (sizeof(T) == 8 && V == 2) {
+    *reinterpret_cast<double2*>(p) = make_double2(r[0], r[1]);
+  } else {
+#pragma unroll
+    for (int u = 0; u < V; ++u) p[u] = r[u];
+  }
+}
 
 // y = x + w .* (b_u - A u - Bt p) on velocity rows; with zero_x, y = w .* b_u.
 // (Braess-Sarazin step, first half: the Jacobi-like velocity predictor.)
-template <typename T, int K, int G>
+template <typename T, int K, int G, int V>
 __global__ void __launch_bounds__(kBlock) k_bs_velocity(LevelView<T> L, const T* __restrict__ b,
                                                         const T* __restrict__ x, T* __restrict__ y, int zero_x) {
-  constexpr int W = K * G;
-  const RowThread<K, G> q(gtid());
-  const int i = q.row, k = q.k;
-  if (i >= L.n_v) return;
-  const size_t nuK = (size_t)L.dim * L.n_v * K;
-  T acc[3] = {T(0), T(0), T(0)};
+  using M = RowMap<K, G, V>;
+  const M q(gtid());
+  const unsigned i = q.row, k0 = q.k0;
+  if (i >= (unsigned)L.n_v) return;
+  const unsigned nvK = (unsigned)L.n_v * K, nuK = (unsigned)L.dim * nvK;
+  T acc[3][V];
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int u = 0; u < V; ++u) acc[c][u] = T(0);
   if (!zero_x) {
     for (int e = L.A.rp[i] + q.lane; e < L.A.rp[i + 1]; e += G) {
       const T a = L.A.v[e];
-      const size_t j = (size_t)L.A.ci[e];
+      const unsigned j = (unsigned)L.A.ci[e] * K + k0;
 #pragma unroll
       for (int c = 0; c < 3; ++c)
-        if (c < L.dim) acc[c] += a * x[((size_t)c * L.n_v + j) * K + k];
+        if (c < L.dim) {
+          T xv[V];
+          vld<T, V>(xv, x + c * nvK + j);
+#pragma unroll
+          for (int u = 0; u < V; ++u) acc[c][u] += a * xv[u];
+        }
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c)
       if (c < L.dim) {
-        const int r = c * L.n_v + i;
-        for (int e = L.Bt.rp[r] + q.lane; e < L.Bt.rp[r + 1]; e += G) acc[c] += L.Bt.v[e] * x[nuK + (size_t)L.Bt.ci[e] * K + k];
-      }
-    const unsigned mask = group_mask<W>();
+        const unsigned r = c * L.n_v + i;
+        for (int e = L.Bt.rp[r] + q.lane; e < L.Bt.rp[r + 1]; e += G) {
+          const T bv = L.Bt.v[e];
+          T xv[V];
+          vld<T, V>(xv, x + nuK + (unsigned)L.Bt.ci[e] * K + k0);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) acc[c] = group_sum<K, G>(acc[c], mask);
+          for (int u = 0; u < V; ++u) acc[c][u] += bv * xv[u];
+        }
+      }
+    if constexpr (G > 1) {
+      const unsigned mask = group_mask<M::W>();
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int u = 0; u < V; ++u) acc[c][u] = group_sum<M::KV, G>(acc[c][u], mask);
+    }
   }
   if (q.lane != 0) return;
   const T wi = L.w[i];
 #pragma unroll
   for (int c = 0; c < 3; ++c)
     if (c < L.dim) {
-      const size_t o = ((size_t)c * L.n_v + i) * K + k;
-      y[o] = (zero_x ? T(0) : x[o]) + wi * (b[o] - acc[c]);
+      const unsigned o = c * nvK + i * K + k0;
+      T bv[V], xv[V], out[V];
+      vld<T, V>(bv, b + o);
+      if (!zero_x) vld<T, V>(xv, x + o);
+#pragma unroll
+      for (int u = 0; u < V; ++u) out[u] = (zero_x ? T(0) : xv[u]) + wi * (bv[u] - acc[c][u]);
+      vst<T, V>(y + o, out);
     }
 }
 
 // Schur right-hand side g = c (B y - b_p) (= B D^-1 r_u - c r_p); pinned row g = r_p.
-template <typename T, int K, int G>
+template <typename T, int K, int G, int V>
 __global__ void __launch_bounds__(kBlock) k_schur_rhs(LevelView<T> L, const T* __restrict__ b,
                                                       const T* __restrict__ x, const T* __restrict__ y,
                                                       T* __restrict__ g, T cfac, int zero_x) {
-  constexpr int W = K * G;
-  const RowThread<K, G> q(gtid());
-  const int i = q.row, k = q.k;
-  if (i >= L.n_p) return;
-  const size_t nuK = (size_t)L.dim * L.n_v * K;
-  T acc = T(0);
-  for (int e = L.B.rp[i] + q.lane; e < L.B.rp[i + 1]; e += G) acc += L.B.v[e] * y[(size_t)L.B.ci[e] * K + k];
-  acc = group_sum<K, G>(acc, group_mask<W>());
+  using M = RowMap<K, G, V>;
+  const M q(gtid());
+  const unsigned i = q.row, k0 = q.k0;
+  if (i >= (unsigned)L.n_p) return;
+  const unsigned nuK = (unsigned)L.dim * L.n_v * K;
+  T acc[V];
+#pragma unroll
+  for (int u = 0; u < V; ++u) acc[u] = T(0);
+  for (int e = L.B.rp[i] + q.lane; e < L.B.rp[i + 1]; e += G) {
+    const T bv = L.B.v[e];
+    T yv[V];
+    vld<T, V>(yv, y + (unsigned)L.B.ci[e] * K + k0);
+#pragma unroll
+    for (int u = 0; u < V; ++u) acc[u] += bv * yv[u];
+  }
+  if constexpr (G > 1) {
+    const unsigned mask = group_mask<M::W>();
+#pragma unroll
+    for (int u = 0; u < V; ++u) acc[u] = group_sum<M::KV, G>(acc[u], mask);
+  }
   if (q.lane != 0) return;
-  const T bp = b[nuK + (size_t)i * K + k];
-  if (i == L.pinned)
-    g[(size_t)i * K + k] = bp - (zero_x ? T(0) : x[nuK + (size_t)i * K + k]);
-  else
-    g[(size_t)i * K + k] = cfac * (acc - bp);
+  T bp[V], out[V];
+  vld<T, V>(bp, b + nuK + i * K + k0);
+  if ((int)i == L.pinned) {
+    T xp[V];
+    if (!zero_x) vld<T, V>(xp, x + nuK + i * K + k0);
+#pragma unroll
+    for (int u = 0; u < V; ++u) out[u] = bp[u] - (zero_x ? T(0) : xp[u]);
+  } else {
+#pragma unroll
+    for (int u = 0; u < V; ++u) out[u] = cfac * (acc[u] - bp[u]);
+  }
+  vst<T, V>(g + i * K + k0, out);
 }
 
 // Bounded grid barrier for the cooperative Gauss-Seidel launch.  Every waiting
@@ -326,7 +414,7 @@ __device__ __forceinline__ void st_release(int* p, int v) {
 }
 
 template <typename T, int K, int G>
-__global__ void __launch_bounds__(kGsBlock) k_gs_pipe(LevelView<T> L, const T* __restrict__ g, T* dp, GsStrips P,
+__global__ void __launch_bounds__(kGsPipeBlock) k_gs_pipe(LevelView<T> L, const T* __restrict__ g, T* dp, GsStrips P,
                                                       const int* __restrict__ ci_rel, int* done, int* err) {
   static_assert(K * G <= 32, "a row group must fit in a warp");
   extern __shared__ __align__(16) unsigned char smem[];
@@ -338,6 +426,7 @@ __global__ void __launch_bounds__(kGsBlock) k_gs_pipe(LevelView<T> L, const T* _
   int* s_perm = s_rp + P.T + 1;
   int* s_ci = s_perm + P.T;
   __shared__ int s_fail;
+  __shared__ int s_so[kMaxColors + 1];  // this strip's color offsets (sorted rows)
   constexpr int kGroup = K * G;
   const int k = threadIdx.x % K;
   const int lane = (threadIdx.x / K) % G;
@@ -347,8 +436,10 @@ __global__ void __launch_bounds__(kGsBlock) k_gs_pipe(LevelView<T> L, const T* _
   const int n_p = L.n_p;
   const int r_lo = s * P.T, r_hi = min(r_lo + P.T, n_p);
   const int h_lo = max(0, r_lo - P.T), h_hi = min(n_p, r_hi + P.T);
-  const int* so = P.soff + (size_t)s * (P.ncol + 1);
-  const int q0 = so[0], q1 = so[P.ncol];
+  const int* so_g = P.soff + (size_t)s * (P.ncol + 1);
+  for (int t = threadIdx.x; t <= P.ncol; t += blockDim.x) s_so[t] = so_g[t];
+  const int* so = s_so;
+  const int q0 = so_g[0], q1 = so_g[P.ncol];
   const int e0 = L.S.rp[q0], e1 = L.S.rp[q1];
   // stage the strip once
   if (threadIdx.x == 0) s_fail = 0;
@@ -394,24 +485,30 @@ __global__ void __launch_bounds__(kGsBlock) k_gs_pipe(LevelView<T> L, const T* _
       for (int t = threadIdx.x; t < (rb - ra) * kGroup; t += blockDim.x) {
         const int r = ra + t / kGroup;
         const int ea = s_rp[r - q0], eb = s_rp[r - q0 + 1];
-        T a0 = T(0), a1 = T(0);
+        T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
         int e = ea + lane;
         if (P.stage == 2) {
-          for (; e + G < eb; e += 2 * G) {
-            const int c0 = s_ci[e - e0], c1 = s_ci[e - e0 + G];
-            a0 += s_v[e - e0] * s_dp[(size_t)c0 * K + k];
-            a1 += s_v[e - e0 + G] * s_dp[(size_t)c1 * K + k];
+          const T* sv = s_v - e0;
+          const int* sc = s_ci - e0;
+          for (; e + 3 * G < eb; e += 4 * G) {
+            const int c0 = sc[e], c1 = sc[e + G], c2 = sc[e + 2 * G], c3 = sc[e + 3 * G];
+            a0 += sv[e] * s_dp[c0 * K + k];
+            a1 += sv[e + G] * s_dp[c1 * K + k];
+            a2 += sv[e + 2 * G] * s_dp[c2 * K + k];
+            a3 += sv[e + 3 * G] * s_dp[c3 * K + k];
           }
-          if (e < eb) a0 += s_v[e - e0] * s_dp[(size_t)s_ci[e - e0] * K + k];
+          for (; e < eb; e += G) a0 += sv[e] * s_dp[sc[e] * K + k];
         } else {
-          for (; e + G < eb; e += 2 * G) {
-            const int c0 = ci_rel[e], c1 = ci_rel[e + G];
-            a0 += L.S.v[e] * s_dp[(size_t)c0 * K + k];
-            a1 += L.S.v[e + G] * s_dp[(size_t)c1 * K + k];
+          for (; e + 3 * G < eb; e += 4 * G) {
+            const int c0 = ci_rel[e], c1 = ci_rel[e + G], c2 = ci_rel[e + 2 * G], c3 = ci_rel[e + 3 * G];
+            a0 += L.S.v[e] * s_dp[c0 * K + k];
+            a1 += L.S.v[e + G] * s_dp[c1 * K + k];
+            a2 += L.S.v[e + 2 * G] * s_dp[c2 * K + k];
+            a3 += L.S.v[e + 3 * G] * s_dp[c3 * K + k];
           }
-          if (e < eb) a0 += L.S.v[e] * s_dp[(size_t)ci_rel[e] * K + k];
+          for (; e < eb; e += G) a0 += L.S.v[e] * s_dp[ci_rel[e] * K + k];
         }
-        const T acc = group_sum<K, G>(a0 + a1, mask);
+        const T acc = group_sum<K, G>((a0 + a1) + (a2 + a3), mask);
         if (lane == 0) {
           const int i = s_perm[r - q0];
           s_dp[(size_t)(i - h_lo) * K + k] = (s_g[(size_t)(i - r_lo) * K + k] - acc) * s_dinv[r - q0];
@@ -429,147 +526,347 @@ __global__ void __launch_bounds__(kGsBlock) k_gs_pipe(LevelView<T> L, const T* _
   }
 }
 
-// u = y - w .* (Bt dp), p = p + dp (p = dp with zero_x): the velocity/pressure update.
+// Single-block Gauss-Seidel for a small level, same ordering: the whole level's
+// S, g, 1/S_ii and dp sit in shared memory and the (parity, color) groups run one
+// after another separated by __syncthreads, with no inter-block waits.
+// plist holds the sorted rows of each (parity, color) group, poff its offsets.
 template <typename T, int K, int G>
+__global__ void __launch_bounds__(kGsBlock) k_gs_level(LevelView<T> L, const T* __restrict__ g, T* dp,
+                                                       const int* __restrict__ plist, const int* __restrict__ poff,
+                                                       int ncol, int iters) {
+  static_assert(K * G <= 32, "a row group must fit in a warp");
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int n_p = L.n_p;
+  const int nnz = L.S.rp[n_p];
+  T* s_dp = reinterpret_cast<T*>(smem);
+  T* s_g = s_dp + (size_t)n_p * K;
+  T* s_dinv = s_g + (size_t)n_p * K;
+  T* s_v = s_dinv + n_p;
+  int* s_rp = reinterpret_cast<int*>(s_v + nnz);
+  int* s_ci = s_rp + n_p + 1;
+  int* s_perm = s_ci + nnz;
+  int* s_plist = s_perm + n_p;
+  int* s_poff = s_plist + n_p;
+  constexpr int kGroup = K * G;
+  const int k = threadIdx.x % K;
+  const int lane = (threadIdx.x / K) % G;
+  const unsigned mask = group_mask<kGroup>();
+  for (int t = threadIdx.x; t < n_p * K; t += blockDim.x) s_dp[t] = T(0);
+  stage_copy<false>(s_g, g, n_p * K);
+  stage_copy<false>(s_dinv, L.S_dinv, n_p);
+  stage_copy<false>(s_v, L.S.v, nnz);
+  stage_copy<false>(s_rp, L.S.rp, n_p + 1);
+  stage_copy<false>(s_ci, L.S.ci, nnz);
+  stage_copy<false>(s_perm, L.S_perm, n_p);
+  stage_copy<false>(s_plist, plist, n_p);
+  stage_copy<false>(s_poff, poff, 2 * ncol + 1);
+  cp_async_wait_all();
+  __syncthreads();
+  for (int it = 0; it < iters; ++it)
+    for (int grp = 0; grp < 2 * ncol; ++grp) {
+      const int a = s_poff[grp], b = s_poff[grp + 1];
+      for (int t = threadIdx.x; t < (b - a) * kGroup; t += blockDim.x) {
+        const int r = s_plist[a + t / kGroup];
+        const int ea = s_rp[r], eb = s_rp[r + 1];
+        T a0 = T(0), a1 = T(0);
+        int e = ea + lane;
+        for (; e + G < eb; e += 2 * G) {
+          a0 += s_v[e] * s_dp[(size_t)s_ci[e] * K + k];
+          a1 += s_v[e + G] * s_dp[(size_t)s_ci[e + G] * K + k];
+        }
+        if (e < eb) a0 += s_v[e] * s_dp[(size_t)s_ci[e] * K + k];
+        const T acc = group_sum<K, G>(a0 + a1, mask);
+        if (lane == 0) {
+          const int i = s_perm[r];
+          s_dp[(size_t)i * K + k] = (s_g[(size_t)i * K + k] - acc) * s_dinv[r];
+        }
+      }
+      __syncthreads();
+    }
+  for (int t = threadIdx.x; t < n_p * K; t += blockDim.x) dp[t] = s_dp[t];
+}
+
+// u = y - w .* (Bt dp), p = p + dp (p = dp with zero_x): the velocity/pressure update.
+template <typename T, int K, int G, int V>
 __global__ void __launch_bounds__(kBlock) k_bs_update(LevelView<T> L, const T* __restrict__ y,
                                                       const T* __restrict__ dp, T* __restrict__ x, int zero_x) {
-  constexpr int W = K * G;
-  const RowThread<K, G> q(gtid());
-  const int i = q.row, k = q.k;
-  const size_t nuK = (size_t)L.dim * L.n_v * K;
-  if (i < L.n_v) {
-    T sum[3] = {T(0), T(0), T(0)};
+  using M = RowMap<K, G, V>;
+  const M q(gtid());
+  const unsigned i = q.row, k0 = q.k0;
+  const unsigned nvK = (unsigned)L.n_v * K, nuK = (unsigned)L.dim * nvK;
+  if (i < (unsigned)L.n_v) {
+    T sum[3][V];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int u = 0; u < V; ++u) sum[c][u] = T(0);
 #pragma unroll
     for (int c = 0; c < 3; ++c)
       if (c < L.dim) {
-        const int r = c * L.n_v + i;
-        for (int e = L.Bt.rp[r] + q.lane; e < L.Bt.rp[r + 1]; e += G) sum[c] += L.Bt.v[e] * dp[(size_t)L.Bt.ci[e] * K + k];
-      }
-    const unsigned mask = group_mask<W>();
+        const unsigned r = c * L.n_v + i;
+        for (int e = L.Bt.rp[r] + q.lane; e < L.Bt.rp[r + 1]; e += G) {
+          const T bv = L.Bt.v[e];
+          T dv[V];
+          vld<T, V>(dv, dp + (unsigned)L.Bt.ci[e] * K + k0);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) sum[c] = group_sum<K, G>(sum[c], mask);
+          for (int u = 0; u < V; ++u) sum[c][u] += bv * dv[u];
+        }
+      }
+    if constexpr (G > 1) {
+      const unsigned mask = group_mask<M::W>();
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int u = 0; u < V; ++u) sum[c][u] = group_sum<M::KV, G>(sum[c][u], mask);
+    }
     if (q.lane != 0) return;
     const T wi = L.w[i];
 #pragma unroll
     for (int c = 0; c < 3; ++c)
       if (c < L.dim) {
-        const size_t o = ((size_t)c * L.n_v + i) * K + k;
-        x[o] = y[o] - wi * sum[c];
+        const unsigned o = c * nvK + i * K + k0;
+        T yv[V], out[V];
+        vld<T, V>(yv, y + o);
+#pragma unroll
+        for (int u = 0; u < V; ++u) out[u] = yv[u] - wi * sum[c][u];
+        vst<T, V>(x + o, out);
       }
-  } else if (i < L.n_v + L.n_p && q.lane == 0) {
-    const int p = i - L.n_v;
-    const size_t o = nuK + (size_t)p * K + k;
-    x[o] = (zero_x ? T(0) : x[o]) + dp[(size_t)p * K + k];
+  } else if (i < (unsigned)(L.n_v + L.n_p) && q.lane == 0) {
+    const unsigned p = i - L.n_v;
+    const unsigned o = nuK + p * K + k0;
+    T xv[V], dv[V], out[V];
+    vld<T, V>(dv, dp + p * K + k0);
+    if (!zero_x) vld<T, V>(xv, x + o);
+#pragma unroll
+    for (int u = 0; u < V; ++u) out[u] = (zero_x ? T(0) : xv[u]) + dv[u];
+    vst<T, V>(x + o, out);
   }
 }
 
 // out = b - A x (HAS_B) or out = A x, for the whole block matrix [I(x)A, Bt; B, C].
-template <typename T, typename TX, typename TO, int K, int G, bool HAS_B>
+template <typename T, int K, int G, int V, bool HAS_B>
 __global__ void __launch_bounds__(kBlock) k_block_spmv(LevelView<T> L, const T* __restrict__ b,
-                                                       const TX* __restrict__ x, TO* __restrict__ out) {
-  constexpr int W = K * G;
-  const RowThread<K, G> q(gtid());
-  const int i = q.row, k = q.k;
-  const size_t nuK = (size_t)L.dim * L.n_v * K;
-  const unsigned mask = group_mask<W>();
-  if (i < L.n_v) {
-    T acc[3] = {T(0), T(0), T(0)};
+                                                       const T* __restrict__ x, T* __restrict__ out) {
+  using M = RowMap<K, G, V>;
+  const M q(gtid());
+  const unsigned i = q.row, k0 = q.k0;
+  const unsigned nvK = (unsigned)L.n_v * K, nuK = (unsigned)L.dim * nvK;
+  const unsigned mask = group_mask<M::W>();
+  if (i < (unsigned)L.n_v) {
+    T acc[3][V];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int u = 0; u < V; ++u) acc[c][u] = T(0);
     for (int e = L.A.rp[i] + q.lane; e < L.A.rp[i + 1]; e += G) {
       const T a = L.A.v[e];
-      const size_t j = (size_t)L.A.ci[e];
+      const unsigned j = (unsigned)L.A.ci[e] * K + k0;
 #pragma unroll
       for (int c = 0; c < 3; ++c)
-        if (c < L.dim) acc[c] += a * (T)x[((size_t)c * L.n_v + j) * K + k];
+        if (c < L.dim) {
+          T xv[V];
+          vld<T, V>(xv, x + c * nvK + j);
+#pragma unroll
+          for (int u = 0; u < V; ++u) acc[c][u] += a * xv[u];
+        }
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c)
       if (c < L.dim) {
-        const int r = c * L.n_v + i;
-        for (int e = L.Bt.rp[r] + q.lane; e < L.Bt.rp[r + 1]; e += G) acc[c] += L.Bt.v[e] * (T)x[nuK + (size_t)L.Bt.ci[e] * K + k];
-      }
+        const unsigned r = c * L.n_v + i;
+        for (int e = L.Bt.rp[r] + q.lane; e < L.Bt.rp[r + 1]; e += G) {
+          const T bv = L.Bt.v[e];
+          T xv[V];
+          vld<T, V>(xv, x + nuK + (unsigned)L.Bt.ci[e] * K + k0);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) acc[c] = group_sum<K, G>(acc[c], mask);
+          for (int u = 0; u < V; ++u) acc[c][u] += bv * xv[u];
+        }
+      }
+    if constexpr (G > 1) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int u = 0; u < V; ++u) acc[c][u] = group_sum<M::KV, G>(acc[c][u], mask);
+    }
     if (q.lane != 0) return;
 #pragma unroll
     for (int c = 0; c < 3; ++c)
       if (c < L.dim) {
-        const size_t o = ((size_t)c * L.n_v + i) * K + k;
-        out[o] = (TO)(HAS_B ? b[o] - acc[c] : acc[c]);
+        const unsigned o = c * nvK + i * K + k0;
+        T r[V];
+        if (HAS_B) {
+          T bv[V];
+          vld<T, V>(bv, b + o);
+#pragma unroll
+          for (int u = 0; u < V; ++u) r[u] = bv[u] - acc[c][u];
+        } else {
+#pragma unroll
+          for (int u = 0; u < V; ++u) r[u] = acc[c][u];
+        }
+        vst<T, V>(out + o, r);
       }
-  } else if (i < L.n_v + L.n_p) {
-    const int p = i - L.n_v;
-    T acc = T(0);
-    for (int e = L.B.rp[p] + q.lane; e < L.B.rp[p + 1]; e += G) acc += L.B.v[e] * (T)x[(size_t)L.B.ci[e] * K + k];
-    acc = group_sum<K, G>(acc, mask);
+  } else if (i < (unsigned)(L.n_v + L.n_p)) {
+    const unsigned p = i - L.n_v;
+    T acc[V];
+#pragma unroll
+    for (int u = 0; u < V; ++u) acc[u] = T(0);
+    for (int e = L.B.rp[p] + q.lane; e < L.B.rp[p + 1]; e += G) {
+      const T bv = L.B.v[e];
+      T xv[V];
+      vld<T, V>(xv, x + (unsigned)L.B.ci[e] * K + k0);
+#pragma unroll
+      for (int u = 0; u < V; ++u) acc[u] += bv * xv[u];
+    }
+    if constexpr (G > 1) {
+#pragma unroll
+      for (int u = 0; u < V; ++u) acc[u] = group_sum<M::KV, G>(acc[u], mask);
+    }
     if (q.lane != 0) return;
-    const size_t o = nuK + (size_t)p * K + k;
-    if (p == L.pinned) acc += (T)x[o];
-    out[o] = (TO)(HAS_B ? b[o] - acc : acc);
+    const unsigned o = nuK + p * K + k0;
+    if ((int)p == L.pinned) {
+      T xv[V];
+      vld<T, V>(xv, x + o);
+#pragma unroll
+      for (int u = 0; u < V; ++u) acc[u] += xv[u];
+    }
+    T r[V];
+    if (HAS_B) {
+      T bv[V];
+      vld<T, V>(bv, b + o);
+#pragma unroll
+      for (int u = 0; u < V; ++u) r[u] = bv[u] - acc[u];
+    } else {
+#pragma unroll
+      for (int u = 0; u < V; ++u) r[u] = acc[u];
+    }
+    vst<T, V>(out + o, r);
   }
 }
 
 // b_c = R r: velocity rows by R (each component), pressure rows by Rp.
-template <typename T, int K, int G>
+template <typename T, int K, int G, int V>
 __global__ void __launch_bounds__(kBlock) k_restrict(LevelView<T> L, const T* __restrict__ r, T* __restrict__ bc) {
-  constexpr int W = K * G;
-  const RowThread<K, G> q(gtid());
-  const int I = q.row, k = q.k;
-  const unsigned mask = group_mask<W>();
-  if (I < L.n_vc) {
-    T s[3] = {T(0), T(0), T(0)};
+  using M = RowMap<K, G, V>;
+  const M q(gtid());
+  const unsigned I = q.row, k0 = q.k0;
+  const unsigned mask = group_mask<M::W>();
+  const unsigned nvK = (unsigned)L.n_v * K;
+  if (I < (unsigned)L.n_vc) {
+    T s[3][V];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int u = 0; u < V; ++u) s[c][u] = T(0);
     for (int e = L.R.rp[I] + q.lane; e < L.R.rp[I + 1]; e += G) {
       const T v = L.R.v[e];
-      const size_t j = (size_t)L.R.ci[e];
+      const unsigned j = (unsigned)L.R.ci[e] * K + k0;
 #pragma unroll
       for (int c = 0; c < 3; ++c)
-        if (c < L.dim) s[c] += v * r[((size_t)c * L.n_v + j) * K + k];
-    }
+        if (c < L.dim) {
+          T rv[V];
+          vld<T, V>(rv, r + c * nvK + j);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) s[c] = group_sum<K, G>(s[c], mask);
+          for (int u = 0; u < V; ++u) s[c][u] += v * rv[u];
+        }
+    }
+    if constexpr (G > 1) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int u = 0; u < V; ++u) s[c][u] = group_sum<M::KV, G>(s[c][u], mask);
+    }
     if (q.lane != 0) return;
 #pragma unroll
     for (int c = 0; c < 3; ++c)
-      if (c < L.dim) bc[((size_t)c * L.n_vc + I) * K + k] = s[c];
-  } else if (I < L.n_vc + L.n_pc) {
-    const int p = I - L.n_vc;
-    const size_t nuK = (size_t)L.dim * L.n_v * K;
-    T s = T(0);
-    for (int e = L.Rp.rp[p] + q.lane; e < L.Rp.rp[p + 1]; e += G) s += L.Rp.v[e] * r[nuK + (size_t)L.Rp.ci[e] * K + k];
-    s = group_sum<K, G>(s, mask);
+      if (c < L.dim) vst<T, V>(bc + ((unsigned)c * L.n_vc + I) * K + k0, s[c]);
+  } else if (I < (unsigned)(L.n_vc + L.n_pc)) {
+    const unsigned p = I - L.n_vc;
+    const unsigned nuK = (unsigned)L.dim * nvK;
+    T s[V];
+#pragma unroll
+    for (int u = 0; u < V; ++u) s[u] = T(0);
+    for (int e = L.Rp.rp[p] + q.lane; e < L.Rp.rp[p + 1]; e += G) {
+      const T v = L.Rp.v[e];
+      T rv[V];
+      vld<T, V>(rv, r + nuK + (unsigned)L.Rp.ci[e] * K + k0);
+#pragma unroll
+      for (int u = 0; u < V; ++u) s[u] += v * rv[u];
+    }
+    if constexpr (G > 1) {
+#pragma unroll
+      for (int u = 0; u < V; ++u) s[u] = group_sum<M::KV, G>(s[u], mask);
+    }
     if (q.lane != 0) return;
-    bc[((size_t)L.dim * L.n_vc + p) * K + k] = s;
+    vst<T, V>(bc + ((unsigned)L.dim * L.n_vc + p) * K + k0, s);
   }
 }
 
 // x += P x_c: velocity rows by P (each component), pressure rows by Pp.
-template <typename T, int K, int G>
+template <typename T, int K, int G, int V>
 __global__ void __launch_bounds__(kBlock) k_prolong(LevelView<T> L, const T* __restrict__ xc, T* __restrict__ x) {
-  constexpr int W = K * G;
-  const RowThread<K, G> q(gtid());
-  const int i = q.row, k = q.k;
-  const unsigned mask = group_mask<W>();
-  if (i < L.n_v) {
-    T s[3] = {T(0), T(0), T(0)};
+  using M = RowMap<K, G, V>;
+  const M q(gtid());
+  const unsigned i = q.row, k0 = q.k0;
+  const unsigned mask = group_mask<M::W>();
+  const unsigned ncK = (unsigned)L.n_vc * K;
+  if (i < (unsigned)L.n_v) {
+    T s[3][V];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int u = 0; u < V; ++u) s[c][u] = T(0);
     for (int e = L.P.rp[i] + q.lane; e < L.P.rp[i + 1]; e += G) {
       const T v = L.P.v[e];
-      const size_t j = (size_t)L.P.ci[e];
+      const unsigned j = (unsigned)L.P.ci[e] * K + k0;
 #pragma unroll
       for (int c = 0; c < 3; ++c)
-        if (c < L.dim) s[c] += v * xc[((size_t)c * L.n_vc + j) * K + k];
-    }
+        if (c < L.dim) {
+          T cv[V];
+          vld<T, V>(cv, xc + c * ncK + j);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) s[c] = group_sum<K, G>(s[c], mask);
+          for (int u = 0; u < V; ++u) s[c][u] += v * cv[u];
+        }
+    }
+    if constexpr (G > 1) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int u = 0; u < V; ++u) s[c][u] = group_sum<M::KV, G>(s[c][u], mask);
+    }
     if (q.lane != 0) return;
 #pragma unroll
     for (int c = 0; c < 3; ++c)
-      if (c < L.dim) x[((size_t)c * L.n_v + i) * K + k] += s[c];
-  } else if (i < L.n_v + L.n_p) {
-    const int p = i - L.n_v;
-    T s = T(0);
-    for (int e = L.Pp.rp[p] + q.lane; e < L.Pp.rp[p + 1]; e += G) s += L.Pp.v[e] * xc[((size_t)L.dim * L.n_vc + L.Pp.ci[e]) * K + k];
-    s = group_sum<K, G>(s, mask);
+      if (c < L.dim) {
+        const unsigned o = ((unsigned)c * L.n_v + i) * K + k0;
+        T xv[V];
+        vld<T, V>(xv, x + o);
+#pragma unroll
+        for (int u = 0; u < V; ++u) xv[u] += s[c][u];
+        vst<T, V>(x + o, xv);
+      }
+  } else if (i < (unsigned)(L.n_v + L.n_p)) {
+    const unsigned p = i - L.n_v;
+    T s[V];
+#pragma unroll
+    for (int u = 0; u < V; ++u) s[u] = T(0);
+    for (int e = L.Pp.rp[p] + q.lane; e < L.Pp.rp[p + 1]; e += G) {
+      const T v = L.Pp.v[e];
+      T cv[V];
+      vld<T, V>(cv, xc + (unsigned)L.dim * ncK + (unsigned)L.Pp.ci[e] * K + k0);
+#pragma unroll
+      for (int u = 0; u < V; ++u) s[u] += v * cv[u];
+    }
+    if constexpr (G > 1) {
+#pragma unroll
+      for (int u = 0; u < V; ++u) s[u] = group_sum<M::KV, G>(s[u], mask);
+    }
     if (q.lane != 0) return;
-    x[((size_t)L.dim * L.n_v + p) * K + k] += s;
+    const unsigned o = ((unsigned)L.dim * L.n_v + p) * K + k0;
+    T xv[V];
+    vld<T, V>(xv, x + o);
+#pragma unroll
+    for (int u = 0; u < V; ++u) xv[u] += s[u];
+    vst<T, V>(x + o, xv);
   }
 }
 
@@ -604,57 +901,74 @@ struct FFAcc {
   __device__ __forceinline__ void add_small(float a, float z) { c = fmaf(a, z, c); }
 };
 
-template <int K, int G>
+template <int K, int V>
 __global__ void __launch_bounds__(kBlock) k_block_spmv_ff(FFLevel L, const float* __restrict__ z,
                                                           double* __restrict__ out) {
-  constexpr int W = K * G;
-  const RowThread<K, G> q(gtid());
-  const int i = q.row, k = q.k;
-  const size_t nuK = (size_t)L.dim * L.n_v * K;
-  const unsigned mask = group_mask<W>();
-  if (i < L.n_v) {
-    FFAcc acc[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-    for (int e = L.A.rp[i] + q.lane; e < L.A.rp[i + 1]; e += G) {
+  using M = RowMap<K, 1, V>;
+  const M q(gtid());
+  const unsigned i = q.row, k0 = q.k0;
+  const unsigned nvK = (unsigned)L.n_v * K, nuK = (unsigned)L.dim * nvK;
+  if (i < (unsigned)L.n_v) {
+    FFAcc acc[3][V];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int u = 0; u < V; ++u) acc[c][u] = {0.f, 0.f};
+    for (int e = L.A.rp[i]; e < L.A.rp[i + 1]; ++e) {
       const float h = L.A.hi[e], l = L.A.lo[e];
-      const size_t j = (size_t)L.A.ci[e];
+      const unsigned j = (unsigned)L.A.ci[e] * K + k0;
 #pragma unroll
       for (int c = 0; c < 3; ++c)
         if (c < L.dim) {
-          const float zz = z[((size_t)c * L.n_v + j) * K + k];
-          acc[c].add(h, zz);
-          acc[c].add_small(l, zz);
+          float zv[V];
+          vld<float, V>(zv, z + c * nvK + j);
+#pragma unroll
+          for (int u = 0; u < V; ++u) {
+            acc[c][u].add(h, zv[u]);
+            acc[c][u].add_small(l, zv[u]);
+          }
         }
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c)
       if (c < L.dim) {
-        const int r = c * L.n_v + i;
-        for (int e = L.Bt.rp[r] + q.lane; e < L.Bt.rp[r + 1]; e += G) {
-          const float zz = z[nuK + (size_t)L.Bt.ci[e] * K + k];
-          acc[c].add(L.Bt.hi[e], zz);
-          acc[c].add_small(L.Bt.lo[e], zz);
-        }
-      }
+        const unsigned r = c * L.n_v + i;
+        for (int e = L.Bt.rp[r]; e < L.Bt.rp[r + 1]; ++e) {
+          const float h = L.Bt.hi[e], l = L.Bt.lo[e];
+          float zv[V];
+          vld<float, V>(zv, z + nuK + (unsigned)L.Bt.ci[e] * K + k0);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      double v = (double)acc[c].s + (double)acc[c].c;
-      v = group_sum<K, G>(v, mask);
-      if (q.lane == 0 && c < L.dim) out[((size_t)c * L.n_v + i) * K + k] = v;
+          for (int u = 0; u < V; ++u) {
+            acc[c][u].add(h, zv[u]);
+            acc[c][u].add_small(l, zv[u]);
+          }
+        }
+        const unsigned o = c * nvK + i * K + k0;
+#pragma unroll
+        for (int u = 0; u < V; ++u) out[o + u] = (double)acc[c][u].s + (double)acc[c][u].c;
+      }
+  } else if (i < (unsigned)(L.n_v + L.n_p)) {
+    const unsigned p = i - L.n_v;
+    FFAcc acc[V];
+#pragma unroll
+    for (int u = 0; u < V; ++u) acc[u] = {0.f, 0.f};
+    for (int e = L.B.rp[p]; e < L.B.rp[p + 1]; ++e) {
+      const float h = L.B.hi[e], l = L.B.lo[e];
+      float zv[V];
+      vld<float, V>(zv, z + (unsigned)L.B.ci[e] * K + k0);
+#pragma unroll
+      for (int u = 0; u < V; ++u) {
+        acc[u].add(h, zv[u]);
+        acc[u].add_small(l, zv[u]);
+      }
     }
-  } else if (i < L.n_v + L.n_p) {
-    const int p = i - L.n_v;
-    FFAcc acc = {0.f, 0.f};
-    for (int e = L.B.rp[p] + q.lane; e < L.B.rp[p + 1]; e += G) {
-      const float zz = z[(size_t)L.B.ci[e] * K + k];
-      acc.add(L.B.hi[e], zz);
-      acc.add_small(L.B.lo[e], zz);
+    const unsigned o = nuK + p * K + k0;
+#pragma unroll
+    for (int u = 0; u < V; ++u) {
+      double v = (double)acc[u].s + (double)acc[u].c;
+      if ((int)p == L.pinned) v += (double)z[o + u];
+      out[o + u] = v;
     }
-    double v = (double)acc.s + (double)acc.c;
-    v = group_sum<K, G>(v, mask);
-    if (q.lane != 0) return;
-    const size_t o = nuK + (size_t)p * K + k;
-    if (p == L.pinned) v += (double)z[o];
-    out[o] = v;
   }
 }
 

@@ -38,47 +38,65 @@ int round_k(int nrhs) {
 
 constexpr int kRedBlocks = 608;  // 4 blocks per SM on 152 SMs for the streaming reductions
 
-// part[(blk*nv + i)*K + k] = sum over this block's entries with rhs k of V_i[e] * w[e].
+// part[(blk*nd + i)*K + k] = sum over this block's entries with rhs k of V_i[e] * w[e],
+// for i < nv, plus w[e]^2 at i = nv when self is set (nd = nv + self).  Nothing
+// is done when cond is given and *cond == 0.
 template <int K, typename TV>
-__global__ void __launch_bounds__(kBlock) k_mdot_partial(long long NK, int nv, const TV* __restrict__ V,
-                                                         const double* __restrict__ w, double* __restrict__ part) {
+__global__ void __launch_bounds__(kBlock) k_mdot_partial(long long NK, int nv, int self, const TV* __restrict__ V,
+                                                         const double* __restrict__ w, double* __restrict__ part,
+                                                         const int* __restrict__ cond) {
+  if (cond && *cond == 0) return;
   __shared__ double sm[kBlock / 32][K];
   const int k = threadIdx.x % K;
   const long long stride = (long long)gridDim.x * blockDim.x;
-  for (int i = 0; i < nv; ++i) {
-    const TV* Vi = V + (size_t)i * NK;
+  const int nd = nv + self;
+  for (int i = 0; i < nd; ++i) {
     double acc = 0.0;
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < NK; e += stride)
-      acc += (double)Vi[e] * w[e];
+    if (i < nv) {
+      const TV* Vi = V + (size_t)i * NK;
+      for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < NK; e += stride)
+        acc += (double)Vi[e] * w[e];
+    } else {
+      for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < NK; e += stride) acc += w[e] * w[e];
+    }
 #pragma unroll
     for (int off = 16; off >= K; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
     if ((threadIdx.x & 31) < K) sm[threadIdx.x >> 5][k] = acc;
     __syncthreads();
     if (threadIdx.x < K) {
-      double s = 0.0;
-      for (int wp = 0; wp < kBlock / 32; ++wp) s += sm[wp][threadIdx.x];
-      part[((size_t)blockIdx.x * nv + i) * K + threadIdx.x] = s;
+      double t = 0.0;
+      for (int wp = 0; wp < kBlock / 32; ++wp) t += sm[wp][threadIdx.x];
+      part[((size_t)blockIdx.x * nd + i) * K + threadIdx.x] = t;
     }
     __syncthreads();
   }
 }
 
-// out[t] (+)= sum over blocks of part, t = i*K + k, fixed summation order.
+// out[t] (+)= sum over blocks of part, t = i*K + k: one warp per output, each lane
+// summing a fixed stride of the partials, then a fixed shuffle tree, so the
+// result does not depend on scheduling.
 __global__ void k_reduce_partials(int nblk, int nvK, const double* __restrict__ part, double* __restrict__ out,
-                                  int accumulate, int take_sqrt) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+                                  int accumulate, int take_sqrt, const int* __restrict__ cond) {
+  if (cond && *cond == 0) return;
+  const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (t >= nvK) return;
   double s = 0.0;
-  for (int b = 0; b < nblk; ++b) s += part[(size_t)b * nvK + t];
-  if (take_sqrt) s = sqrt(s);
-  out[t] = accumulate ? out[t] + s : s;
+  for (int b = lane; b < nblk; b += 32) s += part[(size_t)b * nvK + t];
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if (lane == 0) {
+    if (take_sqrt) s = sqrt(s);
+    out[t] = accumulate ? out[t] + s : s;
+  }
 }
 
 // w -= sum_i V_i h_i (per rhs); with nrm_part, also the partial sums of |w|^2.
 template <int K, typename TV>
 __global__ void __launch_bounds__(kBlock) k_maxpy(long long NK, int nv, const TV* __restrict__ V,
                                                   const double* __restrict__ h, double* __restrict__ w,
-                                                  double* __restrict__ nrm_part) {
+                                                  double* __restrict__ nrm_part, const int* __restrict__ cond) {
+  if (cond && *cond == 0) return;
   __shared__ double sm[kBlock / 32][K];
   const int k = threadIdx.x % K;
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -101,14 +119,37 @@ __global__ void __launch_bounds__(kBlock) k_maxpy(long long NK, int nv, const TV
   }
 }
 
-// v = w / nrm for active columns, 0 otherwise.
+// v = w / nrm for active columns, 0 otherwise (one FP64 division per column and
+// block; the elements are multiplied by the reciprocal).
 template <int K>
 __global__ void k_scale(long long NK, const double* __restrict__ w, const double* __restrict__ nrm,
                         const int* __restrict__ active, double* __restrict__ v) {
+  __shared__ double inv[K];
+  if (threadIdx.x < K) {
+    const double n = nrm[threadIdx.x];
+    inv[threadIdx.x] = (active[threadIdx.x] && n > 0.0) ? 1.0 / n : 0.0;
+  }
+  __syncthreads();
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= NK) return;
-  const int k = (int)(e % K);
-  v[e] = (active[k] && nrm[k] > 0.0) ? w[e] / nrm[k] : 0.0;
+  v[e] = w[e] * inv[(int)(e % K)];
+}
+
+// Selective re-orthogonalisation test (Daniel, Gragg, Kaufman and Stewart 1976):
+// after one classical Gram-Schmidt pass, w' is re-orthogonalised when
+// |w'| < |w| / sqrt(2) for some active column.  slot holds |w|^2 on entry and
+// |w'| on exit (the norm used when no second pass runs); *flag = 1 asks for it.
+__global__ void k_reorth_check(int K, double* __restrict__ slot, const double* __restrict__ nrm1,
+                               const int* __restrict__ active, int* __restrict__ flag) {
+  const int k = threadIdx.x;
+  int need = 0;
+  if (k < K) {
+    const double w2 = slot[k], n1 = nrm1[k];
+    need = active[k] && (n1 * n1 < 0.5 * w2);
+    slot[k] = n1;
+  }
+  const int any = __syncthreads_or(need);
+  if (threadIdx.x == 0) *flag = any;
 }
 
 struct GmresState {
@@ -223,6 +264,7 @@ struct amg_hierarchy {
   double *hbuf = nullptr, *part = nullptr, *y = nullptr, *bnorm = nullptr, *rnorm = nullptr;
   GmresState st{};
   int* n_active = nullptr;
+  int* reorth = nullptr;     // device flag: the current Arnoldi step needs a second pass
   int* host_i = nullptr;     // pinned
   double* host_d = nullptr;  // pinned
   void* stage_b = nullptr;   // device copies for amg_fgmres_solve_host
@@ -275,6 +317,7 @@ void ensure_ws(amg_hierarchy* h, int K, int m) {
   h->st.flags = dev_alloc<int>(K, h->ws);
   h->st.resest = dev_alloc<double>(K, h->ws);
   h->n_active = dev_alloc<int>(1, h->ws);
+  h->reorth = dev_alloc<int>(1, h->ws);
   h->ws_K = K;
   h->ws_m = m;
   if (!h->host_i) EMIN_CUDA(cudaMallocHost(&h->host_i, 4 * 64 * sizeof(int)));
@@ -285,8 +328,8 @@ void ensure_ws(amg_hierarchy* h, int K, int m) {
 template <int K>
 void col_norms(amg_hierarchy* h, const double* v, double* out, cudaStream_t s) {
   const long long NK = h->N * K;
-  k_mdot_partial<K, double><<<kRedBlocks, kBlock, 0, s>>>(NK, 1, v, v, h->part); ++h->launches;
-  k_reduce_partials<<<1, 64, 0, s>>>(kRedBlocks, K, h->part, out, 0, 1); ++h->launches;
+  k_mdot_partial<K, double><<<kRedBlocks, kBlock, 0, s>>>(NK, 1, 0, v, v, h->part, nullptr); ++h->launches;
+  k_reduce_partials<<<(K * 32 + 127) / 128, 128, 0, s>>>(kRedBlocks, K, h->part, out, 0, 1, nullptr); ++h->launches;
 }
 
 template <int K, typename TZ>
@@ -343,17 +386,22 @@ amg_status fgmres_k(amg_hierarchy* h, const double* b, double* x, int nrhs, doub
         EMIN_CUDA(apply_finest_f64(h->v64, Z + (size_t)j * NK, false, nullptr, h->w, K, s));
         ++h->launches;
       }
-      // classical Gram-Schmidt with one re-orthogonalisation
+      // classical Gram-Schmidt, re-orthogonalised only when the first pass cancelled
+      // more than half of |w| (k_reorth_check)
       const int nv = j + 1;
-      k_mdot_partial<K, double><<<kRedBlocks, kBlock, 0, s>>>(NK, nv, h->V, h->w, h->part); ++h->launches;
-      k_reduce_partials<<<(nv * K + 127) / 128, 128, 0, s>>>(kRedBlocks, nv * K, h->part, h->hbuf, 0, 0); ++h->launches;
-      k_maxpy<K, double><<<kRedBlocks, kBlock, 0, s>>>(NK, nv, h->V, h->hbuf, h->w, nullptr); ++h->launches;
-      k_mdot_partial<K, double><<<kRedBlocks, kBlock, 0, s>>>(NK, nv, h->V, h->w, h->part); ++h->launches;
-      double* h2 = h->y;  // scratch for the correction coefficients
-      k_reduce_partials<<<(nv * K + 127) / 128, 128, 0, s>>>(kRedBlocks, nv * K, h->part, h2, 0, 0); ++h->launches;
-      k_maxpy<K, double><<<kRedBlocks, kBlock, 0, s>>>(NK, nv, h->V, h2, h->w, h->part); ++h->launches;
-      k_reduce_partials<<<1, 64, 0, s>>>(kRedBlocks, K, h->part, h->hbuf + (size_t)nv * K, 0, 1); ++h->launches;
-      k_reduce_partials<<<(nv * K + 127) / 128, 128, 0, s>>>(1, nv * K, h2, h->hbuf, 1, 0); ++h->launches;
+      double* hn = h->hbuf + (size_t)nv * K;  // |w|^2, then the norm of the new vector
+      double* h2 = h->y;                     // scratch for the correction coefficients
+      k_mdot_partial<K, double><<<kRedBlocks, kBlock, 0, s>>>(NK, nv, 1, h->V, h->w, h->part, nullptr); ++h->launches;
+      k_reduce_partials<<<((nv + 1) * K * 32 + 127) / 128, 128, 0, s>>>(kRedBlocks, (nv + 1) * K, h->part, h->hbuf, 0, 0,
+                                                                         nullptr); ++h->launches;
+      k_maxpy<K, double><<<kRedBlocks, kBlock, 0, s>>>(NK, nv, h->V, h->hbuf, h->w, h->part, nullptr); ++h->launches;
+      k_reduce_partials<<<(K * 32 + 127) / 128, 128, 0, s>>>(kRedBlocks, K, h->part, h->rnorm, 0, 1, nullptr); ++h->launches;
+      k_reorth_check<<<1, 32, 0, s>>>(K, hn, h->rnorm, h->st.active, h->reorth); ++h->launches;
+      k_mdot_partial<K, double><<<kRedBlocks, kBlock, 0, s>>>(NK, nv, 0, h->V, h->w, h->part, h->reorth); ++h->launches;
+      k_reduce_partials<<<(nv * K * 32 + 127) / 128, 128, 0, s>>>(kRedBlocks, nv * K, h->part, h2, 0, 0, h->reorth); ++h->launches;
+      k_maxpy<K, double><<<kRedBlocks, kBlock, 0, s>>>(NK, nv, h->V, h2, h->w, h->part, h->reorth); ++h->launches;
+      k_reduce_partials<<<(K * 32 + 127) / 128, 128, 0, s>>>(kRedBlocks, K, h->part, hn, 0, 1, h->reorth); ++h->launches;
+      k_reduce_partials<<<(nv * K * 32 + 127) / 128, 128, 0, s>>>(1, nv * K, h2, h->hbuf, 1, 0, h->reorth); ++h->launches;
       k_givens<<<1, 32, 0, s>>>(j, restart, K, h->hbuf, h->st, h->bnorm, rtol, h->n_active); ++h->launches;
       EMIN_CUDA(cudaGetLastError());
       EMIN_CUDA(cudaMemcpyAsync(h->host_i, h->n_active, sizeof(int), cudaMemcpyDeviceToHost, s));

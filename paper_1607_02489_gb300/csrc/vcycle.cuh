@@ -57,6 +57,8 @@ class DeviceVCycle : public VCycleIface {
   DeviceVCycle(const std::vector<HostLevel>& levels, double cfac, int gs_iters, int pre, int post, int kmax)
       : c_(cfac), cfac_((T)cfac), gs_iters_(gs_iters), pre_(pre), post_(post), kmax_(kmax) {
     try {
+      if ((long long)levels[0].N() * kmax_ >= (1LL << 31))
+        throw std::runtime_error("N * max_nrhs must stay below 2^31 (32-bit vector indices)");
       for (size_t l = 0; l < levels.size(); ++l) upload_level(levels[l], l + 1 == levels.size());
       for (size_t l = 0; l + 1 < levels.size(); ++l) {
         views_[l].n_vc = levels[l + 1].n_v;
@@ -139,18 +141,19 @@ class DeviceVCycle : public VCycleIface {
       const LevelView<T>& L = views_[l];
       mark_begin(l, kResidual, s);
       if (small_level(l, K))
-        k_block_spmv<T, T, T, K, RowLanes<K>::G, true><<<grid_for((long long)(L.n_v + L.n_p) * RowLanes<K>::W), kBlock, 0, s>>>(
-            L, buf_[l].b, buf_[l].x, buf_[l].r);
+        k_block_spmv<T, K, RowLanes<K>::G, 1, true><<<grid_for((long long)(L.n_v + L.n_p) * RowLanes<K>::W), kBlock, 0,
+                                                    s>>>(L, buf_[l].b, buf_[l].x, buf_[l].r);
       else
-        k_block_spmv<T, T, T, K, 1, true><<<grid_for((long long)(L.n_v + L.n_p) * K), kBlock, 0, s>>>(
-            L, buf_[l].b, buf_[l].x, buf_[l].r);
+        k_block_spmv<T, K, 1, VecWidth<T, K>::V, true><<<grid_for((long long)(L.n_v + L.n_p) * (K / VecWidth<T, K>::V)),
+                                                        kBlock, 0, s>>>(L, buf_[l].b, buf_[l].x, buf_[l].r);
       mark_end(s);
       mark_begin(l, kRestrict, s);
       if (small_level(l + 1, K))
-        k_restrict<T, K, RowLanes<K>::G><<<grid_for((long long)(L.n_vc + L.n_pc) * RowLanes<K>::W), kBlock, 0, s>>>(
+        k_restrict<T, K, RowLanes<K>::G, 1><<<grid_for((long long)(L.n_vc + L.n_pc) * RowLanes<K>::W), kBlock, 0, s>>>(
             L, buf_[l].r, buf_[l + 1].b);
       else
-        k_restrict<T, K, 1><<<grid_for((long long)(L.n_vc + L.n_pc) * K), kBlock, 0, s>>>(L, buf_[l].r, buf_[l + 1].b);
+        k_restrict<T, K, 1, VecWidth<T, K>::V><<<grid_for((long long)(L.n_vc + L.n_pc) * (K / VecWidth<T, K>::V)), kBlock,
+                                                 0, s>>>(L, buf_[l].r, buf_[l + 1].b);
       mark_end(s);
     }
     mark_begin(nl - 1, kCoarse, s);  // every kernel launch of the cycle is preceded by mark_begin
@@ -160,10 +163,11 @@ class DeviceVCycle : public VCycleIface {
       const LevelView<T>& L = views_[l];
       mark_begin(l, kProlong, s);
       if (small_level(l, K))
-        k_prolong<T, K, RowLanes<K>::G><<<grid_for((long long)(L.n_v + L.n_p) * RowLanes<K>::W), kBlock, 0, s>>>(
+        k_prolong<T, K, RowLanes<K>::G, 1><<<grid_for((long long)(L.n_v + L.n_p) * RowLanes<K>::W), kBlock, 0, s>>>(
             L, buf_[l + 1].x, buf_[l].x);
       else
-        k_prolong<T, K, 1><<<grid_for((long long)(L.n_v + L.n_p) * K), kBlock, 0, s>>>(L, buf_[l + 1].x, buf_[l].x);
+        k_prolong<T, K, 1, VecWidth<T, K>::V><<<grid_for((long long)(L.n_v + L.n_p) * (K / VecWidth<T, K>::V)), kBlock, 0,
+                                                s>>>(L, buf_[l + 1].x, buf_[l].x);
       mark_end(s);
       smooth<K>(l, post_, false, s);
     }
@@ -191,17 +195,19 @@ class DeviceVCycle : public VCycleIface {
       const int zero = (from_zero && sw == 0) ? 1 : 0;
       mark_begin(l, kVelocity, s);
       if (small)
-        k_bs_velocity<T, K, RowLanes<K>::G><<<grid_for((long long)L.n_v * RowLanes<K>::W), kBlock, 0, s>>>(L, B.b, B.x, B.y,
-                                                                                                   zero);
+        k_bs_velocity<T, K, RowLanes<K>::G, 1><<<grid_for((long long)L.n_v * RowLanes<K>::W), kBlock, 0, s>>>(
+            L, B.b, B.x, B.y, zero);
       else
-        k_bs_velocity<T, K, 1><<<grid_for((long long)L.n_v * K), kBlock, 0, s>>>(L, B.b, B.x, B.y, zero);
+        k_bs_velocity<T, K, 1, VecWidth<T, K>::V><<<grid_for((long long)L.n_v * (K / VecWidth<T, K>::V)), kBlock, 0, s>>>(
+            L, B.b, B.x, B.y, zero);
       mark_end(s);
       mark_begin(l, kSchurRhs, s);
       if (small)
-        k_schur_rhs<T, K, RowLanes<K>::G><<<grid_for((long long)L.n_p * RowLanes<K>::W), kBlock, 0, s>>>(L, B.b, B.x, B.y,
-                                                                                                 B.g, cfac_, zero);
+        k_schur_rhs<T, K, RowLanes<K>::G, 1><<<grid_for((long long)L.n_p * RowLanes<K>::W), kBlock, 0, s>>>(
+            L, B.b, B.x, B.y, B.g, cfac_, zero);
       else
-        k_schur_rhs<T, K, 1><<<grid_for((long long)L.n_p * K), kBlock, 0, s>>>(L, B.b, B.x, B.y, B.g, cfac_, zero);
+        k_schur_rhs<T, K, 1, VecWidth<T, K>::V><<<grid_for((long long)L.n_p * (K / VecWidth<T, K>::V)), kBlock, 0, s>>>(
+            L, B.b, B.x, B.y, B.g, cfac_, zero);
       mark_end(s);
       cudaMemsetAsync(B.dp, 0, sizeof(T) * (size_t)L.n_p * K, s);
       mark_begin(l, kGsColor, s);
@@ -209,10 +215,11 @@ class DeviceVCycle : public VCycleIface {
       mark_end(s);
       mark_begin(l, kUpdate, s);
       if (small)
-        k_bs_update<T, K, RowLanes<K>::G><<<grid_for((long long)(L.n_v + L.n_p) * RowLanes<K>::W), kBlock, 0, s>>>(
+        k_bs_update<T, K, RowLanes<K>::G, 1><<<grid_for((long long)(L.n_v + L.n_p) * RowLanes<K>::W), kBlock, 0, s>>>(
             L, B.y, B.dp, B.x, zero);
       else
-        k_bs_update<T, K, 1><<<grid_for((long long)(L.n_v + L.n_p) * K), kBlock, 0, s>>>(L, B.y, B.dp, B.x, zero);
+        k_bs_update<T, K, 1, VecWidth<T, K>::V><<<grid_for((long long)(L.n_v + L.n_p) * (K / VecWidth<T, K>::V)), kBlock,
+                                                  0, s>>>(L, B.y, B.dp, B.x, zero);
       mark_end(s);
     }
   }
@@ -259,12 +266,42 @@ class DeviceVCycle : public VCycleIface {
   // cooperative grid (bounded barrier) when there are several strips.
   template <int K>
   void launch_gs(int l, cudaStream_t s) {
+    if (launch_gs_level<K>(l, s)) return;
     if (launch_gs_pipe<K>(l, s)) return;
     if (K <= 8 && gs_lanes_[l] == 4) return launch_gs_g<K, (K <= 8 ? 4 : 1)>(l, s);
     launch_gs_g<K, 1>(l, s);
   }
 
   // The pipelined kernel needs every strip resident at once; false if they do not fit.
+  // Levels of at most two strips whose Schur data fits in one block's shared
+  // memory run in a single block: no waits between blocks.
+  size_t level_smem(int l, int K) const {
+    const LevelView<T>& L = views_[l];
+    const size_t nnz = (size_t)s_nnz_[l];
+    return ((size_t)2 * L.n_p * K + L.n_p + nnz) * sizeof(T) +
+           ((size_t)3 * L.n_p + 1 + nnz + 2 * gs_[l].ncol + 1) * sizeof(int) + 16;
+  }
+  template <int K>
+  bool launch_gs_level(int l, cudaStream_t s) {
+    const GsStrips& P = gs_[l];
+    if (P.nstrips > 2 || level_smem(l, K) > 220 * 1024) return false;
+    const double rows_per_group = (double)views_[l].n_p / std::max(1, 2 * P.ncol);
+    int G = 1;
+    while (G < 4 && K * G * 2 <= 32 && rows_per_group * K * G * 2 <= kGsBlock) G *= 2;
+    if (G == 4) return launch_gs_level_g<K, (K <= 8 ? 4 : 1)>(l, s);
+    if (G == 2) return launch_gs_level_g<K, (K <= 16 ? 2 : 1)>(l, s);
+    return launch_gs_level_g<K, 1>(l, s);
+  }
+  template <int K, int G>
+  bool launch_gs_level_g(int l, cudaStream_t s) {
+    const size_t smem = level_smem(l, K);
+    auto kern = k_gs_level<T, K, G>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 48 * 1024));
+    kern<<<1, kGsBlock, smem, s>>>(views_[l], (const T*)buf_[l].g, buf_[l].dp, (const int*)plist_[l],
+                                   (const int*)poff_[l], gs_[l].ncol, gs_iters_);
+    return true;
+  }
+
   // Lanes per row for the pipelined kernel: as many as the block has to spare
   // for the average color of a strip (K * G <= 32).
   template <int K>
@@ -272,7 +309,7 @@ class DeviceVCycle : public VCycleIface {
     const GsStrips& P0 = gs_[l];
     const double rows_per_color = (double)P0.T / std::max(1, P0.ncol);
     int G = 1;
-    while (G < 4 && K * G * 2 <= 32 && rows_per_color * K * G * 2 <= kGsBlock) G *= 2;
+    while (G < 4 && K * G * 2 <= 32 && rows_per_color * K * G * 2 <= kGsPipeBlock) G *= 2;
     if (G == 4) return launch_gs_pipe_g<K, (K <= 8 ? 4 : 1)>(l, s);
     if (G == 2) return launch_gs_pipe_g<K, (K <= 16 ? 2 : 1)>(l, s);
     return launch_gs_pipe_g<K, 1>(l, s);
@@ -284,19 +321,19 @@ class DeviceVCycle : public VCycleIface {
     const Buf& B = buf_[l];
     GsStrips P = gs_[l];
     P.stage = gs_stage(l, K);
-    if (P.stage == 0) return false;
+    if (P.stage == 0 || P.ncol > kMaxColors) return false;
     const size_t smem = gs_smem(l, K, P.stage);
     auto kern = k_gs_pipe<T, K, G>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 48 * 1024));
     int per = 0, sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kGsBlock, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kGsPipeBlock, smem);
     if (P.nstrips > sms * per) return false;
     cudaMemsetAsync(done_[l], 0, sizeof(int) * P.nstrips, s);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(P.nstrips);
-    cfg.blockDim = dim3(kGsBlock);
+    cfg.blockDim = dim3(kGsPipeBlock);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
@@ -360,7 +397,8 @@ class DeviceVCycle : public VCycleIface {
  private:
   template <int K>
   cudaError_t launch_ff(const float* z, double* out, cudaStream_t s) {
-    k_block_spmv_ff<K, 1><<<grid_for((long long)(ff_.n_v + ff_.n_p) * K), kBlock, 0, s>>>(ff_, z, out);
+    constexpr int V = VecWidth<float, K>::V;
+    k_block_spmv_ff<K, V><<<grid_for((long long)(ff_.n_v + ff_.n_p) * (K / V)), kBlock, 0, s>>>(ff_, z, out);
     ++launches_;
     return cudaGetLastError();
   }
@@ -512,11 +550,23 @@ class DeviceVCycle : public VCycleIface {
       }
       ci_rel_.push_back(alloc_copy<int>(rel));
       done_.push_back(alloc<int>(nstrips));
+      // rows of each (strip parity, color) group, for the single-block kernel
+      std::vector<int> plist, poff(1, 0);
+      for (int par = 0; par < 2; ++par)
+        for (int c = 0; c < ncol; ++c) {
+          for (int st = par; st < nstrips; st += 2)
+            for (int r = soff[(size_t)st * (ncol + 1) + c]; r < soff[(size_t)st * (ncol + 1) + c + 1]; ++r)
+              plist.push_back(r);
+          poff.push_back((int)plist.size());
+        }
+      plist_.push_back(alloc_copy<int>(plist));
+      poff_.push_back(alloc_copy<int>(poff));
     }
     // lanes per Schur row: 4 when rows are long enough to share
     const double avg = H.n_p ? (double)So.nnz() / H.n_p : 0.0;
     gs_lanes_.push_back(avg > 16.0 ? 4 : 1);
     gs_.push_back(gp);
+    s_nnz_.push_back((long long)So.nnz());
     std::vector<double> w(H.n_v);
     for (int i = 0; i < H.n_v; ++i) w[i] = H.dirichlet[i] ? 1.0 : 1.0 / (c_ * H.D[i]);
     L.w = alloc_copy<T>(w);
@@ -557,6 +607,8 @@ class DeviceVCycle : public VCycleIface {
   std::vector<int> gs_lanes_;
   std::vector<int*> ci_rel_;
   std::vector<int*> done_;
+  std::vector<int*> plist_, poff_;
+  std::vector<long long> s_nnz_;
   GridBarrier* barrier_ = nullptr;
   int* err_ = nullptr;
   FFLevel ff_{};

@@ -12,32 +12,27 @@ VCycleIface* make_vcycle_f64(const std::vector<HostLevel>& levels, double cfac, 
 }
 
 template <int K>
-static void apply_k(const LevelView<double>& L, const void* x, bool x_fp32, const double* b, double* out,
-                    cudaStream_t s) {
-  const unsigned g = grid_for((long long)(L.n_v + L.n_p) * K);
-  if (x_fp32) {
-    if (b)
-      k_block_spmv<double, float, double, K, 1, true><<<g, kBlock, 0, s>>>(L, b, (const float*)x, out);
-    else
-      k_block_spmv<double, float, double, K, 1, false><<<g, kBlock, 0, s>>>(L, nullptr, (const float*)x, out);
-  } else {
-    if (b)
-      k_block_spmv<double, double, double, K, 1, true><<<g, kBlock, 0, s>>>(L, b, (const double*)x, out);
-    else
-      k_block_spmv<double, double, double, K, 1, false><<<g, kBlock, 0, s>>>(L, nullptr, (const double*)x, out);
-  }
+static void apply_k(const LevelView<double>& L, const double* x, const double* b, double* out, cudaStream_t s) {
+  constexpr int V = VecWidth<double, K>::V;
+  const unsigned g = grid_for((long long)(L.n_v + L.n_p) * (K / V));
+  if (b)
+    k_block_spmv<double, K, 1, V, true><<<g, kBlock, 0, s>>>(L, b, x, out);
+  else
+    k_block_spmv<double, K, 1, V, false><<<g, kBlock, 0, s>>>(L, nullptr, x, out);
 }
 
 cudaError_t apply_finest_f64(VCycleIface* v64, const void* x, bool x_fp32, const double* b, double* out, int K,
                              cudaStream_t s) {
+  if (x_fp32) return cudaErrorInvalidValue;  // FP32 vectors go through apply_ff (float-float)
   const LevelView<double>& L = static_cast<DeviceVCycle<double>*>(v64)->view(0);
+  const double* xd = (const double*)x;
   switch (K) {
-    case 1: apply_k<1>(L, x, x_fp32, b, out, s); break;
-    case 2: apply_k<2>(L, x, x_fp32, b, out, s); break;
-    case 4: apply_k<4>(L, x, x_fp32, b, out, s); break;
-    case 8: apply_k<8>(L, x, x_fp32, b, out, s); break;
-    case 16: apply_k<16>(L, x, x_fp32, b, out, s); break;
-    case 32: apply_k<32>(L, x, x_fp32, b, out, s); break;
+    case 1: apply_k<1>(L, xd, b, out, s); break;
+    case 2: apply_k<2>(L, xd, b, out, s); break;
+    case 4: apply_k<4>(L, xd, b, out, s); break;
+    case 8: apply_k<8>(L, xd, b, out, s); break;
+    case 16: apply_k<16>(L, xd, b, out, s); break;
+    case 32: apply_k<32>(L, xd, b, out, s); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -60,7 +60,7 @@ class Level:
     # smoother (Section 5.2)
     D: np.ndarray = None          # |A| row sums (Dirichlet rows: 1/c so that c*D = 1)
     S: sp.csr_matrix = None       # B D^-1 Bt, pinned row = identity
-    colors: np.ndarray = None     # greedy coloring of the graph of S
+    colors: np.ndarray = None     # greedy coloring of each Gauss-Seidel strip of S's graph
     gs_strip: int = 1             # Gauss-Seidel strip length T = bandwidth of S
     # transfers to the next level (Alg. 2)
     P: sp.csr_matrix = None       # velocity, one component (n_v x n_v_coarse)
@@ -463,16 +463,35 @@ def emin_step(At, rows, ncols, method: str) -> sp.csr_matrix:
 # ----------------------------------------------------------------------------
 # smoother data (Section 5.2) and coarse solve
 
-def greedy_coloring(S) -> np.ndarray:
-    """Colors of the graph of S (off-diagonal stored entries): vertices in index order,
-    each takes the smallest color not used by an already colored neighbour."""
+def strip_length(S) -> int:
+    """Strip length T of the Gauss-Seidel ordering: the smallest T >= bandwidth/2 such
+    that every entry of S couples rows of the same or of adjacent strips of T
+    consecutive rows (so strips two apart never interact).  On a lexicographic
+    grid this is a whole number of grid lines."""
+    Sc = sp.coo_matrix(S)
+    offd = Sc.row != Sc.col
+    if not offd.any():
+        return 1
+    r, c = Sc.row[offd], Sc.col[offd]
+    bw = int(np.abs(r - c).max())
+    for T in range((bw + 1) // 2, bw + 1):
+        if T > 0 and np.abs(r // T - c // T).max() <= 1:
+            return T
+    return bw
+
+
+def greedy_coloring(S, strip: int) -> np.ndarray:
+    """Colors for the Gauss-Seidel ordering: each strip of `strip` consecutive rows is
+    colored on its own induced subgraph of S's graph (off-diagonal stored entries),
+    vertices in index order, each taking the smallest color not used by an already
+    colored neighbour in the same strip."""
     S = sp.csr_matrix(S)
     n = S.shape[0]
     colors = np.full(n, -1, dtype=np.int64)
     for i in range(n):
         used = set()
         for j in S.indices[S.indptr[i]:S.indptr[i + 1]]:
-            if j != i and colors[j] >= 0:
+            if j != i and j // strip == i // strip and colors[j] >= 0:
                 used.add(colors[j])
         c = 0
         while c in used:
@@ -499,10 +518,8 @@ def form_relaxation(L: Level, prm: Params):
         S = sp.csr_matrix(S)
     L.D = D
     L.S = S
-    L.colors = greedy_coloring(S)
-    Sc = sp.coo_matrix(S)
-    offd = Sc.row != Sc.col
-    L.gs_strip = max(1, int(np.abs(Sc.row[offd] - Sc.col[offd]).max())) if offd.any() else 1
+    L.gs_strip = strip_length(S)
+    L.colors = greedy_coloring(S, L.gs_strip)
 
 
 def form_coarse_solve(L: Level, rcond: float = 1e-12):

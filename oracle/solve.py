@@ -30,10 +30,12 @@ def gauss_seidel(L, g, iters: int):
     """`iters` forward Gauss-Seidel iterations on S dp = g from dp = 0 (Section 5.2:
     "several Gauss-Seidel iterations"; five in Section 6).  The paper gives no
     ordering.  Reading: rows ordered by (strip parity, color, index), where the
-    strips are consecutive blocks of T = bandwidth(S) rows (so strips two apart
-    share no entry of S) and the colors come from the greedy coloring of S's
-    graph.  Rows with the same parity and color share no entry of S, so
-    updating them at once gives the same result as one after another."""
+    strips are consecutive blocks of T rows, T the smallest length for which
+    strips two apart share no entry of S (hierarchy.strip_length), and each strip
+    is greedily colored on its own subgraph.
+    Rows with the same parity and color share no entry of S (same strip: the
+    coloring; different strips of one parity: the bandwidth), so updating them
+    at once gives the same result as one after another."""
     S = L.S
     diag = S.diagonal()
     off = S - sp.diags(diag)

@@ -399,8 +399,8 @@ Csr emin_step(const Csr& At, const std::vector<std::vector<int>>& rows, int ncol
 
 // Braess-Sarazin data (Section 5.2): D = |A| row sums (Dirichlet rows 1/c), the
 // explicit Schur complement S = B D^-1 Bt (pinned row = identity), the strip
-// length of the Gauss-Seidel ordering and a greedy coloring of S's graph
-// (vertices in index order, smallest free color).
+// length of the Gauss-Seidel ordering and a greedy coloring of each strip's
+// subgraph of S's graph (vertices in index order, smallest free color).
 void form_relaxation(HostLevel& L, const SetupParams& prm) {
   L.D.assign(L.n_v, 0.0);
   for (int i = 0; i < L.n_v; ++i) {
@@ -435,20 +435,37 @@ void form_relaxation(HostLevel& L, const SetupParams& prm) {
     }
     L.S = std::move(S2);
   }
-  // Gauss-Seidel ordering: strips of T = bandwidth(S) consecutive rows, so strips
-  // two apart share no entry of S; rows go by (strip parity, color, index)
+  // Gauss-Seidel ordering: strips of T consecutive rows, T the smallest length
+  // >= bandwidth/2 for which every entry couples the same or adjacent strips (so
+  // strips two apart never interact); rows go by (strip parity, color, index)
   int bw = 0;
   for (int i = 0; i < L.n_p; ++i)
     for (int64_t t = L.S.row_begin(i); t < L.S.row_end(i); ++t)
       if (L.S.col[t] != i) bw = std::max(bw, std::abs(L.S.col[t] - i));
   L.gs_strip = std::max(bw, 1);
+  for (int T = std::max(1, (bw + 1) / 2); T < bw; ++T) {
+    bool ok = true;
+    for (int i = 0; i < L.n_p && ok; ++i)
+      for (int64_t t = L.S.row_begin(i); t < L.S.row_end(i); ++t) {
+        const int j = L.S.col[t];
+        if (j != i && std::abs(j / T - i / T) > 1) {
+          ok = false;
+          break;
+        }
+      }
+    if (ok) {
+      L.gs_strip = T;
+      break;
+    }
+  }
+  // greedy coloring of each strip's own subgraph (index order, smallest free color)
   L.colors.assign(L.n_p, -1);
   L.n_colors = 0;
   std::vector<int> used_stamp(64, -1);
   for (int i = 0; i < L.n_p; ++i) {
     for (int64_t t = L.S.row_begin(i); t < L.S.row_end(i); ++t) {
       const int j = L.S.col[t];
-      if (j != i && L.colors[j] >= 0) {
+      if (j != i && j / L.gs_strip == i / L.gs_strip && L.colors[j] >= 0) {
         if (L.colors[j] >= (int)used_stamp.size()) used_stamp.resize(2 * L.colors[j] + 2, -1);
         used_stamp[L.colors[j]] = i;
       }

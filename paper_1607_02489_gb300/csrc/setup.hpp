@@ -28,7 +28,7 @@ struct HostLevel {
   // Braess-Sarazin data (Section 5.2)
   std::vector<double> D;               // |A| row sums; Dirichlet rows 1/c
   Csr S;                               // B D^-1 Bt, pinned row = identity
-  std::vector<int> colors;             // greedy coloring of S's graph
+  std::vector<int> colors;             // greedy coloring of each strip's subgraph of S
   int n_colors = 0;
   int gs_strip = 1;                    // Gauss-Seidel strip length: bandwidth of S
   // transfers to the next level

@@ -24,7 +24,7 @@ def test_multicolor_gs_equals_sequential_gs():
     p = stokes_lid_2d(16, nrhs=2)
     H = setup_hierarchy(p)
     L = H.levels[0]
-    assert L.gs_strip == 2 * 17 + 2
+    assert L.gs_strip == 2 * 17   # two grid lines of the 17x17 pressure grid
     rng = np.random.default_rng(0)
     g = rng.standard_normal((L.n_p, 2))
     dp = gauss_seidel(L, g, 3)
@@ -40,12 +40,15 @@ def test_multicolor_gs_equals_sequential_gs():
                     s -= S.data[t] * ref[j]
             ref[i] = s / S[i, i]
     assert np.abs(dp - ref).max() <= 1e-13 * np.abs(ref).max()
-    # a proper coloring, and strips two apart never coupled
+    # a proper coloring inside every strip, and strips two apart never coupled
     rows = np.repeat(np.arange(L.n_p), np.diff(S.indptr))
     off = rows != S.indices
-    assert np.all(L.colors[rows[off]] != L.colors[S.indices[off]])
     strip = np.arange(L.n_p) // L.gs_strip
+    same = off & (strip[rows] == strip[S.indices])
+    assert np.all(L.colors[rows[same]] != L.colors[S.indices[same]])
     assert np.all(np.abs(strip[rows[off]] - strip[S.indices[off]]) <= 1)
+    # a strip of two grid lines of the 25-point stencil needs 6 colors (a 2x3 block is a clique)
+    assert int(L.colors.max()) + 1 == 6
 
 
 @pytest.mark.parametrize("placement", ["direct", "inverse"])

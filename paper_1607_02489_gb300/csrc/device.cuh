@@ -413,10 +413,11 @@ __device__ __forceinline__ void st_release(int* p, int v) {
   asm volatile("st.release.gpu.global.b32 [%0], %1;\n" ::"l"(p), "r"(v) : "memory");
 }
 
-template <typename T, int K, int G>
+template <typename T, int K, int G, int V>
 __global__ void __launch_bounds__(kGsPipeBlock) k_gs_pipe(LevelView<T> L, const T* __restrict__ g, T* dp, GsStrips P,
                                                       const int* __restrict__ ci_rel, int* done, int* err) {
-  static_assert(K * G <= 32, "a row group must fit in a warp");
+  static_assert((K / V) * G <= 32, "a row group must fit in a warp");
+  static_assert(G == 1 || V == 1, "lanes per row or columns per thread, not both");
   extern __shared__ __align__(16) unsigned char smem[];
   T* s_dp = reinterpret_cast<T*>(smem);
   T* s_g = s_dp + (size_t)3 * P.T * K;
@@ -427,9 +428,10 @@ __global__ void __launch_bounds__(kGsPipeBlock) k_gs_pipe(LevelView<T> L, const 
   int* s_ci = s_perm + P.T;
   __shared__ int s_fail;
   __shared__ int s_so[kMaxColors + 1];  // this strip's color offsets (sorted rows)
-  constexpr int kGroup = K * G;
-  const int k = threadIdx.x % K;
-  const int lane = (threadIdx.x / K) % G;
+  constexpr int KV = K / V;
+  constexpr int kGroup = KV * G;
+  const int k = (threadIdx.x % KV) * V;
+  const int lane = (threadIdx.x / KV) % G;
   const unsigned mask = group_mask<kGroup>();
   const int s = blockIdx.x;
   if (s >= P.nstrips) return;
@@ -485,33 +487,69 @@ __global__ void __launch_bounds__(kGsPipeBlock) k_gs_pipe(LevelView<T> L, const 
       for (int t = threadIdx.x; t < (rb - ra) * kGroup; t += blockDim.x) {
         const int r = ra + t / kGroup;
         const int ea = s_rp[r - q0], eb = s_rp[r - q0 + 1];
-        T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
-        int e = ea + lane;
-        if (P.stage == 2) {
-          const T* sv = s_v - e0;
-          const int* sc = s_ci - e0;
-          for (; e + 3 * G < eb; e += 4 * G) {
-            const int c0 = sc[e], c1 = sc[e + G], c2 = sc[e + 2 * G], c3 = sc[e + 3 * G];
-            a0 += sv[e] * s_dp[c0 * K + k];
-            a1 += sv[e + G] * s_dp[c1 * K + k];
-            a2 += sv[e + 2 * G] * s_dp[c2 * K + k];
-            a3 += sv[e + 3 * G] * s_dp[c3 * K + k];
+        T acc[V];
+        if constexpr (V == 1) {
+          T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+          int e = ea + lane;
+          if (P.stage == 2) {
+            const T* sv = s_v - e0;
+            const int* sc = s_ci - e0;
+            for (; e + 3 * G < eb; e += 4 * G) {
+              const int c0 = sc[e], c1 = sc[e + G], c2 = sc[e + 2 * G], c3 = sc[e + 3 * G];
+              a0 += sv[e] * s_dp[c0 * K + k];
+              a1 += sv[e + G] * s_dp[c1 * K + k];
+              a2 += sv[e + 2 * G] * s_dp[c2 * K + k];
+              a3 += sv[e + 3 * G] * s_dp[c3 * K + k];
+            }
+            for (; e < eb; e += G) a0 += sv[e] * s_dp[sc[e] * K + k];
+          } else {
+            for (; e + 3 * G < eb; e += 4 * G) {
+              const int c0 = ci_rel[e], c1 = ci_rel[e + G], c2 = ci_rel[e + 2 * G], c3 = ci_rel[e + 3 * G];
+              a0 += L.S.v[e] * s_dp[c0 * K + k];
+              a1 += L.S.v[e + G] * s_dp[c1 * K + k];
+              a2 += L.S.v[e + 2 * G] * s_dp[c2 * K + k];
+              a3 += L.S.v[e + 3 * G] * s_dp[c3 * K + k];
+            }
+            for (; e < eb; e += G) a0 += L.S.v[e] * s_dp[ci_rel[e] * K + k];
           }
-          for (; e < eb; e += G) a0 += sv[e] * s_dp[sc[e] * K + k];
+          acc[0] = group_sum<K, G>((a0 + a1) + (a2 + a3), mask);
         } else {
-          for (; e + 3 * G < eb; e += 4 * G) {
-            const int c0 = ci_rel[e], c1 = ci_rel[e + G], c2 = ci_rel[e + 2 * G], c3 = ci_rel[e + 3 * G];
-            a0 += L.S.v[e] * s_dp[c0 * K + k];
-            a1 += L.S.v[e + G] * s_dp[c1 * K + k];
-            a2 += L.S.v[e + 2 * G] * s_dp[c2 * K + k];
-            a3 += L.S.v[e + 3 * G] * s_dp[c3 * K + k];
+          // V right-hand sides per thread, G == 1: two independent partial sums per column
+          T a[V], b2[V];
+#pragma unroll
+          for (int u = 0; u < V; ++u) a[u] = b2[u] = T(0);
+          const T* sv = P.stage == 2 ? s_v - e0 : L.S.v;
+          const int* sc = P.stage == 2 ? s_ci - e0 : ci_rel;
+          int e = ea;
+          for (; e + 1 < eb; e += 2) {
+            const int c0 = sc[e], c1 = sc[e + 1];
+            const T v0 = sv[e], v1 = sv[e + 1];
+            T d0[V], d1[V];
+            vld<T, V>(d0, s_dp + c0 * K + k);
+            vld<T, V>(d1, s_dp + c1 * K + k);
+#pragma unroll
+            for (int u = 0; u < V; ++u) {
+              a[u] += v0 * d0[u];
+              b2[u] += v1 * d1[u];
+            }
           }
-          for (; e < eb; e += G) a0 += L.S.v[e] * s_dp[ci_rel[e] * K + k];
+          if (e < eb) {
+            T d0[V];
+            vld<T, V>(d0, s_dp + sc[e] * K + k);
+#pragma unroll
+            for (int u = 0; u < V; ++u) a[u] += sv[e] * d0[u];
+          }
+#pragma unroll
+          for (int u = 0; u < V; ++u) acc[u] = a[u] + b2[u];
         }
-        const T acc = group_sum<K, G>((a0 + a1) + (a2 + a3), mask);
         if (lane == 0) {
           const int i = s_perm[r - q0];
-          s_dp[(size_t)(i - h_lo) * K + k] = (s_g[(size_t)(i - r_lo) * K + k] - acc) * s_dinv[r - q0];
+          const T di = s_dinv[r - q0];
+          T gv[V], out[V];
+          vld<T, V>(gv, s_g + (size_t)(i - r_lo) * K + k);
+#pragma unroll
+          for (int u = 0; u < V; ++u) out[u] = (gv[u] - acc[u]) * di;
+          vst<T, V>(s_dp + (size_t)(i - h_lo) * K + k, out);
         }
       }
       __syncthreads();

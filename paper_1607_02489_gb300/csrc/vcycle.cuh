@@ -310,12 +310,14 @@ class DeviceVCycle : public VCycleIface {
     const double rows_per_color = (double)P0.T / std::max(1, P0.ncol);
     int G = 1;
     while (G < 4 && K * G * 2 <= 32 && rows_per_color * K * G * 2 <= kGsPipeBlock) G *= 2;
-    if (G == 4) return launch_gs_pipe_g<K, (K <= 8 ? 4 : 1)>(l, s);
-    if (G == 2) return launch_gs_pipe_g<K, (K <= 16 ? 2 : 1)>(l, s);
-    return launch_gs_pipe_g<K, 1>(l, s);
+    if (G == 4) return launch_gs_pipe_g<K, (K <= 8 ? 4 : 1), 1>(l, s);
+    if (G == 2) return launch_gs_pipe_g<K, (K <= 16 ? 2 : 1), 1>(l, s);
+    // a color too large for one pass at one column per thread: two columns per thread
+    if (K >= 2 && rows_per_color * K > kGsPipeBlock) return launch_gs_pipe_g<K, 1, (K >= 2 ? 2 : 1)>(l, s);
+    return launch_gs_pipe_g<K, 1, 1>(l, s);
   }
 
-  template <int K, int G>
+  template <int K, int G, int V>
   bool launch_gs_pipe_g(int l, cudaStream_t s) {
     const LevelView<T>& L = views_[l];
     const Buf& B = buf_[l];
@@ -323,7 +325,7 @@ class DeviceVCycle : public VCycleIface {
     P.stage = gs_stage(l, K);
     if (P.stage == 0 || P.ncol > kMaxColors) return false;
     const size_t smem = gs_smem(l, K, P.stage);
-    auto kern = k_gs_pipe<T, K, G>;
+    auto kern = k_gs_pipe<T, K, G, V>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 48 * 1024));
     int per = 0, sms = 0, dev = 0;
     cudaGetDevice(&dev);

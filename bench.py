@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving stream")
+    ap.add_argument("--serve-requests", type=int, default=64)
     ap.add_argument("--ncu", action="store_true",
                     help="short run for an ncu launch list: one warm-up solve, then one solve (FP32 V-cycle)")
     return ap.parse_args()
@@ -195,12 +197,13 @@ def _oracle_worker(n_solves, q):
     Ho = setup_hierarchy(p)
     times = []
     its = []
+    x = None
     for _ in range(n_solves):
         t0 = time.perf_counter()
         x, it, rel, _ = fgmres(Ho, p.b, rtol=RTOL, restart=RESTART, maxit=MAXIT)
         times.append(time.perf_counter() - t0)
         its.append(int(it[0]))
-    q.put((times, its))
+    q.put((times, its, x[:, 0]))
 
 
 def run_oracle(n_solves):
@@ -214,18 +217,18 @@ def run_oracle(n_solves):
     q = ctx.Queue()
     pr = ctx.Process(target=_oracle_worker, args=(n_solves, q))
     pr.start()
-    times, its = q.get()
+    times, its, x = q.get()
     pr.join()
     if env_before is None:
         os.environ.pop("OMP_NUM_THREADS", None)
-    return times, its
+    return times, its, x
 
 
 def reference_main(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    times, its = run_oracle(args.warmup + args.steps)
+    times, its, _ = run_oracle(args.warmup + args.steps)
     timed = times[args.warmup:]
     total = sum(timed)
     value = len(timed) / total
@@ -240,6 +243,76 @@ def reference_main(args):
 
 
 # ----------------------------------------------------------------------------
+# serving: a Poisson stream of Oseen solves over 15 resident hierarchies
+
+SERVE_RATE = 200.0
+SERVE_WARM = 12
+SERVE_ACTIVE = 32
+SERVE_RESTART = 50
+SERVE_WORKLOAD = ("Poisson arrivals at 200 req/s (seed 0) of 2D Oseen Q2-Q1 solves on [-1,1]^2 with the "
+                  "recirculating wind, n from {64,128,256,384,512}, Re from {1,10,100}, 1-8 uniform[-1,1] "
+                  "right-hand sides each, FP32 V-cycle / FP64 FGMRES to 1e-8, host buffers in and out")
+
+
+def serve(g, torch, dev, n_requests, seed=0):
+    """Builds the 15 hierarchies (untimed: setup is per matrix), runs a short
+    warm-up stream, then the timed stream; latency = arrival to result on the host."""
+    import numpy as np
+    from concurrent.futures import ThreadPoolExecutor
+    from synth import MESHES, REYNOLDS, oseen_recirculating_2d, serving_stream, homogeneous_rhs
+
+    def build(key):
+        n, Re = key
+        torch.cuda.set_device(dev)
+        p = oseen_recirculating_2d(n, Re=Re, nrhs=1)
+        return key, (p, g.Hierarchy(p, max_nrhs=8, vcycle_fp32=1))
+
+    t0 = time.perf_counter()
+    keys = [(n, Re) for n in MESHES for Re in REYNOLDS]
+    with ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
+        hs = dict(ex.map(build, keys))
+    setup_s = time.perf_counter() - t0
+
+    def requests(stream):
+        out = []
+        for r in stream:
+            p, H = hs[(r["n"], r["Re"])]
+            b = torch.from_numpy(homogeneous_rhs(p, r["nrhs"], r["rhs_seed"])).pin_memory()
+            out.append(dict(t=r["t"], H=H, b=b, x=torch.zeros_like(b).pin_memory(), rtol=RTOL, n=r["n"],
+                            nrhs=r["nrhs"]))
+        return out
+
+    sv = g.Server(max_active=SERVE_ACTIVE, restart=SERVE_RESTART, maxit=MAXIT)
+    t0 = time.perf_counter()
+    for key in keys:  # one slot per (hierarchy, K) up front: no allocation or capture in the stream
+        for k in (1, 2, 4, 8):
+            sv.reserve(hs[key][1], k, 1)
+    reserve_s = time.perf_counter() - t0
+    g.run_stream(sv, requests(serving_stream(SERVE_WARM, SERVE_RATE, seed=1000 + seed)))
+    reqs = requests(serving_stream(n_requests, SERVE_RATE, seed=seed))
+    l0 = sv.stats()["kernel_launches"]
+    res = g.run_stream(sv, reqs)
+    st = sv.stats()
+    sv.close()
+    ok = all(r["status"] == g.AMG_OK and np.all(r["relres"] <= RTOL) for r in res)
+    lat = np.array([r["done"] - r["arrival"] for r in res])
+    wall = max(r["done"] for r in res) - min(r["arrival"] for r in res)
+    rhs = sum(q["nrhs"] for q in reqs)
+    by_n = {}
+    for q, r in zip(reqs, res):
+        by_n.setdefault(q["n"], []).append(1000.0 * (r["done"] - r["arrival"]))
+    return {"workload": SERVE_WORKLOAD, "requests": len(reqs), "rhs_solves": rhs, "all_converged": bool(ok),
+            "wall_s": wall, "requests_per_s": len(reqs) / wall, "solves_per_s": rhs / wall,
+            "offered_rps": SERVE_RATE, "max_active": SERVE_ACTIVE, "restart": SERVE_RESTART,
+            "latency_ms": {"p50": float(np.percentile(lat, 50) * 1000), "p99": float(np.percentile(lat, 99) * 1000),
+                           "max": float(lat.max() * 1000)},
+            "latency_p50_ms_by_mesh": {str(n): float(np.percentile(v, 50)) for n, v in sorted(by_n.items())},
+            "queued_p50_ms": float(np.percentile([r["queued"] for r in res], 50) * 1000),
+            "iterations_max": int(max(int(np.max(r["iters"])) for r in res)),
+            "gpu_launches": int(st["kernel_launches"] - l0), "slots_created": int(st["slots_created"]),
+            "slots_released": int(st["slots_released"]), "errors": int(st["errors"]),
+            "setup_s_untimed": setup_s, "reserve_s_untimed": reserve_s}
+
 
 def main():
     args = parse()
@@ -261,8 +334,9 @@ def main():
 
     # the CPU oracle runs first, in a spawned process, before any CUDA work
     cpu = None
+    x_oracle = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        t, its_cpu = run_oracle(1)
+        t, its_cpu, x_oracle = run_oracle(1)
         cpu = {"value": 1.0 / t[0], "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": CPU_SAMPLE,
                "seconds": t[0], "iterations": its_cpu[0]}
 
@@ -320,7 +394,23 @@ def main():
     sampler.start()
     ms32, launches32, its32, rel32, lat32 = timed(H32, args.steps, args.warmup)
     clocks = sampler.stop()
+    x32 = x[:, 0].cpu().numpy()
     ms64, launches64, its64, rel64, lat64 = timed(H64, args.steps, args.warmup)
+    x64 = x[:, 0].cpu().numpy()
+    accuracy = None
+    if x_oracle is not None:
+        nu = 2 * p.n_v
+
+        def err(a):  # relative 2-norm error, pressure compared up to its constant
+            d = a - x_oracle
+            d[nu:] -= d[nu:].mean()
+            ref = x_oracle.copy()
+            ref[nu:] -= ref[nu:].mean()
+            return float(np.linalg.norm(d) / np.linalg.norm(ref))
+
+        accuracy = {"fp32_vcycle_vs_oracle": err(x32), "fp64_vcycle_vs_oracle": err(x64),
+                    "what": "relative 2-norm error of right-hand side 0's FGMRES solution (both stopped at "
+                            f"{RTOL:g}) against the FP64 oracle's, pressure mean removed"}
 
     solves = NRHS * args.steps * world
     value = solves / (ms32 / 1000.0)
@@ -367,6 +457,17 @@ def main():
     breakdown = {f"L{l}/{c}": round(float(ms_tab[l, k] / reps * 1000.0), 2)
                  for l in range(ms_tab.shape[0]) for k, c in enumerate(g.KERNEL_CLASSES) if cnt_tab[l, k]}
 
+    serving = None
+    if not args.no_serve:
+        serving = serve(g, torch, dev, args.serve_requests, seed=rank)
+        if world > 1:
+            t = torch.tensor([serving["wall_s"], serving["requests"], serving["rhs_solves"]], device=dev,
+                             dtype=torch.float64)
+            w = t[:1].clone()
+            dist.all_reduce(w, op=dist.ReduceOp.MAX)
+            dist.all_reduce(t, op=dist.ReduceOp.SUM)
+            serving["all_ranks"] = {"requests_per_s": float(t[1] / w[0]), "solves_per_s": float(t[2] / w[0])}
+
     if rank == 0:
         lat_sorted = sorted(lat32)
         line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
@@ -378,8 +479,12 @@ def main():
                 "fp64_vcycle": {"value": value64, "unit": "solves/s", "ms_per_step": ms64 / args.steps,
                                 "iterations": its64.tolist(), "gpu_launches": launches64},
                 "iterations": its32.tolist(), "relres_max": float(np.max(rel32)),
-                "latency_ms": {"p50": 1000 * lat_sorted[len(lat_sorted) // 2],
-                               "p99": 1000 * lat_sorted[min(len(lat_sorted) - 1, int(0.99 * len(lat_sorted)))]},
+                "step_latency_ms": {"p50": 1000 * lat_sorted[len(lat_sorted) // 2],
+                                    "p99": 1000 * lat_sorted[min(len(lat_sorted) - 1, int(0.99 * len(lat_sorted)))]},
+                "latency_ms": (None if serving is None else
+                               {"p50": serving["latency_ms"]["p50"], "p99": serving["latency_ms"]["p99"],
+                                "source": "serving stream (arrival to result on the host)"}),
+                "serving": serving, "accuracy": accuracy,
                 "e2e": e2e, "gpu_launches": launches32, "clocks": clocks, "roofline": roofline,
                 "vcycle_us_by_kernel": breakdown, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)

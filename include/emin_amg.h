@@ -188,6 +188,93 @@ void amg_hierarchy_destroy(amg_handle h);
 
 const char* amg_last_error(void);
 
+/* ------------------------------------------------------------------------
+ * Request server: continuous batching of FGMRES solves on one device.
+ *
+ * The paper has no counterpart: it solves one system at a time.  The server
+ * serves many solves (different hierarchies: mesh sizes, Reynolds numbers)
+ * concurrently.  Each running request owns a slot: a clone of its hierarchy's
+ * V-cycle (matrices shared with the hierarchy, vectors and CUDA graphs its own),
+ * an FGMRES workspace for K = nrhs rounded up to a power of two, device copies of
+ * b and x, and a stream.  amg_server_progress() advances every running request
+ * whose last chunk of device work has finished by one more chunk (an Arnoldi
+ * step or a cycle end) and admits queued requests as slots and memory free up,
+ * so their kernels overlap on the device.  A request's result is bit-identical
+ * to amg_fgmres_solve_host() of the same right-hand sides with restart and maxit
+ * set to the server's.
+ *
+ * Admission: a queued request takes an idle slot of the same (hierarchy, K), or
+ * a new slot while fewer than max_active requests run and the slot's bytes fit
+ * device_bytes (idle slots of other shapes are released, least recently used
+ * first, to make room).  Requests are considered in submission order; one that
+ * does not fit yet stays queued while later ones may start.
+ *
+ * One host thread drives a server.  Its hierarchies must outlive it, and must
+ * not be used through the other entry points while the server has requests on
+ * them (amg_fgmres_solve shares nothing with the server's slots, but the handle
+ * is not thread safe).
+ * ---------------------------------------------------------------------- */
+typedef struct amg_server* amg_server_handle;
+
+typedef struct {
+  int max_active;      /* requests running at once (one stream each), 1..256; default 16 */
+  size_t device_bytes; /* device memory the slots may hold; 0 = 80% of the free memory at creation */
+  int restart;         /* FGMRES restart length of every request; default 100 */
+  int maxit;           /* iteration limit per right-hand side; default 500 */
+} amg_server_params;
+
+typedef struct {
+  int queued, running, slots;
+  size_t bytes_in_use, budget;
+  long long kernel_launches; /* kernels launched for the server's requests (graph nodes counted) */
+  long long slots_created, slots_released, errors;
+} amg_server_stats;
+
+void amg_server_params_default(amg_server_params* p);
+amg_status amg_server_create(const amg_server_params* prm, amg_server_handle* out);
+
+/* Queue one solve of A x = b with nrhs right-hand sides (1..32) to relative
+ * residual rtol.  b_host and x_host are HOST arrays, N x nrhs row-major, owned
+ * by the caller: b_host is read and x_host written while the request runs, so
+ * both must stay valid until its result has been collected.  Page-locked
+ * memory keeps the copies asynchronous (pageable x_host makes the final copy
+ * wait for the request's own stream).  *ticket identifies the request. */
+amg_status amg_server_submit(amg_server_handle sv, amg_handle h, const double* b_host, double* x_host, int nrhs,
+                             double rtol, long long* ticket);
+
+/* Create idle slots for requests of nrhs right-hand sides on h until count
+ * slots of that shape exist, capturing their V-cycle graphs, so the first such
+ * requests start without allocation or capture.  AMG_ERR_OOM when the budget is
+ * exhausted first (the slots made so far stay).  Reserved slots are released
+ * like any idle slot when room is needed for another shape. */
+amg_status amg_server_reserve(amg_server_handle sv, amg_handle h, int nrhs, int count);
+
+/* Never blocks: advances the running requests whose device work has finished,
+ * admits queued requests, and writes up to cap tickets of requests that have
+ * completed since they were last reported to done[] (count in *n_done). */
+amg_status amg_server_progress(amg_server_handle sv, long long* done, int cap, int* n_done);
+
+/* *state = 0 queued, 1 running, 2 done.  For a done request also fills iters
+ * and relres (nrhs entries each, as amg_fgmres_solve), seconds[0] = queueing
+ * time and seconds[1] = submission to completion (host clock; completion is
+ * when progress() saw the last chunk finish), *status = the solve's status; the
+ * request is then forgotten (a second call with its ticket is AMG_ERR_ARG).
+ * Any output pointer may be NULL. */
+amg_status amg_server_result(amg_server_handle sv, long long ticket, int* state, int* iters, double* relres,
+                             double* seconds, amg_status* status);
+
+/* *state of a request (0 queued, 1 running, 2 done) without collecting it. */
+amg_status amg_server_state(amg_server_handle sv, long long ticket, int* state);
+
+amg_status amg_server_get_stats(amg_server_handle sv, amg_server_stats* st);
+
+/* Waits for the device work in flight, then frees every slot. */
+void amg_server_destroy(amg_server_handle sv);
+
+/* Message of the server's last asynchronous failure, else of the calling
+ * thread's last failing amg_server_* call. */
+const char* amg_server_last_error(amg_server_handle sv);
+
 #ifdef __cplusplus
 }
 #endif

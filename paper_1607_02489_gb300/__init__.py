@@ -23,7 +23,9 @@ STATUS_NAMES = {0: "OK", 1: "NOT_CONVERGED", 2: "BREAKDOWN", -1: "ERR_ARG", -2: 
                 -4: "ERR_SETUP"}
 EXPORTED = ["amg_params_default", "amg_hierarchy_create", "amg_vcycle_apply", "amg_apply", "amg_fgmres_solve",
             "amg_fgmres_solve_host", "amg_num_levels", "amg_level_get_info", "amg_level_get_matrix",
-            "amg_level_get_points", "amg_hierarchy_destroy", "amg_last_error", "amg_profile_vcycle", "amg_kernel_launches", "amg_apply_noalloc"]
+            "amg_level_get_points", "amg_hierarchy_destroy", "amg_last_error", "amg_profile_vcycle", "amg_kernel_launches", "amg_apply_noalloc",
+            "amg_server_params_default", "amg_server_create", "amg_server_reserve", "amg_server_submit", "amg_server_progress",
+            "amg_server_result", "amg_server_state", "amg_server_get_stats", "amg_server_destroy", "amg_server_last_error"]
 KERNEL_CLASSES = ["velocity", "schur_rhs", "gs_color", "update", "residual", "restrict", "prolong", "coarse"]
 MATRICES = {"A": 0, "B": 1, "Bt": 2, "S": 3, "P": 4, "Pp": 5, "R": 6, "Rp": 7}
 
@@ -55,6 +57,18 @@ class AmgLevelInfo(ctypes.Structure):
                 ("nnz_P", ctypes.c_longlong), ("nnz_Pp", ctypes.c_longlong), ("nnz_R", ctypes.c_longlong),
                 ("nnz_Rp", ctypes.c_longlong), ("n_cp", ctypes.c_int), ("n_cv", ctypes.c_int),
                 ("gs_strip", ctypes.c_int)]
+
+
+class AmgServerParams(ctypes.Structure):
+    _fields_ = [("max_active", ctypes.c_int), ("device_bytes", ctypes.c_size_t), ("restart", ctypes.c_int),
+                ("maxit", ctypes.c_int)]
+
+
+class AmgServerStats(ctypes.Structure):
+    _fields_ = [("queued", ctypes.c_int), ("running", ctypes.c_int), ("slots", ctypes.c_int),
+                ("bytes_in_use", ctypes.c_size_t), ("budget", ctypes.c_size_t),
+                ("kernel_launches", ctypes.c_longlong), ("slots_created", ctypes.c_longlong),
+                ("slots_released", ctypes.c_longlong), ("errors", ctypes.c_longlong)]
 
 
 _lib = None
@@ -103,6 +117,26 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.amg_hierarchy_destroy.restype = None
     lib.amg_last_error.argtypes = []
     lib.amg_last_error.restype = ctypes.c_char_p
+    lib.amg_server_params_default.argtypes = [ctypes.POINTER(AmgServerParams)]
+    lib.amg_server_params_default.restype = None
+    lib.amg_server_create.argtypes = [ctypes.POINTER(AmgServerParams), ctypes.POINTER(vp)]
+    lib.amg_server_create.restype = ctypes.c_int
+    lib.amg_server_submit.argtypes = [vp, vp, vp, vp, ctypes.c_int, ctypes.c_double, _i64p]
+    lib.amg_server_submit.restype = ctypes.c_int
+    lib.amg_server_reserve.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int]
+    lib.amg_server_reserve.restype = ctypes.c_int
+    lib.amg_server_progress.argtypes = [vp, _i64p, ctypes.c_int, _i32p]
+    lib.amg_server_progress.restype = ctypes.c_int
+    lib.amg_server_result.argtypes = [vp, ctypes.c_longlong, _i32p, _i32p, _f64p, _f64p, _i32p]
+    lib.amg_server_result.restype = ctypes.c_int
+    lib.amg_server_state.argtypes = [vp, ctypes.c_longlong, _i32p]
+    lib.amg_server_state.restype = ctypes.c_int
+    lib.amg_server_get_stats.argtypes = [vp, ctypes.POINTER(AmgServerStats)]
+    lib.amg_server_get_stats.restype = ctypes.c_int
+    lib.amg_server_destroy.argtypes = [vp]
+    lib.amg_server_destroy.restype = None
+    lib.amg_server_last_error.argtypes = [vp]
+    lib.amg_server_last_error.restype = ctypes.c_char_p
     _lib = lib
     return lib
 
@@ -289,3 +323,126 @@ class Hierarchy:
         _check(load().amg_level_get_points(self._h, level, _ptr(cp, ctypes.c_int), _ptr(cv, ctypes.c_int),
                                            _ptr(colors, ctypes.c_int), _ptr(D, ctypes.c_double)))
         return dict(Cp=cp[:info["n_cp"]], Cv=cv[:info["n_cv"]], colors=colors[:info["n_p"]], D=D[:info["n_v"]])
+
+
+def _host_ptr(a, what):
+    import torch
+    if isinstance(a, torch.Tensor):
+        if a.is_cuda or a.dtype != torch.float64 or not a.is_contiguous():
+            raise TypeError(f"{what} must be a contiguous float64 host tensor")
+        return ctypes.c_void_p(a.data_ptr())
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous):
+        raise TypeError(f"{what} must be a contiguous float64 host array")
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+class Server:
+    """Request server (amg_server_*): continuous batching of FGMRES solves over
+    resident hierarchies.  submit() queues a solve on host buffers, progress()
+    never blocks and returns the tickets that completed, result() collects one."""
+
+    def __init__(self, max_active=16, device_bytes=0, restart=100, maxit=500):
+        lib = load()
+        prm = AmgServerParams()
+        lib.amg_server_params_default(ctypes.byref(prm))
+        prm.max_active, prm.device_bytes, prm.restart, prm.maxit = int(max_active), int(device_bytes), int(restart), \
+            int(maxit)
+        h = ctypes.c_void_p()
+        self._check(lib.amg_server_create(ctypes.byref(prm), ctypes.byref(h)))
+        self._s = h
+        self._keep = {}  # ticket -> (hierarchy, b, x, nrhs): alive until collected
+
+    def _check(self, st):
+        if st < 0:
+            raise AmgError(st, load().amg_server_last_error(getattr(self, "_s", None)).decode())
+        return st
+
+    def submit(self, H: "Hierarchy", b_host, x_host, rtol=1e-8) -> int:
+        k = 1 if b_host.ndim == 1 else int(b_host.shape[1])
+        t = ctypes.c_longlong()
+        self._check(load().amg_server_submit(self._s, H._h, _host_ptr(b_host, "b"), _host_ptr(x_host, "x"), k,
+                                             float(rtol), ctypes.byref(t)))
+        self._keep[t.value] = (H, b_host, x_host, k)
+        return t.value
+
+    def reserve(self, H: "Hierarchy", nrhs: int, count: int = 1):
+        """Pre-create idle slots (graphs captured) for requests of nrhs right-hand sides on H."""
+        self._check(load().amg_server_reserve(self._s, H._h, int(nrhs), int(count)))
+
+    def progress(self, cap=256):
+        done = np.zeros(cap, dtype=np.int64)
+        n = ctypes.c_int()
+        self._check(load().amg_server_progress(self._s, _ptr(done, ctypes.c_longlong), int(cap), ctypes.byref(n)))
+        return [int(v) for v in done[:n.value]]
+
+    def result(self, ticket):
+        """(status, iters, relres, (queue_s, total_s)) of a completed request; None if it is not done."""
+        k = self._keep[ticket][3]
+        state = ctypes.c_int()
+        its = np.zeros(k, dtype=np.int32)
+        rel = np.zeros(k, dtype=np.float64)
+        sec = np.zeros(2, dtype=np.float64)
+        st = ctypes.c_int()
+        self._check(load().amg_server_result(self._s, int(ticket), ctypes.byref(state), _ptr(its, ctypes.c_int),
+                                             _ptr(rel, ctypes.c_double), _ptr(sec, ctypes.c_double),
+                                             ctypes.byref(st)))
+        if state.value != 2:
+            return None
+        del self._keep[ticket]
+        return st.value, its, rel, (float(sec[0]), float(sec[1]))
+
+    def state(self, ticket) -> int:
+        """0 queued, 1 running, 2 done (the request is not collected)."""
+        st = ctypes.c_int()
+        self._check(load().amg_server_state(self._s, int(ticket), ctypes.byref(st)))
+        return st.value
+
+    def stats(self) -> dict:
+        s = AmgServerStats()
+        self._check(load().amg_server_get_stats(self._s, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in AmgServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_s", None):
+            load().amg_server_destroy(self._s)
+            self._s = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def run_stream(server: Server, requests, clock=None):
+    """Drive a request stream through a Server in real time.
+
+    requests: sequence of dicts with t (arrival, seconds after the start), H (a
+    Hierarchy), b and x (host float64 tensors, N x nrhs; pinned keeps the copies
+    asynchronous) and rtol.  Each request is submitted once its arrival time has
+    passed; progress() is polled without sleeping.  Returns, per request, a dict
+    with arrival, submit and done times (seconds after the start), queued (seconds
+    from submission to admission), status, iters and relres."""
+    import time
+    clock = clock or time.perf_counter
+    order = sorted(range(len(requests)), key=lambda i: requests[i]["t"])
+    out = [None] * len(requests)
+    ticket_of, submitted = {}, {}
+    nxt, finished = 0, 0
+    t0 = clock()
+    while finished < len(requests):
+        now = clock() - t0
+        while nxt < len(order) and requests[order[nxt]]["t"] <= now:
+            i = order[nxt]
+            r = requests[i]
+            ticket_of[server.submit(r["H"], r["b"], r["x"], rtol=r.get("rtol", 1e-8))] = i
+            submitted[i] = clock() - t0
+            nxt += 1
+        for t in server.progress():
+            i = ticket_of.pop(t)
+            st, its, rel, sec = server.result(t)
+            out[i] = dict(arrival=requests[i]["t"], submit=submitted[i], done=clock() - t0, status=st, iters=its,
+                          relres=rel, queued=sec[0])
+            finished += 1
+    return out

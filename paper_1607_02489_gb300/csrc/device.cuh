@@ -224,56 +224,22 @@ __global__ void __launch_bounds__(kBlock) k_schur_rhs(LevelView<T> L, const T* _
   vst<T, V>(g + i * K + k0, out);
 }
 
-// Bounded grid barrier for the cooperative Gauss-Seidel launch.  Every waiting
-// block gives up after kSpinLimit polls (about a second), sets *err and returns
-// false, so a barrier can never hang the GPU; the host checks *err.
-struct GridBarrier {
-  unsigned int count;
-  unsigned int gen;
-};
+// Bounded waits: a block polling a counter that another block publishes gives
+// up after kSpinLimit polls (seconds), sets *err and returns, so a wait can
+// never hang the GPU; the host checks *err after the cycle.
 constexpr unsigned long long kSpinLimit = 1ull << 24;
 
-__device__ __forceinline__ bool grid_sync(GridBarrier* gb, int* err, unsigned nblocks) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned int* vgen = &gb->gen;
-    const unsigned int g0 = *vgen;
-    __threadfence();
-    const unsigned int arrived = atomicAdd(&gb->count, 1u) + 1u;
-    int ok = 1;
-    if (arrived == nblocks) {
-      gb->count = 0u;
-      __threadfence();
-      atomicAdd(&gb->gen, 1u);
-    } else {
-      unsigned long long spins = 0;
-      while (*vgen == g0) {
-        if (++spins > kSpinLimit || *(volatile int*)err) {
-          ok = 0;
-          atomicExch(err, 1);
-          break;
-        }
-        __nanosleep(64);
-      }
-    }
-    __threadfence();
-    s_ok = ok;
-  }
-  __syncthreads();
-  return s_ok != 0;
-}
-
 // Strip-ordered Gauss-Seidel for the Schur system S dp = g, gs_iters iterations
-// from dp = 0 in one launch.  Rows are relaxed in the order (strip parity,
-// color, index): strips are T consecutive rows with T >= bandwidth(S), so the
-// strips of one parity never share an entry of S and are relaxed concurrently,
-// one block per strip; inside a strip the rows of one color are independent.
-// A strip reads only rows within T of itself, so its block stages that halo of
-// dp (stage >= 1) and its own rows of S (stage == 2) in shared memory and runs
-// the color sub-steps there with __syncthreads; the strip parities are
-// separated by the bounded grid barrier (cooperative launch).  G lanes share a
-// row and combine their sums with warp shuffles.
+// from dp = 0.  Rows are relaxed in the order (strip parity, color, index):
+// strips are T consecutive rows and every entry of S couples rows of the same
+// or adjacent strips, so the strips of one parity never share an entry of S and
+// are relaxed concurrently, one block per strip; inside a strip the rows of one
+// color are independent.  A strip reads only rows within T of itself, so its
+// block stages that halo of dp (stage >= 1) and its own rows of S (stage == 2)
+// in shared memory and runs the color sub-steps there with __syncthreads.
+// k_gs_strips runs the phases [ph0, ph1) (phase = 2 * iteration + parity); a
+// launch of several blocks runs exactly one phase, so no block ever waits for
+// another.  G lanes share a row and combine their sums with warp shuffles.
 struct GsStrips {
   const int* soff;  // nstrips x (ncol + 1): first sorted row of each (strip, color)
   int nstrips, ncol, T, iters, stage, max_strip_nnz;
@@ -316,7 +282,7 @@ __device__ __forceinline__ void stage_copy(U* sdst, const U* gsrc, int n) {
 
 template <typename T, int K, int G>
 __global__ void __launch_bounds__(kGsBlock) k_gs_strips(LevelView<T> L, const T* __restrict__ g, T* dp, GsStrips P,
-                                                        GridBarrier* gb, int* err) {
+                                                        int ph0, int ph1) {
   static_assert(K * G <= 32, "a row group must fit in a warp");
   extern __shared__ __align__(16) unsigned char smem[];
   // layout: dp halo (3T x K), g (T x K), 1/S_ii (T), [S values], then ints:
@@ -334,8 +300,9 @@ __global__ void __launch_bounds__(kGsBlock) k_gs_strips(LevelView<T> L, const T*
   const unsigned mask = kGroup == 32 ? 0xffffffffu
                                      : (((1u << kGroup) - 1u) << ((threadIdx.x & 31) & ~(unsigned)(kGroup - 1)));
   const int n_p = L.n_p;
-  for (int it = 0; it < P.iters; ++it)
-    for (int bc = 0; bc < 2; ++bc) {
+  for (int ph = ph0; ph < ph1; ++ph) {
+    const int bc = ph & 1;
+    {
       for (int s = bc + 2 * blockIdx.x; s < P.nstrips; s += 2 * gridDim.x) {
         const int r_lo = s * P.T, r_hi = min(r_lo + P.T, n_p);
         const int h_lo = max(0, r_lo - P.T), h_hi = min(n_p, r_hi + P.T);
@@ -390,20 +357,24 @@ __global__ void __launch_bounds__(kGsBlock) k_gs_strips(LevelView<T> L, const T*
             dp[(size_t)r_lo * K + t] = s_dp[(size_t)(r_lo - h_lo) * K + t];
         __syncthreads();
       }
-      if (gridDim.x > 1 && !grid_sync(gb, err, gridDim.x)) return;
     }
+  }
 }
 
-// Pipelined strip Gauss-Seidel: the same ordering as k_gs_strips, one resident
-// block per strip for the whole call (cooperative launch), so a block stages
-// its strip's rows of S, 1/S_ii and g in shared memory once and keeps its own
-// dp rows there.  Instead of a grid barrier per phase, each strip waits only
-// for its two neighbours through per-strip counters of completed iterations:
-// an even strip at iteration it needs its odd neighbours to have completed it
-// iterations, an odd strip needs its even neighbours to have completed it + 1.
-// That is exactly the dependency of the sequential order, and it also keeps a
-// strip from overwriting rows a neighbour has not read yet.  Waits are bounded
-// (kSpinLimit polls), set *err and return on timeout.
+// Pipelined strip Gauss-Seidel: the same ordering as k_gs_strips in one launch
+// and without grid barriers.  The work is cut into units (iteration it, strip s),
+// numbered iteration by iteration with the even strips before the odd ones, which
+// is a topological order of their dependencies: an even strip at iteration it
+// needs its odd neighbours to have completed it iterations, an odd strip needs its
+// even neighbours to have completed it + 1, and each strip needs its own previous
+// unit.  (That is the sequential order's dependency, and it also keeps a strip from
+// overwriting rows a neighbour has not read yet.)  Blocks take units from a ticket
+// counter in that order, so a unit only ever waits for units already taken by
+// running blocks: the kernel needs no co-residency, runs with any grid size and
+// alongside any other work on the device.  Per-strip counters of completed
+// iterations carry the dependencies (release / acquire).  A block stages the
+// strip's rows of S, 1/S_ii and g while it waits, then the dp halo.  Waits are
+// bounded (kSpinLimit polls), set *err and return on timeout.
 __device__ __forceinline__ int ld_acquire(const int* p) {
   int v;
   asm volatile("ld.acquire.gpu.global.b32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
@@ -413,6 +384,8 @@ __device__ __forceinline__ void st_release(int* p, int v) {
   asm volatile("st.release.gpu.global.b32 [%0], %1;\n" ::"l"(p), "r"(v) : "memory");
 }
 
+// done[0..nstrips) are the per-strip counters and done[nstrips] the ticket
+// counter; all are zero at launch, and dp is zero.
 template <typename T, int K, int G, int V>
 __global__ void __launch_bounds__(kGsPipeBlock) k_gs_pipe(LevelView<T> L, const T* __restrict__ g, T* dp, GsStrips P,
                                                       const int* __restrict__ ci_rel, int* done, int* err) {
@@ -426,62 +399,75 @@ __global__ void __launch_bounds__(kGsPipeBlock) k_gs_pipe(LevelView<T> L, const 
   int* s_rp = reinterpret_cast<int*>(s_v + (P.stage == 2 ? P.max_strip_nnz : 0));
   int* s_perm = s_rp + P.T + 1;
   int* s_ci = s_perm + P.T;
-  __shared__ int s_fail;
+  __shared__ int s_fail, s_unit;
   __shared__ int s_so[kMaxColors + 1];  // this strip's color offsets (sorted rows)
   constexpr int KV = K / V;
   constexpr int kGroup = KV * G;
   const int k = (threadIdx.x % KV) * V;
   const int lane = (threadIdx.x / KV) % G;
   const unsigned mask = group_mask<kGroup>();
-  const int s = blockIdx.x;
-  if (s >= P.nstrips) return;
   const int n_p = L.n_p;
-  const int r_lo = s * P.T, r_hi = min(r_lo + P.T, n_p);
-  const int h_lo = max(0, r_lo - P.T), h_hi = min(n_p, r_hi + P.T);
-  const int* so_g = P.soff + (size_t)s * (P.ncol + 1);
-  for (int t = threadIdx.x; t <= P.ncol; t += blockDim.x) s_so[t] = so_g[t];
-  const int* so = s_so;
-  const int q0 = so_g[0], q1 = so_g[P.ncol];
-  const int e0 = L.S.rp[q0], e1 = L.S.rp[q1];
-  // stage the strip once
-  if (threadIdx.x == 0) s_fail = 0;
-  for (int t = threadIdx.x; t < (h_hi - h_lo) * K; t += blockDim.x) s_dp[t] = T(0);
-  stage_copy<false>(s_g, g + (size_t)r_lo * K, (r_hi - r_lo) * K);
-  stage_copy<false>(s_dinv, L.S_dinv + q0, q1 - q0);
-  stage_copy<false>(s_perm, L.S_perm + q0, q1 - q0);
-  stage_copy<false>(s_rp, L.S.rp + q0, q1 - q0 + 1);
-  if (P.stage == 2) {
-    stage_copy<false>(s_v, L.S.v + e0, e1 - e0);
-    stage_copy<false>(s_ci, ci_rel + e0, e1 - e0);
-  }
-  cp_async_wait_all();
-  __syncthreads();
-  const int par = s & 1;
-  for (int it = 0; it < P.iters; ++it) {
-    const int need = par == 0 ? it : it + 1;
-    if (need > 0) {
-      if (threadIdx.x == 0) {
-        for (int nb = s - 1; nb <= s + 1; nb += 2) {
-          if (nb < 0 || nb >= P.nstrips) continue;
-          unsigned long long spins = 0;
-          while (ld_acquire(done + nb) < need) {
-            if (++spins > kSpinLimit || *(volatile int*)err) {
-              atomicExch(err, 1);
-              s_fail = 1;
-              break;
-            }
-            __nanosleep(32);
-          }
-        }
-      }
-      __syncthreads();
-      if (s_fail) return;
-      // neighbour rows of the halo, as the neighbours last wrote them (through L2)
-      stage_copy<true>(s_dp, dp + (size_t)h_lo * K, (r_lo - h_lo) * K);
-      stage_copy<true>(s_dp + (size_t)(r_hi - h_lo) * K, dp + (size_t)r_hi * K, (h_hi - r_hi) * K);
-      cp_async_wait_all();
-      __syncthreads();
+  const int nunits = P.iters * P.nstrips;
+  const int n_even = (P.nstrips + 1) / 2;
+  int* ticket = done + P.nstrips;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      s_unit = atomicAdd(ticket, 1);
+      s_fail = 0;
     }
+    __syncthreads();
+    const int u = s_unit;
+    if (u >= nunits) return;
+    const int it = u / P.nstrips, w = u - it * P.nstrips;
+    const int s = w < n_even ? 2 * w : 2 * (w - n_even) + 1;
+    const int par = s & 1;
+    const int r_lo = s * P.T, r_hi = min(r_lo + P.T, n_p);
+    const int h_lo = max(0, r_lo - P.T), h_hi = min(n_p, r_hi + P.T);
+    const int* so_g = P.soff + (size_t)s * (P.ncol + 1);
+    for (int t = threadIdx.x; t <= P.ncol; t += blockDim.x) s_so[t] = so_g[t];
+    const int q0 = so_g[0], q1 = so_g[P.ncol];
+    const int e0 = L.S.rp[q0], e1 = L.S.rp[q1];
+    // data no other unit writes, in flight while this unit waits
+    stage_copy<false>(s_g, g + (size_t)r_lo * K, (r_hi - r_lo) * K);
+    stage_copy<false>(s_dinv, L.S_dinv + q0, q1 - q0);
+    stage_copy<false>(s_perm, L.S_perm + q0, q1 - q0);
+    stage_copy<false>(s_rp, L.S.rp + q0, q1 - q0 + 1);
+    if (P.stage == 2) {
+      stage_copy<false>(s_v, L.S.v + e0, e1 - e0);
+      stage_copy<false>(s_ci, ci_rel + e0, e1 - e0);
+    }
+    const int need_nb = par == 0 ? it : it + 1;
+    if (threadIdx.x == 0) {
+      for (int nb = s - 1; nb <= s + 1; ++nb) {
+        const int need = nb == s ? it : need_nb;
+        if (nb < 0 || nb >= P.nstrips || need == 0) continue;
+        unsigned long long spins = 0;
+        while (ld_acquire(done + nb) < need) {
+          if (++spins > kSpinLimit || *(volatile int*)err) {
+            atomicExch(err, 1);
+            s_fail = 1;
+            break;
+          }
+          __nanosleep(32);
+        }
+        if (s_fail) break;
+      }
+    }
+    __syncthreads();
+    if (s_fail) {
+      cp_async_wait_all();
+      return;
+    }
+    if (need_nb == 0) {
+      // first unit of an even strip: dp is still zero around it
+      for (int t = threadIdx.x; t < (h_hi - h_lo) * K; t += blockDim.x) s_dp[t] = T(0);
+    } else {
+      // the halo and this strip's rows as last written (through L2)
+      stage_copy<true>(s_dp, dp + (size_t)h_lo * K, (h_hi - h_lo) * K);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    const int* so = s_so;
     for (int pc = 0; pc < P.ncol; ++pc) {
       const int ra = so[pc], rb = so[pc + 1];
       for (int t = threadIdx.x; t < (rb - ra) * kGroup; t += blockDim.x) {
@@ -517,7 +503,7 @@ __global__ void __launch_bounds__(kGsPipeBlock) k_gs_pipe(LevelView<T> L, const 
           // V right-hand sides per thread, G == 1: two independent partial sums per column
           T a[V], b2[V];
 #pragma unroll
-          for (int u = 0; u < V; ++u) a[u] = b2[u] = T(0);
+          for (int uu = 0; uu < V; ++uu) a[uu] = b2[uu] = T(0);
           const T* sv = P.stage == 2 ? s_v - e0 : L.S.v;
           const int* sc = P.stage == 2 ? s_ci - e0 : ci_rel;
           int e = ea;
@@ -528,19 +514,19 @@ __global__ void __launch_bounds__(kGsPipeBlock) k_gs_pipe(LevelView<T> L, const 
             vld<T, V>(d0, s_dp + c0 * K + k);
             vld<T, V>(d1, s_dp + c1 * K + k);
 #pragma unroll
-            for (int u = 0; u < V; ++u) {
-              a[u] += v0 * d0[u];
-              b2[u] += v1 * d1[u];
+            for (int uu = 0; uu < V; ++uu) {
+              a[uu] += v0 * d0[uu];
+              b2[uu] += v1 * d1[uu];
             }
           }
           if (e < eb) {
             T d0[V];
             vld<T, V>(d0, s_dp + sc[e] * K + k);
 #pragma unroll
-            for (int u = 0; u < V; ++u) a[u] += sv[e] * d0[u];
+            for (int uu = 0; uu < V; ++uu) a[uu] += sv[e] * d0[uu];
           }
 #pragma unroll
-          for (int u = 0; u < V; ++u) acc[u] = a[u] + b2[u];
+          for (int uu = 0; uu < V; ++uu) acc[uu] = a[uu] + b2[uu];
         }
         if (lane == 0) {
           const int i = s_perm[r - q0];
@@ -548,7 +534,7 @@ __global__ void __launch_bounds__(kGsPipeBlock) k_gs_pipe(LevelView<T> L, const 
           T gv[V], out[V];
           vld<T, V>(gv, s_g + (size_t)(i - r_lo) * K + k);
 #pragma unroll
-          for (int u = 0; u < V; ++u) out[u] = (gv[u] - acc[u]) * di;
+          for (int uu = 0; uu < V; ++uu) out[uu] = (gv[uu] - acc[uu]) * di;
           vst<T, V>(s_dp + (size_t)(i - h_lo) * K + k, out);
         }
       }

@@ -11,9 +11,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/emin_amg.h"
-#include "setup.hpp"
-#include "vcycle.cuh"
+#include "hierarchy.hpp"
 
 using namespace emin;
 
@@ -24,12 +22,6 @@ thread_local std::string g_last_error;
 amg_status fail(amg_status st, const std::string& msg) {
   g_last_error = msg;
   return st;
-}
-
-int round_k(int nrhs) {
-  int K = 1;
-  while (K < nrhs) K <<= 1;
-  return K;
 }
 
 // ---------------------------------------------------------------------------
@@ -152,18 +144,6 @@ __global__ void k_reorth_check(int K, double* __restrict__ slot, const double* _
   if (threadIdx.x == 0) *flag = any;
 }
 
-struct GmresState {
-  double* Hm;   // (m+1) x m x K upper Hessenberg, rotated
-  double* cs;   // m x K
-  double* sn;   // m x K
-  double* gv;   // (m+1) x K
-  int* active;  // K
-  int* jcount;  // K: basis vectors used in this cycle
-  int* budget;  // K: iterations left for the column
-  int* flags;   // K: 1 converged (recurrence), 2 breakdown
-  double* resest;  // K
-};
-
 // Column j of the Hessenberg matrix for every rhs: apply the previous Givens
 // rotations, form the new one, update the residual recurrence, retire
 // columns that converged, broke down or ran out of iterations.
@@ -238,229 +218,380 @@ __global__ void __launch_bounds__(kBlock) k_update_x(long long NK, int nz, const
 }
 
 // ---------------------------------------------------------------------------
+// Workspace carving: the same walk counts the bytes (Krylov::bytes_for) and
+// allocates them (Krylov::init), so the two always agree.
 
-template <typename U>
-U* dev_alloc(size_t n, std::vector<void*>& list) {
-  void* p = nullptr;
-  cudaError_t e = cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(U));
-  if (e != cudaSuccess) throw std::runtime_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
-  list.push_back(p);
-  return (U*)p;
+struct Carver {
+  bool count_only = true;
+  size_t total = 0;
+  std::vector<void*>* list = nullptr;
+  template <typename U>
+  U* get(size_t n) {
+    const size_t b = (std::max<size_t>(n, 1) * sizeof(U) + 255) / 256 * 256;
+    total += b;
+    if (count_only) return nullptr;
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, b);
+    if (e != cudaSuccess) throw std::runtime_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    list->push_back(p);
+    return (U*)p;
+  }
+};
+
+void carve(Krylov& w, Carver& c) {
+  const size_t NK = (size_t)w.N * w.K, K = w.K, m = w.m;
+  w.V = c.get<double>(NK * (m + 1));
+  w.Z = w.f32 ? (void*)c.get<float>(NK * m) : (void*)c.get<double>(NK * m);
+  w.w = c.get<double>(NK);
+  w.bK = c.get<double>(NK);
+  w.xK = c.get<double>(NK);
+  w.rK = c.get<double>(NK);
+  w.hbuf = c.get<double>((m + 2) * K);
+  w.part = c.get<double>((size_t)kRedBlocks * (m + 2) * K);
+  w.y = c.get<double>((m + 1) * K);
+  w.bnorm = c.get<double>(K);
+  w.rnorm = c.get<double>(K);
+  w.st.Hm = c.get<double>((m + 1) * m * K);
+  w.st.cs = c.get<double>(m * K);
+  w.st.sn = c.get<double>(m * K);
+  w.st.gv = c.get<double>((m + 1) * K);
+  w.st.active = c.get<int>(K);
+  w.st.jcount = c.get<int>(K);
+  w.st.budget = c.get<int>(K);
+  w.st.flags = c.get<int>(K);
+  w.st.resest = c.get<double>(K);
+  w.n_active = c.get<int>(1);
+  w.reorth = c.get<int>(1);
 }
 
 }  // namespace
 
-struct amg_hierarchy {
-  std::vector<HostLevel> host;
-  amg_params prm{};
-  VCycleIface* v64 = nullptr;
-  VCycleIface* v32 = nullptr;
-  long long N = 0;
-  // FGMRES workspace, sized for (ws_K, ws_m)
-  int ws_K = 0, ws_m = 0;
-  std::vector<void*> ws;
-  double *V = nullptr, *w = nullptr, *bK = nullptr, *xK = nullptr, *rK = nullptr;
-  void* Z = nullptr;
-  double *hbuf = nullptr, *part = nullptr, *y = nullptr, *bnorm = nullptr, *rnorm = nullptr;
-  GmresState st{};
-  int* n_active = nullptr;
-  int* reorth = nullptr;     // device flag: the current Arnoldi step needs a second pass
-  int* host_i = nullptr;     // pinned
-  double* host_d = nullptr;  // pinned
-  void* stage_b = nullptr;   // device copies for amg_fgmres_solve_host
-  void* stage_x = nullptr;
-  long long launches = 0;    // kernels launched by this file's code (the V-cycles count their own)
+namespace emin {
 
-  VCycleIface* vc() { return prm.vcycle_fp32 ? v32 : v64; }
+int round_k(int nrhs) {
+  int K = 1;
+  while (K < nrhs) K <<= 1;
+  return K;
+}
 
-  void free_ws() {
-    for (void* p : ws) cudaFree(p);
-    ws.clear();
-    ws_K = ws_m = 0;
+size_t Krylov::bytes_for(long long N, int K, int m, bool f32) {
+  Krylov w;
+  w.N = N;
+  w.K = K;
+  w.m = m;
+  w.f32 = f32;
+  Carver c;
+  carve(w, c);
+  return c.total;
+}
+
+void Krylov::init(long long N_, int K_, int m_, bool f32_) {
+  release();
+  N = N_;
+  K = K_;
+  m = m_;
+  f32 = f32_;
+  Carver c;
+  c.count_only = false;
+  c.list = &mem;
+  try {
+    carve(*this, c);
+    bytes = c.total;
+    if (cudaMallocHost(&host_i, sizeof(int) * kHostInts) != cudaSuccess ||
+        cudaMallocHost(&host_d, sizeof(double) * kHostDoubles) != cudaSuccess)
+      throw std::runtime_error("cudaMallocHost for the solver's pinned words failed");
+  } catch (...) {
+    release();
+    throw;
   }
-  ~amg_hierarchy() {
-    free_ws();
-    if (host_i) cudaFreeHost(host_i);
-    if (host_d) cudaFreeHost(host_d);
-    if (stage_b) cudaFree(stage_b);
-    if (stage_x) cudaFree(stage_x);
-    delete v64;
-    delete v32;
+}
+
+void Krylov::release() {
+  for (void* p : mem) cudaFree(p);
+  mem.clear();
+  if (host_i) cudaFreeHost(host_i);
+  if (host_d) cudaFreeHost(host_d);
+  host_i = nullptr;
+  host_d = nullptr;
+  bytes = 0;
+  K = m = 0;
+}
+
+namespace fgmres_detail {
+
+// Norms of the K columns of an N x K FP64 block into out[k] (deterministic).
+template <int K>
+void col_norms(const Krylov& w, const double* v, double* out, cudaStream_t s, long long& launches) {
+  const long long NK = w.N * K;
+  k_mdot_partial<K, double><<<kRedBlocks, kBlock, 0, s>>>(NK, 1, 0, v, v, w.part, nullptr);
+  k_reduce_partials<<<(K * 32 + 127) / 128, 128, 0, s>>>(kRedBlocks, K, w.part, out, 0, 1, nullptr);
+  launches += 2;
+}
+
+// Restarted flexible GMRES for K interleaved columns, one chunk per advance():
+//   start       b -> bK (packed), x = 0, |b| per column      -> host
+//   cycle begin r0 / |r0| into V_0 for the columns still running
+//   step j      z_j = M^-1 v_j (V-cycle graph), w = A z_j, classical Gram-Schmidt
+//               with selective second pass, Givens update   -> host: columns active
+//   cycle end   x += Z y, r = b - A x in FP64, |r|           -> host
+//   finish      x unpacked into the caller's layout (and copied to the host)
+template <int K, typename TZ>
+class FgmresTask final : public SolveTask {
+ public:
+  FgmresTask(amg_hierarchy_core* h, VCycleIface* vc, Krylov* ws, const double* b, double* x, const double* bh,
+             double* xh, int nrhs, double rtol, int restart, int maxit, cudaStream_t s)
+      : h_(h), vc_(vc), w_(ws), b_(b), x_(x), bh_(bh), xh_(xh), nrhs_(nrhs), restart_(restart), maxit_(maxit),
+        rtol_(rtol), s_(s), N_(h->N), NK_(h->N * K), gNK_(grid_for(h->N * K)), bn_(K, 0.0), rel_(K, 0.0),
+        total_(K, 0), done_(K, 0), flag_(K, 0) {}
+
+  bool advance() override {
+    switch (phase_) {
+      case kStart:
+        start();
+        phase_ = kNorms;
+        return true;
+      case kNorms:
+        for (int k = 0; k < K; ++k) {
+          bn_[k] = w_->host_d[k];
+          if (k >= nrhs_ || bn_[k] == 0.0) done_[k] = 1;
+        }
+        if (!any_left()) return finish();
+        begin_cycle();
+        step();
+        phase_ = kStep;
+        return true;
+      case kStep:
+        if (w_->host_i[1] != 0) throw std::runtime_error("cuda: a Gauss-Seidel wait timed out");
+        if (w_->host_i[0] == 0) {
+          ++j_;
+          end_cycle();
+          return true;
+        }
+        k_scale<K><<<gNK_, kBlock, 0, s_>>>(NK_, w_->w, w_->hbuf + (size_t)(j_ + 1) * K, w_->st.active,
+                                            w_->V + (size_t)(j_ + 1) * NK_);
+        ++launches;
+        ++j_;
+        if (j_ < restart_) {
+          step();
+          return true;
+        }
+        end_cycle();
+        return true;
+      case kCycle: {
+        bool left = false;
+        for (int k = 0; k < K; ++k) {
+          if (done_[k]) continue;
+          const int used = w_->host_i[k];
+          total_[k] += used;
+          rel_[k] = w_->host_d[k] / bn_[k];
+          if (w_->host_i[64 + k] == 2 && rel_[k] > rtol_) flag_[k] = 2;
+          if (rel_[k] <= rtol_ || total_[k] >= maxit_ || flag_[k] == 2 || used == 0)
+            done_[k] = 1;
+          else
+            left = true;
+        }
+        if (!left) return finish();
+        begin_cycle();
+        step();
+        phase_ = kStep;
+        return true;
+      }
+      case kFinish:
+        phase_ = kDone;
+        return false;
+      case kDone:
+        return false;
+    }
+    return false;
   }
+
+  amg_status result(int* iters, double* relres) const override {
+    amg_status st = AMG_OK;
+    for (int k = 0; k < nrhs_; ++k) {
+      if (iters) iters[k] = total_[k];
+      if (relres) relres[k] = bn_[k] == 0.0 ? 0.0 : rel_[k];
+      if (bn_[k] != 0.0 && rel_[k] > rtol_) st = flag_[k] == 2 ? AMG_BREAKDOWN : AMG_NOT_CONVERGED;
+    }
+    return st;
+  }
+
+ private:
+  enum Phase { kStart, kNorms, kStep, kCycle, kFinish, kDone };
+
+  bool any_left() const {
+    return std::any_of(done_.begin(), done_.end(), [](int d) { return !d; });
+  }
+
+  void start() {
+    if (bh_)
+      EMIN_CUDA(cudaMemcpyAsync(const_cast<double*>(b_), bh_, sizeof(double) * N_ * nrhs_, cudaMemcpyHostToDevice, s_));
+    k_pack<double, double, K><<<gNK_, kBlock, 0, s_>>>(N_, b_, nrhs_, nrhs_, w_->bK);
+    ++launches;
+    EMIN_CUDA(cudaMemsetAsync(w_->xK, 0, sizeof(double) * NK_, s_));
+    col_norms<K>(*w_, w_->bK, w_->bnorm, s_, launches);
+    EMIN_CUDA(cudaMemcpyAsync(w_->host_d, w_->bnorm, sizeof(double) * K, cudaMemcpyDeviceToHost, s_));
+    // r = b for the first cycle
+    EMIN_CUDA(cudaMemcpyAsync(w_->rK, w_->bK, sizeof(double) * NK_, cudaMemcpyDeviceToDevice, s_));
+  }
+
+  // Start vector v0 = r / |r| for the columns still running; g = (|r|, 0, ...).
+  void begin_cycle() {
+    int* act = w_->host_i + 128;
+    int* bud = w_->host_i + 192;
+    for (int k = 0; k < K; ++k) {
+      act[k] = !done_[k];
+      bud[k] = std::min(restart_, maxit_ - total_[k]);
+      if (bud[k] <= 0) act[k] = 0;
+    }
+    EMIN_CUDA(cudaMemcpyAsync(w_->st.active, act, sizeof(int) * K, cudaMemcpyHostToDevice, s_));
+    EMIN_CUDA(cudaMemcpyAsync(w_->st.budget, bud, sizeof(int) * K, cudaMemcpyHostToDevice, s_));
+    EMIN_CUDA(cudaMemsetAsync(w_->st.jcount, 0, sizeof(int) * K, s_));
+    EMIN_CUDA(cudaMemsetAsync(w_->st.flags, 0, sizeof(int) * K, s_));
+    EMIN_CUDA(cudaMemsetAsync(w_->st.gv, 0, sizeof(double) * (restart_ + 1) * K, s_));
+    col_norms<K>(*w_, w_->rK, w_->rnorm, s_, launches);
+    EMIN_CUDA(cudaMemcpyAsync(w_->st.gv, w_->rnorm, sizeof(double) * K, cudaMemcpyDeviceToDevice, s_));
+    k_scale<K><<<gNK_, kBlock, 0, s_>>>(NK_, w_->rK, w_->rnorm, w_->st.active, w_->V);
+    ++launches;
+    j_ = 0;
+  }
+
+  void step() {
+    const int j = j_;
+    double* Vj = w_->V + (size_t)j * NK_;
+    TZ* Z = (TZ*)w_->Z;
+    // z_j = M^-1 v_j through the captured V-cycle
+    k_pack<double, TZ, K><<<gNK_, kBlock, 0, s_>>>(N_, Vj, K, K, (TZ*)vc_->input(0));
+    ++launches;
+    EMIN_CUDA(cudaGetLastError());
+    EMIN_CUDA(vc_->run(K, s_));
+    EMIN_CUDA(cudaMemcpyAsync(Z + (size_t)j * NK_, vc_->output(0), sizeof(TZ) * NK_, cudaMemcpyDeviceToDevice, s_));
+    // w = A z_j in FP64
+    if (vc_->is_fp32()) {
+      EMIN_CUDA(vc_->apply_ff((const float*)(Z + (size_t)j * NK_), w_->w, K, s_));
+    } else {
+      EMIN_CUDA(apply_finest_f64(h_->v64, Z + (size_t)j * NK_, false, nullptr, w_->w, K, s_));
+      ++launches;
+    }
+    // classical Gram-Schmidt, re-orthogonalised only when the first pass cancelled
+    // more than half of |w| (k_reorth_check)
+    const int nv = j + 1;
+    double* hn = w_->hbuf + (size_t)nv * K;  // |w|^2, then the norm of the new vector
+    double* h2 = w_->y;                      // scratch for the correction coefficients
+    const unsigned r1 = (unsigned)((K * 32 + 127) / 128), rnv = (unsigned)((nv * K * 32 + 127) / 128);
+    k_mdot_partial<K, double><<<kRedBlocks, kBlock, 0, s_>>>(NK_, nv, 1, w_->V, w_->w, w_->part, nullptr);
+    k_reduce_partials<<<((nv + 1) * K * 32 + 127) / 128, 128, 0, s_>>>(kRedBlocks, (nv + 1) * K, w_->part, w_->hbuf,
+                                                                        0, 0, nullptr);
+    k_maxpy<K, double><<<kRedBlocks, kBlock, 0, s_>>>(NK_, nv, w_->V, w_->hbuf, w_->w, w_->part, nullptr);
+    k_reduce_partials<<<r1, 128, 0, s_>>>(kRedBlocks, K, w_->part, w_->rnorm, 0, 1, nullptr);
+    k_reorth_check<<<1, 32, 0, s_>>>(K, hn, w_->rnorm, w_->st.active, w_->reorth);
+    k_mdot_partial<K, double><<<kRedBlocks, kBlock, 0, s_>>>(NK_, nv, 0, w_->V, w_->w, w_->part, w_->reorth);
+    k_reduce_partials<<<rnv, 128, 0, s_>>>(kRedBlocks, nv * K, w_->part, h2, 0, 0, w_->reorth);
+    k_maxpy<K, double><<<kRedBlocks, kBlock, 0, s_>>>(NK_, nv, w_->V, h2, w_->w, w_->part, w_->reorth);
+    k_reduce_partials<<<r1, 128, 0, s_>>>(kRedBlocks, K, w_->part, hn, 0, 1, w_->reorth);
+    k_reduce_partials<<<rnv, 128, 0, s_>>>(1, nv * K, h2, w_->hbuf, 1, 0, w_->reorth);
+    k_givens<<<1, 32, 0, s_>>>(j, restart_, K, w_->hbuf, w_->st, w_->bnorm, rtol_, w_->n_active);
+    launches += 11;
+    EMIN_CUDA(cudaGetLastError());
+    EMIN_CUDA(cudaMemcpyAsync(w_->host_i, w_->n_active, sizeof(int), cudaMemcpyDeviceToHost, s_));
+    EMIN_CUDA(cudaMemcpyAsync(w_->host_i + 1, vc_->error_flag(), sizeof(int), cudaMemcpyDeviceToHost, s_));
+  }
+
+  // x += Z y with y from the triangular systems; true residual r = b - A x in FP64.
+  void end_cycle() {
+    const int nmax = std::min(j_, restart_);
+    k_solve_y<<<1, 32, 0, s_>>>(restart_, K, w_->st, w_->y, nmax);
+    k_update_x<K, TZ><<<gNK_, kBlock, 0, s_>>>(NK_, nmax, (const TZ*)w_->Z, w_->y, w_->xK);
+    launches += 2;
+    EMIN_CUDA(apply_finest_f64(h_->v64, w_->xK, false, w_->bK, w_->rK, K, s_));
+    ++launches;
+    col_norms<K>(*w_, w_->rK, w_->rnorm, s_, launches);
+    EMIN_CUDA(cudaMemcpyAsync(w_->host_d, w_->rnorm, sizeof(double) * K, cudaMemcpyDeviceToHost, s_));
+    EMIN_CUDA(cudaMemcpyAsync(w_->host_i, w_->st.jcount, sizeof(int) * K, cudaMemcpyDeviceToHost, s_));
+    EMIN_CUDA(cudaMemcpyAsync(w_->host_i + 64, w_->st.flags, sizeof(int) * K, cudaMemcpyDeviceToHost, s_));
+    phase_ = kCycle;
+  }
+
+  bool finish() {
+    k_unpack<double, double, K><<<grid_for(N_ * nrhs_), kBlock, 0, s_>>>(N_, w_->xK, nrhs_, x_, nrhs_);
+    ++launches;
+    EMIN_CUDA(cudaGetLastError());
+    if (xh_) EMIN_CUDA(cudaMemcpyAsync(xh_, x_, sizeof(double) * N_ * nrhs_, cudaMemcpyDeviceToHost, s_));
+    phase_ = kFinish;
+    return true;
+  }
+
+  amg_hierarchy_core* h_;
+  VCycleIface* vc_;
+  Krylov* w_;
+  const double* b_;
+  double* x_;
+  const double* bh_;
+  double* xh_;
+  int nrhs_, restart_, maxit_;
+  double rtol_;
+  cudaStream_t s_;
+  long long N_, NK_;
+  unsigned gNK_;
+  std::vector<double> bn_, rel_;
+  std::vector<int> total_, done_, flag_;
+  Phase phase_ = kStart;
+  int j_ = 0;
 };
+
+template <typename TZ>
+std::unique_ptr<SolveTask> make_task_t(int K, amg_hierarchy_core* h, VCycleIface* vc, Krylov* ws, const double* b,
+                                       double* x, const double* bh, double* xh, int nrhs, double rtol, int restart,
+                                       int maxit, cudaStream_t s) {
+  switch (K) {
+    case 1: return std::make_unique<FgmresTask<1, TZ>>(h, vc, ws, b, x, bh, xh, nrhs, rtol, restart, maxit, s);
+    case 2: return std::make_unique<FgmresTask<2, TZ>>(h, vc, ws, b, x, bh, xh, nrhs, rtol, restart, maxit, s);
+    case 4: return std::make_unique<FgmresTask<4, TZ>>(h, vc, ws, b, x, bh, xh, nrhs, rtol, restart, maxit, s);
+    case 8: return std::make_unique<FgmresTask<8, TZ>>(h, vc, ws, b, x, bh, xh, nrhs, rtol, restart, maxit, s);
+    case 16: return std::make_unique<FgmresTask<16, TZ>>(h, vc, ws, b, x, bh, xh, nrhs, rtol, restart, maxit, s);
+    case 32: return std::make_unique<FgmresTask<32, TZ>>(h, vc, ws, b, x, bh, xh, nrhs, rtol, restart, maxit, s);
+  }
+  throw std::runtime_error("nrhs must be in 1..32");
+}
+
+}  // namespace fgmres_detail
+
+std::unique_ptr<SolveTask> make_solve_task(amg_hierarchy_core* h, VCycleIface* vc, Krylov* ws, const double* b,
+                                           double* x, const double* b_host, double* x_host, int nrhs, double rtol,
+                                           int restart, int maxit, cudaStream_t s) {
+  const int K = round_k(nrhs);
+  if (nrhs < 1 || K > 32 || K > vc->kmax()) throw std::runtime_error("nrhs exceeds the V-cycle's max_nrhs");
+  if (ws->N != h->N || ws->K != K || ws->m < restart || ws->f32 != vc->is_fp32())
+    throw std::runtime_error("solver workspace does not match the solve");
+  using fgmres_detail::make_task_t;
+  if (vc->is_fp32()) return make_task_t<float>(K, h, vc, ws, b, x, b_host, x_host, nrhs, rtol, restart, maxit, s);
+  return make_task_t<double>(K, h, vc, ws, b, x, b_host, x_host, nrhs, rtol, restart, maxit, s);
+}
+
+}  // namespace emin
 
 namespace {
 
 void ensure_ws(amg_hierarchy* h, int K, int m) {
-  if (h->ws_K == K && h->ws_m >= m) return;
-  h->free_ws();
-  const size_t NK = (size_t)h->N * K;
   const bool f32 = h->prm.vcycle_fp32 != 0;
-  h->V = dev_alloc<double>(NK * (m + 1), h->ws);
-  h->Z = f32 ? (void*)dev_alloc<float>(NK * m, h->ws) : (void*)dev_alloc<double>(NK * m, h->ws);
-  h->w = dev_alloc<double>(NK, h->ws);
-  h->bK = dev_alloc<double>(NK, h->ws);
-  h->xK = dev_alloc<double>(NK, h->ws);
-  h->rK = dev_alloc<double>(NK, h->ws);
-  h->hbuf = dev_alloc<double>((size_t)(m + 2) * K, h->ws);
-  h->part = dev_alloc<double>((size_t)kRedBlocks * (m + 2) * K, h->ws);
-  h->y = dev_alloc<double>((size_t)(m + 1) * K, h->ws);
-  h->bnorm = dev_alloc<double>(K, h->ws);
-  h->rnorm = dev_alloc<double>(K, h->ws);
-  h->st.Hm = dev_alloc<double>((size_t)(m + 1) * m * K, h->ws);
-  h->st.cs = dev_alloc<double>((size_t)m * K, h->ws);
-  h->st.sn = dev_alloc<double>((size_t)m * K, h->ws);
-  h->st.gv = dev_alloc<double>((size_t)(m + 1) * K, h->ws);
-  h->st.active = dev_alloc<int>(K, h->ws);
-  h->st.jcount = dev_alloc<int>(K, h->ws);
-  h->st.budget = dev_alloc<int>(K, h->ws);
-  h->st.flags = dev_alloc<int>(K, h->ws);
-  h->st.resest = dev_alloc<double>(K, h->ws);
-  h->n_active = dev_alloc<int>(1, h->ws);
-  h->reorth = dev_alloc<int>(1, h->ws);
-  h->ws_K = K;
-  h->ws_m = m;
-  if (!h->host_i) EMIN_CUDA(cudaMallocHost(&h->host_i, 4 * 64 * sizeof(int)));
-  if (!h->host_d) EMIN_CUDA(cudaMallocHost(&h->host_d, 4 * 64 * sizeof(double)));
+  if (h->kry && h->kry->K == K && h->kry->m >= m && h->kry->f32 == f32) return;
+  h->kry.reset();
+  auto w = std::make_unique<Krylov>();
+  w->init(h->N, K, m, f32);
+  h->kry = std::move(w);
 }
 
-// Norms of the K columns of an N x K FP64 block into out[k] (deterministic).
-template <int K>
-void col_norms(amg_hierarchy* h, const double* v, double* out, cudaStream_t s) {
-  const long long NK = h->N * K;
-  k_mdot_partial<K, double><<<kRedBlocks, kBlock, 0, s>>>(NK, 1, 0, v, v, h->part, nullptr); ++h->launches;
-  k_reduce_partials<<<(K * 32 + 127) / 128, 128, 0, s>>>(kRedBlocks, K, h->part, out, 0, 1, nullptr); ++h->launches;
-}
-
-template <int K, typename TZ>
-amg_status fgmres_k(amg_hierarchy* h, const double* b, double* x, int nrhs, double rtol, int restart, int maxit,
-                    int* iters, double* relres, cudaStream_t s) {
-  const long long N = h->N, NK = N * K;
-  ensure_ws(h, K, restart);
-  VCycleIface* vc = h->vc();
-  const bool f32 = vc->is_fp32();
-  const unsigned gNK = grid_for(NK);
-  // b (user layout) -> bK; x = 0
-  k_pack<double, double, K><<<gNK, kBlock, 0, s>>>(N, b, nrhs, nrhs, h->bK); ++h->launches;
-  EMIN_CUDA(cudaMemsetAsync(h->xK, 0, sizeof(double) * NK, s));
-  col_norms<K>(h, h->bK, h->bnorm, s);
-  EMIN_CUDA(cudaMemcpyAsync(h->host_d, h->bnorm, sizeof(double) * K, cudaMemcpyDeviceToHost, s));
-  EMIN_CUDA(cudaStreamSynchronize(s));
-  std::vector<double> bn(h->host_d, h->host_d + K);
-  std::vector<int> total(K, 0), done(K, 0), flag(K, 0);
-  std::vector<double> rel(K, 0.0);
-  for (int k = 0; k < K; ++k)
-    if (k >= nrhs || bn[k] == 0.0) done[k] = 1;
-  // r = b for the first cycle
-  EMIN_CUDA(cudaMemcpyAsync(h->rK, h->bK, sizeof(double) * NK, cudaMemcpyDeviceToDevice, s));
-  TZ* Z = (TZ*)h->Z;
-  bool any_left = std::any_of(done.begin(), done.end(), [](int d) { return !d; });
-  while (any_left) {
-    // start vector v0 = r / ||r|| for the columns still running; g = (||r||, 0, ...)
-    std::vector<int> act(K), bud(K);
-    for (int k = 0; k < K; ++k) {
-      act[k] = !done[k];
-      bud[k] = std::min(restart, maxit - total[k]);
-      if (bud[k] <= 0) act[k] = 0;
-    }
-    EMIN_CUDA(cudaMemcpyAsync(h->st.active, act.data(), sizeof(int) * K, cudaMemcpyHostToDevice, s));
-    EMIN_CUDA(cudaMemcpyAsync(h->st.budget, bud.data(), sizeof(int) * K, cudaMemcpyHostToDevice, s));
-    EMIN_CUDA(cudaMemsetAsync(h->st.jcount, 0, sizeof(int) * K, s));
-    EMIN_CUDA(cudaMemsetAsync(h->st.flags, 0, sizeof(int) * K, s));
-    EMIN_CUDA(cudaMemsetAsync(h->st.gv, 0, sizeof(double) * (restart + 1) * K, s));
-    col_norms<K>(h, h->rK, h->rnorm, s);
-    EMIN_CUDA(cudaMemcpyAsync(h->st.gv, h->rnorm, sizeof(double) * K, cudaMemcpyDeviceToDevice, s));
-    k_scale<K><<<gNK, kBlock, 0, s>>>(NK, h->rK, h->rnorm, h->st.active, h->V); ++h->launches;
-    int j = 0;
-    for (; j < restart; ++j) {
-      double* Vj = h->V + (size_t)j * NK;
-      // z_j = M^-1 v_j through the captured V-cycle
-      k_pack<double, TZ, K><<<gNK, kBlock, 0, s>>>(N, Vj, K, K, (TZ*)vc->input(0)); ++h->launches;
-      EMIN_CUDA(cudaGetLastError());
-      EMIN_CUDA(vc->run(K, s));
-      EMIN_CUDA(cudaMemcpyAsync(Z + (size_t)j * NK, vc->output(0), sizeof(TZ) * NK, cudaMemcpyDeviceToDevice, s));
-      // w = A z_j in FP64
-      if (f32)
-        EMIN_CUDA(vc->apply_ff((const float*)(Z + (size_t)j * NK), h->w, K, s));
-      else {
-        EMIN_CUDA(apply_finest_f64(h->v64, Z + (size_t)j * NK, false, nullptr, h->w, K, s));
-        ++h->launches;
-      }
-      // classical Gram-Schmidt, re-orthogonalised only when the first pass cancelled
-      // more than half of |w| (k_reorth_check)
-      const int nv = j + 1;
-      double* hn = h->hbuf + (size_t)nv * K;  // |w|^2, then the norm of the new vector
-      double* h2 = h->y;                     // scratch for the correction coefficients
-      k_mdot_partial<K, double><<<kRedBlocks, kBlock, 0, s>>>(NK, nv, 1, h->V, h->w, h->part, nullptr); ++h->launches;
-      k_reduce_partials<<<((nv + 1) * K * 32 + 127) / 128, 128, 0, s>>>(kRedBlocks, (nv + 1) * K, h->part, h->hbuf, 0, 0,
-                                                                         nullptr); ++h->launches;
-      k_maxpy<K, double><<<kRedBlocks, kBlock, 0, s>>>(NK, nv, h->V, h->hbuf, h->w, h->part, nullptr); ++h->launches;
-      k_reduce_partials<<<(K * 32 + 127) / 128, 128, 0, s>>>(kRedBlocks, K, h->part, h->rnorm, 0, 1, nullptr); ++h->launches;
-      k_reorth_check<<<1, 32, 0, s>>>(K, hn, h->rnorm, h->st.active, h->reorth); ++h->launches;
-      k_mdot_partial<K, double><<<kRedBlocks, kBlock, 0, s>>>(NK, nv, 0, h->V, h->w, h->part, h->reorth); ++h->launches;
-      k_reduce_partials<<<(nv * K * 32 + 127) / 128, 128, 0, s>>>(kRedBlocks, nv * K, h->part, h2, 0, 0, h->reorth); ++h->launches;
-      k_maxpy<K, double><<<kRedBlocks, kBlock, 0, s>>>(NK, nv, h->V, h2, h->w, h->part, h->reorth); ++h->launches;
-      k_reduce_partials<<<(K * 32 + 127) / 128, 128, 0, s>>>(kRedBlocks, K, h->part, hn, 0, 1, h->reorth); ++h->launches;
-      k_reduce_partials<<<(nv * K * 32 + 127) / 128, 128, 0, s>>>(1, nv * K, h2, h->hbuf, 1, 0, h->reorth); ++h->launches;
-      k_givens<<<1, 32, 0, s>>>(j, restart, K, h->hbuf, h->st, h->bnorm, rtol, h->n_active); ++h->launches;
-      EMIN_CUDA(cudaGetLastError());
-      EMIN_CUDA(cudaMemcpyAsync(h->host_i, h->n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
-      EMIN_CUDA(cudaMemcpyAsync(h->host_i + 1, vc->error_flag(), sizeof(int), cudaMemcpyDeviceToHost, s));
-      EMIN_CUDA(cudaStreamSynchronize(s));
-      if (h->host_i[1] != 0) throw std::runtime_error("cuda: a Gauss-Seidel grid barrier timed out");
-      if (*h->host_i == 0) {
-        ++j;
-        break;
-      }
-      k_scale<K><<<gNK, kBlock, 0, s>>>(NK, h->w, h->hbuf + (size_t)nv * K, h->st.active, h->V + (size_t)(j + 1) * NK); ++h->launches;
-    }
-    const int nmax = std::min(j, restart);
-    // x += Z y with y from the triangular systems; true residual r = b - A x
-    k_solve_y<<<1, 32, 0, s>>>(restart, K, h->st, h->y, nmax); ++h->launches;
-    k_update_x<K, TZ><<<gNK, kBlock, 0, s>>>(NK, nmax, Z, h->y, h->xK); ++h->launches;
-    EMIN_CUDA(apply_finest_f64(h->v64, h->xK, false, h->bK, h->rK, K, s)); ++h->launches;
-    col_norms<K>(h, h->rK, h->rnorm, s);
-    EMIN_CUDA(cudaMemcpyAsync(h->host_d, h->rnorm, sizeof(double) * K, cudaMemcpyDeviceToHost, s));
-    EMIN_CUDA(cudaMemcpyAsync(h->host_i, h->st.jcount, sizeof(int) * K, cudaMemcpyDeviceToHost, s));
-    EMIN_CUDA(cudaMemcpyAsync(h->host_i + 64, h->st.flags, sizeof(int) * K, cudaMemcpyDeviceToHost, s));
+amg_status fgmres_blocking(amg_hierarchy* h, const double* b, double* x, const double* bh, double* xh, int nrhs,
+                           double rtol, int restart, int maxit, int* iters, double* relres, cudaStream_t s) {
+  ensure_ws(h, round_k(nrhs), restart);
+  auto task = make_solve_task(h, h->vc(), h->kry.get(), b, x, bh, xh, nrhs, rtol, restart, maxit, s);
+  bool more = true;
+  while (more) {
+    more = task->advance();
+    h->launches += task->launches;
+    task->launches = 0;
     EMIN_CUDA(cudaStreamSynchronize(s));
-    any_left = false;
-    for (int k = 0; k < K; ++k) {
-      if (done[k]) continue;
-      total[k] += h->host_i[k];
-      rel[k] = h->host_d[k] / bn[k];
-      if (h->host_i[64 + k] == 2 && rel[k] > rtol) flag[k] = 2;
-      if (rel[k] <= rtol || total[k] >= maxit || flag[k] == 2 || h->host_i[k] == 0) {
-        done[k] = 1;
-      } else {
-        any_left = true;
-      }
-    }
   }
-  k_unpack<double, double, K><<<grid_for(N * nrhs), kBlock, 0, s>>>(N, h->xK, nrhs, x, nrhs); ++h->launches;
-  EMIN_CUDA(cudaGetLastError());
-  EMIN_CUDA(cudaStreamSynchronize(s));
-  amg_status st = AMG_OK;
-  for (int k = 0; k < nrhs; ++k) {
-    if (iters) iters[k] = total[k];
-    if (relres) relres[k] = bn[k] == 0.0 ? 0.0 : rel[k];
-    if (bn[k] != 0.0 && rel[k] > rtol) st = flag[k] == 2 ? AMG_BREAKDOWN : AMG_NOT_CONVERGED;
-  }
-  return st;
-}
-
-template <typename TZ>
-amg_status fgmres_dispatch(amg_hierarchy* h, const double* b, double* x, int nrhs, double rtol, int restart,
-                           int maxit, int* iters, double* relres, cudaStream_t s) {
-  switch (round_k(nrhs)) {
-    case 1: return fgmres_k<1, TZ>(h, b, x, nrhs, rtol, restart, maxit, iters, relres, s);
-    case 2: return fgmres_k<2, TZ>(h, b, x, nrhs, rtol, restart, maxit, iters, relres, s);
-    case 4: return fgmres_k<4, TZ>(h, b, x, nrhs, rtol, restart, maxit, iters, relres, s);
-    case 8: return fgmres_k<8, TZ>(h, b, x, nrhs, rtol, restart, maxit, iters, relres, s);
-    case 16: return fgmres_k<16, TZ>(h, b, x, nrhs, rtol, restart, maxit, iters, relres, s);
-    case 32: return fgmres_k<32, TZ>(h, b, x, nrhs, rtol, restart, maxit, iters, relres, s);
-  }
-  return fail(AMG_ERR_ARG, "nrhs must be in 1..32");
+  return task->result(iters, relres);
 }
 
 template <int K, typename T>
@@ -489,10 +620,10 @@ void vcycle_dispatch(amg_hierarchy* h, const double* r, double* z, int nrhs, cud
 template <int K>
 void apply_k(amg_hierarchy* h, const double* x, double* y, int nrhs, cudaStream_t s) {
   const long long N = h->N;
-  k_pack<double, double, K><<<grid_for(N * K), kBlock, 0, s>>>(N, x, nrhs, nrhs, h->bK); ++h->launches;
+  k_pack<double, double, K><<<grid_for(N * K), kBlock, 0, s>>>(N, x, nrhs, nrhs, h->kry->bK); ++h->launches;
   EMIN_CUDA(cudaGetLastError());
-  EMIN_CUDA(apply_finest_f64(h->v64, h->bK, false, nullptr, h->w, K, s)); ++h->launches;
-  k_unpack<double, double, K><<<grid_for(N * nrhs), kBlock, 0, s>>>(N, h->w, nrhs, y, nrhs); ++h->launches;
+  EMIN_CUDA(apply_finest_f64(h->v64, h->kry->bK, false, nullptr, h->kry->w, K, s)); ++h->launches;
+  k_unpack<double, double, K><<<grid_for(N * nrhs), kBlock, 0, s>>>(N, h->kry->w, nrhs, y, nrhs); ++h->launches;
   EMIN_CUDA(cudaGetLastError());
 }
 
@@ -710,7 +841,7 @@ amg_status amg_apply(amg_handle h, const double* x, double* y, int nrhs, void* s
   if (!h->vc()) return fail(AMG_ERR_ARG, "hierarchy was built with host_only");
   if (nrhs < 1 || round_k(nrhs) > h->vc()->kmax()) return fail(AMG_ERR_ARG, "nrhs exceeds max_nrhs");
   try {
-    ensure_ws(h, round_k(nrhs), std::max(h->ws_m, 1));
+    ensure_ws(h, round_k(nrhs), h->kry ? h->kry->m : 1);
     cudaStream_t s = (cudaStream_t)stream;
     switch (round_k(nrhs)) {
       case 1: apply_k<1>(h, x, y, nrhs, s); break;
@@ -733,9 +864,7 @@ amg_status amg_fgmres_solve(amg_handle h, const double* b, double* x, int nrhs, 
   if (nrhs < 1 || round_k(nrhs) > h->vc()->kmax()) return fail(AMG_ERR_ARG, "nrhs exceeds max_nrhs");
   if (restart < 1 || maxit < 1 || !(rtol > 0.0)) return fail(AMG_ERR_ARG, "restart, maxit and rtol must be positive");
   try {
-    if (h->prm.vcycle_fp32)
-      return fgmres_dispatch<float>(h, b, x, nrhs, rtol, restart, maxit, iters, relres, (cudaStream_t)stream);
-    return fgmres_dispatch<double>(h, b, x, nrhs, rtol, restart, maxit, iters, relres, (cudaStream_t)stream);
+    return fgmres_blocking(h, b, x, nullptr, nullptr, nrhs, rtol, restart, maxit, iters, relres, (cudaStream_t)stream);
   } catch (const std::bad_alloc&) {
     return fail(AMG_ERR_OOM, "host allocation failed");
   } catch (const std::exception& e) {
@@ -749,22 +878,21 @@ amg_status amg_fgmres_solve_host(amg_handle h, const double* b_host, double* x_h
   if (!h || !b_host || !x_host) return fail(AMG_ERR_ARG, "null argument");
   if (!h->vc()) return fail(AMG_ERR_ARG, "hierarchy was built with host_only");
   if (nrhs < 1 || round_k(nrhs) > h->vc()->kmax()) return fail(AMG_ERR_ARG, "nrhs exceeds max_nrhs");
-  cudaStream_t s = (cudaStream_t)stream;
-  const size_t bytes = sizeof(double) * (size_t)h->N * nrhs;
+  if (restart < 1 || maxit < 1 || !(rtol > 0.0)) return fail(AMG_ERR_ARG, "restart, maxit and rtol must be positive");
   if (!h->stage_b) {
     const size_t cap = sizeof(double) * (size_t)h->N * h->vc()->kmax();
     if (cudaMalloc(&h->stage_b, cap) != cudaSuccess || cudaMalloc(&h->stage_x, cap) != cudaSuccess)
       return fail(AMG_ERR_OOM, "cudaMalloc for the host-solve staging buffers");
   }
-  cudaError_t e = cudaMemcpyAsync(h->stage_b, b_host, bytes, cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) return fail(AMG_ERR_CUDA, cudaGetErrorString(e));
-  amg_status st = amg_fgmres_solve(h, (const double*)h->stage_b, (double*)h->stage_x, nrhs, rtol, restart, maxit,
-                                   iters, relres, stream);
-  if (st < 0) return st;
-  e = cudaMemcpyAsync(x_host, h->stage_x, bytes, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return fail(AMG_ERR_CUDA, cudaGetErrorString(e));
-  return st;
+  try {
+    return fgmres_blocking(h, (const double*)h->stage_b, (double*)h->stage_x, b_host, x_host, nrhs, rtol, restart,
+                           maxit, iters, relres, (cudaStream_t)stream);
+  } catch (const std::bad_alloc&) {
+    return fail(AMG_ERR_OOM, "host allocation failed");
+  } catch (const std::exception& e) {
+    const std::string m = e.what();
+    return fail(m.find("cudaMalloc") != std::string::npos ? AMG_ERR_OOM : AMG_ERR_CUDA, m);
+  }
 }
 
 amg_status amg_profile_vcycle(amg_handle h, int nrhs, int reps, double* ms, long long* count, void* stream) {

@@ -23,6 +23,8 @@ struct VCycleIface {
   virtual void* output(int level) = 0;  // level's solution buffer, N_l x K
   // Enqueue one cycle on level 0 (reads input(0), writes output(0)).
   virtual cudaError_t run(int K, cudaStream_t s) = 0;
+  // Capture the cycle's graph for K without running it (run() captures on first use).
+  virtual cudaError_t prepare(int K) = 0;
   virtual size_t device_bytes() const = 0;
   virtual int levels() const = 0;
   // Run `reps` cycles without the graph, with CUDA events around every launch;
@@ -35,6 +37,13 @@ struct VCycleIface {
   // FP32 cycles only: out = A z on the finest level for an FP32 z, FP64 result by
   // float-float arithmetic on the FP64 matrix split into two floats.
   virtual cudaError_t apply_ff(const float* z, double* out, int K, cudaStream_t s) = 0;
+  // A second cycle on the same device-resident hierarchy: it shares every matrix
+  // (read-only) and owns its vectors, counters, error word and graphs, so cycles of
+  // the original and its clones can run at the same time on different streams.
+  // The original must outlive its clones.  Throws std::runtime_error on failure.
+  virtual VCycleIface* clone(int kmax) const = 0;
+  // Device bytes a clone with kmax right-hand sides allocates.
+  virtual size_t clone_bytes(int kmax) const = 0;
 };
 
 // Kernel classes reported by profile().
@@ -68,9 +77,7 @@ class DeviceVCycle : public VCycleIface {
       Nc_ = C.N();
       pinv_ = alloc_copy<double>(C.pinv);
       if (sizeof(T) == 4) build_ff(levels[0]);
-      barrier_ = alloc<GridBarrier>(levels.size());
       err_ = alloc<int>(1);
-      EMIN_CUDA(cudaMemset(barrier_, 0, sizeof(GridBarrier) * levels.size()));
       EMIN_CUDA(cudaMemset(err_, 0, sizeof(int)));
     } catch (...) {
       release();
@@ -78,6 +85,19 @@ class DeviceVCycle : public VCycleIface {
     }
   }
   ~DeviceVCycle() override { release(); }
+  DeviceVCycle(const DeviceVCycle&) = delete;
+  DeviceVCycle& operator=(const DeviceVCycle&) = delete;
+
+  VCycleIface* clone(int kmax) const override { return new DeviceVCycle(*this, kmax, CloneTag{}); }
+  size_t clone_bytes(int kmax) const override {
+    size_t b = 256;
+    for (const LevelView<T>& L : views_) {
+      const size_t N = (size_t)L.dim * L.n_v + L.n_p;
+      b += ((3 * N + (size_t)L.dim * L.n_v + 2 * (size_t)L.n_p) * kmax * sizeof(T) + 255) / 256 * 256;
+    }
+    for (const GsStrips& P : gs_) b += ((size_t)(P.nstrips + 1) * sizeof(int) + 255) / 256 * 256;
+    return b;
+  }
 
   bool is_fp32() const override { return sizeof(T) == 4; }
   int kmax() const override { return kmax_; }
@@ -131,6 +151,12 @@ class DeviceVCycle : public VCycleIface {
     return e;
   }
   long long launches() const override { return launches_; }
+
+  cudaError_t prepare(int K) override {
+    const int slot = kslot(K);
+    if (slot < 0 || K > kmax_) return cudaErrorInvalidValue;
+    return graphs_[slot] ? cudaSuccess : capture(K, slot);
+  }
 
   // Enqueue the cycle without a graph (used for capture).
   template <int K>
@@ -237,6 +263,7 @@ class DeviceVCycle : public VCycleIface {
     cudaEventRecord(r.a, s);
     recs_.push_back(r);
   }
+  void mark_extra(cudaStream_t) { ++enq_kernels_; }
   void mark_end(cudaStream_t s) {
     if (prof_on_) cudaEventRecord(recs_.back().b, s);
   }
@@ -262,8 +289,9 @@ class DeviceVCycle : public VCycleIface {
     return 0;
   }
 
-  // Strip-ordered Gauss-Seidel: one block per strip of the active parity, a
-  // cooperative grid (bounded barrier) when there are several strips.
+  // Strip-ordered Gauss-Seidel: the single-block kernel for levels of at most two
+  // strips, else the pipelined kernel, else (strip data too large for shared
+  // memory) one launch per phase.  No kernel needs its blocks co-resident.
   template <int K>
   void launch_gs(int l, cudaStream_t s) {
     if (launch_gs_level<K>(l, s)) return;
@@ -272,7 +300,6 @@ class DeviceVCycle : public VCycleIface {
     launch_gs_g<K, 1>(l, s);
   }
 
-  // The pipelined kernel needs every strip resident at once; false if they do not fit.
   // Levels of at most two strips whose Schur data fits in one block's shared
   // memory run in a single block: no waits between blocks.
   size_t level_smem(int l, int K) const {
@@ -327,23 +354,9 @@ class DeviceVCycle : public VCycleIface {
     const size_t smem = gs_smem(l, K, P.stage);
     auto kern = k_gs_pipe<T, K, G, V>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 48 * 1024));
-    int per = 0, sms = 0, dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kGsPipeBlock, smem);
-    if (P.nstrips > sms * per) return false;
-    cudaMemsetAsync(done_[l], 0, sizeof(int) * P.nstrips, s);
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(P.nstrips);
-    cfg.blockDim = dim3(kGsPipeBlock);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, kern, L, (const T*)B.g, B.dp, P, (const int*)ci_rel_[l], done_[l], err_);
+    cudaMemsetAsync(done_[l], 0, sizeof(int) * (P.nstrips + 1), s);
+    // one block per strip: as many units in flight as the pipeline can overlap
+    kern<<<P.nstrips, kGsPipeBlock, smem, s>>>(L, (const T*)B.g, B.dp, P, (const int*)ci_rel_[l], done_[l], err_);
     return true;
   }
 
@@ -356,31 +369,19 @@ class DeviceVCycle : public VCycleIface {
     const size_t smem = gs_smem(l, K, P.stage);
     auto kern = k_gs_strips<T, K, G>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 48 * 1024));
-    int per = 0, sms = 0, dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kGsBlock, smem);
-    const int coop = std::max(1, sms * std::max(per, 1));
-    const int nb = std::max(1, std::min((P.nstrips + 1) / 2, coop));
+    const int nb = std::max(1, (P.nstrips + 1) / 2);
     if (nb == 1) {
-      kern<<<1, kGsBlock, smem, s>>>(L, B.g, B.dp, P, barrier_ + l, err_);
+      kern<<<1, kGsBlock, smem, s>>>(L, B.g, B.dp, P, 0, 2 * P.iters);
       return;
     }
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(nb);
-    cfg.blockDim = dim3(kGsBlock);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, kern, L, (const T*)B.g, B.dp, P, barrier_ + l, err_);
+    for (int ph = 0; ph < 2 * P.iters; ++ph) {
+      if (ph) mark_extra(s);
+      kern<<<nb, kGsBlock, smem, s>>>(L, B.g, B.dp, P, ph, ph + 1);
+    }
   }
 
  public:
-  // Nonzero when a grid barrier gave up (checked by the solver after a cycle).
+  // Nonzero when a bounded wait gave up (checked by the solver after a cycle).
   int* error_flag() const override { return err_; }
 
   cudaError_t apply_ff(const float* z, double* out, int K, cudaStream_t s) override {
@@ -483,6 +484,46 @@ class DeviceVCycle : public VCycleIface {
     return d;
   }
 
+  struct CloneTag {};
+  DeviceVCycle(const DeviceVCycle& o, int kmax, CloneTag)
+      : c_(o.c_), cfac_(o.cfac_), gs_iters_(o.gs_iters_), pre_(o.pre_), post_(o.post_), kmax_(kmax) {
+    try {
+      if ((long long)((size_t)o.views_[0].dim * o.views_[0].n_v + o.views_[0].n_p) * kmax_ >= (1LL << 31))
+        throw std::runtime_error("N * max_nrhs must stay below 2^31 (32-bit vector indices)");
+      views_ = o.views_;
+      gs_ = o.gs_;
+      gs_lanes_ = o.gs_lanes_;
+      ci_rel_ = o.ci_rel_;
+      plist_ = o.plist_;
+      poff_ = o.poff_;
+      s_nnz_ = o.s_nnz_;
+      ff_ = o.ff_;
+      pinv_ = o.pinv_;
+      Nc_ = o.Nc_;
+      for (size_t l = 0; l < views_.size(); ++l) {
+        buf_.push_back(alloc_bufs(views_[l]));
+        done_.push_back(alloc<int>(gs_[l].nstrips + 1));
+      }
+      err_ = alloc<int>(1);
+      EMIN_CUDA(cudaMemset(err_, 0, sizeof(int)));
+    } catch (...) {
+      release();
+      throw;
+    }
+  }
+
+  Buf alloc_bufs(const LevelView<T>& L) {
+    const size_t N = ((size_t)L.dim * L.n_v + L.n_p) * kmax_;
+    Buf B;
+    B.b = alloc<T>(N);
+    B.x = alloc<T>(N);
+    B.r = alloc<T>(N);
+    B.y = alloc<T>((size_t)L.dim * L.n_v * kmax_);
+    B.g = alloc<T>((size_t)L.n_p * kmax_);
+    B.dp = alloc<T>((size_t)L.n_p * kmax_);
+    return B;
+  }
+
   void upload_level(const HostLevel& H, bool coarsest) {
     LevelView<T> L{};
     L.dim = H.dim;
@@ -551,7 +592,7 @@ class DeviceVCycle : public VCycleIface {
           for (int64_t t = So.rowptr[r]; t < So.rowptr[r + 1]; ++t) rel[t] = So.col[t] - h0;
       }
       ci_rel_.push_back(alloc_copy<int>(rel));
-      done_.push_back(alloc<int>(nstrips));
+      done_.push_back(alloc<int>(nstrips + 1));
       // rows of each (strip parity, color) group, for the single-block kernel
       std::vector<int> plist, poff(1, 0);
       for (int par = 0; par < 2; ++par)
@@ -578,16 +619,8 @@ class DeviceVCycle : public VCycleIface {
       L.R = upload(H.R);
       L.Rp = upload(H.Rp);
     }
-    const size_t N = (size_t)H.N() * kmax_;
-    Buf B;
-    B.b = alloc<T>(N);
-    B.x = alloc<T>(N);
-    B.r = alloc<T>(N);
-    B.y = alloc<T>((size_t)H.dim * H.n_v * kmax_);
-    B.g = alloc<T>((size_t)H.n_p * kmax_);
-    B.dp = alloc<T>((size_t)H.n_p * kmax_);
     views_.push_back(L);
-    buf_.push_back(B);
+    buf_.push_back(alloc_bufs(L));
   }
 
   void release() {
@@ -611,7 +644,6 @@ class DeviceVCycle : public VCycleIface {
   std::vector<int*> done_;
   std::vector<int*> plist_, poff_;
   std::vector<long long> s_nnz_;
-  GridBarrier* barrier_ = nullptr;
   int* err_ = nullptr;
   FFLevel ff_{};
   double* pinv_ = nullptr;

@@ -33,6 +33,12 @@ def uniform_pm1(seed: int, n: int) -> np.ndarray:
     return (z >> np.uint64(11)).astype(np.float64) * (2.0 ** -53) * 2.0 - 1.0
 
 
+def uniform01(seed: int, n: int) -> np.ndarray:
+    """n i.i.d. uniform[0, 1) doubles: u = (x >> 11) * 2^-53."""
+    z = splitmix64(seed, n)
+    return (z >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+
+
 def exponential(seed: int, n: int, rate: float) -> np.ndarray:
     """n exponential(rate) inter-arrival gaps by inversion of the 53-bit uniform."""
     z = splitmix64(seed, n)

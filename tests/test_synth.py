@@ -103,3 +103,27 @@ def test_boundary_conditions_and_colocation():
     # the two right-hand sides differ only by their seeded body loads
     assert not np.allclose(p.b[:, 0], p.b[:, 1])
     assert abs(p.b[2 * p.n_v:].sum(axis=0)).max() < 1e-14
+
+
+def test_serving_stream_is_a_seeded_poisson_mix():
+    """Exponential gaps with the stated mean rate, every (n, Re, nrhs) choice from its set
+    with roughly uniform frequencies, and the same stream for the same seed."""
+    from synth import serving_stream, MESHES, REYNOLDS
+    s = serving_stream(4000, rate=200.0, seed=0)
+    assert s == serving_stream(4000, rate=200.0, seed=0)
+    t = np.array([r["t"] for r in s])
+    assert np.all(np.diff(t) > 0)
+    gaps = np.diff(np.concatenate([[0.0], t]))
+    assert abs(gaps.mean() - 1 / 200.0) < 0.05 / 200.0        # 4000 draws: sd of the mean ~1.6%
+    assert abs(np.std(gaps) / gaps.mean() - 1.0) < 0.06       # exponential: cv = 1
+    for key, choices in (("n", MESHES), ("Re", REYNOLDS), ("nrhs", range(1, 9))):
+        vals = [r[key] for r in s]
+        assert set(vals) == set(choices)
+        counts = np.array([vals.count(c) for c in choices])
+        assert counts.min() > 0.8 * len(s) / len(choices)
+
+
+def test_homogeneous_rhs_equals_make_problem_draws():
+    from synth import homogeneous_rhs, oseen_recirculating_2d
+    p = oseen_recirculating_2d(12, Re=100.0, nrhs=4, seed=9)
+    assert np.array_equal(homogeneous_rhs(p, 4, 9), p.b)

@@ -73,7 +73,9 @@ typedef struct {
 
 /* Method parameters; amg_params_default fills the values of Section 6. */
 typedef struct {
-  double tau1;        /* eq. e:filtering drop tolerance, 0.06 */
+  double tau1;        /* eq. e:filtering drop tolerance; < 0 (the default) takes 0.06 in 2D
+                        (Section 6) and 0.015 in 3D, the threshold that keeps every
+                        nearest-neighbour coupling of the Q2 velocity block there */
   double tau2sq;      /* Alg. 4 tolerance squared, 1.5e-3 */
   double omega;       /* Braess-Sarazin relaxation, 0.666 */
   int omega_on_D;     /* 0: M = [omega D, B^T; B, 0] (eq. bs2's factorisation, default);

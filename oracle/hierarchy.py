@@ -26,8 +26,16 @@ UNMARKED, CPT, FPT, EXCL = 0, 1, 2, 3
 @dataclasses.dataclass
 class Params:
     """Section 6 defaults: tau1=0.06 (eq. e:filtering), tau2=sqrt(1.5e-3) (Alg. 4),
-    BS relaxation 0.666 with 5 Gauss-Seidel iterations, BS(2,2), one EMIN step."""
-    tau1: float = 0.06
+    BS relaxation 0.666 with 5 Gauss-Seidel iterations, BS(2,2), one EMIN step.
+
+    tau1 = None takes the dimension's default: 0.06 in 2D (Section 6); in 3D,
+    where the paper has no experiments, 0.015.  On a uniform 2D Q2 mesh the
+    scaled couplings |a_ij| / sqrt(a_ii a_jj) are >= 0.09 between nearest nodes
+    and <= 0.036 farther away, so 0.06 keeps exactly the nearest-neighbour
+    graph; in 3D the two ranges overlap (nearest down to 0.016, farther up to
+    0.06), 0.06 leaves most velocity nodes without an edge, and 0.015 is the
+    threshold that keeps every nearest neighbour."""
+    tau1: float | None = None
     tau2sq: float = 1.5e-3
     omega: float = 0.666
     omega_in_M: str = "direct"    # eq. bs2's factorisation: M = [omega D, B^T; B, 0]; "inverse": eq. bs
@@ -37,6 +45,11 @@ class Params:
     emin: str = "auto"            # "cg" (Stokes), "gmres" (Oseen); auto picks by symmetry
     max_coarse: int = 200
     max_levels: int = 12
+
+    def tau1_for(self, dim: int) -> float:
+        if self.tau1 is not None:
+            return self.tau1
+        return 0.06 if dim == 2 else 0.015
 
     @property
     def c(self) -> float:
@@ -551,8 +564,8 @@ def form_interpolation(L: Level, prm: Params, method: str):
     Returns the next level, or None when coarsening makes no progress."""
     # form_aux_block_diagonal
     Zp = spgemm(L.B, L.B.T)
-    Ap, adjp = filter_lump(Zp, prm.tau1)
-    Av, adjv = filter_lump(L.A, prm.tau1)
+    Ap, adjp = filter_lump(Zp, prm.tau1_for(L.dim))
+    Av, adjv = filter_lump(L.A, prm.tau1_for(L.dim))
     excluded = [L.pinned] if L.pinned >= 0 else []
     # find_coarse_pressure (Alg. 3)
     state, S, order = find_coarse_pressures(adjp, L.pcoords, excluded)

@@ -565,8 +565,8 @@ bool form_interpolation(HostLevel& L, HostLevel& Lc, const SetupParams& prm) {
   Csr Zp = spgemm(L.B, transpose(L.B));
   Csr Ap, Av;
   Graph Gp, Gv;
-  filter_lump(Zp, prm.tau1, Ap, Gp);
-  filter_lump(L.A, prm.tau1, Av, Gv);
+  filter_lump(Zp, prm.tau1_for(L.dim), Ap, Gp);
+  filter_lump(L.A, prm.tau1_for(L.dim), Av, Gv);
   // Alg. 3
   CoarsePressures cp = find_coarse_pressures(Gp, L.pX.data(), d, L.pinned);
   find_extra_dist3_cpoints(Gp, L.pX.data(), d, cp);

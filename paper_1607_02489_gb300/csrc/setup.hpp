@@ -9,7 +9,8 @@
 namespace emin {
 
 struct SetupParams {
-  double tau1 = 0.06;      // eq. e:filtering
+  double tau1 = -1.0;      // eq. e:filtering; < 0: 0.06 in 2D, 0.015 in 3D
+  double tau1_for(int dim) const { return tau1 >= 0.0 ? tau1 : (dim == 2 ? 0.06 : 0.015); }
   double tau2sq = 1.5e-3;  // Alg. 4, tau2 = sqrt(1.5e-3)
   double c = 0.666;        // scale of D in the (1,1) block of the Braess-Sarazin matrix
   int max_coarse = 200;

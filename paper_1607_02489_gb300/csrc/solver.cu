@@ -743,7 +743,7 @@ amg_status amg_apply_noalloc(amg_handle h, const double* x, double* y, int nrhs,
 
 void amg_params_default(amg_params* p) {
   if (!p) return;
-  p->tau1 = 0.06;
+  p->tau1 = -1.0;
   p->tau2sq = 1.5e-3;
   p->omega = 0.666;
   p->omega_on_D = 0;

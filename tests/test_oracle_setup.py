@@ -224,3 +224,57 @@ def test_3d_hierarchy_builds_with_null_vector():
     z[Lc.dim * Lc.n_v:] = 1.0
     Ac = Lc.full_matrix()
     assert np.abs(Ac @ z).max() <= 1e-12 * abs(Ac).max()
+
+
+def _scaled_couplings(p):
+    """(nearest, farther) scaled couplings |a_ij| / sqrt(a_ii a_jj) between interior velocity nodes."""
+    A = p.A.tocsr()
+    X = np.asarray(p.vcoords)
+    h = (X[:, 0].max() - X[:, 0].min()) / (2 * p.n)
+    d = A.diagonal()
+    inter = ~np.asarray(p.v_dirichlet)
+    near, far = [], []
+    for i in np.flatnonzero(inter):
+        for t in range(A.indptr[i], A.indptr[i + 1]):
+            j = A.indices[t]
+            if j != i and inter[j]:
+                s = abs(A.data[t]) / np.sqrt(abs(d[i] * d[j]))
+                (near if np.abs(X[j] - X[i]).max() <= 1.5 * h else far).append(s)
+    return np.array(near), np.array(far)
+
+
+def test_default_tau1_keeps_nearest_neighbours_in_2d_and_3d():
+    """Reading of eq. e:filtering's tau1 by dimension: in 2D, 0.06 separates the nearest-neighbour
+    couplings of the Q2 velocity block from the farther ones exactly; in 3D the two ranges overlap
+    and 0.06 would leave velocity nodes with no edge, while the 3D default 0.015 keeps every
+    nearest neighbour."""
+    from oracle.hierarchy import filter_lump
+    p2 = stokes_lid_2d(12, nrhs=1)
+    near, far = _scaled_couplings(p2)
+    assert near.min() > 0.06 > far.max()
+    assert Params().tau1_for(2) == 0.06 and Params().tau1_for(3) == 0.015 and Params(tau1=0.2).tau1_for(3) == 0.2
+    p3 = make_problem(6, 3, 0.0, 1.0, bc="lid", nrhs=1)
+    near, far = _scaled_couplings(p3)
+    assert near.min() > 0.015 and far.max() > near.min()
+    _, adj = filter_lump(p3.A, 0.06)
+    inter = ~np.asarray(p3.v_dirichlet)
+    assert any(len(adj[i]) == 0 for i in np.flatnonzero(inter))
+    _, adj = filter_lump(p3.A, Params().tau1_for(3))
+    X = np.asarray(p3.vcoords)
+    h = 1.0 / (2 * p3.n)
+    A = p3.A.tocsr()
+    for i in np.flatnonzero(inter):
+        nb = {int(j) for j in A.indices[A.indptr[i]:A.indptr[i + 1]]
+              if j != i and inter[j] and np.abs(X[j] - X[i]).max() <= 1.5 * h}
+        assert nb <= set(int(j) for j in adj[i]), i
+
+
+def test_3d_velocities_coarsen_with_the_3d_tau1():
+    """With the 3D tau1 the first coarse level keeps a small fraction of the velocity nodes, as in
+    2D; with 0.06 most velocity nodes are isolated in the filtered graph and become coarse."""
+    p = make_problem(8, 3, 0.0, 1.0, bc="lid", nrhs=1)
+    H = setup_hierarchy(p)
+    assert H.levels[1].n_v < 0.1 * H.levels[0].n_v
+    assert H.levels[-1].N <= 200
+    H06 = setup_hierarchy(p, Params(tau1=0.06, max_levels=2))
+    assert H06.levels[1].n_v > 0.3 * H06.levels[0].n_v

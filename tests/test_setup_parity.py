@@ -115,3 +115,7 @@ def test_invalid_problem_is_rejected():
         g.Hierarchy(p, host_only=1, max_nrhs=64)
     H = g.Hierarchy(p, host_only=1)
     assert H.num_levels() >= 1
+
+
+def test_3d_setup_matches_oracle_at_8():
+    _compare(make_problem(8, 3, 0.0, 1.0, bc="lid", nrhs=1))

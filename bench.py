@@ -454,6 +454,8 @@ def main():
                 "bytes_per_launch": bytes_launch, "avg_launch_us": avg_ms * 1000.0,
                 "vcycle_kernels_GBs": vcycle_bytes / (vcycle_ms / 1000.0) / 1e9,
                 "vcycle_kernels_frac": vcycle_bytes / (vcycle_ms / 1000.0) / 1e9 / peak}
+    gs_variants = [f"L{l}: {v}{' x' + str(c) if v == 'cluster' else ''} ({1000.0 * t:.1f} us)"
+                   for l, (v, c, t) in enumerate(H32.gs_variants(NRHS))]
     breakdown = {f"L{l}/{c}": round(float(ms_tab[l, k] / reps * 1000.0), 2)
                  for l in range(ms_tab.shape[0]) for k, c in enumerate(g.KERNEL_CLASSES) if cnt_tab[l, k]}
 
@@ -486,7 +488,7 @@ def main():
                                 "source": "serving stream (arrival to result on the host)"}),
                 "serving": serving, "accuracy": accuracy,
                 "e2e": e2e, "gpu_launches": launches32, "clocks": clocks, "roofline": roofline,
-                "vcycle_us_by_kernel": breakdown, "cpu_baseline": cpu}
+                "vcycle_us_by_kernel": breakdown, "gs_variants": gs_variants, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -88,6 +88,11 @@ typedef struct {
   int max_nrhs;       /* largest nrhs later passed to vcycle/fgmres (workspace size), 8 */
   int host_only;      /* 1: build the hierarchy on the host and upload nothing (inspection
                          calls work, solve calls return AMG_ERR_ARG); 0 (default): upload */
+  int autotune;       /* 1 (default): before a cycle for K right-hand sides is first captured,
+                         time each Gauss-Seidel variant that applies to each level (one block,
+                         a thread-block cluster of 2-16 blocks, the pipelined kernel, one launch
+                         per phase, the dense map on levels of <= 1024 pressures) and keep the
+                         fastest; 0: fixed choice by level size, sweeps only */
 } amg_params;
 
 void amg_params_default(amg_params* prm);
@@ -185,6 +190,15 @@ amg_status amg_level_get_matrix(amg_handle h, int level, int which, long long* r
  * velocity nodes, ascending), the Gauss-Seidel colors of the pressure nodes
  * (n_p) and the Braess-Sarazin diagonal D (n_v).  Any pointer may be NULL. */
 amg_status amg_level_get_points(amg_handle h, int level, int* cp, int* cv, int* colors, double* D);
+
+/* The Gauss-Seidel variant the V-cycle (FP32 one if built, else FP64) uses on a
+ * level for nrhs right-hand sides: -1 not chosen yet (the cycle for that K has
+ * not run), 0 one block, 1 a cluster of *cluster blocks, 2 the pipelined strip
+ * kernel, 3 one launch per phase, 4 the dense map (levels of at most 1024
+ * pressures: the iterations' linear map formed at setup by the same sweeps and
+ * applied as one dense product); *ms is the time the autotuner measured for one
+ * launch (0 without autotuning).  Either output may be NULL. */
+int amg_gs_variant(amg_handle h, int level, int nrhs, int* cluster, float* ms);
 
 void amg_hierarchy_destroy(amg_handle h);
 

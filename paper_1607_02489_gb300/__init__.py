@@ -23,7 +23,7 @@ STATUS_NAMES = {0: "OK", 1: "NOT_CONVERGED", 2: "BREAKDOWN", -1: "ERR_ARG", -2: 
                 -4: "ERR_SETUP"}
 EXPORTED = ["amg_params_default", "amg_hierarchy_create", "amg_vcycle_apply", "amg_apply", "amg_fgmres_solve",
             "amg_fgmres_solve_host", "amg_num_levels", "amg_level_get_info", "amg_level_get_matrix",
-            "amg_level_get_points", "amg_hierarchy_destroy", "amg_last_error", "amg_profile_vcycle", "amg_kernel_launches", "amg_apply_noalloc",
+            "amg_level_get_points", "amg_hierarchy_destroy", "amg_last_error", "amg_profile_vcycle", "amg_kernel_launches", "amg_apply_noalloc", "amg_gs_variant",
             "amg_server_params_default", "amg_server_create", "amg_server_reserve", "amg_server_submit", "amg_server_progress",
             "amg_server_result", "amg_server_state", "amg_server_get_stats", "amg_server_destroy", "amg_server_last_error"]
 KERNEL_CLASSES = ["velocity", "schur_rhs", "gs_color", "update", "residual", "restrict", "prolong", "coarse"]
@@ -47,7 +47,8 @@ class AmgParams(ctypes.Structure):
     _fields_ = [("tau1", ctypes.c_double), ("tau2sq", ctypes.c_double), ("omega", ctypes.c_double),
                 ("omega_on_D", ctypes.c_int), ("gs_iters", ctypes.c_int), ("pre", ctypes.c_int),
                 ("post", ctypes.c_int), ("max_coarse", ctypes.c_int), ("max_levels", ctypes.c_int),
-                ("vcycle_fp32", ctypes.c_int), ("max_nrhs", ctypes.c_int), ("host_only", ctypes.c_int)]
+                ("vcycle_fp32", ctypes.c_int), ("max_nrhs", ctypes.c_int), ("host_only", ctypes.c_int),
+                ("autotune", ctypes.c_int)]
 
 
 class AmgLevelInfo(ctypes.Structure):
@@ -103,6 +104,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         f.restype = ctypes.c_int
     lib.amg_profile_vcycle.argtypes = [vp, ctypes.c_int, ctypes.c_int, _f64p, _i64p, vp]
     lib.amg_profile_vcycle.restype = ctypes.c_int
+    lib.amg_gs_variant.argtypes = [vp, ctypes.c_int, ctypes.c_int, _i32p, ctypes.POINTER(ctypes.c_float)]
+    lib.amg_gs_variant.restype = ctypes.c_int
     lib.amg_kernel_launches.argtypes = [vp]
     lib.amg_kernel_launches.restype = ctypes.c_longlong
     lib.amg_num_levels.argtypes = [vp]
@@ -280,6 +283,19 @@ class Hierarchy:
         _check(load().amg_profile_vcycle(self._h, int(nrhs), int(reps), _ptr(ms, ctypes.c_double),
                                          _ptr(cnt, ctypes.c_longlong), _stream_ptr(stream)))
         return ms.reshape(L, -1), cnt.reshape(L, -1)
+
+    GS_VARIANTS = {-1: "not chosen", 0: "one block", 1: "cluster", 2: "pipelined", 3: "phase launches", 4: "dense map"}
+
+    def gs_variants(self, nrhs) -> list:
+        """Per level: (variant name, cluster size, measured ms) of the Gauss-Seidel kernel
+        the autotuner chose for nrhs right-hand sides (amg_gs_variant)."""
+        out = []
+        for l in range(self.num_levels()):
+            c = ctypes.c_int()
+            ms = ctypes.c_float()
+            v = load().amg_gs_variant(self._h, l, int(nrhs), ctypes.byref(c), ctypes.byref(ms))
+            out.append((self.GS_VARIANTS.get(v, str(v)), c.value, ms.value))
+        return out
 
     def kernel_launches(self) -> int:
         """Kernels launched by this hierarchy so far (amg_kernel_launches)."""

@@ -9,6 +9,7 @@
 // partial sums are combined with warp shuffles.
 #pragma once
 
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -548,6 +549,142 @@ __global__ void __launch_bounds__(kGsPipeBlock) k_gs_pipe(LevelView<T> L, const 
       st_release(done + s, it + 1);
     }
   }
+}
+
+// Cluster Gauss-Seidel for a mid-size level: the same ordering, with the level's
+// strips split over the C blocks of one thread-block cluster, each block holding
+// its strips' rows of S, g, 1/S_ii and a dp window (its rows plus one strip on
+// each side) in shared memory.  A phase (iteration, parity) relaxes every strip
+// of that parity; phases are separated by the cluster barrier, after which a
+// block copies the rows of the neighbouring strips that other blocks relaxed in
+// the previous phase out of their shared memory (distributed shared memory), so
+// nothing goes through global memory between phases.  The hardware schedules a
+// cluster's blocks together, so the barrier needs no other guarantee.
+// Block c owns strips [c*spc, min((c+1)*spc, nstrips)); plist holds, at each
+// block's sorted rows, those rows grouped by (parity, color), poff[c] the offsets.
+struct GsCluster {
+  const int* soff;   // nstrips x (ncol + 1), as GsStrips
+  const int* plist;  // n_p sorted rows, each block's segment grouped by (parity, color)
+  const int* poff;   // C x (2 ncol + 1)
+  int nstrips, ncol, T, iters, spc;
+  int win_max, rows_max, nnz_max;  // shared-memory extents, equal in every block
+};
+
+template <typename T, int K, int G>
+__global__ void __launch_bounds__(kGsBlock) k_gs_cluster(LevelView<T> L, const T* __restrict__ g, T* dp, GsCluster Q) {
+  static_assert(K * G <= 32, "a row group must fit in a warp");
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const int c = (int)cl.block_rank();
+  extern __shared__ __align__(16) unsigned char smem[];
+  T* s_dp = reinterpret_cast<T*>(smem);
+  T* s_g = s_dp + (size_t)Q.win_max * K;
+  T* s_dinv = s_g + (size_t)Q.rows_max * K;
+  T* s_v = s_dinv + Q.rows_max;
+  int* s_rp = reinterpret_cast<int*>(s_v + Q.nnz_max);
+  int* s_perm = s_rp + Q.rows_max + 1;
+  int* s_ci = s_perm + Q.rows_max;
+  int* s_plist = s_ci + Q.nnz_max;
+  int* s_poff = s_plist + Q.rows_max;
+  constexpr int kGroup = K * G;
+  const int k = threadIdx.x % K;
+  const int lane = (threadIdx.x / K) % G;
+  const unsigned mask = group_mask<kGroup>();
+  const int n_p = L.n_p, Ts = Q.T, ncol = Q.ncol;
+  const int s0 = min(c * Q.spc, Q.nstrips), s1 = min(s0 + Q.spc, Q.nstrips);
+  const int r_lo = min(s0 * Ts, n_p), r_hi = min(s1 * Ts, n_p);
+  const int w_lo = max(0, r_lo - Ts), w_hi = min(n_p, r_hi + Ts);
+  const int q0 = s1 > s0 ? Q.soff[(size_t)s0 * (ncol + 1)] : 0;
+  const int q1 = s1 > s0 ? Q.soff[(size_t)(s1 - 1) * (ncol + 1) + ncol] : 0;
+  const int e0 = L.S.rp[q0], e1 = s1 > s0 ? L.S.rp[q1] : e0;
+  for (int t = threadIdx.x; t < (w_hi - w_lo) * K; t += blockDim.x) s_dp[t] = T(0);
+  if (s1 > s0) {
+    stage_copy<false>(s_g, g + (size_t)r_lo * K, (r_hi - r_lo) * K);
+    stage_copy<false>(s_dinv, L.S_dinv + q0, q1 - q0);
+    stage_copy<false>(s_perm, L.S_perm + q0, q1 - q0);
+    stage_copy<false>(s_rp, L.S.rp + q0, q1 - q0 + 1);
+    stage_copy<false>(s_v, L.S.v + e0, e1 - e0);
+    stage_copy<false>(s_ci, L.S.ci + e0, e1 - e0);
+    stage_copy<false>(s_plist, Q.plist + q0, q1 - q0);
+  }
+  stage_copy<false>(s_poff, Q.poff + (size_t)c * (2 * ncol + 1), 2 * ncol + 1);
+  cp_async_wait_all();
+  __syncthreads();
+  for (int t = threadIdx.x; t < e1 - e0; t += blockDim.x) s_ci[t] -= w_lo;  // window-relative columns
+  for (int t = threadIdx.x; t <= q1 - q0; t += blockDim.x) s_rp[t] -= e0;
+  for (int t = threadIdx.x; t < q1 - q0; t += blockDim.x) s_plist[t] -= q0;
+  // neighbouring strips held by other blocks, and where their windows start
+  const bool has_left = s1 > s0 && s0 > 0, has_right = s1 > s0 && s1 < Q.nstrips;
+  const T* left_dp = has_left ? cl.map_shared_rank(s_dp, c - 1) : nullptr;
+  const T* right_dp = has_right ? cl.map_shared_rank(s_dp, c + 1) : nullptr;
+  const int left_wlo = max(0, (s0 - Q.spc) * Ts - Ts);  // block c-1 owns spc strips ending at s0
+  const int right_wlo = max(0, s1 * Ts - Ts);
+  __syncthreads();
+  for (int it = 0; it < Q.iters; ++it)
+    for (int par = 0; par < 2; ++par) {
+      cl.sync();  // every block finished the previous phase; its rows are visible
+      if (has_left && ((s0 - 1) & 1) != par) {
+        const int a = (s0 - 1) * Ts, b = min(s0 * Ts, n_p);
+        for (int t = threadIdx.x; t < (b - a) * K; t += blockDim.x)
+          s_dp[(size_t)(a - w_lo) * K + t] = left_dp[(size_t)(a - left_wlo) * K + t];
+      }
+      if (has_right && (s1 & 1) != par) {
+        const int a = s1 * Ts, b = min((s1 + 1) * Ts, n_p);
+        for (int t = threadIdx.x; t < (b - a) * K; t += blockDim.x)
+          s_dp[(size_t)(a - w_lo) * K + t] = right_dp[(size_t)(a - right_wlo) * K + t];
+      }
+      __syncthreads();
+      for (int pc = 0; pc < ncol; ++pc) {
+        const int a = s_poff[par * ncol + pc], b = s_poff[par * ncol + pc + 1];
+        for (int t = threadIdx.x; t < (b - a) * kGroup; t += blockDim.x) {
+          const int r = s_plist[a + t / kGroup];
+          const int ea = s_rp[r], eb = s_rp[r + 1];
+          T a0 = T(0), a1 = T(0);
+          int e = ea + lane;
+          for (; e + G < eb; e += 2 * G) {
+            a0 += s_v[e] * s_dp[(size_t)s_ci[e] * K + k];
+            a1 += s_v[e + G] * s_dp[(size_t)s_ci[e + G] * K + k];
+          }
+          if (e < eb) a0 += s_v[e] * s_dp[(size_t)s_ci[e] * K + k];
+          const T acc = group_sum<K, G>(a0 + a1, mask);
+          if (lane == 0) {
+            const int i = s_perm[r];
+            s_dp[(size_t)(i - w_lo) * K + k] = (s_g[(size_t)(i - r_lo) * K + k] - acc) * s_dinv[r];
+          }
+        }
+        __syncthreads();
+      }
+    }
+  cl.sync();  // no block leaves while another may still read its window
+  for (int t = threadIdx.x; t < (r_hi - r_lo) * K; t += blockDim.x)
+    dp[(size_t)r_lo * K + t] = s_dp[(size_t)(r_lo - w_lo) * K + t];
+}
+
+// Dense form of the Gauss-Seidel call on a small level: the gs_iters iterations
+// from dp = 0 in the (strip parity, color, index) order are a fixed linear map of
+// g, dp = M g, with M (n_p x n_p, row-major) formed at setup by the same sweeps.
+// One warp per row i: lane (jsplit, k) sums M[i, j] g[j, k] over j = jsplit,
+// jsplit + 32/K, ..., then the 32/K partial sums of each column are combined.
+template <typename T, int K>
+__global__ void __launch_bounds__(kBlock) k_gs_dense(int n_p, const T* __restrict__ M, const T* __restrict__ g,
+                                                     T* __restrict__ dp) {
+  constexpr int J = 32 / K;  // row entries a column's lanes split
+  const int i = (int)(gtid() >> 5);
+  if (i >= n_p) return;
+  const int lane = threadIdx.x & 31;
+  const int k = lane % K, js = lane / K;
+  const T* Mi = M + (size_t)i * n_p;
+  T a0 = T(0), a1 = T(0);
+  int j = js;
+  for (; j + J < n_p; j += 2 * J) {
+    a0 += Mi[j] * g[(size_t)j * K + k];
+    a1 += Mi[j + J] * g[(size_t)(j + J) * K + k];
+  }
+  if (j < n_p) a0 += Mi[j] * g[(size_t)j * K + k];
+  T acc = a0 + a1;
+#pragma unroll
+  for (int off = 16; off >= K; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  if (js == 0) dp[(size_t)i * K + k] = acc;
 }
 
 // Single-block Gauss-Seidel for a small level, same ordering: the whole level's

@@ -755,6 +755,7 @@ void amg_params_default(amg_params* p) {
   p->vcycle_fp32 = 0;
   p->max_nrhs = 8;
   p->host_only = 0;
+  p->autotune = 1;
 }
 
 const char* amg_last_error(void) { return g_last_error.c_str(); }
@@ -807,8 +808,11 @@ amg_status amg_hierarchy_create(const amg_problem* pb, const amg_params* prm_in,
     h->N = h->host[0].N();
     if (!prm.host_only) {
       h->v64 = make_vcycle_f64(h->host, sp.c, prm.gs_iters, prm.pre, prm.post, round_k(prm.max_nrhs));
-      if (prm.vcycle_fp32)
+      h->v64->set_autotune(prm.autotune != 0);
+      if (prm.vcycle_fp32) {
         h->v32 = make_vcycle_f32(h->host, sp.c, prm.gs_iters, prm.pre, prm.post, round_k(prm.max_nrhs));
+        h->v32->set_autotune(prm.autotune != 0);
+      }
       EMIN_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
     }
   } catch (const std::bad_alloc&) {
@@ -966,6 +970,11 @@ amg_status amg_level_get_points(amg_handle h, int level, int* cp, int* cv, int* 
   if (colors) std::copy(L.colors.begin(), L.colors.end(), colors);
   if (D) std::copy(L.D.begin(), L.D.end(), D);
   return AMG_OK;
+}
+
+int amg_gs_variant(amg_handle h, int level, int nrhs, int* cluster, float* ms) {
+  if (!h || !h->vc() || nrhs < 1 || nrhs > 32) return -1;
+  return h->vc()->gs_choice(level, round_k(nrhs), cluster, ms);
 }
 
 void amg_hierarchy_destroy(amg_handle h) { delete h; }

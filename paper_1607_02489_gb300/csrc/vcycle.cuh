@@ -5,6 +5,7 @@
 
 #include <cuda_runtime.h>
 
+#include <memory>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -44,6 +45,12 @@ struct VCycleIface {
   virtual VCycleIface* clone(int kmax) const = 0;
   // Device bytes a clone with kmax right-hand sides allocates.
   virtual size_t clone_bytes(int kmax) const = 0;
+  // Gauss-Seidel variant selection: timed per (level, K) before the first capture
+  // when on (the default), fixed heuristics when off.  gs_choice reports the
+  // variant of a level for K (-1 not tuned yet, 0 one block, 1 cluster, 2
+  // pipelined, 3 one launch per phase), the cluster size and the time measured.
+  virtual void set_autotune(bool on) = 0;
+  virtual int gs_choice(int level, int K, int* cluster, float* ms) const = 0;
 };
 
 // Kernel classes reported by profile().
@@ -62,6 +69,20 @@ class DeviceVCycle : public VCycleIface {
   struct Buf {
     T *b = nullptr, *x = nullptr, *y = nullptr, *g = nullptr, *dp = nullptr, *r = nullptr;
   };
+  // Strips of a level split over a cluster of C blocks (k_gs_cluster): block c owns
+  // spc consecutive strips; plist / poff as GsCluster; extents are maxima over blocks.
+  enum GsKind { kGsSingle = 0, kGsCluster = 1, kGsPipe = 2, kGsPhases = 3, kGsDense = 4 };
+  static constexpr int kGsDenseMax = 1024;  // pressures of a level whose Gauss-Seidel map is formed densely
+  struct GsChoice {
+    int kind = -1;  // GsKind, -1 = not tuned yet
+    int C = 0;      // cluster size
+    float ms = 0.f; // measured time per launch
+  };
+  struct ClusterPlan {
+    int C = 0, spc = 0, win_max = 0, rows_max = 0, nnz_max = 0;
+    int* plist = nullptr;
+    int* poff = nullptr;
+  };
 
   DeviceVCycle(const std::vector<HostLevel>& levels, double cfac, int gs_iters, int pre, int post, int kmax)
       : c_(cfac), cfac_((T)cfac), gs_iters_(gs_iters), pre_(pre), post_(post), kmax_(kmax) {
@@ -69,6 +90,7 @@ class DeviceVCycle : public VCycleIface {
       if ((long long)levels[0].N() * kmax_ >= (1LL << 31))
         throw std::runtime_error("N * max_nrhs must stay below 2^31 (32-bit vector indices)");
       for (size_t l = 0; l < levels.size(); ++l) upload_level(levels[l], l + 1 == levels.size());
+      tune_ = std::make_shared<std::vector<GsChoice>>(levels.size() * 6);
       for (size_t l = 0; l + 1 < levels.size(); ++l) {
         views_[l].n_vc = levels[l + 1].n_v;
         views_[l].n_pc = levels[l + 1].n_p;
@@ -89,6 +111,14 @@ class DeviceVCycle : public VCycleIface {
   DeviceVCycle& operator=(const DeviceVCycle&) = delete;
 
   VCycleIface* clone(int kmax) const override { return new DeviceVCycle(*this, kmax, CloneTag{}); }
+  void set_autotune(bool on) override { autotune_ = on; }
+  int gs_choice(int level, int K, int* cluster, float* ms) const override {
+    if (level < 0 || level >= (int)views_.size() || kslot(K) < 0) return -1;
+    const GsChoice& c = (*tune_)[(size_t)level * 6 + kslot(K)];
+    if (cluster) *cluster = c.C;
+    if (ms) *ms = c.ms;
+    return c.kind;
+  }
   size_t clone_bytes(int kmax) const override {
     size_t b = 256;
     for (const LevelView<T>& L : views_) {
@@ -110,6 +140,11 @@ class DeviceVCycle : public VCycleIface {
 
   cudaError_t profile(int K, int reps, cudaStream_t s, double* ms, long long* count) override {
     if (kslot(K) < 0 || K > kmax_) return cudaErrorInvalidValue;
+    try {
+      if (autotune_) tune_for(K, s);
+    } catch (const std::exception&) {
+      return cudaErrorLaunchFailure;
+    }
     for (int rep = 0; rep < reps; ++rep) {
       recs_.clear();
       enq_kernels_ = 0;
@@ -294,10 +329,90 @@ class DeviceVCycle : public VCycleIface {
   // memory) one launch per phase.  No kernel needs its blocks co-resident.
   template <int K>
   void launch_gs(int l, cudaStream_t s) {
+    const GsChoice c = (*tune_)[(size_t)l * 6 + kslot(K)];
+    if (c.kind >= 0 && launch_gs_as<K>(l, c, s)) return;
     if (launch_gs_level<K>(l, s)) return;
     if (launch_gs_pipe<K>(l, s)) return;
+    launch_gs_fallback<K>(l, s);
+  }
+  template <int K>
+  void launch_gs_fallback(int l, cudaStream_t s) {
     if (K <= 8 && gs_lanes_[l] == 4) return launch_gs_g<K, (K <= 8 ? 4 : 1)>(l, s);
     launch_gs_g<K, 1>(l, s);
+  }
+  template <int K>
+  bool launch_gs_as(int l, const GsChoice& c, cudaStream_t s) {
+    switch (c.kind) {
+      case kGsSingle: return launch_gs_level<K>(l, s, true);
+      case kGsCluster: return launch_gs_cluster<K>(l, s, c.C);
+      case kGsPipe: return launch_gs_pipe<K>(l, s);
+      case kGsPhases: launch_gs_fallback<K>(l, s); return true;
+      case kGsDense:
+        if (!gsM_[l]) return false;
+        k_gs_dense<T, K><<<grid_for((long long)views_[l].n_p * 32), kBlock, 0, s>>>(views_[l].n_p, gsM_[l], buf_[l].g,
+                                                                                   buf_[l].dp);
+        return true;
+    }
+    return false;
+  }
+
+  // Gauss-Seidel autotuner: for each level, time every variant that applies to K
+  // right-hand sides (one block, a cluster of C blocks, the pipelined kernel, one
+  // launch per phase) with CUDA events on stream s and keep the fastest.  The
+  // variants relax the same rows in the same order but sum a row in different
+  // orders, so the table is shared with every clone of the cycle: all of them
+  // round alike.  Runs outside graph capture, before the first capture for K.
+  template <int K>
+  void tune_gs(cudaStream_t s) {
+    const int ks = kslot(K);
+    cudaEvent_t e0, e1;
+    EMIN_CUDA(cudaEventCreate(&e0));
+    EMIN_CUDA(cudaEventCreate(&e1));
+    for (int l = 0; l < (int)views_.size(); ++l) {
+      GsChoice& slot = (*tune_)[(size_t)l * 6 + ks];
+      if (slot.kind >= 0) continue;
+      std::vector<GsChoice> cands;
+      if (level_smem(l, K) <= 220 * 1024) cands.push_back({kGsSingle, 1, 0.f});
+      for (const ClusterPlan& P : cplans_[l])
+        if (cluster_smem(P, K, gs_[l].ncol) <= 220 * 1024) cands.push_back({kGsCluster, P.C, 0.f});
+      if (gs_stage(l, K) > 0 && gs_[l].ncol <= kMaxColors) cands.push_back({kGsPipe, 0, 0.f});
+      cands.push_back({kGsPhases, 0, 0.f});
+      if (gsM_[l]) cands.push_back({kGsDense, 0, 0.f});
+      GsChoice best{kGsPhases, 0, 1e30f};
+      for (GsChoice c : cands) {
+        float total = 0.f;
+        bool ok = true;
+        for (int rep = 0; rep < 4 && ok; ++rep) {
+          cudaMemsetAsync(buf_[l].dp, 0, sizeof(T) * (size_t)views_[l].n_p * K, s);
+          cudaEventRecord(e0, s);
+          ok = launch_gs_as<K>(l, c, s);
+          cudaEventRecord(e1, s);
+          if (ok) ++launches_;
+          if (cudaEventSynchronize(e1) != cudaSuccess) ok = false;
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          if (rep > 0) total += ms;  // the first run warms caches and loads the kernel
+        }
+        cudaGetLastError();
+        if (ok && total / 3.f < best.ms) best = {c.kind, c.C, total / 3.f};
+      }
+      slot = best;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    int err = 0;
+    cudaMemcpy(&err, err_, sizeof(int), cudaMemcpyDeviceToHost);
+    if (err) throw std::runtime_error("cuda: a Gauss-Seidel wait timed out while tuning");
+  }
+  void tune_for(int K, cudaStream_t s) {
+    switch (K) {
+      case 1: tune_gs<1>(s); break;
+      case 2: tune_gs<2>(s); break;
+      case 4: tune_gs<4>(s); break;
+      case 8: tune_gs<8>(s); break;
+      case 16: tune_gs<16>(s); break;
+      case 32: tune_gs<32>(s); break;
+    }
   }
 
   // Levels of at most two strips whose Schur data fits in one block's shared
@@ -309,9 +424,9 @@ class DeviceVCycle : public VCycleIface {
            ((size_t)3 * L.n_p + 1 + nnz + 2 * gs_[l].ncol + 1) * sizeof(int) + 16;
   }
   template <int K>
-  bool launch_gs_level(int l, cudaStream_t s) {
+  bool launch_gs_level(int l, cudaStream_t s, bool any_strips = false) {
     const GsStrips& P = gs_[l];
-    if (P.nstrips > 2 || level_smem(l, K) > 220 * 1024) return false;
+    if ((P.nstrips > 2 && !any_strips) || level_smem(l, K) > 220 * 1024) return false;
     const double rows_per_group = (double)views_[l].n_p / std::max(1, 2 * P.ncol);
     int G = 1;
     while (G < 4 && K * G * 2 <= 32 && rows_per_group * K * G * 2 <= kGsBlock) G *= 2;
@@ -327,6 +442,67 @@ class DeviceVCycle : public VCycleIface {
     kern<<<1, kGsBlock, smem, s>>>(views_[l], (const T*)buf_[l].g, buf_[l].dp, (const int*)plist_[l],
                                    (const int*)poff_[l], gs_[l].ncol, gs_iters_);
     return true;
+  }
+
+  // A thread-block cluster holding the whole level: the smallest cluster whose
+  // blocks fit their share in shared memory and relax a (parity, color) group in
+  // one pass, else the largest that fits; false if none fits or launches.
+  static size_t cluster_smem(const ClusterPlan& P, int K, int ncol) {
+    // dp window, g, 1/S_ii, S values | row offsets, permutation, S columns, plist, poff
+    const size_t b = ((size_t)P.win_max * K + (size_t)P.rows_max * K + P.rows_max + P.nnz_max) * sizeof(T) +
+                     ((size_t)3 * P.rows_max + 1 + P.nnz_max + 2 * ncol + 1) * sizeof(int);
+    return (b + 15) / 16 * 16;
+  }
+  template <int K>
+  bool launch_gs_cluster(int l, cudaStream_t s, int C) {
+    const GsStrips& S0 = gs_[l];
+    const ClusterPlan* pick = nullptr;
+    for (const ClusterPlan& P : cplans_[l])
+      if (P.C == C && cluster_smem(P, K, S0.ncol) <= 220 * 1024) pick = &P;
+    if (!pick) return false;
+    const double rows_per_group = (double)pick->rows_max / (2.0 * std::max(1, S0.ncol));
+    int G = 1;
+    while (G < 4 && K * G * 2 <= 32 && rows_per_group * K * G * 2 <= kGsBlock) G *= 2;
+    if (G == 4) return launch_gs_cluster_g<K, (K <= 8 ? 4 : 1)>(l, *pick, s);
+    if (G == 2) return launch_gs_cluster_g<K, (K <= 16 ? 2 : 1)>(l, *pick, s);
+    return launch_gs_cluster_g<K, 1>(l, *pick, s);
+  }
+  template <int K, int G>
+  bool launch_gs_cluster_g(int l, const ClusterPlan& P, cudaStream_t s) {
+    const size_t smem = cluster_smem(P, K, gs_[l].ncol);
+    auto kern = k_gs_cluster<T, K, G>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 48 * 1024));
+    if (P.C > 8) cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    GsCluster Q{};
+    Q.soff = gs_[l].soff;
+    Q.plist = P.plist;
+    Q.poff = P.poff;
+    Q.nstrips = gs_[l].nstrips;
+    Q.ncol = gs_[l].ncol;
+    Q.T = gs_[l].T;
+    Q.iters = gs_iters_;
+    Q.spc = P.spc;
+    Q.win_max = P.win_max;
+    Q.rows_max = P.rows_max;
+    Q.nnz_max = P.nnz_max;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(P.C);
+    cfg.blockDim = dim3(kGsBlock);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = P.C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) != cudaSuccess || nclusters < 1) {
+      cudaGetLastError();
+      return false;
+    }
+    return cudaLaunchKernelEx(&cfg, kern, views_[l], (const T*)buf_[l].g, buf_[l].dp, Q) == cudaSuccess;
   }
 
   // Lanes per row for the pipelined kernel: as many as the block has to spare
@@ -435,6 +611,12 @@ class DeviceVCycle : public VCycleIface {
     cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
     if (e != cudaSuccess) return e;
     cudaGraph_t g = nullptr;
+    try {
+      if (autotune_) tune_for(K, cs);
+    } catch (const std::exception&) {
+      cudaStreamDestroy(cs);
+      return cudaErrorLaunchFailure;
+    }
     enq_kernels_ = 0;
     e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
@@ -494,6 +676,10 @@ class DeviceVCycle : public VCycleIface {
       gs_ = o.gs_;
       gs_lanes_ = o.gs_lanes_;
       ci_rel_ = o.ci_rel_;
+      cplans_ = o.cplans_;
+      gsM_ = o.gsM_;
+      tune_ = o.tune_;
+      autotune_ = o.autotune_;
       plist_ = o.plist_;
       poff_ = o.poff_;
       s_nnz_ = o.s_nnz_;
@@ -522,6 +708,71 @@ class DeviceVCycle : public VCycleIface {
     B.g = alloc<T>((size_t)L.n_p * kmax_);
     B.dp = alloc<T>((size_t)L.n_p * kmax_);
     return B;
+  }
+
+  // M with dp = M g for gs_iters_ Gauss-Seidel iterations from dp = 0, relaxing the
+  // sorted rows group by group in the order (strip parity, color, index): every
+  // column of M at once, in FP64.  Row i of M becomes (e_i - sum_j S_ij M_j) / S_ii
+  // when row i is relaxed.
+  std::vector<double> dense_gs_map(int n_p, int ncol, int nstrips, const std::vector<int>& soff,
+                                   const std::vector<int>& perm, const Csr& So, const std::vector<double>& dinv) {
+    std::vector<double> M((size_t)n_p * n_p, 0.0), row(n_p);
+    const int stride = ncol + 1;
+    for (int it = 0; it < gs_iters_; ++it)
+      for (int par = 0; par < 2; ++par)
+        for (int c = 0; c < ncol; ++c)
+          for (int st = par; st < nstrips; st += 2)
+            for (int r = soff[(size_t)st * stride + c]; r < soff[(size_t)st * stride + c + 1]; ++r) {
+              const int i = perm[r];
+              std::fill(row.begin(), row.end(), 0.0);
+              row[i] = 1.0;
+              for (int64_t t = So.rowptr[r]; t < So.rowptr[r + 1]; ++t) {
+                const double v = So.val[t];
+                const double* Mj = M.data() + (size_t)So.col[t] * n_p;
+                for (int q = 0; q < n_p; ++q) row[q] -= v * Mj[q];
+              }
+              double* Mi = M.data() + (size_t)i * n_p;
+              for (int q = 0; q < n_p; ++q) Mi[q] = row[q] * dinv[r];
+            }
+    return M;
+  }
+
+  // Cluster plans for C = 2, 4, 8, 16 blocks (levels of more than two strips).
+  std::vector<ClusterPlan> cluster_plans(int n_p, int Tst, int ncol, int nstrips, const std::vector<int>& soff,
+                                         const Csr& So) {
+    std::vector<ClusterPlan> plans;
+    if (nstrips <= 2) return plans;
+    const int stride = ncol + 1;
+    for (int C = 2; C <= 16; C *= 2) {
+      if (C > nstrips) break;
+      ClusterPlan P;
+      P.C = C;
+      P.spc = (nstrips + C - 1) / C;
+      std::vector<int> plist(n_p), poff((size_t)C * (2 * ncol + 1), 0);
+      for (int c = 0; c < C; ++c) {
+        const int s0 = std::min(c * P.spc, nstrips), s1 = std::min(s0 + P.spc, nstrips);
+        if (s1 <= s0) continue;
+        const int q0 = soff[(size_t)s0 * stride], q1 = soff[(size_t)(s1 - 1) * stride + ncol];
+        const int r_lo = std::min(s0 * Tst, n_p), r_hi = std::min(s1 * Tst, n_p);
+        int pos = q0;
+        int* po = poff.data() + (size_t)c * (2 * ncol + 1);
+        for (int par = 0; par < 2; ++par)
+          for (int pc = 0; pc < ncol; ++pc) {
+            po[par * ncol + pc] = pos - q0;
+            for (int st = s0; st < s1; ++st)
+              if ((st & 1) == par)
+                for (int r = soff[(size_t)st * stride + pc]; r < soff[(size_t)st * stride + pc + 1]; ++r) plist[pos++] = r;
+          }
+        po[2 * ncol] = pos - q0;
+        P.rows_max = std::max(P.rows_max, q1 - q0);
+        P.win_max = std::max(P.win_max, std::min(n_p, r_hi + Tst) - std::max(0, r_lo - Tst));
+        P.nnz_max = std::max(P.nnz_max, (int)(So.rowptr[q1] - So.rowptr[q0]));
+      }
+      P.plist = alloc_copy<int>(plist);
+      P.poff = alloc_copy<int>(poff);
+      plans.push_back(P);
+    }
+    return plans;
   }
 
   void upload_level(const HostLevel& H, bool coarsest) {
@@ -604,6 +855,9 @@ class DeviceVCycle : public VCycleIface {
         }
       plist_.push_back(alloc_copy<int>(plist));
       poff_.push_back(alloc_copy<int>(poff));
+      cplans_.push_back(cluster_plans(H.n_p, Tst, ncol, nstrips, soff, So));
+      gsM_.push_back(H.n_p <= kGsDenseMax ? alloc_copy<T>(dense_gs_map(H.n_p, ncol, nstrips, soff, perm, So, dinv))
+                                          : nullptr);
     }
     // lanes per Schur row: 4 when rows are long enough to share
     const double avg = H.n_p ? (double)So.nnz() / H.n_p : 0.0;
@@ -636,6 +890,7 @@ class DeviceVCycle : public VCycleIface {
   double c_;
   T cfac_;
   int gs_iters_, pre_, post_, kmax_;
+  bool autotune_ = true;
   std::vector<LevelView<T>> views_;
   std::vector<Buf> buf_;
   std::vector<GsStrips> gs_;
@@ -643,6 +898,9 @@ class DeviceVCycle : public VCycleIface {
   std::vector<int*> ci_rel_;
   std::vector<int*> done_;
   std::vector<int*> plist_, poff_;
+  std::vector<std::vector<ClusterPlan>> cplans_;
+  std::vector<T*> gsM_;  // dense Gauss-Seidel map of small levels (nullptr elsewhere)
+  std::shared_ptr<std::vector<GsChoice>> tune_;  // [level * 6 + K slot], shared with clones
   std::vector<long long> s_nnz_;
   int* err_ = nullptr;
   FFLevel ff_{};

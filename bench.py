@@ -47,8 +47,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving stream")
     ap.add_argument("--serve-requests", type=int, default=64)
+    ap.add_argument("--serve-active", type=int, default=None, help="requests running at once (default SERVE_ACTIVE)")
+    ap.add_argument("--serve-merge", type=int, default=None, help="columns stacked per cohort (default SERVE_MERGE)")
     ap.add_argument("--ncu", action="store_true",
-                    help="short run for an ncu launch list: one warm-up solve, then one solve (FP32 V-cycle)")
+                    help="short run for an ncu launch list: one warm-up solve, then one solve (FP32 V-cycle) "
+                         "inside a cudaProfilerStart/Stop range")
     return ap.parse_args()
 
 
@@ -243,18 +246,40 @@ def reference_main(args):
 
 
 # ----------------------------------------------------------------------------
+# replicas: one independent batch per GPU
+
+def replica_aggregate(dist, device, seconds, units):
+    """Weak scaling over ranks: (max of the ranks' times, sum of their units of work).
+    Every rank calls it; with one process it returns its arguments."""
+    import torch
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    if dist is not None and dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+def rank_batch(rank, mesh=MESH, nrhs=NRHS):
+    """The seeded batch a rank solves: the lid cavity with right-hand-side seed = rank."""
+    from synth import stokes_lid_2d
+    return stokes_lid_2d(mesh, nrhs=nrhs, seed=rank)
+
+
+# ----------------------------------------------------------------------------
 # serving: a Poisson stream of Oseen solves over 15 resident hierarchies
 
 SERVE_RATE = 200.0
 SERVE_WARM = 12
-SERVE_ACTIVE = 32
+SERVE_ACTIVE = 8
 SERVE_RESTART = 50
+SERVE_MERGE = 8
 SERVE_WORKLOAD = ("Poisson arrivals at 200 req/s (seed 0) of 2D Oseen Q2-Q1 solves on [-1,1]^2 with the "
                   "recirculating wind, n from {64,128,256,384,512}, Re from {1,10,100}, 1-8 uniform[-1,1] "
                   "right-hand sides each, FP32 V-cycle / FP64 FGMRES to 1e-8, host buffers in and out")
 
 
-def serve(g, torch, dev, n_requests, seed=0):
+def serve(g, torch, dev, n_requests, seed=0, max_active=None, merge_k=None):
     """Builds the 15 hierarchies (untimed: setup is per matrix), runs a short
     warm-up stream, then the timed stream; latency = arrival to result on the host."""
     import numpy as np
@@ -282,7 +307,9 @@ def serve(g, torch, dev, n_requests, seed=0):
                             nrhs=r["nrhs"]))
         return out
 
-    sv = g.Server(max_active=SERVE_ACTIVE, restart=SERVE_RESTART, maxit=MAXIT)
+    max_active = max_active or SERVE_ACTIVE
+    merge_k = SERVE_MERGE if merge_k is None else merge_k
+    sv = g.Server(max_active=max_active, restart=SERVE_RESTART, maxit=MAXIT, merge_k=merge_k)
     t0 = time.perf_counter()
     for key in keys:  # one slot per (hierarchy, K) up front: no allocation or capture in the stream
         for k in (1, 2, 4, 8):
@@ -290,7 +317,7 @@ def serve(g, torch, dev, n_requests, seed=0):
     reserve_s = time.perf_counter() - t0
     g.run_stream(sv, requests(serving_stream(SERVE_WARM, SERVE_RATE, seed=1000 + seed)))
     reqs = requests(serving_stream(n_requests, SERVE_RATE, seed=seed))
-    l0 = sv.stats()["kernel_launches"]
+    l0, c0 = sv.stats()["kernel_launches"], sv.stats()["cohorts"]
     res = g.run_stream(sv, reqs)
     st = sv.stats()
     sv.close()
@@ -303,7 +330,8 @@ def serve(g, torch, dev, n_requests, seed=0):
         by_n.setdefault(q["n"], []).append(1000.0 * (r["done"] - r["arrival"]))
     return {"workload": SERVE_WORKLOAD, "requests": len(reqs), "rhs_solves": rhs, "all_converged": bool(ok),
             "wall_s": wall, "requests_per_s": len(reqs) / wall, "solves_per_s": rhs / wall,
-            "offered_rps": SERVE_RATE, "max_active": SERVE_ACTIVE, "restart": SERVE_RESTART,
+            "offered_rps": SERVE_RATE, "max_active": max_active, "restart": SERVE_RESTART,
+            "merge_k": merge_k, "cohorts": int(st["cohorts"] - c0),
             "latency_ms": {"p50": float(np.percentile(lat, 50) * 1000), "p99": float(np.percentile(lat, 99) * 1000),
                            "max": float(lat.max() * 1000)},
             "latency_p50_ms_by_mesh": {str(n): float(np.percentile(v, 50)) for n, v in sorted(by_n.items())},
@@ -341,17 +369,20 @@ def main():
                "seconds": t[0], "iterations": its_cpu[0]}
 
     import paper_1607_02489_gb300 as g
-    from synth import stokes_lid_2d
     g._build.build()
-    p = stokes_lid_2d(MESH, nrhs=NRHS, seed=rank)
+    p = rank_batch(rank)
     if args.ncu:
         H = g.Hierarchy(p, max_nrhs=NRHS, vcycle_fp32=1)
         b = torch.tensor(p.b, device=dev)
         x = torch.zeros_like(b)
         for rep in range(2):
             n0 = H.kernel_launches()
+            if rep == 1:  # the profiled range (ncu --profile-from-start off): the second solve only
+                torch.cuda.profiler.start()
             st, its, rel = H.fgmres(b, x, rtol=RTOL, restart=RESTART, maxit=MAXIT)
             torch.cuda.synchronize()
+            if rep == 1:
+                torch.cuda.profiler.stop()
             print(f"solve {rep}: status {st}, iterations {its.tolist()}, kernels {H.kernel_launches() - n0}",
                   flush=True)
         return
@@ -383,19 +414,15 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
-        ms = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms, H.kernel_launches() - n0, its, rel, lat
+        ms, solves = replica_aggregate(dist, dev, e0.elapsed_time(e1), NRHS * steps)
+        return ms, solves, H.kernel_launches() - n0, its, rel, lat
 
     sampler = ClockSampler(local)
     sampler.start()
-    ms32, launches32, its32, rel32, lat32 = timed(H32, args.steps, args.warmup)
+    ms32, solves, launches32, its32, rel32, lat32 = timed(H32, args.steps, args.warmup)
     clocks = sampler.stop()
     x32 = x[:, 0].cpu().numpy()
-    ms64, launches64, its64, rel64, lat64 = timed(H64, args.steps, args.warmup)
+    ms64, _, launches64, its64, rel64, lat64 = timed(H64, args.steps, args.warmup)
     x64 = x[:, 0].cpu().numpy()
     accuracy = None
     if x_oracle is not None:
@@ -412,7 +439,6 @@ def main():
                     "what": "relative 2-norm error of right-hand side 0's FGMRES solution (both stopped at "
                             f"{RTOL:g}) against the FP64 oracle's, pressure mean removed"}
 
-    solves = NRHS * args.steps * world
     value = solves / (ms32 / 1000.0)
     value64 = solves / (ms64 / 1000.0)
 
@@ -427,11 +453,7 @@ def main():
     for _ in range(args.steps):
         st, its_e, rel_e = H32.fgmres_host(bh, xh, rtol=RTOL, restart=RESTART, maxit=MAXIT)
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s, _ = replica_aggregate(dist, dev, time.perf_counter() - t0, 0)
     e2e = {"value": solves / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": int(bh.numel() * 8),
            "d2h_bytes_per_step": int(xh.numel() * 8)}
 
@@ -454,21 +476,20 @@ def main():
                 "bytes_per_launch": bytes_launch, "avg_launch_us": avg_ms * 1000.0,
                 "vcycle_kernels_GBs": vcycle_bytes / (vcycle_ms / 1000.0) / 1e9,
                 "vcycle_kernels_frac": vcycle_bytes / (vcycle_ms / 1000.0) / 1e9 / peak}
-    gs_variants = [f"L{l}: {v}{' x' + str(c) if v == 'cluster' else ''} ({1000.0 * t:.1f} us)"
+    gs_variants = [f"L{l}: {v}{' x' + str(c) if v == 'cluster' else (' shape ' + str(c) if v == 'pipelined' else '')}"
+                   f" ({1000.0 * t:.1f} us)"
                    for l, (v, c, t) in enumerate(H32.gs_variants(NRHS))]
     breakdown = {f"L{l}/{c}": round(float(ms_tab[l, k] / reps * 1000.0), 2)
                  for l in range(ms_tab.shape[0]) for k, c in enumerate(g.KERNEL_CLASSES) if cnt_tab[l, k]}
 
     serving = None
     if not args.no_serve:
-        serving = serve(g, torch, dev, args.serve_requests, seed=rank)
+        serving = serve(g, torch, dev, args.serve_requests, seed=rank, max_active=args.serve_active,
+                        merge_k=args.serve_merge)
         if world > 1:
-            t = torch.tensor([serving["wall_s"], serving["requests"], serving["rhs_solves"]], device=dev,
-                             dtype=torch.float64)
-            w = t[:1].clone()
-            dist.all_reduce(w, op=dist.ReduceOp.MAX)
-            dist.all_reduce(t, op=dist.ReduceOp.SUM)
-            serving["all_ranks"] = {"requests_per_s": float(t[1] / w[0]), "solves_per_s": float(t[2] / w[0])}
+            wall, reqs = replica_aggregate(dist, dev, serving["wall_s"], serving["requests"])
+            _, rhs = replica_aggregate(dist, dev, serving["wall_s"], serving["rhs_solves"])
+            serving["all_ranks"] = {"requests_per_s": reqs / wall, "solves_per_s": rhs / wall}
 
     if rank == 0:
         lat_sorted = sorted(lat32)

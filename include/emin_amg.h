@@ -215,9 +215,17 @@ const char* amg_last_error(void);
  * b and x, and a stream.  amg_server_progress() advances every running request
  * whose last chunk of device work has finished by one more chunk (an Arnoldi
  * step or a cycle end) and admits queued requests as slots and memory free up,
- * so their kernels overlap on the device.  A request's result is bit-identical
- * to amg_fgmres_solve_host() of the same right-hand sides with restart and maxit
- * set to the server's.
+ * so their kernels overlap on the device.
+ *
+ * Batching: a request starts together with the later queued requests on the
+ * same hierarchy and rtol whose right-hand sides fit beside its own within
+ * merge_k columns; the cohort's columns are stacked into one FGMRES solve (each
+ * column keeps its own Krylov space, Hessenberg matrix and convergence test), so
+ * one matrix pass of every V-cycle kernel serves all of them.  With merge_k <= 1 a
+ * request runs alone and its result is bit-identical to amg_fgmres_solve_host()
+ * of the same right-hand sides (restart and maxit set to the server's); in a
+ * cohort of K columns its columns are computed by the K-column kernels, which
+ * round differently from the kernels of its own width.
  *
  * Admission: a queued request takes an idle slot of the same (hierarchy, K), or
  * a new slot while fewer than max_active requests run and the slot's bytes fit
@@ -237,13 +245,16 @@ typedef struct {
   size_t device_bytes; /* device memory the slots may hold; 0 = 80% of the free memory at creation */
   int restart;         /* FGMRES restart length of every request; default 100 */
   int maxit;           /* iteration limit per right-hand side; default 500 */
+  int merge_k;         /* most columns stacked into one cohort, 0..32; default 8; <= 1: no batching */
 } amg_server_params;
 
 typedef struct {
-  int queued, running, slots;
+  int queued, running, slots; /* running: requests; slots: slots held (busy or idle) */
+  int busy_slots;             /* slots running a cohort */
   size_t bytes_in_use, budget;
   long long kernel_launches; /* kernels launched for the server's requests (graph nodes counted) */
   long long slots_created, slots_released, errors;
+  long long cohorts;          /* solves started (a cohort is one or more requests) */
 } amg_server_stats;
 
 void amg_server_params_default(amg_server_params* p);

@@ -62,14 +62,14 @@ class AmgLevelInfo(ctypes.Structure):
 
 class AmgServerParams(ctypes.Structure):
     _fields_ = [("max_active", ctypes.c_int), ("device_bytes", ctypes.c_size_t), ("restart", ctypes.c_int),
-                ("maxit", ctypes.c_int)]
+                ("maxit", ctypes.c_int), ("merge_k", ctypes.c_int)]
 
 
 class AmgServerStats(ctypes.Structure):
     _fields_ = [("queued", ctypes.c_int), ("running", ctypes.c_int), ("slots", ctypes.c_int),
-                ("bytes_in_use", ctypes.c_size_t), ("budget", ctypes.c_size_t),
+                ("busy_slots", ctypes.c_int), ("bytes_in_use", ctypes.c_size_t), ("budget", ctypes.c_size_t),
                 ("kernel_launches", ctypes.c_longlong), ("slots_created", ctypes.c_longlong),
-                ("slots_released", ctypes.c_longlong), ("errors", ctypes.c_longlong)]
+                ("slots_released", ctypes.c_longlong), ("errors", ctypes.c_longlong), ("cohorts", ctypes.c_longlong)]
 
 
 _lib = None
@@ -357,12 +357,13 @@ class Server:
     resident hierarchies.  submit() queues a solve on host buffers, progress()
     never blocks and returns the tickets that completed, result() collects one."""
 
-    def __init__(self, max_active=16, device_bytes=0, restart=100, maxit=500):
+    def __init__(self, max_active=16, device_bytes=0, restart=100, maxit=500, merge_k=8):
         lib = load()
         prm = AmgServerParams()
         lib.amg_server_params_default(ctypes.byref(prm))
         prm.max_active, prm.device_bytes, prm.restart, prm.maxit = int(max_active), int(device_bytes), int(restart), \
             int(maxit)
+        prm.merge_k = int(merge_k)
         h = ctypes.c_void_p()
         self._check(lib.amg_server_create(ctypes.byref(prm), ctypes.byref(h)))
         self._s = h

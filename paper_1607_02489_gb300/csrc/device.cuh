@@ -387,11 +387,10 @@ __device__ __forceinline__ void st_release(int* p, int v) {
 
 // done[0..nstrips) are the per-strip counters and done[nstrips] the ticket
 // counter; all are zero at launch, and dp is zero.
-template <typename T, int K, int G, int V>
-__global__ void __launch_bounds__(kGsPipeBlock) k_gs_pipe(LevelView<T> L, const T* __restrict__ g, T* dp, GsStrips P,
-                                                      const int* __restrict__ ci_rel, int* done, int* err) {
+template <typename T, int K, int G, int V, int NT>
+__global__ void __launch_bounds__(NT) k_gs_pipe(LevelView<T> L, const T* __restrict__ g, T* dp, GsStrips P,
+                                                const int* __restrict__ ci_rel, int* done, int* err) {
   static_assert((K / V) * G <= 32, "a row group must fit in a warp");
-  static_assert(G == 1 || V == 1, "lanes per row or columns per thread, not both");
   extern __shared__ __align__(16) unsigned char smem[];
   T* s_dp = reinterpret_cast<T*>(smem);
   T* s_g = s_dp + (size_t)3 * P.T * K;
@@ -475,38 +474,13 @@ __global__ void __launch_bounds__(kGsPipeBlock) k_gs_pipe(LevelView<T> L, const 
         const int r = ra + t / kGroup;
         const int ea = s_rp[r - q0], eb = s_rp[r - q0 + 1];
         T acc[V];
-        if constexpr (V == 1) {
-          T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
-          int e = ea + lane;
-          if (P.stage == 2) {
-            const T* sv = s_v - e0;
-            const int* sc = s_ci - e0;
-            for (; e + 3 * G < eb; e += 4 * G) {
-              const int c0 = sc[e], c1 = sc[e + G], c2 = sc[e + 2 * G], c3 = sc[e + 3 * G];
-              a0 += sv[e] * s_dp[c0 * K + k];
-              a1 += sv[e + G] * s_dp[c1 * K + k];
-              a2 += sv[e + 2 * G] * s_dp[c2 * K + k];
-              a3 += sv[e + 3 * G] * s_dp[c3 * K + k];
-            }
-            for (; e < eb; e += G) a0 += sv[e] * s_dp[sc[e] * K + k];
-          } else {
-            for (; e + 3 * G < eb; e += 4 * G) {
-              const int c0 = ci_rel[e], c1 = ci_rel[e + G], c2 = ci_rel[e + 2 * G], c3 = ci_rel[e + 3 * G];
-              a0 += L.S.v[e] * s_dp[c0 * K + k];
-              a1 += L.S.v[e + G] * s_dp[c1 * K + k];
-              a2 += L.S.v[e + 2 * G] * s_dp[c2 * K + k];
-              a3 += L.S.v[e + 3 * G] * s_dp[c3 * K + k];
-            }
-            for (; e < eb; e += G) a0 += L.S.v[e] * s_dp[ci_rel[e] * K + k];
-          }
-          acc[0] = group_sum<K, G>((a0 + a1) + (a2 + a3), mask);
-        } else {
-          // V right-hand sides per thread, G == 1: two independent partial sums per column
+        const T* sv = P.stage == 2 ? s_v - e0 : L.S.v;
+        const int* sc = P.stage == 2 ? s_ci - e0 : ci_rel;
+        if constexpr (V > 1 && G == 1) {
+          // V columns per thread, whole row: two independent partial sums per column
           T a[V], b2[V];
 #pragma unroll
           for (int uu = 0; uu < V; ++uu) a[uu] = b2[uu] = T(0);
-          const T* sv = P.stage == 2 ? s_v - e0 : L.S.v;
-          const int* sc = P.stage == 2 ? s_ci - e0 : ci_rel;
           int e = ea;
           for (; e + 1 < eb; e += 2) {
             const int c0 = sc[e], c1 = sc[e + 1];
@@ -528,6 +502,36 @@ __global__ void __launch_bounds__(kGsPipeBlock) k_gs_pipe(LevelView<T> L, const 
           }
 #pragma unroll
           for (int uu = 0; uu < V; ++uu) acc[uu] = a[uu] + b2[uu];
+        } else {
+          // V columns per thread, G lanes per row, four independent partial sums
+          T a1[V], a2[V], a3[V];
+#pragma unroll
+          for (int uu = 0; uu < V; ++uu) acc[uu] = a1[uu] = a2[uu] = a3[uu] = T(0);
+          int e = ea + lane;
+          for (; e + 3 * G < eb; e += 4 * G) {
+            const int c0 = sc[e], c1 = sc[e + G], c2 = sc[e + 2 * G], c3 = sc[e + 3 * G];
+            const T v0 = sv[e], v1 = sv[e + G], v2 = sv[e + 2 * G], v3 = sv[e + 3 * G];
+            T d0[V], d1[V], d2[V], d3[V];
+            vld<T, V>(d0, s_dp + c0 * K + k);
+            vld<T, V>(d1, s_dp + c1 * K + k);
+            vld<T, V>(d2, s_dp + c2 * K + k);
+            vld<T, V>(d3, s_dp + c3 * K + k);
+#pragma unroll
+            for (int uu = 0; uu < V; ++uu) {
+              acc[uu] += v0 * d0[uu];
+              a1[uu] += v1 * d1[uu];
+              a2[uu] += v2 * d2[uu];
+              a3[uu] += v3 * d3[uu];
+            }
+          }
+          for (; e < eb; e += G) {
+            T d0[V];
+            vld<T, V>(d0, s_dp + sc[e] * K + k);
+#pragma unroll
+            for (int uu = 0; uu < V; ++uu) acc[uu] += sv[e] * d0[uu];
+          }
+#pragma unroll
+          for (int uu = 0; uu < V; ++uu) acc[uu] = group_sum<KV, G>((acc[uu] + a1[uu]) + (a2[uu] + a3[uu]), mask);
         }
         if (lane == 0) {
           const int i = s_perm[r - q0];
@@ -1155,6 +1159,28 @@ __global__ void __launch_bounds__(kBlock) k_pack(long long N, const TS* __restri
   const long long i = t / K;
   const int k = (int)(t % K);
   dst[t] = k < nrhs ? (TD)src[i * ld + k] : TD(0);
+}
+
+// Columns [col0, col0 + ncols) of dst (N x K) = src (N x ncols); other columns untouched.
+template <int K>
+__global__ void __launch_bounds__(kBlock) k_pack_cols(long long N, const double* __restrict__ src, int ncols,
+                                                      double* __restrict__ dst, int col0) {
+  const long long t = gtid();
+  if (t >= N * ncols) return;
+  const long long i = t / ncols;
+  const int k = (int)(t % ncols);
+  dst[i * K + col0 + k] = src[t];
+}
+
+// dst (N x ncols) = columns [col0, col0 + ncols) of src (N x K).
+template <int K>
+__global__ void __launch_bounds__(kBlock) k_unpack_cols(long long N, const double* __restrict__ src, int col0,
+                                                        int ncols, double* __restrict__ dst) {
+  const long long t = gtid();
+  if (t >= N * ncols) return;
+  const long long i = t / ncols;
+  const int k = (int)(t % ncols);
+  dst[t] = src[i * K + col0 + k];
 }
 
 template <typename TS, typename TD, int K>

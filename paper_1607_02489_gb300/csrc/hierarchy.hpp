@@ -67,12 +67,29 @@ class SolveTask {
   virtual ~SolveTask() = default;
   virtual bool advance() = 0;
   virtual amg_status result(int* iters, double* relres) const = 0;
+  // Status of one column: AMG_OK, AMG_NOT_CONVERGED or AMG_BREAKDOWN.
+  virtual amg_status column_status(int k) const = 0;
   long long launches = 0;  // kernels this task launched outside the V-cycle graphs
 };
 
-// b and x are device buffers in the caller's layout (N x nrhs, row-major); when
-// b_host / x_host are given, the first chunk copies b_host into b and the last
-// copies x out to x_host.  The V-cycle vc must have K = round_k(nrhs) <= vc->kmax().
+// A group of right-hand sides of a solve: ncols columns in the caller's layout
+// (device b and x, N x ncols row-major); when b_host / x_host are given, the first
+// chunk copies b_host into b and the last copies x out to x_host.
+struct SolveSegment {
+  const double* b = nullptr;
+  double* x = nullptr;
+  const double* b_host = nullptr;
+  double* x_host = nullptr;
+  int ncols = 0;
+};
+
+// One solve of the segments' columns side by side (column order = segment order).
+// Every column runs its own FGMRES; they share the kernels of K = round_k(total
+// columns) <= vc->kmax().
+std::unique_ptr<SolveTask> make_solve_task(struct amg_hierarchy_core* h, VCycleIface* vc, Krylov* ws,
+                                           const std::vector<SolveSegment>& segs, double rtol, int restart, int maxit,
+                                           cudaStream_t s);
+// The single-segment form.
 std::unique_ptr<SolveTask> make_solve_task(struct amg_hierarchy_core* h, VCycleIface* vc, Krylov* ws, const double* b,
                                            double* x, const double* b_host, double* x_host, int nrhs, double rtol,
                                            int restart, int maxit, cudaStream_t s);

@@ -54,8 +54,9 @@ struct Slot {
   cudaStream_t s = nullptr;
   cudaEvent_t ev = nullptr;
   size_t bytes = 0;
-  long long req = -1;  // running request, -1 when idle
+  std::vector<long long> members;  // requests of the running cohort, empty when idle
   std::unique_ptr<SolveTask> task;
+  bool busy() const { return !members.empty(); }
   unsigned long long last_used = 0;
 
   ~Slot() {
@@ -77,6 +78,7 @@ struct Request {
   const double* bh = nullptr;
   double* xh = nullptr;
   int state = 0;  // 0 queued, 1 running, 2 done
+  int col0 = 0;   // first column of the request in its cohort
   amg_status status = AMG_OK;
   std::vector<int> iters;
   std::vector<double> relres;
@@ -102,12 +104,17 @@ struct amg_server {
   unsigned long long tick = 0;
   long long task_launches = 0;      // kernels launched by the solve tasks outside the graphs
   long long retired_vc_launches = 0;  // graph kernels of slots already released
-  long long slots_created = 0, slots_released = 0, errors = 0;
+  long long slots_created = 0, slots_released = 0, errors = 0, cohorts = 0;
   std::string last_error;
 
-  int running() const {
+  int busy_slots() const {
     int n = 0;
-    for (const auto& sl : slots) n += sl->req >= 0;
+    for (const auto& sl : slots) n += sl->busy();
+    return n;
+  }
+  int running_requests() const {
+    int n = 0;
+    for (const auto& sl : slots) n += (int)sl->members.size();
     return n;
   }
 
@@ -118,24 +125,47 @@ struct amg_server {
     ++slots_released;
   }
 
-  void finish(Slot& sl, Request& r, amg_status st, const std::string& err) {
+  void fail_request(long long id, amg_status st, const std::string& err) {
+    Request& r = reqs.at(id);
     r.state = 2;
+    r.status = st;
     r.t_done = now_s();
-    if (st == AMG_OK || st == AMG_NOT_CONVERGED || st == AMG_BREAKDOWN) {
-      r.status = sl.task->result(r.iters.data(), r.relres.data());
+    last_error = err;
+    ++errors;
+    completed.push_back(id);
+  }
+
+  // The cohort of a slot is done (st = AMG_OK) or failed (st < 0): report every member.
+  void finish(Slot& sl, amg_status st, const std::string& err) {
+    const double t = now_s();
+    if (st >= 0 && sl.task) {
+      int total = 0;
+      for (long long id : sl.members) total += reqs.at(id).nrhs;
+      std::vector<int> it(total);
+      std::vector<double> rel(total);
+      sl.task->result(it.data(), rel.data());
+      for (long long id : sl.members) {
+        Request& r = reqs.at(id);
+        r.state = 2;
+        r.t_done = t;
+        r.status = AMG_OK;
+        for (int k = 0; k < r.nrhs; ++k) {
+          r.iters[k] = it[r.col0 + k];
+          r.relres[k] = rel[r.col0 + k];
+          const amg_status cs = sl.task->column_status(r.col0 + k);
+          if (cs != AMG_OK && r.status != AMG_BREAKDOWN) r.status = cs;
+        }
+        completed.push_back(id);
+      }
     } else {
-      r.status = st;
-      last_error = err;
-      ++errors;
+      for (long long id : sl.members) fail_request(id, st < 0 ? st : AMG_ERR_CUDA, err);
     }
-    completed.push_back(sl.req);
-    sl.req = -1;
+    sl.members.clear();
     sl.task.reset();
   }
 
-  // Runs the next chunk of a slot's request; false when the request finished.
+  // Runs the next chunk of a slot's cohort; reports it when the solve finished.
   void step(Slot& sl) {
-    Request& r = reqs.at(sl.req);
     try {
       const bool more = sl.task->advance();
       task_launches += sl.task->launches;
@@ -143,10 +173,10 @@ struct amg_server {
       if (more) {
         EMIN_CUDA(cudaEventRecord(sl.ev, sl.s));
       } else {
-        finish(sl, r, AMG_OK, "");
+        finish(sl, AMG_OK, "");
       }
     } catch (const std::exception& e) {
-      finish(sl, r, AMG_ERR_CUDA, e.what());
+      finish(sl, AMG_ERR_CUDA, e.what());
     }
   }
 
@@ -173,13 +203,13 @@ struct amg_server {
   Slot* find_slot(amg_hierarchy* h, int K, bool& no_room) {
     no_room = false;
     for (auto& sl : slots)
-      if (sl->req < 0 && sl->h == h && sl->K == K) return sl.get();
-    if (running() >= prm.max_active) return nullptr;
+      if (!sl->busy() && sl->h == h && sl->K == K) return sl.get();
+    if (busy_slots() >= prm.max_active) return nullptr;
     const size_t need = slot_bytes(h, K, prm.restart);
     while (bytes + need > budget) {
       size_t victim = slots.size();
       for (size_t i = 0; i < slots.size(); ++i)
-        if (slots[i]->req < 0 && (victim == slots.size() || slots[i]->last_used < slots[victim]->last_used))
+        if (!slots[i]->busy() && (victim == slots.size() || slots[i]->last_used < slots[victim]->last_used))
           victim = i;
       if (victim == slots.size()) break;
       release_slot(victim);
@@ -191,71 +221,93 @@ struct amg_server {
     return make_slot(h, K);
   }
 
+  // Starts queued requests, in submission order, while slots and memory allow.  A
+  // request starts together with the later queued requests on the same hierarchy
+  // (same rtol) whose columns fit beside its own within merge_k: one cohort, one
+  // FGMRES over the stacked columns, one slot of K = columns rounded up.
   void admit() {
-    for (auto it = queue.begin(); it != queue.end();) {
-      if (running() >= prm.max_active) return;
-      Request& r = reqs.at(*it);
+    std::vector<long long> q(queue.begin(), queue.end());
+    std::vector<char> taken(q.size(), 0);
+    for (size_t a = 0; a < q.size(); ++a) {
+      if (taken[a]) continue;
+      if (busy_slots() >= prm.max_active) break;
+      const Request& r = reqs.at(q[a]);
+      std::vector<size_t> cohort{a};
+      int total = r.nrhs;
+      if (prm.merge_k > 1)
+        for (size_t b = a + 1; b < q.size(); ++b) {
+          if (taken[b]) continue;
+          const Request& o = reqs.at(q[b]);
+          if (o.h == r.h && o.rtol == r.rtol && total + o.nrhs <= prm.merge_k) {
+            cohort.push_back(b);
+            total += o.nrhs;
+          }
+        }
       bool no_room = false;
       Slot* sl = nullptr;
       try {
-        sl = find_slot(r.h, round_k(r.nrhs), no_room);
+        sl = find_slot(r.h, round_k(total), no_room);
       } catch (const std::exception& e) {
-        // a slot that could not be built: the request fails, the server carries on
-        r.state = 2;
-        r.status = std::string(e.what()).find("cudaMalloc") != std::string::npos ? AMG_ERR_OOM : AMG_ERR_CUDA;
-        r.t_done = now_s();
-        last_error = e.what();
-        ++errors;
-        completed.push_back(*it);
-        it = queue.erase(it);
+        // a slot that could not be built: the cohort fails, the server carries on
+        const amg_status st =
+            std::string(e.what()).find("cudaMalloc") != std::string::npos ? AMG_ERR_OOM : AMG_ERR_CUDA;
+        for (size_t idx : cohort) {
+          fail_request(q[idx], st, e.what());
+          taken[idx] = 1;
+        }
         continue;
       }
       if (!sl) {
-        if (no_room && running() == 0 && slots.empty()) {
+        if (no_room && busy_slots() == 0 && slots.empty()) {
           // it can never fit: the whole budget is smaller than one slot
-          r.state = 2;
-          r.status = AMG_ERR_OOM;
-          r.t_done = now_s();
-          last_error = "request needs more device memory than the server's budget";
-          ++errors;
-          completed.push_back(*it);
-          it = queue.erase(it);
-          continue;
+          fail_request(q[a], AMG_ERR_OOM, "request needs more device memory than the server's budget");
+          taken[a] = 1;
         }
-        ++it;  // stays queued; a smaller request behind it may still fit
-        continue;
+        continue;  // stays queued; a smaller request behind it may still fit
       }
-      sl->req = *it;
+      const double t = now_s();
+      std::vector<SolveSegment> segs;
+      int col0 = 0;
+      sl->members.clear();
+      for (size_t idx : cohort) {
+        Request& m = reqs.at(q[idx]);
+        m.state = 1;
+        m.t_start = t;
+        m.col0 = col0;
+        SolveSegment g;
+        g.b = sl->dev_b + (size_t)sl->h->N * col0;
+        g.x = sl->dev_x + (size_t)sl->h->N * col0;
+        g.b_host = m.bh;
+        g.x_host = m.xh;
+        g.ncols = m.nrhs;
+        segs.push_back(g);
+        col0 += m.nrhs;
+        sl->members.push_back(q[idx]);
+        taken[idx] = 1;
+      }
       sl->last_used = ++tick;
-      r.state = 1;
-      r.t_start = now_s();
       try {
-        sl->task = make_solve_task(r.h, sl->vc.get(), &sl->ws, sl->dev_b, sl->dev_x, r.bh, r.xh, r.nrhs, r.rtol,
-                                   prm.restart, prm.maxit, sl->s);
+        sl->task = make_solve_task(sl->h, sl->vc.get(), &sl->ws, segs, r.rtol, prm.restart, prm.maxit, sl->s);
       } catch (const std::exception& e) {
-        sl->task.reset();
-        r.state = 2;
-        r.status = AMG_ERR_CUDA;
-        r.t_done = now_s();
-        last_error = e.what();
-        ++errors;
-        completed.push_back(sl->req);
-        sl->req = -1;
-        it = queue.erase(it);
+        finish(*sl, AMG_ERR_CUDA, e.what());
         continue;
       }
-      it = queue.erase(it);
+      ++cohorts;
       step(*sl);
     }
+    std::deque<long long> rest;
+    for (size_t i = 0; i < q.size(); ++i)
+      if (!taken[i]) rest.push_back(q[i]);
+    queue.swap(rest);
   }
 
   void poll() {
     for (auto& sl : slots) {
-      if (sl->req < 0) continue;
+      if (!sl->busy()) continue;
       const cudaError_t e = cudaEventQuery(sl->ev);
       if (e == cudaErrorNotReady) continue;
       if (e != cudaSuccess) {
-        finish(*sl, reqs.at(sl->req), AMG_ERR_CUDA, std::string("cuda: ") + cudaGetErrorString(e));
+        finish(*sl, AMG_ERR_CUDA, std::string("cuda: ") + cudaGetErrorString(e));
         continue;
       }
       sl->last_used = ++tick;
@@ -284,6 +336,7 @@ void amg_server_params_default(amg_server_params* p) {
   p->device_bytes = 0;
   p->restart = 100;
   p->maxit = 500;
+  p->merge_k = 8;
 }
 
 const char* amg_server_last_error(amg_server_handle sv) {
@@ -300,6 +353,7 @@ amg_status amg_server_create(const amg_server_params* prm_in, amg_server_handle*
     amg_server_params_default(&prm);
   if (prm.max_active < 1 || prm.max_active > 256) return sfail(AMG_ERR_ARG, "max_active must be in 1..256");
   if (prm.restart < 1 || prm.maxit < 1) return sfail(AMG_ERR_ARG, "restart and maxit must be positive");
+  if (prm.merge_k < 0 || prm.merge_k > 32) return sfail(AMG_ERR_ARG, "merge_k must be in 0..32");
   std::unique_ptr<amg_server> sv(new amg_server());
   sv->prm = prm;
   if (prm.device_bytes > 0) {
@@ -404,7 +458,9 @@ amg_status amg_server_state(amg_server_handle sv, long long ticket, int* state) 
 amg_status amg_server_get_stats(amg_server_handle sv, amg_server_stats* st) {
   if (!sv || !st) return sfail(AMG_ERR_ARG, "null argument");
   st->queued = (int)sv->queue.size();
-  st->running = sv->running();
+  st->running = sv->running_requests();
+  st->busy_slots = sv->busy_slots();
+  st->cohorts = sv->cohorts;
   st->slots = (int)sv->slots.size();
   st->bytes_in_use = sv->bytes;
   st->budget = sv->budget;

@@ -338,11 +338,11 @@ void col_norms(const Krylov& w, const double* v, double* out, cudaStream_t s, lo
 template <int K, typename TZ>
 class FgmresTask final : public SolveTask {
  public:
-  FgmresTask(amg_hierarchy_core* h, VCycleIface* vc, Krylov* ws, const double* b, double* x, const double* bh,
-             double* xh, int nrhs, double rtol, int restart, int maxit, cudaStream_t s)
-      : h_(h), vc_(vc), w_(ws), b_(b), x_(x), bh_(bh), xh_(xh), nrhs_(nrhs), restart_(restart), maxit_(maxit),
-        rtol_(rtol), s_(s), N_(h->N), NK_(h->N * K), gNK_(grid_for(h->N * K)), bn_(K, 0.0), rel_(K, 0.0),
-        total_(K, 0), done_(K, 0), flag_(K, 0) {}
+  FgmresTask(amg_hierarchy_core* h, VCycleIface* vc, Krylov* ws, const std::vector<SolveSegment>& segs, int nrhs,
+             double rtol, int restart, int maxit, cudaStream_t s)
+      : h_(h), vc_(vc), w_(ws), segs_(segs), nrhs_(nrhs), restart_(restart), maxit_(maxit), rtol_(rtol), s_(s),
+        N_(h->N), NK_(h->N * K), gNK_(grid_for(h->N * K)), bn_(K, 0.0), rel_(K, 0.0), total_(K, 0), done_(K, 0),
+        flag_(K, 0) {}
 
   bool advance() override {
     switch (phase_) {
@@ -405,6 +405,11 @@ class FgmresTask final : public SolveTask {
     return false;
   }
 
+  amg_status column_status(int k) const override {
+    if (k < 0 || k >= nrhs_ || bn_[k] == 0.0 || rel_[k] <= rtol_) return AMG_OK;
+    return flag_[k] == 2 ? AMG_BREAKDOWN : AMG_NOT_CONVERGED;
+  }
+
   amg_status result(int* iters, double* relres) const override {
     amg_status st = AMG_OK;
     for (int k = 0; k < nrhs_; ++k) {
@@ -423,10 +428,22 @@ class FgmresTask final : public SolveTask {
   }
 
   void start() {
-    if (bh_)
-      EMIN_CUDA(cudaMemcpyAsync(const_cast<double*>(b_), bh_, sizeof(double) * N_ * nrhs_, cudaMemcpyHostToDevice, s_));
-    k_pack<double, double, K><<<gNK_, kBlock, 0, s_>>>(N_, b_, nrhs_, nrhs_, w_->bK);
-    ++launches;
+    for (const SolveSegment& g : segs_)
+      if (g.b_host)
+        EMIN_CUDA(cudaMemcpyAsync(const_cast<double*>(g.b), g.b_host, sizeof(double) * N_ * g.ncols,
+                                  cudaMemcpyHostToDevice, s_));
+    if (segs_.size() == 1) {
+      k_pack<double, double, K><<<gNK_, kBlock, 0, s_>>>(N_, segs_[0].b, nrhs_, nrhs_, w_->bK);
+      ++launches;
+    } else {
+      if (nrhs_ < K) EMIN_CUDA(cudaMemsetAsync(w_->bK, 0, sizeof(double) * NK_, s_));
+      int col0 = 0;
+      for (const SolveSegment& g : segs_) {
+        k_pack_cols<K><<<grid_for(N_ * g.ncols), kBlock, 0, s_>>>(N_, g.b, g.ncols, w_->bK, col0);
+        ++launches;
+        col0 += g.ncols;
+      }
+    }
     EMIN_CUDA(cudaMemsetAsync(w_->xK, 0, sizeof(double) * NK_, s_));
     col_norms<K>(*w_, w_->bK, w_->bnorm, s_, launches);
     EMIN_CUDA(cudaMemcpyAsync(w_->host_d, w_->bnorm, sizeof(double) * K, cudaMemcpyDeviceToHost, s_));
@@ -512,10 +529,21 @@ class FgmresTask final : public SolveTask {
   }
 
   bool finish() {
-    k_unpack<double, double, K><<<grid_for(N_ * nrhs_), kBlock, 0, s_>>>(N_, w_->xK, nrhs_, x_, nrhs_);
-    ++launches;
+    if (segs_.size() == 1) {
+      k_unpack<double, double, K><<<grid_for(N_ * nrhs_), kBlock, 0, s_>>>(N_, w_->xK, nrhs_, segs_[0].x, nrhs_);
+      ++launches;
+    } else {
+      int col0 = 0;
+      for (const SolveSegment& g : segs_) {
+        k_unpack_cols<K><<<grid_for(N_ * g.ncols), kBlock, 0, s_>>>(N_, w_->xK, col0, g.ncols, g.x);
+        ++launches;
+        col0 += g.ncols;
+      }
+    }
     EMIN_CUDA(cudaGetLastError());
-    if (xh_) EMIN_CUDA(cudaMemcpyAsync(xh_, x_, sizeof(double) * N_ * nrhs_, cudaMemcpyDeviceToHost, s_));
+    for (const SolveSegment& g : segs_)
+      if (g.x_host)
+        EMIN_CUDA(cudaMemcpyAsync(g.x_host, g.x, sizeof(double) * N_ * g.ncols, cudaMemcpyDeviceToHost, s_));
     phase_ = kFinish;
     return true;
   }
@@ -523,10 +551,7 @@ class FgmresTask final : public SolveTask {
   amg_hierarchy_core* h_;
   VCycleIface* vc_;
   Krylov* w_;
-  const double* b_;
-  double* x_;
-  const double* bh_;
-  double* xh_;
+  std::vector<SolveSegment> segs_;
   int nrhs_, restart_, maxit_;
   double rtol_;
   cudaStream_t s_;
@@ -539,32 +564,49 @@ class FgmresTask final : public SolveTask {
 };
 
 template <typename TZ>
-std::unique_ptr<SolveTask> make_task_t(int K, amg_hierarchy_core* h, VCycleIface* vc, Krylov* ws, const double* b,
-                                       double* x, const double* bh, double* xh, int nrhs, double rtol, int restart,
+std::unique_ptr<SolveTask> make_task_t(int K, amg_hierarchy_core* h, VCycleIface* vc, Krylov* ws,
+                                       const std::vector<SolveSegment>& g, int nrhs, double rtol, int restart,
                                        int maxit, cudaStream_t s) {
   switch (K) {
-    case 1: return std::make_unique<FgmresTask<1, TZ>>(h, vc, ws, b, x, bh, xh, nrhs, rtol, restart, maxit, s);
-    case 2: return std::make_unique<FgmresTask<2, TZ>>(h, vc, ws, b, x, bh, xh, nrhs, rtol, restart, maxit, s);
-    case 4: return std::make_unique<FgmresTask<4, TZ>>(h, vc, ws, b, x, bh, xh, nrhs, rtol, restart, maxit, s);
-    case 8: return std::make_unique<FgmresTask<8, TZ>>(h, vc, ws, b, x, bh, xh, nrhs, rtol, restart, maxit, s);
-    case 16: return std::make_unique<FgmresTask<16, TZ>>(h, vc, ws, b, x, bh, xh, nrhs, rtol, restart, maxit, s);
-    case 32: return std::make_unique<FgmresTask<32, TZ>>(h, vc, ws, b, x, bh, xh, nrhs, rtol, restart, maxit, s);
+    case 1: return std::make_unique<FgmresTask<1, TZ>>(h, vc, ws, g, nrhs, rtol, restart, maxit, s);
+    case 2: return std::make_unique<FgmresTask<2, TZ>>(h, vc, ws, g, nrhs, rtol, restart, maxit, s);
+    case 4: return std::make_unique<FgmresTask<4, TZ>>(h, vc, ws, g, nrhs, rtol, restart, maxit, s);
+    case 8: return std::make_unique<FgmresTask<8, TZ>>(h, vc, ws, g, nrhs, rtol, restart, maxit, s);
+    case 16: return std::make_unique<FgmresTask<16, TZ>>(h, vc, ws, g, nrhs, rtol, restart, maxit, s);
+    case 32: return std::make_unique<FgmresTask<32, TZ>>(h, vc, ws, g, nrhs, rtol, restart, maxit, s);
   }
   throw std::runtime_error("nrhs must be in 1..32");
 }
 
 }  // namespace fgmres_detail
 
-std::unique_ptr<SolveTask> make_solve_task(amg_hierarchy_core* h, VCycleIface* vc, Krylov* ws, const double* b,
-                                           double* x, const double* b_host, double* x_host, int nrhs, double rtol,
-                                           int restart, int maxit, cudaStream_t s) {
+std::unique_ptr<SolveTask> make_solve_task(amg_hierarchy_core* h, VCycleIface* vc, Krylov* ws,
+                                           const std::vector<SolveSegment>& segs, double rtol, int restart, int maxit,
+                                           cudaStream_t s) {
+  int nrhs = 0;
+  for (const SolveSegment& g : segs) {
+    if (g.ncols < 1 || !g.b || !g.x) throw std::runtime_error("empty or null solve segment");
+    nrhs += g.ncols;
+  }
   const int K = round_k(nrhs);
   if (nrhs < 1 || K > 32 || K > vc->kmax()) throw std::runtime_error("nrhs exceeds the V-cycle's max_nrhs");
   if (ws->N != h->N || ws->K != K || ws->m < restart || ws->f32 != vc->is_fp32())
     throw std::runtime_error("solver workspace does not match the solve");
   using fgmres_detail::make_task_t;
-  if (vc->is_fp32()) return make_task_t<float>(K, h, vc, ws, b, x, b_host, x_host, nrhs, rtol, restart, maxit, s);
-  return make_task_t<double>(K, h, vc, ws, b, x, b_host, x_host, nrhs, rtol, restart, maxit, s);
+  if (vc->is_fp32()) return make_task_t<float>(K, h, vc, ws, segs, nrhs, rtol, restart, maxit, s);
+  return make_task_t<double>(K, h, vc, ws, segs, nrhs, rtol, restart, maxit, s);
+}
+
+std::unique_ptr<SolveTask> make_solve_task(amg_hierarchy_core* h, VCycleIface* vc, Krylov* ws, const double* b,
+                                           double* x, const double* b_host, double* x_host, int nrhs, double rtol,
+                                           int restart, int maxit, cudaStream_t s) {
+  SolveSegment g;
+  g.b = b;
+  g.x = x;
+  g.b_host = b_host;
+  g.x_host = x_host;
+  g.ncols = nrhs;
+  return make_solve_task(h, vc, ws, std::vector<SolveSegment>{g}, rtol, restart, maxit, s);
 }
 
 }  // namespace emin

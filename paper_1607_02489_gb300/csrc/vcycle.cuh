@@ -75,7 +75,7 @@ class DeviceVCycle : public VCycleIface {
   static constexpr int kGsDenseMax = 1024;  // pressures of a level whose Gauss-Seidel map is formed densely
   struct GsChoice {
     int kind = -1;  // GsKind, -1 = not tuned yet
-    int C = 0;      // cluster size
+    int C = 0;      // cluster size; shape of the pipelined kernel (0 heuristic, 1-3 launch_gs_pipe)
     float ms = 0.f; // measured time per launch
   };
   struct ClusterPlan {
@@ -345,7 +345,7 @@ class DeviceVCycle : public VCycleIface {
     switch (c.kind) {
       case kGsSingle: return launch_gs_level<K>(l, s, true);
       case kGsCluster: return launch_gs_cluster<K>(l, s, c.C);
-      case kGsPipe: return launch_gs_pipe<K>(l, s);
+      case kGsPipe: return launch_gs_pipe<K>(l, s, c.C);
       case kGsPhases: launch_gs_fallback<K>(l, s); return true;
       case kGsDense:
         if (!gsM_[l]) return false;
@@ -375,7 +375,8 @@ class DeviceVCycle : public VCycleIface {
       if (level_smem(l, K) <= 220 * 1024) cands.push_back({kGsSingle, 1, 0.f});
       for (const ClusterPlan& P : cplans_[l])
         if (cluster_smem(P, K, gs_[l].ncol) <= 220 * 1024) cands.push_back({kGsCluster, P.C, 0.f});
-      if (gs_stage(l, K) > 0 && gs_[l].ncol <= kMaxColors) cands.push_back({kGsPipe, 0, 0.f});
+      if (gs_stage(l, K) > 0 && gs_[l].ncol <= kMaxColors)
+        for (int v = 0; v < 4; ++v) cands.push_back({kGsPipe, v, 0.f});
       cands.push_back({kGsPhases, 0, 0.f});
       if (gsM_[l]) cands.push_back({kGsDense, 0, 0.f});
       GsChoice best{kGsPhases, 0, 1e30f};
@@ -508,19 +509,35 @@ class DeviceVCycle : public VCycleIface {
   // Lanes per row for the pipelined kernel: as many as the block has to spare
   // for the average color of a strip (K * G <= 32).
   template <int K>
-  bool launch_gs_pipe(int l, cudaStream_t s) {
+  bool launch_gs_pipe(int l, cudaStream_t s, int variant = 0) {
+    // shapes the autotuner also tries: 1024 threads with (lanes per row, columns per thread)
+    switch (variant) {
+      case 1: return launch_gs_pipe_v<K, 2, 2, 1024>(l, s);
+      case 2: return launch_gs_pipe_v<K, 1, 2, 1024>(l, s);
+      case 3: return launch_gs_pipe_v<K, 4, 1, 1024>(l, s);
+      default: break;
+    }
     const GsStrips& P0 = gs_[l];
     const double rows_per_color = (double)P0.T / std::max(1, P0.ncol);
     int G = 1;
     while (G < 4 && K * G * 2 <= 32 && rows_per_color * K * G * 2 <= kGsPipeBlock) G *= 2;
-    if (G == 4) return launch_gs_pipe_g<K, (K <= 8 ? 4 : 1), 1>(l, s);
-    if (G == 2) return launch_gs_pipe_g<K, (K <= 16 ? 2 : 1), 1>(l, s);
+    if (G == 4) return launch_gs_pipe_g<K, (K <= 8 ? 4 : 1), 1, kGsPipeBlock>(l, s);
+    if (G == 2) return launch_gs_pipe_g<K, (K <= 16 ? 2 : 1), 1, kGsPipeBlock>(l, s);
     // a color too large for one pass at one column per thread: two columns per thread
-    if (K >= 2 && rows_per_color * K > kGsPipeBlock) return launch_gs_pipe_g<K, 1, (K >= 2 ? 2 : 1)>(l, s);
-    return launch_gs_pipe_g<K, 1, 1>(l, s);
+    if (K >= 2 && rows_per_color * K > kGsPipeBlock)
+      return launch_gs_pipe_g<K, 1, (K >= 2 ? 2 : 1), kGsPipeBlock>(l, s);
+    return launch_gs_pipe_g<K, 1, 1, kGsPipeBlock>(l, s);
+  }
+  // (GW lanes, VW columns) clamped to what K allows: V <= K, (K / V) * G <= 32.
+  template <int K, int GW, int VW, int NT>
+  bool launch_gs_pipe_v(int l, cudaStream_t s) {
+    constexpr int V = VW <= K ? VW : K;
+    constexpr int KV = K / V;
+    constexpr int G = GW * KV <= 32 ? GW : (KV >= 32 ? 1 : 32 / KV);
+    return launch_gs_pipe_g<K, G, V, NT>(l, s);
   }
 
-  template <int K, int G, int V>
+  template <int K, int G, int V, int NT>
   bool launch_gs_pipe_g(int l, cudaStream_t s) {
     const LevelView<T>& L = views_[l];
     const Buf& B = buf_[l];
@@ -528,11 +545,11 @@ class DeviceVCycle : public VCycleIface {
     P.stage = gs_stage(l, K);
     if (P.stage == 0 || P.ncol > kMaxColors) return false;
     const size_t smem = gs_smem(l, K, P.stage);
-    auto kern = k_gs_pipe<T, K, G, V>;
+    auto kern = k_gs_pipe<T, K, G, V, NT>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 48 * 1024));
     cudaMemsetAsync(done_[l], 0, sizeof(int) * (P.nstrips + 1), s);
     // one block per strip: as many units in flight as the pipeline can overlap
-    kern<<<P.nstrips, kGsPipeBlock, smem, s>>>(L, (const T*)B.g, B.dp, P, (const int*)ci_rel_[l], done_[l], err_);
+    kern<<<P.nstrips, NT, smem, s>>>(L, (const T*)B.g, B.dp, P, (const int*)ci_rel_[l], done_[l], err_);
     return true;
   }
 

@@ -509,7 +509,9 @@ def main():
                                 "source": "serving stream (arrival to result on the host)"}),
                 "serving": serving, "accuracy": accuracy,
                 "e2e": e2e, "gpu_launches": launches32, "clocks": clocks, "roofline": roofline,
-                "vcycle_us_by_kernel": breakdown, "gs_variants": gs_variants, "cpu_baseline": cpu}
+                "vcycle_us_by_kernel": breakdown, "gs_variants": gs_variants,
+                "row_shapes": {f"L{l}": "".join(str(v) for v in d.values()) for l, d in H32.row_shapes(NRHS).items()},
+                "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -200,6 +200,14 @@ amg_status amg_level_get_points(amg_handle h, int level, int* cp, int* cv, int* 
  * launch (0 without autotuning).  Either output may be NULL. */
 int amg_gs_variant(amg_handle h, int level, int nrhs, int* cluster, float* ms);
 
+/* The row mapping of a sparse kernel on a level for nrhs right-hand sides, as the
+ * autotuner chose it (or by default): kernel = 0 velocity predictor, 1 Schur
+ * right-hand side, 3 update, 4 residual, 5 restriction, 6 prolongation (the
+ * classes of amg_profile_vcycle); result 0 one group of K/V threads per row with V
+ * columns of 16 bytes each, 1 and 2 a row split over 2 or 4 such groups, 3 one
+ * column per thread with several lanes per row; -1 for a bad argument. */
+int amg_row_shape(amg_handle h, int level, int nrhs, int kernel);
+
 void amg_hierarchy_destroy(amg_handle h);
 
 const char* amg_last_error(void);

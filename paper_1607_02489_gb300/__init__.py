@@ -23,7 +23,7 @@ STATUS_NAMES = {0: "OK", 1: "NOT_CONVERGED", 2: "BREAKDOWN", -1: "ERR_ARG", -2: 
                 -4: "ERR_SETUP"}
 EXPORTED = ["amg_params_default", "amg_hierarchy_create", "amg_vcycle_apply", "amg_apply", "amg_fgmres_solve",
             "amg_fgmres_solve_host", "amg_num_levels", "amg_level_get_info", "amg_level_get_matrix",
-            "amg_level_get_points", "amg_hierarchy_destroy", "amg_last_error", "amg_profile_vcycle", "amg_kernel_launches", "amg_apply_noalloc", "amg_gs_variant",
+            "amg_level_get_points", "amg_hierarchy_destroy", "amg_last_error", "amg_profile_vcycle", "amg_kernel_launches", "amg_apply_noalloc", "amg_gs_variant", "amg_row_shape",
             "amg_server_params_default", "amg_server_create", "amg_server_reserve", "amg_server_submit", "amg_server_progress",
             "amg_server_result", "amg_server_state", "amg_server_get_stats", "amg_server_destroy", "amg_server_last_error"]
 KERNEL_CLASSES = ["velocity", "schur_rhs", "gs_color", "update", "residual", "restrict", "prolong", "coarse"]
@@ -106,6 +106,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.amg_profile_vcycle.restype = ctypes.c_int
     lib.amg_gs_variant.argtypes = [vp, ctypes.c_int, ctypes.c_int, _i32p, ctypes.POINTER(ctypes.c_float)]
     lib.amg_gs_variant.restype = ctypes.c_int
+    lib.amg_row_shape.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    lib.amg_row_shape.restype = ctypes.c_int
     lib.amg_kernel_launches.argtypes = [vp]
     lib.amg_kernel_launches.restype = ctypes.c_longlong
     lib.amg_num_levels.argtypes = [vp]
@@ -295,6 +297,14 @@ class Hierarchy:
             ms = ctypes.c_float()
             v = load().amg_gs_variant(self._h, l, int(nrhs), ctypes.byref(c), ctypes.byref(ms))
             out.append((self.GS_VARIANTS.get(v, str(v)), c.value, ms.value))
+        return out
+
+    def row_shapes(self, nrhs) -> dict:
+        """{level: {kernel class: row mapping 0-3}} of the sparse kernels (amg_row_shape)."""
+        out = {}
+        for l in range(self.num_levels() - 1):
+            out[l] = {c: load().amg_row_shape(self._h, l, int(nrhs), k) for k, c in enumerate(KERNEL_CLASSES)
+                      if c not in ("gs_color", "coarse")}
         return out
 
     def kernel_launches(self) -> int:

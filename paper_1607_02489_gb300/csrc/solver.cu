@@ -1019,6 +1019,11 @@ int amg_gs_variant(amg_handle h, int level, int nrhs, int* cluster, float* ms) {
   return h->vc()->gs_choice(level, round_k(nrhs), cluster, ms);
 }
 
+int amg_row_shape(amg_handle h, int level, int nrhs, int kernel) {
+  if (!h || !h->vc() || nrhs < 1 || nrhs > 32) return -1;
+  return h->vc()->row_shape(level, round_k(nrhs), kernel);
+}
+
 void amg_hierarchy_destroy(amg_handle h) { delete h; }
 
 }  // extern "C"

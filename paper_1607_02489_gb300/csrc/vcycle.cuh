@@ -51,6 +51,9 @@ struct VCycleIface {
   // pipelined, 3 one launch per phase), the cluster size and the time measured.
   virtual void set_autotune(bool on) = 0;
   virtual int gs_choice(int level, int K, int* cluster, float* ms) const = 0;
+  // Row mapping (0-3, see DeviceVCycle::Shape) of a sparse kernel class on a level
+  // for K right-hand sides, as tuned or by default; -1 for a bad argument.
+  virtual int row_shape(int level, int K, int cls) const = 0;
 };
 
 // Kernel classes reported by profile().
@@ -91,6 +94,7 @@ class DeviceVCycle : public VCycleIface {
         throw std::runtime_error("N * max_nrhs must stay below 2^31 (32-bit vector indices)");
       for (size_t l = 0; l < levels.size(); ++l) upload_level(levels[l], l + 1 == levels.size());
       tune_ = std::make_shared<std::vector<GsChoice>>(levels.size() * 6);
+      rowmap_ = std::make_shared<std::vector<int>>(levels.size() * 6 * kRowClasses, -1);
       for (size_t l = 0; l + 1 < levels.size(); ++l) {
         views_[l].n_vc = levels[l + 1].n_v;
         views_[l].n_pc = levels[l + 1].n_p;
@@ -112,6 +116,10 @@ class DeviceVCycle : public VCycleIface {
 
   VCycleIface* clone(int kmax) const override { return new DeviceVCycle(*this, kmax, CloneTag{}); }
   void set_autotune(bool on) override { autotune_ = on; }
+  int row_shape(int level, int K, int cls) const override {
+    if (level < 0 || level + 1 >= (int)views_.size() || kslot(K) < 0 || cls < 0 || cls >= kRowClasses) return -1;
+    return shape(level, K, cls);
+  }
   int gs_choice(int level, int K, int* cluster, float* ms) const override {
     if (level < 0 || level >= (int)views_.size() || kslot(K) < 0) return -1;
     const GsChoice& c = (*tune_)[(size_t)level * 6 + kslot(K)];
@@ -199,36 +207,19 @@ class DeviceVCycle : public VCycleIface {
     const int nl = (int)views_.size();
     for (int l = 0; l + 1 < nl; ++l) {
       smooth<K>(l, pre_, true, s);
-      const LevelView<T>& L = views_[l];
       mark_begin(l, kResidual, s);
-      if (small_level(l, K))
-        k_block_spmv<T, K, RowLanes<K>::G, 1, true><<<grid_for((long long)(L.n_v + L.n_p) * RowLanes<K>::W), kBlock, 0,
-                                                    s>>>(L, buf_[l].b, buf_[l].x, buf_[l].r);
-      else
-        k_block_spmv<T, K, 1, VecWidth<T, K>::V, true><<<grid_for((long long)(L.n_v + L.n_p) * (K / VecWidth<T, K>::V)),
-                                                        kBlock, 0, s>>>(L, buf_[l].b, buf_[l].x, buf_[l].r);
+      launch_rows<K>(kResidual, l, shape(l, K, kResidual), 0, s);
       mark_end(s);
       mark_begin(l, kRestrict, s);
-      if (small_level(l + 1, K))
-        k_restrict<T, K, RowLanes<K>::G, 1><<<grid_for((long long)(L.n_vc + L.n_pc) * RowLanes<K>::W), kBlock, 0, s>>>(
-            L, buf_[l].r, buf_[l + 1].b);
-      else
-        k_restrict<T, K, 1, VecWidth<T, K>::V><<<grid_for((long long)(L.n_vc + L.n_pc) * (K / VecWidth<T, K>::V)), kBlock,
-                                                 0, s>>>(L, buf_[l].r, buf_[l + 1].b);
+      launch_rows<K>(kRestrict, l, shape(l, K, kRestrict), 0, s);
       mark_end(s);
     }
     mark_begin(nl - 1, kCoarse, s);  // every kernel launch of the cycle is preceded by mark_begin
     k_coarse_solve<T, K><<<grid_for((long long)Nc_ * K), kBlock, 0, s>>>(Nc_, pinv_, buf_[nl - 1].b, buf_[nl - 1].x);
     mark_end(s);
     for (int l = nl - 2; l >= 0; --l) {
-      const LevelView<T>& L = views_[l];
       mark_begin(l, kProlong, s);
-      if (small_level(l, K))
-        k_prolong<T, K, RowLanes<K>::G, 1><<<grid_for((long long)(L.n_v + L.n_p) * RowLanes<K>::W), kBlock, 0, s>>>(
-            L, buf_[l + 1].x, buf_[l].x);
-      else
-        k_prolong<T, K, 1, VecWidth<T, K>::V><<<grid_for((long long)(L.n_v + L.n_p) * (K / VecWidth<T, K>::V)), kBlock, 0,
-                                                s>>>(L, buf_[l + 1].x, buf_[l].x);
+      launch_rows<K>(kProlong, l, shape(l, K, kProlong), 0, s);
       mark_end(s);
       smooth<K>(l, post_, false, s);
     }
@@ -247,42 +238,126 @@ class DeviceVCycle : public VCycleIface {
     }
   }
 
+  // Row mappings of the sparse kernels (velocity, Schur RHS, update, residual,
+  // restriction, prolongation): shape 0 one thread group of K/V threads per row
+  // with V = 16 bytes of right-hand sides each; shapes 1 and 2 split a row's
+  // entries over 2 or 4 such groups (warp-shuffle sums); shape 3 one column per
+  // thread and RowLanes<K>::G lanes per row (the mapping for latency-bound small
+  // levels).  The autotuner picks one per (level, K, kernel); without it, shape 3
+  // on small levels and shape 0 elsewhere.
+  template <int K, int SHAPE>
+  struct Shape {
+    static constexpr int V = SHAPE == 3 ? 1 : VecWidth<T, K>::V;
+    static constexpr int KV = K / V;
+    static constexpr int G0 = SHAPE == 0 ? 1 : SHAPE == 1 ? 2 : SHAPE == 2 ? 4 : RowLanes<K>::G;
+    static constexpr int G = G0 * KV <= 32 ? G0 : (KV >= 32 ? 1 : 32 / KV);
+    static constexpr int W = KV * G;
+  };
+  static constexpr int kRowShapes = 4;
+  static constexpr int kRowClasses = kNumClasses;  // indexed by KernelClass
+
+  int shape(int l, int K, int cls) const {
+    const int v = (*rowmap_)[((size_t)l * 6 + kslot(K)) * kRowClasses + cls];
+    if (v >= 0) return v;
+    return small_level(cls == kRestrict ? l + 1 : l, K) ? 3 : 0;
+  }
+
+  template <int K>
+  void launch_rows(int cls, int l, int shp, int zero, cudaStream_t s) {
+    switch (shp) {
+      case 1: return launch_rows_as<K, 1>(cls, l, zero, s);
+      case 2: return launch_rows_as<K, 2>(cls, l, zero, s);
+      case 3: return launch_rows_as<K, 3>(cls, l, zero, s);
+      default: return launch_rows_as<K, 0>(cls, l, zero, s);
+    }
+  }
+  template <int K, int SHAPE>
+  void launch_rows_as(int cls, int l, int zero, cudaStream_t s) {
+    using S = Shape<K, SHAPE>;
+    constexpr int G = S::G, V = S::V, W = S::W;
+    const LevelView<T>& L = views_[l];
+    const Buf& B = buf_[l];
+    switch (cls) {
+      case kVelocity:
+        k_bs_velocity<T, K, G, V><<<grid_for((long long)L.n_v * W), kBlock, 0, s>>>(L, B.b, B.x, B.y, zero);
+        break;
+      case kSchurRhs:
+        k_schur_rhs<T, K, G, V><<<grid_for((long long)L.n_p * W), kBlock, 0, s>>>(L, B.b, B.x, B.y, B.g, cfac_, zero);
+        break;
+      case kUpdate:
+        k_bs_update<T, K, G, V><<<grid_for((long long)(L.n_v + L.n_p) * W), kBlock, 0, s>>>(L, B.y, B.dp, B.x, zero);
+        break;
+      case kResidual:
+        k_block_spmv<T, K, G, V, true><<<grid_for((long long)(L.n_v + L.n_p) * W), kBlock, 0, s>>>(L, B.b, B.x, B.r);
+        break;
+      case kRestrict:
+        k_restrict<T, K, G, V><<<grid_for((long long)(L.n_vc + L.n_pc) * W), kBlock, 0, s>>>(L, B.r, buf_[l + 1].b);
+        break;
+      case kProlong:
+        k_prolong<T, K, G, V><<<grid_for((long long)(L.n_v + L.n_p) * W), kBlock, 0, s>>>(L, buf_[l + 1].x, B.x);
+        break;
+    }
+  }
+
   template <int K>
   void smooth(int l, int sweeps, bool from_zero, cudaStream_t s) {
     const LevelView<T>& L = views_[l];
     const Buf& B = buf_[l];
-    const bool small = small_level(l, K);
     for (int sw = 0; sw < sweeps; ++sw) {
       const int zero = (from_zero && sw == 0) ? 1 : 0;
       mark_begin(l, kVelocity, s);
-      if (small)
-        k_bs_velocity<T, K, RowLanes<K>::G, 1><<<grid_for((long long)L.n_v * RowLanes<K>::W), kBlock, 0, s>>>(
-            L, B.b, B.x, B.y, zero);
-      else
-        k_bs_velocity<T, K, 1, VecWidth<T, K>::V><<<grid_for((long long)L.n_v * (K / VecWidth<T, K>::V)), kBlock, 0, s>>>(
-            L, B.b, B.x, B.y, zero);
+      launch_rows<K>(kVelocity, l, shape(l, K, kVelocity), zero, s);
       mark_end(s);
       mark_begin(l, kSchurRhs, s);
-      if (small)
-        k_schur_rhs<T, K, RowLanes<K>::G, 1><<<grid_for((long long)L.n_p * RowLanes<K>::W), kBlock, 0, s>>>(
-            L, B.b, B.x, B.y, B.g, cfac_, zero);
-      else
-        k_schur_rhs<T, K, 1, VecWidth<T, K>::V><<<grid_for((long long)L.n_p * (K / VecWidth<T, K>::V)), kBlock, 0, s>>>(
-            L, B.b, B.x, B.y, B.g, cfac_, zero);
+      launch_rows<K>(kSchurRhs, l, shape(l, K, kSchurRhs), zero, s);
       mark_end(s);
       cudaMemsetAsync(B.dp, 0, sizeof(T) * (size_t)L.n_p * K, s);
       mark_begin(l, kGsColor, s);
       launch_gs<K>(l, s);
       mark_end(s);
       mark_begin(l, kUpdate, s);
-      if (small)
-        k_bs_update<T, K, RowLanes<K>::G, 1><<<grid_for((long long)(L.n_v + L.n_p) * RowLanes<K>::W), kBlock, 0, s>>>(
-            L, B.y, B.dp, B.x, zero);
-      else
-        k_bs_update<T, K, 1, VecWidth<T, K>::V><<<grid_for((long long)(L.n_v + L.n_p) * (K / VecWidth<T, K>::V)), kBlock,
-                                                  0, s>>>(L, B.y, B.dp, B.x, zero);
+      launch_rows<K>(kUpdate, l, shape(l, K, kUpdate), zero, s);
       mark_end(s);
     }
+  }
+
+  // Row-mapping autotuner: each sparse kernel of each level timed in every shape
+  // (CUDA events, stream s, on the level's own buffers) and the fastest kept;
+  // shared with the clones like the Gauss-Seidel table.
+  template <int K>
+  void tune_rows(cudaStream_t s) {
+    const int ks = kslot(K);
+    cudaEvent_t e0, e1;
+    EMIN_CUDA(cudaEventCreate(&e0));
+    EMIN_CUDA(cudaEventCreate(&e1));
+    const int classes[] = {kVelocity, kSchurRhs, kUpdate, kResidual, kRestrict, kProlong};
+    for (int l = 0; l + 1 < (int)views_.size(); ++l)
+      for (int cls : classes) {
+        int& slot = (*rowmap_)[((size_t)l * 6 + ks) * kRowClasses + cls];
+        if (slot >= 0) continue;
+        int best = -1;
+        float best_ms = 1e30f;
+        for (int shp = 0; shp < kRowShapes; ++shp) {
+          float total = 0.f;
+          for (int rep = 0; rep < 4; ++rep) {
+            cudaEventRecord(e0, s);
+            launch_rows<K>(cls, l, shp, 0, s);
+            cudaEventRecord(e1, s);
+            ++launches_;
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) total += ms;
+          }
+          if (cudaGetLastError() == cudaSuccess && total < best_ms) {
+            best_ms = total;
+            best = shp;
+          }
+        }
+        slot = best;
+      }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
   }
 
   struct Rec {
@@ -407,12 +482,12 @@ class DeviceVCycle : public VCycleIface {
   }
   void tune_for(int K, cudaStream_t s) {
     switch (K) {
-      case 1: tune_gs<1>(s); break;
-      case 2: tune_gs<2>(s); break;
-      case 4: tune_gs<4>(s); break;
-      case 8: tune_gs<8>(s); break;
-      case 16: tune_gs<16>(s); break;
-      case 32: tune_gs<32>(s); break;
+      case 1: tune_rows<1>(s); tune_gs<1>(s); break;
+      case 2: tune_rows<2>(s); tune_gs<2>(s); break;
+      case 4: tune_rows<4>(s); tune_gs<4>(s); break;
+      case 8: tune_rows<8>(s); tune_gs<8>(s); break;
+      case 16: tune_rows<16>(s); tune_gs<16>(s); break;
+      case 32: tune_rows<32>(s); tune_gs<32>(s); break;
     }
   }
 
@@ -696,6 +771,7 @@ class DeviceVCycle : public VCycleIface {
       cplans_ = o.cplans_;
       gsM_ = o.gsM_;
       tune_ = o.tune_;
+      rowmap_ = o.rowmap_;
       autotune_ = o.autotune_;
       plist_ = o.plist_;
       poff_ = o.poff_;
@@ -918,6 +994,7 @@ class DeviceVCycle : public VCycleIface {
   std::vector<std::vector<ClusterPlan>> cplans_;
   std::vector<T*> gsM_;  // dense Gauss-Seidel map of small levels (nullptr elsewhere)
   std::shared_ptr<std::vector<GsChoice>> tune_;  // [level * 6 + K slot], shared with clones
+  std::shared_ptr<std::vector<int>> rowmap_;     // [(level * 6 + K slot) * classes + class], -1 untuned
   std::vector<long long> s_nnz_;
   int* err_ = nullptr;
   FFLevel ff_{};

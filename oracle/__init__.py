@@ -6,7 +6,8 @@ product path (the C++ setup, the CUDA kernels and their Python binding)
 shares no code with it, and it imports nothing from the product.
 
 It is a plain, slow restatement of the method, step by step in the paper's
-order (Alg. 1-4, Section 4.3 for EMIN, Section 5.2 for Braess-Sarazin),
+order (Alg. 1-4, Section 4.3 for EMIN, Section 5.2 for Braess-Sarazin,
+Section 5.1 for Vanka),
 written with numpy / scipy.sparse primitives and Python loops over graph
 vertices.  Where the paper is silent or garbled, the reading taken is stated
 in the docstring of the function that implements the step.
@@ -18,6 +19,9 @@ tests/test_synth.py):
     velocity_pattern, emin_step, the Galerkin products, gauss_seidel,
     bs_sweep, coarse_solve, vcycle, fgmres: pinned (closed forms, the
     paper's worked special cases, invariants, dense brute force, Table 1).
+  * vanka.py (Vanka relaxation, Section 5.1): pinned (block definition,
+    exact local solves, colored sweep = block-by-block sweep, dense solves,
+    Table 1's Vanka(1,1) counts).
   * find_extra_dist3_cpoints: the paper names its criteria but gives no
     thresholds, and no uniform-mesh case triggers it, so its choices are
     parity unpinned (only the coverage invariant it must keep is pinned).

@@ -43,6 +43,8 @@ class Params:
     pre: int = 2
     post: int = 2
     emin: str = "auto"            # "cg" (Stokes), "gmres" (Oseen); auto picks by symmetry
+    smoother: str = "bs"          # "bs" Braess-Sarazin (Section 5.2), "vanka" (Section 5.1)
+    vanka_omega: float = 0.5      # Vanka under-relaxation (Section 6)
     max_coarse: int = 200
     max_levels: int = 12
 
@@ -82,6 +84,8 @@ class Level:
     Rp: sp.csr_matrix = None
     # coarsest-level solve
     coarse_pinv: np.ndarray = None
+    # Vanka smoother data (oracle.vanka.form_vanka), when that smoother is chosen
+    vanka: dict = None
     # setup diagnostics (for the tests)
     info: dict = dataclasses.field(default_factory=dict)
 
@@ -628,4 +632,8 @@ def setup_hierarchy(prob, prm: Params = None) -> Hierarchy:
             break
         levels.append(Lc)
     form_coarse_solve(levels[-1])
+    if prm.smoother == "vanka":
+        from .vanka import form_vanka
+        for L in levels[:-1]:
+            form_vanka(L)
     return Hierarchy(levels=levels, params=prm, symmetric=bool(prob.symmetric))

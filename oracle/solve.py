@@ -99,14 +99,18 @@ def vcycle(H, b, level: int = 0):
     L = H.levels[level]
     if level == len(H.levels) - 1:
         return coarse_solve(L, b)
+    if prm.smoother == "vanka":
+        from .vanka import vanka_sweep as sweep
+    else:
+        sweep = bs_sweep
     x = np.zeros_like(b)
     for _ in range(prm.pre):
-        x = bs_sweep(L, prm, b, x)
+        x = sweep(L, prm, b, x)
     r = b - apply_A(L, x)
     xc = vcycle(H, restrict(L, r), level + 1)
     x = x + prolong(L, H.levels[level + 1], xc)
     for _ in range(prm.post):
-        x = bs_sweep(L, prm, b, x)
+        x = sweep(L, prm, b, x)
     return x
 
 

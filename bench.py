@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving stream")
+    ap.add_argument("--no-vanka", action="store_true", help="skip the Vanka-smoother side line")
     ap.add_argument("--serve-requests", type=int, default=64)
     ap.add_argument("--serve-active", type=int, default=None, help="requests running at once (default SERVE_ACTIVE)")
     ap.add_argument("--serve-merge", type=int, default=None, help="columns stacked per cohort (default SERVE_MERGE)")
@@ -149,7 +150,29 @@ def algorithmic_bytes(H, level, cls, K, s, zero_fraction=0.25):
         return (mat(info["nnz_P"], nv) + mat(info["nnz_Pp"], np_) + 2 * vec(N) + vec(c["dim"] * c["n_v"] + c["n_p"]))
     if cls == "coarse":
         return N * N * 8 + 2 * vec(N)
+    if cls == "vanka":
+        raise KeyError("vanka bytes are counted per step by vanka_bytes")
     raise KeyError(cls)
+
+
+def vanka_bytes(H, level, K, s):
+    """Compulsory bytes of one Vanka step (all colors) on `level`: every block's
+    inverse (m^2 values), for every dof of every block its row of the block matrix
+    (values, columns, and the K gathered x values per entry), f read and x
+    written for the block's dofs (K values each)."""
+    import numpy as np
+    info = H.level_info(level)
+    d, nv = info["dim"], info["n_v"]
+    V = H.level_vanka(level)
+    m = np.diff(V["ptr"]).astype(np.int64)
+    rA = np.diff(H.level_matrix(level, "A")[0])
+    rBt = np.diff(H.level_matrix(level, "Bt")[0])
+    rB = np.diff(H.level_matrix(level, "B")[0])
+    q = V["dofs"].astype(np.int64)
+    nu = d * nv
+    row_nnz = np.where(q < nu, rA[np.minimum(q, nu - 1) % nv] + rBt[np.minimum(q, nu - 1)],
+                       rB[np.maximum(q - nu, 0)])
+    return int((m * m).sum() * s + (row_nnz * (4 + s + K * s)).sum() + 2 * K * s * len(q))
 
 
 def load_traffic(kernel, level, K, s):
@@ -482,6 +505,30 @@ def main():
     breakdown = {f"L{l}/{c}": round(float(ms_tab[l, k] / reps * 1000.0), 2)
                  for l in range(ms_tab.shape[0]) for k, c in enumerate(g.KERNEL_CLASSES) if cnt_tab[l, k]}
 
+    # the Vanka smoother (Section 5.1) on the same workload: FP32 and FP64 V-cycles
+    vanka = None
+    if not args.no_vanka and world == 1:
+        V32 = g.Hierarchy(p, max_nrhs=NRHS, vcycle_fp32=1, smoother=1, pre=1, post=1)
+        V64 = g.Hierarchy(p, max_nrhs=NRHS, smoother=1, pre=1, post=1)
+        vsteps = max(2, args.steps // 2)
+        msv32, sv32, _, itsv32, relv32, _ = timed(V32, vsteps, args.warmup)
+        msv64, sv64, _, itsv64, _, _ = timed(V64, vsteps, args.warmup)
+        V32.vcycle(b, x)
+        vms, vcnt = V32.profile_vcycle(NRHS, reps=10)
+        vi = g.KERNEL_CLASSES.index("vanka")
+        l0_ms = vms[0, vi] / 10
+        l0_bytes = 2 * vanka_bytes(V32, 0, NRHS, 4)  # V(1,1): two steps per cycle on level 0
+        vanka = {"workload": "same 256x256 lid cavity, 8 rhs, Vanka(1,1), omega 0.5, FGMRES to 1e-8",
+                 "value": sv32 / (msv32 / 1000.0), "unit": "solves/s", "fp64_vcycle_value": sv64 / (msv64 / 1000.0),
+                 "iterations": itsv32.tolist(), "iterations_fp64": itsv64.tolist(),
+                 "relres_max": float(np.max(relv32)),
+                 "vcycle_us_by_kernel": {f"L{l}/{c}": round(float(vms[l, k] / 10 * 1000.0), 2)
+                                         for l in range(vms.shape[0]) for k, c in enumerate(g.KERNEL_CLASSES)
+                                         if vcnt[l, k]},
+                 "level0_step_GBs": l0_bytes / (l0_ms / 1000.0) / 1e9,
+                 "level0_step_frac": l0_bytes / (l0_ms / 1000.0) / 1e9 / measured_peaks()[0]}
+        del V32, V64
+
     serving = None
     if not args.no_serve:
         serving = serve(g, torch, dev, args.serve_requests, seed=rank, max_active=args.serve_active,
@@ -507,7 +554,7 @@ def main():
                 "latency_ms": (None if serving is None else
                                {"p50": serving["latency_ms"]["p50"], "p99": serving["latency_ms"]["p99"],
                                 "source": "serving stream (arrival to result on the host)"}),
-                "serving": serving, "accuracy": accuracy,
+                "serving": serving, "accuracy": accuracy, "vanka": vanka,
                 "e2e": e2e, "gpu_launches": launches32, "clocks": clocks, "roofline": roofline,
                 "vcycle_us_by_kernel": breakdown, "gs_variants": gs_variants,
                 "row_shapes": {f"L{l}": "".join(str(v) for v in d.values()) for l, d in H32.row_shapes(NRHS).items()},

@@ -93,6 +93,12 @@ typedef struct {
                          a thread-block cluster of 2-16 blocks, the pipelined kernel, one launch
                          per phase, the dense map on levels of <= 1024 pressures) and keep the
                          fastest; 0: fixed choice by level size, sweeps only */
+  int smoother;       /* 0 (default): Braess-Sarazin (Section 5.2); 1: Vanka (Section 5.1):
+                         overlapping blocks, one per pressure dof (the columns of its row of
+                         B plus the pressure), relaxed in the order (color, index) of a
+                         greedy coloring of the blocks' interaction graph, Dirichlet dofs
+                         exactly; pre and post count Vanka steps (the paper's Vanka(1,1)) */
+  double vanka_omega; /* Vanka under-relaxation, 0.5 (Section 6) */
 } amg_params;
 
 void amg_params_default(amg_params* prm);
@@ -152,12 +158,13 @@ amg_status amg_fgmres_solve_host(amg_handle h, const double* b_host, double* x_h
 /* Kernel timing: run `reps` V-cycles on the current contents of the level-0
  * input buffer without the CUDA graph, with a CUDA event pair on `stream`
  * around every kernel launch.  ms and count are caller arrays of
- * amg_num_levels(h) * AMG_NUM_KERNEL_CLASSES; entry [level * 8 + class] gets the
+ * amg_num_levels(h) * AMG_NUM_KERNEL_CLASSES; entry [level * AMG_NUM_KERNEL_CLASSES + class] gets the
  * summed milliseconds and the number of launches of that class on that level.
  * Classes: 0 velocity predictor, 1 Schur right-hand side, 2 Gauss-Seidel color
  * sweep, 3 velocity/pressure update, 4 block residual, 5 restriction,
- * 6 prolongation, 7 coarsest solve.  Synchronises `stream`. */
-#define AMG_NUM_KERNEL_CLASSES 8
+ * 6 prolongation, 7 coarsest solve, 8 Vanka step (its color launches and the exact
+ * Dirichlet relaxation).  Synchronises `stream`. */
+#define AMG_NUM_KERNEL_CLASSES 9
 amg_status amg_profile_vcycle(amg_handle h, int nrhs, int reps, double* ms, long long* count, void* stream);
 
 /* Number of CUDA kernels this handle has launched so far (a replayed V-cycle graph
@@ -190,6 +197,13 @@ amg_status amg_level_get_matrix(amg_handle h, int level, int which, long long* r
  * velocity nodes, ascending), the Gauss-Seidel colors of the pressure nodes
  * (n_p) and the Braess-Sarazin diagonal D (n_v).  Any pointer may be NULL. */
 amg_status amg_level_get_points(amg_handle h, int level, int* cp, int* cv, int* colors, double* D);
+
+/* The Vanka blocks of a level (hierarchies built with smoother = 1, every level but
+ * the coarsest): *nblocks, *ndofs (total dofs over blocks) and *ncolors when the
+ * arrays are NULL; otherwise ptr (nblocks + 1), dofs (ndofs, global dof indices)
+ * and colors (nblocks) are filled.  AMG_ERR_ARG for a level without blocks. */
+amg_status amg_level_get_vanka(amg_handle h, int level, int* nblocks, int* ndofs, int* ncolors, int* ptr,
+                               int* dofs, int* colors);
 
 /* The Gauss-Seidel variant the V-cycle (FP32 one if built, else FP64) uses on a
  * level for nrhs right-hand sides: -1 not chosen yet (the cycle for that K has

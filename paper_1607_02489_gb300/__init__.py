@@ -23,10 +23,10 @@ STATUS_NAMES = {0: "OK", 1: "NOT_CONVERGED", 2: "BREAKDOWN", -1: "ERR_ARG", -2: 
                 -4: "ERR_SETUP"}
 EXPORTED = ["amg_params_default", "amg_hierarchy_create", "amg_vcycle_apply", "amg_apply", "amg_fgmres_solve",
             "amg_fgmres_solve_host", "amg_num_levels", "amg_level_get_info", "amg_level_get_matrix",
-            "amg_level_get_points", "amg_hierarchy_destroy", "amg_last_error", "amg_profile_vcycle", "amg_kernel_launches", "amg_apply_noalloc", "amg_gs_variant", "amg_row_shape",
+            "amg_level_get_points", "amg_hierarchy_destroy", "amg_last_error", "amg_profile_vcycle", "amg_kernel_launches", "amg_apply_noalloc", "amg_gs_variant", "amg_row_shape", "amg_level_get_vanka",
             "amg_server_params_default", "amg_server_create", "amg_server_reserve", "amg_server_submit", "amg_server_progress",
             "amg_server_result", "amg_server_state", "amg_server_get_stats", "amg_server_destroy", "amg_server_last_error"]
-KERNEL_CLASSES = ["velocity", "schur_rhs", "gs_color", "update", "residual", "restrict", "prolong", "coarse"]
+KERNEL_CLASSES = ["velocity", "schur_rhs", "gs_color", "update", "residual", "restrict", "prolong", "coarse", "vanka"]
 MATRICES = {"A": 0, "B": 1, "Bt": 2, "S": 3, "P": 4, "Pp": 5, "R": 6, "Rp": 7}
 
 _i32p = ctypes.POINTER(ctypes.c_int)
@@ -48,7 +48,7 @@ class AmgParams(ctypes.Structure):
                 ("omega_on_D", ctypes.c_int), ("gs_iters", ctypes.c_int), ("pre", ctypes.c_int),
                 ("post", ctypes.c_int), ("max_coarse", ctypes.c_int), ("max_levels", ctypes.c_int),
                 ("vcycle_fp32", ctypes.c_int), ("max_nrhs", ctypes.c_int), ("host_only", ctypes.c_int),
-                ("autotune", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("smoother", ctypes.c_int), ("vanka_omega", ctypes.c_double)]
 
 
 class AmgLevelInfo(ctypes.Structure):
@@ -118,6 +118,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.amg_level_get_matrix.restype = ctypes.c_int
     lib.amg_level_get_points.argtypes = [vp, ctypes.c_int, _i32p, _i32p, _i32p, _f64p]
     lib.amg_level_get_points.restype = ctypes.c_int
+    lib.amg_level_get_vanka.argtypes = [vp, ctypes.c_int, _i32p, _i32p, _i32p, _i32p, _i32p, _i32p]
+    lib.amg_level_get_vanka.restype = ctypes.c_int
     lib.amg_hierarchy_destroy.argtypes = [vp]
     lib.amg_hierarchy_destroy.restype = None
     lib.amg_last_error.argtypes = []
@@ -339,6 +341,18 @@ class Hierarchy:
         _check(load().amg_level_get_matrix(self._h, level, MATRICES[which], _ptr(rp, ctypes.c_longlong),
                                            _ptr(col, ctypes.c_int), _ptr(val, ctypes.c_double)))
         return rp, col[:info[nnz]], val[:info[nnz]], shape
+
+    def level_vanka(self, level: int) -> dict:
+        """Vanka blocks of a level (amg_level_get_vanka): ptr, dofs, colors, ncolors."""
+        nb, nd, nc = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(load().amg_level_get_vanka(self._h, level, ctypes.byref(nb), ctypes.byref(nd), ctypes.byref(nc),
+                                          None, None, None))
+        ptr = np.zeros(nb.value + 1, dtype=np.int32)
+        dofs = np.zeros(max(nd.value, 1), dtype=np.int32)
+        colors = np.zeros(max(nb.value, 1), dtype=np.int32)
+        _check(load().amg_level_get_vanka(self._h, level, None, None, None, _ptr(ptr, ctypes.c_int),
+                                          _ptr(dofs, ctypes.c_int), _ptr(colors, ctypes.c_int)))
+        return dict(ptr=ptr, dofs=dofs[:nd.value], colors=colors[:nb.value], ncolors=nc.value)
 
     def level_points(self, level: int) -> dict:
         info = self.level_info(level)

@@ -691,6 +691,73 @@ __global__ void __launch_bounds__(kBlock) k_gs_dense(int n_p, const T* __restric
   if (js == 0) dp[(size_t)i * K + k] = acc;
 }
 
+// Vanka relaxation (Section 5.1) on one color of blocks: one thread block per
+// Vanka block.  It gathers the block's residual rows r = f - A x (K columns), then
+// adds omega * inv * r to x on the block's dofs, inv the block's local matrix
+// inverted at setup.  Blocks of one color share no dof and no entry of A, so the
+// blocks of a launch neither race nor see each other's updates.
+template <typename T>
+struct VankaView {
+  const int* ptr;           // block b's dofs are dofs[ptr[b] .. ptr[b+1])
+  const int* dofs;
+  const T* inv;             // block b's inverse, row-major, at inv_off[b]
+  const long long* inv_off;
+  const int* order;         // blocks sorted by (color, index)
+};
+
+template <typename T, int K>
+__global__ void __launch_bounds__(128) k_vanka_color(LevelView<T> L, VankaView<T> V, int first,
+                                                     const T* __restrict__ f, T* x, T omega) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int blk = V.order[first + blockIdx.x];
+  const int p0 = V.ptr[blk], m = V.ptr[blk + 1] - p0;
+  int* s_dof = reinterpret_cast<int*>(smem);
+  T* s_r = reinterpret_cast<T*>(smem + ((size_t)m * sizeof(int) + 15) / 16 * 16);
+  for (int j = threadIdx.x; j < m; j += blockDim.x) s_dof[j] = V.dofs[p0 + j];
+  __syncthreads();
+  const int nu = L.dim * L.n_v;
+  for (int t = threadIdx.x; t < m * K; t += blockDim.x) {
+    const int j = t / K, k = t % K;
+    const int q = s_dof[j];
+    T acc = T(0);
+    if (q < nu) {
+      const int c = q / L.n_v, i = q - c * L.n_v;
+      const T* xc = x + (size_t)c * L.n_v * K;
+      for (int e = L.A.rp[i]; e < L.A.rp[i + 1]; ++e) acc += L.A.v[e] * xc[(size_t)L.A.ci[e] * K + k];
+      for (int e = L.Bt.rp[q]; e < L.Bt.rp[q + 1]; ++e) acc += L.Bt.v[e] * x[(size_t)(nu + L.Bt.ci[e]) * K + k];
+    } else {
+      const int i = q - nu;
+      for (int e = L.B.rp[i]; e < L.B.rp[i + 1]; ++e) acc += L.B.v[e] * x[(size_t)L.B.ci[e] * K + k];
+      if (i == L.pinned) acc += x[(size_t)q * K + k];
+    }
+    s_r[t] = f[(size_t)q * K + k] - acc;
+  }
+  __syncthreads();
+  const T* Ib = V.inv + V.inv_off[blk];
+  for (int t = threadIdx.x; t < m * K; t += blockDim.x) {
+    const int j = t / K, k = t % K;
+    const T* row = Ib + (size_t)j * m;
+    T a0 = T(0), a1 = T(0);
+    int l = 0;
+    for (; l + 1 < m; l += 2) {
+      a0 += row[l] * s_r[l * K + k];
+      a1 += row[l + 1] * s_r[(l + 1) * K + k];
+    }
+    if (l < m) a0 += row[l] * s_r[l * K + k];
+    x[(size_t)s_dof[j] * K + k] += omega * (a0 + a1);
+  }
+}
+
+// x = f on the listed (Dirichlet) dofs, all K columns.
+template <typename T, int K>
+__global__ void __launch_bounds__(kBlock) k_vanka_exact(int n, const int* __restrict__ dofs, const T* __restrict__ f,
+                                                       T* __restrict__ x) {
+  const long long t = gtid();
+  if (t >= (long long)n * K) return;
+  const size_t q = (size_t)dofs[t / K] * K + t % K;
+  x[q] = f[q];
+}
+
 // Single-block Gauss-Seidel for a small level, same ordering: the whole level's
 // S, g, 1/S_ii and dp sit in shared memory and the (parity, color) groups run one
 // after another separated by __syncthreads, with no inter-block waits.

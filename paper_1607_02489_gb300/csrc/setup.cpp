@@ -11,6 +11,7 @@
 #include <limits>
 #include <stdexcept>
 #include <string>
+#include <thread>
 
 namespace emin {
 namespace {
@@ -635,6 +636,176 @@ bool form_interpolation(HostLevel& L, HostLevel& Lc, const SetupParams& prm) {
   return true;
 }
 
+
+// ---------------------------------------------------------------------------
+// Vanka blocks (Section 5.1): block i = the columns of row i of B plus pressure i;
+// a non-Dirichlet dof in no block is a block of its own; Dirichlet velocity dofs
+// (zero columns of B, identity rows of A) are relaxed exactly instead.  Order of
+// relaxation: (color, index), a greedy coloring (index order, smallest free
+// color) of the graph in which two blocks are adjacent when a row of the block
+// matrix in one has an entry in a column of the other (or they share a dof).
+
+// Columns and values of row q of the block matrix [I_d (x) A, Bt; B, C].
+template <typename F>
+void block_matrix_row(const HostLevel& L, int q, F&& f) {
+  const int nu = L.dim * L.n_v;
+  if (q < nu) {
+    const int c = q / L.n_v, i = q % L.n_v;
+    for (int64_t t = L.A.row_begin(i); t < L.A.row_end(i); ++t) f(c * L.n_v + L.A.col[t], L.A.val[t]);
+    for (int64_t t = L.Bt.row_begin(q); t < L.Bt.row_end(q); ++t) f(nu + L.Bt.col[t], L.Bt.val[t]);
+  } else {
+    const int i = q - nu;
+    for (int64_t t = L.B.row_begin(i); t < L.B.row_end(i); ++t) f(L.B.col[t], L.B.val[t]);
+    if (i == L.pinned) f(q, 1.0);
+  }
+}
+
+// In-place inverse of a dense n x n row-major matrix by Gauss-Jordan elimination
+// with partial pivoting; false if a pivot vanishes.
+bool invert_dense(std::vector<double>& a, int n) {
+  std::vector<int> piv(n);
+  for (int i = 0; i < n; ++i) piv[i] = i;
+  std::vector<double> inv((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) inv[(size_t)i * n + i] = 1.0;
+  for (int col = 0; col < n; ++col) {
+    int best = col;
+    for (int r = col + 1; r < n; ++r)
+      if (std::fabs(a[(size_t)r * n + col]) > std::fabs(a[(size_t)best * n + col])) best = r;
+    if (a[(size_t)best * n + col] == 0.0) return false;
+    if (best != col)
+      for (int k = 0; k < n; ++k) {
+        std::swap(a[(size_t)best * n + k], a[(size_t)col * n + k]);
+        std::swap(inv[(size_t)best * n + k], inv[(size_t)col * n + k]);
+      }
+    const double d = 1.0 / a[(size_t)col * n + col];
+    for (int k = 0; k < n; ++k) {
+      a[(size_t)col * n + k] *= d;
+      inv[(size_t)col * n + k] *= d;
+    }
+    for (int r = 0; r < n; ++r) {
+      if (r == col) continue;
+      const double f = a[(size_t)r * n + col];
+      if (f == 0.0) continue;
+      for (int k = 0; k < n; ++k) {
+        a[(size_t)r * n + k] -= f * a[(size_t)col * n + k];
+        inv[(size_t)r * n + k] -= f * inv[(size_t)col * n + k];
+      }
+    }
+  }
+  a.swap(inv);
+  return true;
+}
+
+void form_vanka(HostLevel& L, const SetupParams& prm) {
+  const int nu = L.dim * L.n_v, N = L.N();
+  std::vector<char> covered(N, 0);
+  L.vk_ptr.assign(1, 0);
+  L.vk_dofs.clear();
+  for (int i = 0; i < L.n_p; ++i) {
+    std::vector<int> cols(L.B.col.begin() + L.B.row_begin(i), L.B.col.begin() + L.B.row_end(i));
+    std::sort(cols.begin(), cols.end());
+    for (int v : cols) {
+      L.vk_dofs.push_back(v);
+      covered[v] = 1;
+    }
+    L.vk_dofs.push_back(nu + i);
+    covered[nu + i] = 1;
+    L.vk_ptr.push_back((int)L.vk_dofs.size());
+  }
+  L.vk_dirichlet.clear();
+  for (int c = 0; c < L.dim; ++c)
+    for (int i = 0; i < L.n_v; ++i)
+      if (L.dirichlet[i]) {
+        L.vk_dirichlet.push_back(c * L.n_v + i);
+        covered[c * L.n_v + i] = 1;
+      }
+  for (int q = 0; q < N; ++q)
+    if (!covered[q]) {
+      L.vk_dofs.push_back(q);
+      L.vk_ptr.push_back((int)L.vk_dofs.size());
+    }
+  const int nb = (int)L.vk_ptr.size() - 1;
+  // dof -> blocks holding it
+  std::vector<int> dptr(N + 1, 0), dblk(L.vk_dofs.size());
+  for (int v : L.vk_dofs) ++dptr[v + 1];
+  for (int q = 0; q < N; ++q) dptr[q + 1] += dptr[q];
+  {
+    std::vector<int> pos(dptr.begin(), dptr.end() - 1);
+    for (int b = 0; b < nb; ++b)
+      for (int t = L.vk_ptr[b]; t < L.vk_ptr[b + 1]; ++t) dblk[pos[L.vk_dofs[t]]++] = b;
+  }
+  // interaction graph (symmetrised) and greedy coloring
+  std::vector<std::vector<int>> adj(nb);
+  std::vector<int> stamp(nb, -1);
+  for (int b = 0; b < nb; ++b) {
+    auto touch = [&](int v) {
+      for (int t = dptr[v]; t < dptr[v + 1]; ++t) {
+        const int o = dblk[t];
+        if (o != b && stamp[o] != b) {
+          stamp[o] = b;
+          adj[b].push_back(o);
+        }
+      }
+    };
+    for (int t = L.vk_ptr[b]; t < L.vk_ptr[b + 1]; ++t) {
+      const int q = L.vk_dofs[t];
+      touch(q);
+      block_matrix_row(L, q, [&](int v, double) { touch(v); });
+    }
+  }
+  for (int b = 0; b < nb; ++b)
+    for (int o : adj[b])
+      if (std::find(adj[o].begin(), adj[o].end(), b) == adj[o].end()) adj[o].push_back(b);
+  L.vk_colors.assign(nb, -1);
+  L.vk_ncolors = 0;
+  std::vector<int> mark;
+  for (int b = 0; b < nb; ++b) {
+    mark.assign(mark.size(), 0);
+    for (int o : adj[b])
+      if (L.vk_colors[o] >= 0) {
+        if ((int)mark.size() <= L.vk_colors[o]) mark.resize(L.vk_colors[o] + 1, 0);
+        mark[L.vk_colors[o]] = 1;
+      }
+    int c = 0;
+    while (c < (int)mark.size() && mark[c]) ++c;
+    L.vk_colors[b] = c;
+    L.vk_ncolors = std::max(L.vk_ncolors, c + 1);
+  }
+  // local matrices and their inverses, blocks split over the host's threads
+  L.vk_inv_off.assign(nb + 1, 0);
+  for (int b = 0; b < nb; ++b) {
+    const int64_t m = L.vk_ptr[b + 1] - L.vk_ptr[b];
+    L.vk_inv_off[b + 1] = L.vk_inv_off[b] + m * m;
+  }
+  if ((size_t)L.vk_inv_off[nb] * sizeof(double) > prm.vanka_max_bytes)
+    throw std::runtime_error("Vanka block inverses of a level need " +
+                             std::to_string((size_t)L.vk_inv_off[nb] * sizeof(double) >> 20) +
+                             " MiB, more than the limit (blocks too large, e.g. in 3D)");
+  L.vk_inv.assign((size_t)L.vk_inv_off[nb], 0.0);
+  std::string failure;
+  auto work = [&](int b0, int b1) {
+    std::vector<int> loc(N, -1);
+    std::vector<double> a;
+    for (int b = b0; b < b1; ++b) {
+      const int p0 = L.vk_ptr[b], m = L.vk_ptr[b + 1] - p0;
+      for (int j = 0; j < m; ++j) loc[L.vk_dofs[p0 + j]] = j;
+      a.assign((size_t)m * m, 0.0);
+      for (int j = 0; j < m; ++j)
+        block_matrix_row(L, L.vk_dofs[p0 + j], [&](int v, double val) {
+          if (loc[v] >= 0) a[(size_t)j * m + loc[v]] += val;
+        });
+      if (!invert_dense(a, m)) failure = "a Vanka block matrix is singular";
+      std::copy(a.begin(), a.end(), L.vk_inv.begin() + L.vk_inv_off[b]);
+      for (int j = 0; j < m; ++j) loc[L.vk_dofs[p0 + j]] = -1;
+    }
+  };
+  const int nt = std::max(1, std::min<int>((int)std::thread::hardware_concurrency(), 16));
+  std::vector<std::thread> pool;
+  for (int t = 0; t < nt; ++t) pool.emplace_back(work, (int)((int64_t)nb * t / nt), (int)((int64_t)nb * (t + 1) / nt));
+  for (auto& th : pool) th.join();
+  if (!failure.empty()) throw std::runtime_error(failure);
+}
+
 }  // namespace
 
 std::vector<HostLevel> build_hierarchy(HostLevel fine, const SetupParams& prm) {
@@ -656,6 +827,8 @@ std::vector<HostLevel> build_hierarchy(HostLevel fine, const SetupParams& prm) {
   HostLevel& C = levels.back();
   if (C.N() > 4096) throw std::runtime_error("coarsest level too large for the dense solve: " + std::to_string(C.N()));
   C.pinv = pseudo_inverse(dense_level(C), C.N(), 1e-12);
+  if (prm.vanka)
+    for (size_t l = 0; l + 1 < levels.size(); ++l) form_vanka(levels[l], prm);
   return levels;
 }
 

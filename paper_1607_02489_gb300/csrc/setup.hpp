@@ -16,6 +16,8 @@ struct SetupParams {
   int max_coarse = 200;
   int max_levels = 12;
   bool symmetric = true;   // one EMIN CG step, R = P^T; otherwise EMIN GMRES for P and R
+  bool vanka = false;      // form the Vanka smoother's blocks (Section 5.1) on every level but the coarsest
+  size_t vanka_max_bytes = (size_t)16 << 30;  // limit on the FP64 block inverses of one level
 };
 
 struct HostLevel {
@@ -32,6 +34,13 @@ struct HostLevel {
   std::vector<int> colors;             // greedy coloring of each strip's subgraph of S
   int n_colors = 0;
   int gs_strip = 1;                    // Gauss-Seidel strip length: bandwidth of S
+  // Vanka data (Section 5.1): blocks (global dofs of block b in vk_dofs[vk_ptr[b]..vk_ptr[b+1]),
+  // a greedy coloring of the block interaction graph, each block's local matrix
+  // inverted (row-major, at vk_inv_off[b]), and the Dirichlet dofs relaxed exactly.
+  std::vector<int> vk_ptr, vk_dofs, vk_colors, vk_dirichlet;
+  std::vector<int64_t> vk_inv_off;
+  std::vector<double> vk_inv;
+  int vk_ncolors = 0;
   // transfers to the next level
   Csr P, Pp, R, Rp;
   std::vector<int> Cp, Cv;             // coarse points (fine indices, ascending)

@@ -798,6 +798,8 @@ void amg_params_default(amg_params* p) {
   p->max_nrhs = 8;
   p->host_only = 0;
   p->autotune = 1;
+  p->smoother = 0;
+  p->vanka_omega = 0.5;
 }
 
 const char* amg_last_error(void) { return g_last_error.c_str(); }
@@ -817,6 +819,8 @@ amg_status amg_hierarchy_create(const amg_problem* pb, const amg_params* prm_in,
   if (prm.max_nrhs < 1 || prm.max_nrhs > 32) return fail(AMG_ERR_ARG, "max_nrhs must be in 1..32");
   if (prm.gs_iters < 0 || prm.pre < 0 || prm.post < 0 || prm.omega <= 0.0)
     return fail(AMG_ERR_ARG, "invalid smoother parameters");
+  if (prm.smoother != 0 && prm.smoother != 1) return fail(AMG_ERR_ARG, "smoother must be 0 (Braess-Sarazin) or 1 (Vanka)");
+  if (prm.smoother == 1 && !(prm.vanka_omega > 0.0)) return fail(AMG_ERR_ARG, "vanka_omega must be positive");
   if (pb->pinned_p >= pb->n_pnodes) return fail(AMG_ERR_ARG, "pinned pressure out of range");
   std::string why;
   if (!check_csr(pb->A_rowptr, pb->A_col, pb->n_vnodes, pb->n_vnodes, why)) return fail(AMG_ERR_ARG, "A: " + why);
@@ -845,14 +849,16 @@ amg_status amg_hierarchy_create(const amg_problem* pb, const amg_params* prm_in,
     sp.max_coarse = prm.max_coarse;
     sp.max_levels = prm.max_levels;
     sp.symmetric = pb->symmetric != 0;
+    sp.vanka = prm.smoother == 1;
     h->host = build_hierarchy(std::move(fine), sp);
     h->prm = prm;
     h->N = h->host[0].N();
     if (!prm.host_only) {
-      h->v64 = make_vcycle_f64(h->host, sp.c, prm.gs_iters, prm.pre, prm.post, round_k(prm.max_nrhs));
+      const double vomega = prm.smoother == 1 ? prm.vanka_omega : 0.0;
+      h->v64 = make_vcycle_f64(h->host, sp.c, prm.gs_iters, prm.pre, prm.post, round_k(prm.max_nrhs), vomega);
       h->v64->set_autotune(prm.autotune != 0);
       if (prm.vcycle_fp32) {
-        h->v32 = make_vcycle_f32(h->host, sp.c, prm.gs_iters, prm.pre, prm.post, round_k(prm.max_nrhs));
+        h->v32 = make_vcycle_f32(h->host, sp.c, prm.gs_iters, prm.pre, prm.post, round_k(prm.max_nrhs), vomega);
         h->v32->set_autotune(prm.autotune != 0);
       }
       EMIN_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
@@ -1011,6 +1017,20 @@ amg_status amg_level_get_points(amg_handle h, int level, int* cp, int* cv, int* 
   if (cv) std::copy(L.Cv.begin(), L.Cv.end(), cv);
   if (colors) std::copy(L.colors.begin(), L.colors.end(), colors);
   if (D) std::copy(L.D.begin(), L.D.end(), D);
+  return AMG_OK;
+}
+
+amg_status amg_level_get_vanka(amg_handle h, int level, int* nblocks, int* ndofs, int* ncolors, int* ptr,
+                               int* dofs, int* colors) {
+  if (!h || level < 0 || level >= (int)h->host.size()) return fail(AMG_ERR_ARG, "bad handle or level");
+  const HostLevel& L = h->host[level];
+  if (L.vk_ptr.empty()) return fail(AMG_ERR_ARG, "the level has no Vanka blocks");
+  if (nblocks) *nblocks = (int)L.vk_ptr.size() - 1;
+  if (ndofs) *ndofs = (int)L.vk_dofs.size();
+  if (ncolors) *ncolors = L.vk_ncolors;
+  if (ptr) std::copy(L.vk_ptr.begin(), L.vk_ptr.end(), ptr);
+  if (dofs) std::copy(L.vk_dofs.begin(), L.vk_dofs.end(), dofs);
+  if (colors) std::copy(L.vk_colors.begin(), L.vk_colors.end(), colors);
   return AMG_OK;
 }
 

@@ -57,7 +57,9 @@ struct VCycleIface {
 };
 
 // Kernel classes reported by profile().
-enum KernelClass { kVelocity = 0, kSchurRhs, kGsColor, kUpdate, kResidual, kRestrict, kProlong, kCoarse, kNumClasses };
+enum KernelClass {
+  kVelocity = 0, kSchurRhs, kGsColor, kUpdate, kResidual, kRestrict, kProlong, kCoarse, kVanka, kNumClasses
+};
 
 #define EMIN_CUDA(call)                                                                 \
   do {                                                                                  \
@@ -87,12 +89,16 @@ class DeviceVCycle : public VCycleIface {
     int* poff = nullptr;
   };
 
-  DeviceVCycle(const std::vector<HostLevel>& levels, double cfac, int gs_iters, int pre, int post, int kmax)
-      : c_(cfac), cfac_((T)cfac), gs_iters_(gs_iters), pre_(pre), post_(post), kmax_(kmax) {
+  DeviceVCycle(const std::vector<HostLevel>& levels, double cfac, int gs_iters, int pre, int post, int kmax,
+               double vanka_omega = 0.0)
+      : c_(cfac), cfac_((T)cfac), gs_iters_(gs_iters), pre_(pre), post_(post), kmax_(kmax),
+        vanka_omega_((T)vanka_omega) {
     try {
       if ((long long)levels[0].N() * kmax_ >= (1LL << 31))
         throw std::runtime_error("N * max_nrhs must stay below 2^31 (32-bit vector indices)");
       for (size_t l = 0; l < levels.size(); ++l) upload_level(levels[l], l + 1 == levels.size());
+      if (vanka_omega > 0.0)
+        for (size_t l = 0; l + 1 < levels.size(); ++l) upload_vanka(levels[l]);
       tune_ = std::make_shared<std::vector<GsChoice>>(levels.size() * 6);
       rowmap_ = std::make_shared<std::vector<int>>(levels.size() * 6 * kRowClasses, -1);
       for (size_t l = 0; l + 1 < levels.size(); ++l) {
@@ -299,10 +305,38 @@ class DeviceVCycle : public VCycleIface {
     }
   }
 
+  // Vanka step (Section 5.1): the Dirichlet dofs exactly, then one launch per color.
+  template <int K>
+  void vanka_sweep(int l, bool from_zero, cudaStream_t s) {
+    const Buf& B = buf_[l];
+    const VankaLevel& V = vk_[l];
+    const LevelView<T>& L = views_[l];
+    if (from_zero) cudaMemsetAsync(B.x, 0, sizeof(T) * ((size_t)L.dim * L.n_v + L.n_p) * K, s);
+    if (V.n_dirichlet > 0) {
+      mark_begin(l, kVanka, s);
+      k_vanka_exact<T, K><<<grid_for((long long)V.n_dirichlet * K), kBlock, 0, s>>>(V.n_dirichlet, V.dirichlet, B.b, B.x);
+      mark_end(s);
+    }
+    const size_t smem = ((size_t)V.max_block * sizeof(int) + 15) / 16 * 16 + (size_t)V.max_block * K * sizeof(T);
+    auto kern = k_vanka_color<T, K>;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    for (size_t c = 0; c + 1 < V.coff.size(); ++c) {
+      const int nb = V.coff[c + 1] - V.coff[c];
+      if (nb == 0) continue;
+      mark_begin(l, kVanka, s);
+      kern<<<nb, 128, smem, s>>>(L, V.view, V.coff[c], B.b, B.x, vanka_omega_);
+      mark_end(s);
+    }
+  }
+
   template <int K>
   void smooth(int l, int sweeps, bool from_zero, cudaStream_t s) {
     const LevelView<T>& L = views_[l];
     const Buf& B = buf_[l];
+    if (vanka_omega_ > T(0)) {
+      for (int sw = 0; sw < sweeps; ++sw) vanka_sweep<K>(l, from_zero && sw == 0, s);
+      return;
+    }
     for (int sw = 0; sw < sweeps; ++sw) {
       const int zero = (from_zero && sw == 0) ? 1 : 0;
       mark_begin(l, kVelocity, s);
@@ -331,8 +365,10 @@ class DeviceVCycle : public VCycleIface {
     EMIN_CUDA(cudaEventCreate(&e0));
     EMIN_CUDA(cudaEventCreate(&e1));
     const int classes[] = {kVelocity, kSchurRhs, kUpdate, kResidual, kRestrict, kProlong};
+    const bool vanka = vanka_omega_ > T(0);
     for (int l = 0; l + 1 < (int)views_.size(); ++l)
       for (int cls : classes) {
+        if (vanka && (cls == kVelocity || cls == kSchurRhs || cls == kUpdate)) continue;  // not in a Vanka cycle
         int& slot = (*rowmap_)[((size_t)l * 6 + ks) * kRowClasses + cls];
         if (slot >= 0) continue;
         int best = -1;
@@ -439,6 +475,7 @@ class DeviceVCycle : public VCycleIface {
   // round alike.  Runs outside graph capture, before the first capture for K.
   template <int K>
   void tune_gs(cudaStream_t s) {
+    if (vanka_omega_ > T(0)) return;  // no Gauss-Seidel in a Vanka cycle
     const int ks = kslot(K);
     cudaEvent_t e0, e1;
     EMIN_CUDA(cudaEventCreate(&e0));
@@ -760,7 +797,8 @@ class DeviceVCycle : public VCycleIface {
 
   struct CloneTag {};
   DeviceVCycle(const DeviceVCycle& o, int kmax, CloneTag)
-      : c_(o.c_), cfac_(o.cfac_), gs_iters_(o.gs_iters_), pre_(o.pre_), post_(o.post_), kmax_(kmax) {
+      : c_(o.c_), cfac_(o.cfac_), gs_iters_(o.gs_iters_), pre_(o.pre_), post_(o.post_), kmax_(kmax),
+        vanka_omega_(o.vanka_omega_) {
     try {
       if ((long long)((size_t)o.views_[0].dim * o.views_[0].n_v + o.views_[0].n_p) * kmax_ >= (1LL << 31))
         throw std::runtime_error("N * max_nrhs must stay below 2^31 (32-bit vector indices)");
@@ -769,6 +807,7 @@ class DeviceVCycle : public VCycleIface {
       gs_lanes_ = o.gs_lanes_;
       ci_rel_ = o.ci_rel_;
       cplans_ = o.cplans_;
+      vk_ = o.vk_;
       gsM_ = o.gsM_;
       tune_ = o.tune_;
       rowmap_ = o.rowmap_;
@@ -866,6 +905,30 @@ class DeviceVCycle : public VCycleIface {
       plans.push_back(P);
     }
     return plans;
+  }
+
+  void upload_vanka(const HostLevel& H) {
+    if (H.vk_ptr.empty()) throw std::runtime_error("the hierarchy was built without the Vanka blocks");
+    const int nb = (int)H.vk_ptr.size() - 1;
+    VankaLevel V;
+    std::vector<int> order(nb);
+    V.coff.assign(H.vk_ncolors + 1, 0);
+    for (int b = 0; b < nb; ++b) ++V.coff[H.vk_colors[b] + 1];
+    for (int c = 0; c < H.vk_ncolors; ++c) V.coff[c + 1] += V.coff[c];
+    {
+      std::vector<int> pos(V.coff.begin(), V.coff.end() - 1);
+      for (int b = 0; b < nb; ++b) order[pos[H.vk_colors[b]]++] = b;  // index order within a color
+    }
+    for (int b = 0; b < nb; ++b) V.max_block = std::max(V.max_block, H.vk_ptr[b + 1] - H.vk_ptr[b]);
+    std::vector<long long> off(H.vk_inv_off.begin(), H.vk_inv_off.end());
+    V.view.ptr = alloc_copy<int>(H.vk_ptr);
+    V.view.dofs = alloc_copy<int>(H.vk_dofs);
+    V.view.inv = alloc_copy<T>(H.vk_inv);
+    V.view.inv_off = alloc_copy<long long>(off);
+    V.view.order = alloc_copy<int>(order);
+    V.dirichlet = alloc_copy<int>(H.vk_dirichlet);
+    V.n_dirichlet = (int)H.vk_dirichlet.size();
+    vk_.push_back(V);
   }
 
   void upload_level(const HostLevel& H, bool coarsest) {
@@ -983,6 +1046,7 @@ class DeviceVCycle : public VCycleIface {
   double c_;
   T cfac_;
   int gs_iters_, pre_, post_, kmax_;
+  T vanka_omega_ = T(0);  // > 0: the Vanka smoother replaces Braess-Sarazin
   bool autotune_ = true;
   std::vector<LevelView<T>> views_;
   std::vector<Buf> buf_;
@@ -992,6 +1056,14 @@ class DeviceVCycle : public VCycleIface {
   std::vector<int*> done_;
   std::vector<int*> plist_, poff_;
   std::vector<std::vector<ClusterPlan>> cplans_;
+  // Vanka data per smoothed level (device copies of HostLevel's vk_*)
+  struct VankaLevel {
+    VankaView<T> view{};
+    std::vector<int> coff;  // host: first position in view.order of each color, ncolors + 1
+    const int* dirichlet = nullptr;
+    int n_dirichlet = 0, max_block = 0;
+  };
+  std::vector<VankaLevel> vk_;
   std::vector<T*> gsM_;  // dense Gauss-Seidel map of small levels (nullptr elsewhere)
   std::shared_ptr<std::vector<GsChoice>> tune_;  // [level * 6 + K slot], shared with clones
   std::shared_ptr<std::vector<int>> rowmap_;     // [(level * 6 + K slot) * classes + class], -1 untuned
@@ -1010,8 +1082,11 @@ class DeviceVCycle : public VCycleIface {
 };
 
 // Factories, one translation unit per type.
-VCycleIface* make_vcycle_f64(const std::vector<HostLevel>& levels, double cfac, int gs, int pre, int post, int kmax);
-VCycleIface* make_vcycle_f32(const std::vector<HostLevel>& levels, double cfac, int gs, int pre, int post, int kmax);
+// vanka_omega > 0 smooths with Vanka (the levels must carry the Vanka blocks), else Braess-Sarazin.
+VCycleIface* make_vcycle_f64(const std::vector<HostLevel>& levels, double cfac, int gs, int pre, int post, int kmax,
+                             double vanka_omega);
+VCycleIface* make_vcycle_f32(const std::vector<HostLevel>& levels, double cfac, int gs, int pre, int post, int kmax,
+                             double vanka_omega);
 // Finest-level FP64 block product out = A x (TX = double or float), or out = b - A x.
 cudaError_t apply_finest_f64(VCycleIface* v64, const void* x, bool x_fp32, const double* b, double* out, int K,
                              cudaStream_t s);

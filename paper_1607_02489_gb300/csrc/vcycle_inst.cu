@@ -7,8 +7,9 @@ namespace emin {
 
 #ifdef EMIN_VCYCLE_DOUBLE
 
-VCycleIface* make_vcycle_f64(const std::vector<HostLevel>& levels, double cfac, int gs, int pre, int post, int kmax) {
-  return new DeviceVCycle<double>(levels, cfac, gs, pre, post, kmax);
+VCycleIface* make_vcycle_f64(const std::vector<HostLevel>& levels, double cfac, int gs, int pre, int post, int kmax,
+                             double vanka_omega) {
+  return new DeviceVCycle<double>(levels, cfac, gs, pre, post, kmax, vanka_omega);
 }
 
 template <int K>
@@ -40,8 +41,9 @@ cudaError_t apply_finest_f64(VCycleIface* v64, const void* x, bool x_fp32, const
 
 #else
 
-VCycleIface* make_vcycle_f32(const std::vector<HostLevel>& levels, double cfac, int gs, int pre, int post, int kmax) {
-  return new DeviceVCycle<float>(levels, cfac, gs, pre, post, kmax);
+VCycleIface* make_vcycle_f32(const std::vector<HostLevel>& levels, double cfac, int gs, int pre, int post, int kmax,
+                             double vanka_omega) {
+  return new DeviceVCycle<float>(levels, cfac, gs, pre, post, kmax, vanka_omega);
 }
 
 #endif

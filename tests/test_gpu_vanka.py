@@ -1,0 +1,110 @@
+"""GPU parity of the Vanka smoother (Section 5.1, amg_params.smoother = 1) through
+the C ABI against the oracle's Vanka V-cycle and FGMRES.
+
+Tolerances as for Braess-Sarazin (test_gpu_parity.py): FP64 V-cycle relative
+2-norm error <= max(1e-11, 2 kappa u) per column; FP32 V-cycle <= 1e-4; FGMRES
+iterations within +-1 (FP64 cycle), true residual re-checked on the host."""
+import numpy as np
+import pytest
+
+from synth import make_problem, oseen_recirculating_2d, stokes_lid_2d, stokes_pinned_2d, uniform_pm1
+from oracle import Params, fgmres, setup_hierarchy, vcycle
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+g = pytest.importorskip("paper_1607_02489_gb300")
+
+VK = dict(smoother=1, pre=1, post=1)
+VKO = Params(smoother="vanka", pre=1, post=1)
+
+CASES = {
+    "pinned16": lambda: stokes_pinned_2d(16, nrhs=1),
+    "lid32": lambda: stokes_lid_2d(32, nrhs=2),
+    "oseen32": lambda: oseen_recirculating_2d(32, Re=100.0, nrhs=4),
+    "lid18_ragged3": lambda: make_problem(18, 2, 0.0, 1.0, bc="lid", nrhs=3, seed=5),
+    "lid3d": lambda: make_problem(4, 3, 0.0, 1.0, bc="lid", nrhs=1),
+}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu_and_lib():
+    assert torch.cuda.is_available(), "the gpu tests need a CUDA device"
+    g._build.build()
+    g.load()
+
+
+def _relerr(a, b):
+    return np.linalg.norm(a - b, axis=0) / np.maximum(np.linalg.norm(b, axis=0), 1e-300)
+
+
+def _coarse_condition(Ho):
+    s = np.linalg.svd(Ho.levels[-1].full_matrix().toarray(), compute_uv=False)
+    s = s[s > 1e-12 * s[0]]
+    return s[0] / s[-1]
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_vanka_vcycle_fp64_matches_oracle(case):
+    p = CASES[case]()
+    Ho = setup_hierarchy(p, VKO)
+    Hg = g.Hierarchy(p, max_nrhs=p.b.shape[1], **VK)
+    r = uniform_pm1(31, p.N * p.b.shape[1]).reshape(p.N, -1)
+    zo = vcycle(Ho, r)
+    rt = torch.tensor(r, device="cuda")
+    zt = torch.empty_like(rt)
+    Hg.vcycle(rt, zt)
+    torch.cuda.synchronize()
+    tol = max(1e-11, 2.0 * _coarse_condition(Ho) * 2.0 ** -53)
+    err = _relerr(zt.cpu().numpy(), zo)
+    assert np.all(err <= tol), (err, tol)
+    z2 = torch.empty_like(rt)
+    Hg.vcycle(rt, z2)
+    torch.cuda.synchronize()
+    assert torch.equal(zt, z2)
+
+
+@pytest.mark.parametrize("case", ["lid32", "oseen32"])
+def test_vanka_vcycle_fp32_close_to_oracle(case):
+    p = CASES[case]()
+    Ho = setup_hierarchy(p, VKO)
+    Hg = g.Hierarchy(p, max_nrhs=p.b.shape[1], vcycle_fp32=1, **VK)
+    r = uniform_pm1(32, p.N * p.b.shape[1]).reshape(p.N, -1)
+    zo = vcycle(Ho, r)
+    rt = torch.tensor(r, device="cuda")
+    zt = torch.empty_like(rt)
+    Hg.vcycle(rt, zt)
+    torch.cuda.synchronize()
+    err = _relerr(zt.cpu().numpy(), zo)
+    assert np.all(err <= 1e-4) and np.all(err > 0), err
+
+
+@pytest.mark.parametrize("case", ["pinned16", "lid32", "oseen32"])
+@pytest.mark.parametrize("fp32", [0, 1])
+def test_vanka_fgmres_matches_oracle(case, fp32):
+    p = CASES[case]()
+    Ho = setup_hierarchy(p, VKO)
+    xo, its_o, rel_o, _ = fgmres(Ho, p.b, rtol=1e-8)
+    Hg = g.Hierarchy(p, max_nrhs=p.b.shape[1], vcycle_fp32=fp32, **VK)
+    bt = torch.tensor(p.b, device="cuda")
+    xt = torch.zeros_like(bt)
+    st, its, rel = Hg.fgmres(bt, xt, rtol=1e-8, restart=100, maxit=300)
+    assert st == g.AMG_OK and np.all(rel <= 1e-8)
+    if not fp32:
+        assert np.all(np.abs(its - its_o) <= 1), (its, its_o)
+    else:
+        assert np.all(its <= its_o + 2), (its, its_o)
+    A = p.full_matrix()
+    x = xt.cpu().numpy()
+    assert np.all(np.linalg.norm(p.b - A @ x, axis=0) <= 1.01e-8 * np.linalg.norm(p.b, axis=0))
+
+
+def test_vanka_profile_counts_its_launches():
+    p = stokes_lid_2d(32, nrhs=1)
+    Hg = g.Hierarchy(p, max_nrhs=1, **VK)
+    b = torch.tensor(p.b, device="cuda")
+    z = torch.empty_like(b)
+    Hg.vcycle(b, z)
+    ms, cnt = Hg.profile_vcycle(1, reps=2)
+    v = g.KERNEL_CLASSES.index("vanka")
+    gs = g.KERNEL_CLASSES.index("gs_color")
+    assert cnt[0, v] > 0 and cnt[:, gs].sum() == 0

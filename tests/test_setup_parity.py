@@ -119,3 +119,27 @@ def test_invalid_problem_is_rejected():
 
 def test_3d_setup_matches_oracle_at_8():
     _compare(make_problem(8, 3, 0.0, 1.0, bc="lid", nrhs=1))
+
+
+@pytest.mark.parametrize("case", ["lid32", "pinned16", "oseen32", "lid18", "lid3d"])
+def test_vanka_blocks_and_colors_match_oracle(case):
+    """The library's Vanka setup (smoother = 1) against the oracle's: the same blocks
+    (dofs in the same order) and the same greedy colors on every smoothed level."""
+    from synth import stokes_pinned_2d, oseen_recirculating_2d
+    prob = {"lid32": lambda: stokes_lid_2d(32, nrhs=1), "pinned16": lambda: stokes_pinned_2d(16, nrhs=1),
+            "oseen32": lambda: oseen_recirculating_2d(32, Re=100.0, nrhs=1),
+            "lid18": lambda: make_problem(18, 2, 0.0, 1.0, bc="lid", nrhs=1),
+            "lid3d": lambda: make_problem(4, 3, 0.0, 1.0, bc="lid", nrhs=1)}[case]()
+    Ho = setup_hierarchy(prob, Params(smoother="vanka", pre=1, post=1))
+    Hg = g.Hierarchy(prob, host_only=1, smoother=1, pre=1, post=1)
+    assert Hg.num_levels() == len(Ho.levels)
+    for l, L in enumerate(Ho.levels[:-1]):
+        V = Hg.level_vanka(l)
+        blocks = L.vanka["blocks"]
+        assert len(V["ptr"]) - 1 == len(blocks)
+        for b, T in enumerate(blocks):
+            assert np.array_equal(V["dofs"][V["ptr"][b]:V["ptr"][b + 1]], T), (l, b)
+        assert np.array_equal(V["colors"], L.vanka["colors"]), l
+        assert V["ncolors"] == int(L.vanka["colors"].max()) + 1
+    with pytest.raises(g.AmgError):
+        Hg.level_vanka(len(Ho.levels) - 1)

@@ -694,7 +694,7 @@ __global__ void __launch_bounds__(kBlock) k_gs_dense(int n_p, const T* __restric
 // Vanka relaxation (Section 5.1) on one color of blocks: one thread block per
 // Vanka block.  It gathers the block's residual rows r = f - A x (K columns), then
 // adds omega * inv * r to x on the block's dofs, inv the block's local matrix
-// inverted at setup.  Blocks of one color share no dof and no entry of A, so the
+// inverted at setup; a warp takes one row at a time in both products.  Blocks of one color share no dof and no entry of A, so the
 // blocks of a launch neither race nor see each other's updates.
 template <typename T>
 struct VankaView {
@@ -705,9 +705,13 @@ struct VankaView {
   const int* order;         // blocks sorted by (color, index)
 };
 
+// Two forms, picked per level by the autotuner: k_vanka_color_pairs gives each
+// thread one (row, column) pair and walks the row itself (small blocks, many per
+// color); k_vanka_color gives each warp one row at a time, its lanes splitting the
+// row's entries (large blocks, few per color).
 template <typename T, int K>
-__global__ void __launch_bounds__(128) k_vanka_color(LevelView<T> L, VankaView<T> V, int first,
-                                                     const T* __restrict__ f, T* x, T omega) {
+__global__ void __launch_bounds__(128) k_vanka_color_pairs(LevelView<T> L, VankaView<T> V, int first,
+                                                           const T* __restrict__ f, T* x, T omega) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int blk = V.order[first + blockIdx.x];
   const int p0 = V.ptr[blk], m = V.ptr[blk + 1] - p0;
@@ -745,6 +749,54 @@ __global__ void __launch_bounds__(128) k_vanka_color(LevelView<T> L, VankaView<T
     }
     if (l < m) a0 += row[l] * s_r[l * K + k];
     x[(size_t)s_dof[j] * K + k] += omega * (a0 + a1);
+  }
+}
+
+template <typename T, int K, int NT>
+__global__ void __launch_bounds__(NT) k_vanka_color(LevelView<T> L, VankaView<T> V, int first,
+                                                    const T* __restrict__ f, T* x, T omega) {
+  // one warp per block row: lane (g, k) takes column k and every GL-th entry of the row from g
+  constexpr int GL = K >= 32 ? 1 : 32 / K;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int blk = V.order[first + blockIdx.x];
+  const int p0 = V.ptr[blk], m = V.ptr[blk + 1] - p0;
+  int* s_dof = reinterpret_cast<int*>(smem);
+  T* s_r = reinterpret_cast<T*>(smem + ((size_t)m * sizeof(int) + 15) / 16 * 16);
+  for (int j = threadIdx.x; j < m; j += blockDim.x) s_dof[j] = V.dofs[p0 + j];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int k = lane % K, g = lane / K;
+  const int nu = L.dim * L.n_v;
+  for (int j = warp; j < m; j += nwarps) {
+    const int q = s_dof[j];
+    T acc = T(0);
+    if (g < GL) {
+      if (q < nu) {
+        const int c = q / L.n_v, i = q - c * L.n_v;
+        const T* xc = x + (size_t)c * L.n_v * K;
+        for (int e = L.A.rp[i] + g; e < L.A.rp[i + 1]; e += GL) acc += L.A.v[e] * xc[(size_t)L.A.ci[e] * K + k];
+        for (int e = L.Bt.rp[q] + g; e < L.Bt.rp[q + 1]; e += GL)
+          acc += L.Bt.v[e] * x[(size_t)(nu + L.Bt.ci[e]) * K + k];
+      } else {
+        const int i = q - nu;
+        for (int e = L.B.rp[i] + g; e < L.B.rp[i + 1]; e += GL) acc += L.B.v[e] * x[(size_t)L.B.ci[e] * K + k];
+        if (i == L.pinned && g == 0) acc += x[(size_t)q * K + k];
+      }
+    }
+#pragma unroll
+    for (int off = 16; off >= K; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (g == 0 && k < K) s_r[j * K + k] = f[(size_t)q * K + k] - acc;
+  }
+  __syncthreads();
+  const T* Ib = V.inv + V.inv_off[blk];
+  for (int j = warp; j < m; j += nwarps) {
+    const T* row = Ib + (size_t)j * m;
+    T acc = T(0);
+    if (g < GL)
+      for (int l = g; l < m; l += GL) acc += row[l] * s_r[l * K + k];
+#pragma unroll
+    for (int off = 16; off >= K; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (g == 0 && k < K) x[(size_t)s_dof[j] * K + k] += omega * acc;
   }
 }
 

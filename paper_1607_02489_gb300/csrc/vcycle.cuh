@@ -101,6 +101,7 @@ class DeviceVCycle : public VCycleIface {
         for (size_t l = 0; l + 1 < levels.size(); ++l) upload_vanka(levels[l]);
       tune_ = std::make_shared<std::vector<GsChoice>>(levels.size() * 6);
       rowmap_ = std::make_shared<std::vector<int>>(levels.size() * 6 * kRowClasses, -1);
+      vkform_ = std::make_shared<std::vector<int>>(levels.size() * 6, -1);
       for (size_t l = 0; l + 1 < levels.size(); ++l) {
         views_[l].n_vc = levels[l + 1].n_v;
         views_[l].n_pc = levels[l + 1].n_p;
@@ -317,16 +318,70 @@ class DeviceVCycle : public VCycleIface {
       k_vanka_exact<T, K><<<grid_for((long long)V.n_dirichlet * K), kBlock, 0, s>>>(V.n_dirichlet, V.dirichlet, B.b, B.x);
       mark_end(s);
     }
-    const size_t smem = ((size_t)V.max_block * sizeof(int) + 15) / 16 * 16 + (size_t)V.max_block * K * sizeof(T);
-    auto kern = k_vanka_color<T, K>;
-    if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int form = (*vkform_)[(size_t)l * 6 + kslot(K)];
     for (size_t c = 0; c + 1 < V.coff.size(); ++c) {
-      const int nb = V.coff[c + 1] - V.coff[c];
-      if (nb == 0) continue;
+      if (V.coff[c + 1] == V.coff[c]) continue;
       mark_begin(l, kVanka, s);
-      kern<<<nb, 128, smem, s>>>(L, V.view, V.coff[c], B.b, B.x, vanka_omega_);
+      vanka_color<K>(l, (int)c, form < 0 ? 0 : form, s);
       mark_end(s);
     }
+  }
+  // One color of a level's Vanka blocks in one of three forms (0 pairs, 1 warp rows
+  // with 256 threads, 2 warp rows with 1024 threads).
+  template <int K>
+  void vanka_color(int l, int c, int form, cudaStream_t s) {
+    const VankaLevel& V = vk_[l];
+    const Buf& B = buf_[l];
+    const int nb = V.coff[c + 1] - V.coff[c];
+    const size_t smem = ((size_t)V.max_block * sizeof(int) + 15) / 16 * 16 + (size_t)V.max_block * K * sizeof(T);
+    if (form == 1 || form == 2) {
+      auto kern = form == 1 ? k_vanka_color<T, K, 256> : k_vanka_color<T, K, 1024>;
+      if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      kern<<<nb, form == 1 ? 256 : 1024, smem, s>>>(views_[l], V.view, V.coff[c], B.b, B.x, vanka_omega_);
+    } else {
+      auto kern = k_vanka_color_pairs<T, K>;
+      if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      kern<<<nb, 128, smem, s>>>(views_[l], V.view, V.coff[c], B.b, B.x, vanka_omega_);
+    }
+  }
+  // Vanka autotuner: each form timed on a whole step of each level (CUDA events),
+  // the fastest kept in a table shared with the clones.
+  template <int K>
+  void tune_vanka(cudaStream_t s) {
+    if (!(vanka_omega_ > T(0))) return;
+    const int ks = kslot(K);
+    cudaEvent_t e0, e1;
+    EMIN_CUDA(cudaEventCreate(&e0));
+    EMIN_CUDA(cudaEventCreate(&e1));
+    for (int l = 0; l < (int)vk_.size(); ++l) {
+      int& slot = (*vkform_)[(size_t)l * 6 + ks];
+      if (slot >= 0) continue;
+      int best = 0;
+      float best_ms = 1e30f;
+      for (int form = 0; form < 3; ++form) {
+        float total = 0.f;
+        for (int rep = 0; rep < 3; ++rep) {
+          cudaEventRecord(e0, s);
+          for (size_t c = 0; c + 1 < vk_[l].coff.size(); ++c)
+            if (vk_[l].coff[c + 1] > vk_[l].coff[c]) {
+              vanka_color<K>(l, (int)c, form, s);
+              ++launches_;
+            }
+          cudaEventRecord(e1, s);
+          cudaEventSynchronize(e1);
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          if (rep > 0) total += ms;
+        }
+        if (cudaGetLastError() == cudaSuccess && total < best_ms) {
+          best_ms = total;
+          best = form;
+        }
+      }
+      slot = best;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
   }
 
   template <int K>
@@ -519,12 +574,12 @@ class DeviceVCycle : public VCycleIface {
   }
   void tune_for(int K, cudaStream_t s) {
     switch (K) {
-      case 1: tune_rows<1>(s); tune_gs<1>(s); break;
-      case 2: tune_rows<2>(s); tune_gs<2>(s); break;
-      case 4: tune_rows<4>(s); tune_gs<4>(s); break;
-      case 8: tune_rows<8>(s); tune_gs<8>(s); break;
-      case 16: tune_rows<16>(s); tune_gs<16>(s); break;
-      case 32: tune_rows<32>(s); tune_gs<32>(s); break;
+      case 1: tune_rows<1>(s); tune_gs<1>(s); tune_vanka<1>(s); break;
+      case 2: tune_rows<2>(s); tune_gs<2>(s); tune_vanka<2>(s); break;
+      case 4: tune_rows<4>(s); tune_gs<4>(s); tune_vanka<4>(s); break;
+      case 8: tune_rows<8>(s); tune_gs<8>(s); tune_vanka<8>(s); break;
+      case 16: tune_rows<16>(s); tune_gs<16>(s); tune_vanka<16>(s); break;
+      case 32: tune_rows<32>(s); tune_gs<32>(s); tune_vanka<32>(s); break;
     }
   }
 
@@ -811,6 +866,7 @@ class DeviceVCycle : public VCycleIface {
       gsM_ = o.gsM_;
       tune_ = o.tune_;
       rowmap_ = o.rowmap_;
+      vkform_ = o.vkform_;
       autotune_ = o.autotune_;
       plist_ = o.plist_;
       poff_ = o.poff_;
@@ -1064,6 +1120,7 @@ class DeviceVCycle : public VCycleIface {
     int n_dirichlet = 0, max_block = 0;
   };
   std::vector<VankaLevel> vk_;
+  std::shared_ptr<std::vector<int>> vkform_;  // [level * 6 + K slot]: Vanka kernel form, -1 untuned
   std::vector<T*> gsM_;  // dense Gauss-Seidel map of small levels (nullptr elsewhere)
   std::shared_ptr<std::vector<GsChoice>> tune_;  // [level * 6 + K slot], shared with clones
   std::shared_ptr<std::vector<int>> rowmap_;     // [(level * 6 + K slot) * classes + class], -1 untuned

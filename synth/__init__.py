@@ -8,3 +8,4 @@ from .rng import splitmix64, uniform_pm1, uniform01, exponential  # noqa: F401
 from .serving import MESHES, REYNOLDS, serving_stream, homogeneous_rhs  # noqa: F401
 from .q2q1 import (Problem, make_problem, stokes_pinned_2d, stokes_lid_2d,  # noqa: F401
                    oseen_recirculating_2d, stokes_lid_3d, element_matrices, recirculating_wind)
+from .navier_stokes import picard_lid_cavity, lid_cavity_problem  # noqa: F401

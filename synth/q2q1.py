@@ -167,8 +167,10 @@ def recirculating_wind(x):
     return np.stack([2 * x[..., 1] * (1 - x[..., 0] ** 2), -2 * x[..., 0] * (1 - x[..., 1] ** 2)], axis=-1)
 
 
-def assemble(n: int, dim: int = 2, lo: float = 0.0, hi: float = 1.0, nu: float = 1.0, wind=None):
-    """Unconstrained velocity block (nu*A_hat [+ K_hat]) and B on the uniform n^dim mesh."""
+def assemble(n: int, dim: int = 2, lo: float = 0.0, hi: float = 1.0, nu: float = 1.0, wind=None, wind_nodal=None):
+    """Unconstrained velocity block (nu*A_hat [+ K_hat]) and B on the uniform n^dim mesh.
+    The convection wind is a function of the point (wind) or a discrete Q2 field given by
+    its nodal values, shape (dim, n_v) (wind_nodal), evaluated at the quadrature points."""
     h = (hi - lo) / n
     nv1, np1 = 2 * n + 1, n + 1
     n_v, n_p = nv1 ** dim, np1 ** dim
@@ -178,11 +180,15 @@ def assemble(n: int, dim: int = 2, lo: float = 0.0, hi: float = 1.0, nu: float =
     rows = np.repeat(vloc, nvl, axis=1).ravel()
     cols = np.tile(vloc, (1, nvl)).ravel()
     vals = np.tile((nu * Ae).ravel(), vloc.shape[0])
-    if wind is not None:
+    if wind is not None or wind_nodal is not None:
         phi, dphi, _, wq, spts = _reference_tables(dim)
-        origin = np.stack([lo + h * emi[k] for k in range(dim)], axis=1)   # (E, dim)
-        xq = origin[:, None, :] + h * spts[None, :, :]                     # (E, Q, dim)
-        wv = wind(xq)                                                      # (E, Q, dim)
+        if wind_nodal is not None:
+            wn = np.asarray(wind_nodal, dtype=np.float64).reshape(dim, n_v)
+            wv = np.einsum("qa,kea->eqk", phi, wn[:, vloc])                 # (E, Q, dim)
+        else:
+            origin = np.stack([lo + h * emi[k] for k in range(dim)], axis=1)   # (E, dim)
+            xq = origin[:, None, :] + h * spts[None, :, :]                     # (E, Q, dim)
+            wv = wind(xq)                                                      # (E, Q, dim)
         Ke = np.einsum("q,qi,eqk,qkj->eij", wq * h ** dim, phi, wv, dphi / h)
         vals = vals + Ke.reshape(-1)
     A = sp.csr_matrix((vals, (rows, cols)), shape=(n_v, n_v))
@@ -207,7 +213,7 @@ def assemble(n: int, dim: int = 2, lo: float = 0.0, hi: float = 1.0, nu: float =
 
 def make_problem(n: int, dim: int = 2, lo: float = 0.0, hi: float = 1.0, bc: str = "zero",
                  pin: bool = False, nu: float = 1.0, wind=None, nrhs: int = 1, seed: int = 0,
-                 body: str = "uniform", name: str = "") -> Problem:
+                 body: str = "uniform", name: str = "", wind_nodal=None) -> Problem:
     """Assemble, apply Dirichlet BCs / pin, and draw nrhs seeded right-hand sides.
 
     bc: "zero" (homogeneous Dirichlet) or "lid" (u_x = 1 on the top face
@@ -216,7 +222,7 @@ def make_problem(n: int, dim: int = 2, lo: float = 0.0, hi: float = 1.0, bc: str
     non-Dirichlet velocity rows (RHS j drawn from splitmix64 seed 1000*seed+j,
     one draw per velocity dof in dof order); "none" is the zero body force.
     """
-    A, B, vcoords, pcoords, p2v, bnd, top = assemble(n, dim, lo, hi, nu, wind)
+    A, B, vcoords, pcoords, p2v, bnd, top = assemble(n, dim, lo, hi, nu, wind, wind_nodal)
     n_v, n_p = A.shape[0], B.shape[0]
     N = dim * n_v + n_p
     g = np.zeros((dim, n_v))
@@ -257,7 +263,8 @@ def make_problem(n: int, dim: int = 2, lo: float = 0.0, hi: float = 1.0, bc: str
         b[: dim * n_v, j] = bu.reshape(-1)
         b[dim * n_v:, j] = bp
     return Problem(dim=dim, n=n, n_v=n_v, n_p=n_p, A=A, B=B, vcoords=vcoords, pcoords=pcoords,
-                   p2v=p2v, v_dirichlet=bnd, pinned=pinned, symmetric=wind is None, b=b, name=name)
+                   p2v=p2v, v_dirichlet=bnd, pinned=pinned, symmetric=wind is None and wind_nodal is None, b=b,
+                   name=name)
 
 
 # ----------------------------------------------------------------------------

@@ -1,0 +1,69 @@
+"""Steady Navier-Stokes lid cavity (Section 6.2): the Picard generator of the test
+systems (synth.navier_stokes) and the oracle's AMG on them against Table 5.
+
+Pins: the discrete-wind assembly equals the analytic-wind assembly for a wind
+the Q2 space holds exactly; the Picard sequence reaches the paper's 1e-8
+nonlinear residual; on the last Picard system the oracle's GMRES (to 1e-6, the
+paper's tolerance) with Vanka(1,1) and BS(2,2) stays within [0.45, 1.25] x the
+iteration counts of Table 5 and keeps its trends (more iterations at the smaller
+viscosity; Vanka no worse than Braess-Sarazin).  The oracle's counts sit below
+the paper's because its coarsest level is solved exactly (the paper relaxes it
+with Vanka)."""
+import numpy as np
+import pytest
+
+from synth import make_problem, picard_lid_cavity
+from synth.q2q1 import assemble
+from oracle import Params, fgmres, setup_hierarchy
+
+# Table 5 (Navier-Stokes lid cavity): (Vanka(1,1), BS(2,2)) iterations
+TABLE5 = {(8, 0.01): (20, 19), (16, 0.01): (26, 22), (32, 0.01): (22, 26),
+          (16, 0.002): (49, 55), (32, 0.002): (53, 60)}
+
+
+def test_discrete_wind_assembly_equals_analytic_for_a_q2_wind():
+    """w = (x y, x^2 - y) lies in Q2: its nodal interpolant gives the same convection matrix."""
+    n = 6
+    wind = lambda X: np.stack([X[..., 0] * X[..., 1], X[..., 0] ** 2 - X[..., 1]], axis=-1)  # noqa: E731
+    A1, _, vX, _, _, _, _ = assemble(n, 2, -1.0, 1.0, nu=0.3, wind=wind)
+    wn = wind(np.asarray(vX)).T
+    A2, _, _, _, _, _, _ = assemble(n, 2, -1.0, 1.0, nu=0.3, wind_nodal=wn)
+    assert abs(A1 - A2).max() <= 1e-13 * abs(A1).max()
+
+
+@pytest.fixture(scope="module")
+def picard_systems():
+    return {key: picard_lid_cavity(*key) for key in TABLE5}
+
+
+def test_picard_reaches_the_nonlinear_tolerance(picard_systems):
+    for key, (last, x, hist) in picard_systems.items():
+        assert hist[-1] < 1e-8, (key, hist[-5:])
+        assert hist[0] > 1e-4, key          # the Stokes start is not a Navier-Stokes solution
+        # the final iterate solves the nonlinear equations: its own Oseen system has a small residual
+        q = make_problem(key[0], 2, -1.0, 1.0, bc="lid", nu=key[1], body="none",
+                         wind_nodal=x[:2 * last.n_v].reshape(2, last.n_v))
+        assert np.linalg.norm(q.b[:, 0] - q.full_matrix() @ x) < 1e-8
+
+
+def _its(last, prm):
+    H = setup_hierarchy(last, prm)
+    _, its, rel, _ = fgmres(H, last.b, rtol=1e-6, maxit=300)
+    assert rel[0] <= 1e-6
+    return int(its[0])
+
+
+def test_table5_iterations_and_trends(picard_systems):
+    vk = Params(smoother="vanka", pre=1, post=1)
+    bs = Params()
+    ours = {}
+    for key, (last, _, _) in picard_systems.items():
+        assert not last.symmetric   # Oseen systems: EMIN GMRES for P and R
+        v, b = _its(last, vk), _its(last, bs)
+        ours[key] = (v, b)
+        pv, pb = TABLE5[key]
+        assert 0.45 * pv <= v <= 1.25 * pv, (key, v, pv)
+        assert 0.45 * pb <= b <= 1.25 * pb, (key, b, pb)
+        assert v <= b, (key, v, b)
+    for n in (16, 32):
+        assert ours[(n, 0.002)][0] > ours[(n, 0.01)][0] and ours[(n, 0.002)][1] > ours[(n, 0.01)][1]

@@ -110,6 +110,17 @@ void amg_params_default(amg_params* prm);
 amg_status amg_hierarchy_create(const amg_problem* prob, const amg_params* prm, void* stream,
                                 amg_handle* out);
 
+/* A hierarchy for a new matrix of the same structure as prev's finest level (same
+ * sizes, same sparsity of A and B; AMG_ERR_ARG otherwise), e.g. the next linear
+ * system of a Picard sequence: the number of levels, the coarse pressures and
+ * velocities (Alg. 3-4) and the sparsity patterns of the transfers are taken from
+ * prev, and filtering, the EMIN steps, restriction, the Galerkin products, the
+ * smoother data and the coarsest solve are redone on the new values (Section 6.1:
+ * the graph phase dominates setup and "can be performed just once over a sequence
+ * associated with a nonlinear solve").  prev stays valid and independent. */
+amg_status amg_hierarchy_create_reuse(amg_handle prev, const amg_problem* problem, const amg_params* params,
+                                      void* stream, amg_handle* out);
+
 /* z = M^-1 r: one V(pre, post) cycle from a zero initial guess (Alg. 1's relaxation
  * form on every level, coarse correction by R and P).  r and z: device, N x nrhs,
  * FP64; 1 <= nrhs <= max_nrhs.  r and z must not overlap.  Asynchronous. */

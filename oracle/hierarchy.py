@@ -563,13 +563,23 @@ def _make_level(prob_like) -> Level:
                  pinned=int(prob_like.pinned))
 
 
-def form_interpolation(L: Level, prm: Params, method: str):
+def form_interpolation(L: Level, prm: Params, method: str, reuse: Level = None):
     """Alg. 2 plus form_restriction and the Petrov-Galerkin product of Alg. 1.
-    Returns the next level, or None when coarsening makes no progress."""
+    Returns the next level, or None when coarsening makes no progress.
+    With `reuse` (the same level of a hierarchy built for a matrix of the same
+    structure), its coarse points and transfer patterns are taken and only the
+    filtering, EMIN, restriction and Galerkin products are redone: Section 6.1
+    says the graph phase can be done once per nonlinear sequence."""
     # form_aux_block_diagonal
     Zp = spgemm(L.B, L.B.T)
     Ap, adjp = filter_lump(Zp, prm.tau1_for(L.dim))
     Av, adjv = filter_lump(L.A, prm.tau1_for(L.dim))
+    if reuse is not None:
+        Cp, Cv = list(reuse.info["Cp"]), list(reuse.info["Cv"])
+        rows_of = lambda M: [list(M.indices[M.indptr[i]:M.indptr[i + 1]]) for i in range(M.shape[0])]  # noqa: E731
+        rows_p, rows_v = rows_of(reuse.Pp), rows_of(reuse.P)
+        L.info.update(dict(Cp=Cp, Cv=Cv, reused=True))
+        return _finish_interpolation(L, method, Ap, Av, Cp, Cv, rows_p, rows_v)
     excluded = [L.pinned] if L.pinned >= 0 else []
     # find_coarse_pressure (Alg. 3)
     state, S, order = find_coarse_pressures(adjp, L.pcoords, excluded)
@@ -577,9 +587,8 @@ def form_interpolation(L: Level, prm: Params, method: str):
     Cp = sorted(int(i) for i in np.flatnonzero(state == CPT))
     if len(Cp) >= L.n_p:
         return None
-    # pressure pattern and prolongator
+    # pressure pattern
     rows_p = pressure_pattern(state, S, Cp)
-    Pp = emin_step(Ap, rows_p, len(Cp), method)
     # coarse velocities (Alg. 4) and co-location
     Cbar, visited = find_velocity_cpoints(state, S, L.pcoords, prm.tau2sq)
     Cv0 = set()
@@ -588,6 +597,16 @@ def form_interpolation(L: Level, prm: Params, method: str):
         if v >= 0 and not L.dirichlet[v]:
             Cv0.add(v)
     rows_v, Cv, extra_v = velocity_pattern(adjv, Cv0, L.dirichlet)
+    L.info.update(dict(n_cp=len(Cp), n_cbar=len(Cbar), n_cv=len(Cv), extra_p=extra, extra_v=extra_v,
+                       selection_order=order, state=state.copy(), S=[dict(s) for s in S],
+                       Cp=Cp, Cbar=sorted(Cbar), Cv=Cv, visited=visited,
+                       adjp=adjp, adjv=adjv, Ap_filtered=Ap, Av_filtered=Av))
+    return _finish_interpolation(L, method, Ap, Av, Cp, Cv, rows_p, rows_v)
+
+
+def _finish_interpolation(L: Level, method: str, Ap, Av, Cp, Cv, rows_p, rows_v):
+    """EMIN prolongators on the patterns, restriction and the Petrov-Galerkin product."""
+    Pp = emin_step(Ap, rows_p, len(Cp), method)
     Pv = emin_step(Av, rows_v, len(Cv), method)
     # form_restriction (Section 4.3): R = P^T, or EMIN on A^T with the transposed pattern
     if method == "cg":
@@ -603,27 +622,31 @@ def form_interpolation(L: Level, prm: Params, method: str):
     # coarse co-location map: restriction of p2v to the coarse points
     vpos = {v: t for t, v in enumerate(Cv)}
     p2v_c = np.array([vpos.get(int(L.p2v[k]), -1) if L.p2v[k] >= 0 else -1 for k in Cp], dtype=np.int64)
-    L.info.update(dict(n_cp=len(Cp), n_cbar=len(Cbar), n_cv=len(Cv), extra_p=extra, extra_v=extra_v,
-                       selection_order=order, state=state.copy(), S=[dict(s) for s in S],
-                       Cp=Cp, Cbar=sorted(Cbar), Cv=Cv, visited=visited,
-                       adjp=adjp, adjv=adjv, Ap_filtered=Ap, Av_filtered=Av))
     # project_coordinates (Alg. 1): reading = injection of the coarse points' coordinates
     return Level(dim=d, n_v=len(Cv), n_p=len(Cp), A=Ac, B=Bc, Bt=Btc,
                  vcoords=L.vcoords[Cv], pcoords=L.pcoords[Cp], p2v=p2v_c,
                  dirichlet=np.zeros(len(Cv), dtype=bool), pinned=-1)
 
 
-def setup_hierarchy(prob, prm: Params = None) -> Hierarchy:
+def setup_hierarchy(prob, prm: Params = None, reuse: Hierarchy = None) -> Hierarchy:
     """Alg. 1 (setup_hierarchy), iterated: relaxation data, then transfers and the
     Galerkin product, until the level has <= max_coarse dofs (the paper reports
     coarsest levels below 205 dofs, Section 6.1), coarsening stalls, or
-    max_levels is reached."""
+    max_levels is reached.  With `reuse` (a hierarchy for a matrix of the same
+    structure, e.g. the previous Picard step), its levels, coarse points and
+    transfer patterns are kept (see form_interpolation)."""
     prm = prm or Params()
     method = prm.emin if prm.emin != "auto" else ("cg" if prob.symmetric else "gmres")
     levels = [_make_level(prob)]
     while True:
         L = levels[-1]
         form_relaxation(L, prm)
+        if reuse is not None:
+            # the reused hierarchy decides the levels, coarse points and patterns
+            if len(levels) >= len(reuse.levels):
+                break
+            levels.append(form_interpolation(L, prm, method, reuse.levels[len(levels) - 1]))
+            continue
         if L.N <= prm.max_coarse or len(levels) == prm.max_levels:
             break
         Lc = form_interpolation(L, prm, method)

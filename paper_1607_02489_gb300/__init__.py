@@ -21,7 +21,7 @@ LIB_PATH = _build.LIB
 AMG_OK, AMG_NOT_CONVERGED, AMG_BREAKDOWN = 0, 1, 2
 STATUS_NAMES = {0: "OK", 1: "NOT_CONVERGED", 2: "BREAKDOWN", -1: "ERR_ARG", -2: "ERR_OOM", -3: "ERR_CUDA",
                 -4: "ERR_SETUP"}
-EXPORTED = ["amg_params_default", "amg_hierarchy_create", "amg_vcycle_apply", "amg_apply", "amg_fgmres_solve",
+EXPORTED = ["amg_params_default", "amg_hierarchy_create", "amg_hierarchy_create_reuse", "amg_vcycle_apply", "amg_apply", "amg_fgmres_solve",
             "amg_fgmres_solve_host", "amg_num_levels", "amg_level_get_info", "amg_level_get_matrix",
             "amg_level_get_points", "amg_hierarchy_destroy", "amg_last_error", "amg_profile_vcycle", "amg_kernel_launches", "amg_apply_noalloc", "amg_gs_variant", "amg_row_shape", "amg_level_get_vanka",
             "amg_server_params_default", "amg_server_create", "amg_server_reserve", "amg_server_submit", "amg_server_progress",
@@ -92,6 +92,9 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.amg_hierarchy_create.argtypes = [ctypes.POINTER(AmgProblem), ctypes.POINTER(AmgParams), vp,
                                          ctypes.POINTER(vp)]
     lib.amg_hierarchy_create.restype = ctypes.c_int
+    lib.amg_hierarchy_create_reuse.argtypes = [vp, ctypes.POINTER(AmgProblem), ctypes.POINTER(AmgParams), vp,
+                                               ctypes.POINTER(vp)]
+    lib.amg_hierarchy_create_reuse.restype = ctypes.c_int
     lib.amg_vcycle_apply.argtypes = [vp, vp, vp, ctypes.c_int, vp]
     lib.amg_vcycle_apply.restype = ctypes.c_int
     lib.amg_apply.argtypes = [vp, vp, vp, ctypes.c_int, vp]
@@ -192,7 +195,7 @@ class Hierarchy:
     """amg_hierarchy_create over a problem with the fields of synth.Problem
     (A, B as scipy CSR, vcoords, pcoords, p2v, v_dirichlet, pinned, symmetric, dim)."""
 
-    def __init__(self, prob, stream=None, **params):
+    def __init__(self, prob, stream=None, reuse: "Hierarchy" = None, **params):
         lib = load()
         self.dim = int(prob.dim)
         self.n_v, self.n_p = int(prob.n_v), int(prob.n_p)
@@ -216,7 +219,13 @@ class Hierarchy:
         self.params = default_params(**params)
         handle = ctypes.c_void_p()
         sptr = ctypes.c_void_p(0) if self.params.host_only else _stream_ptr(stream)
-        _check(lib.amg_hierarchy_create(ctypes.byref(pb), ctypes.byref(self.params), sptr, ctypes.byref(handle)))
+        if reuse is not None:
+            # coarsening and patterns of `reuse` (same structure), EMIN / RAP / smoother redone
+            _check(lib.amg_hierarchy_create_reuse(reuse._h, ctypes.byref(pb), ctypes.byref(self.params), sptr,
+                                                  ctypes.byref(handle)))
+        else:
+            _check(lib.amg_hierarchy_create(ctypes.byref(pb), ctypes.byref(self.params), sptr,
+                                            ctypes.byref(handle)))
         self._h = handle
 
     def close(self):

@@ -560,6 +560,9 @@ std::vector<double> pseudo_inverse(const std::vector<double>& M, int n, double r
 
 // Alg. 2 + form_restriction + the Petrov-Galerkin product; false when the
 // coarsening makes no progress.
+void finish_interpolation(HostLevel& L, HostLevel& Lc, const SetupParams& prm, const Csr& Ap, const Csr& Av,
+                          const std::vector<std::vector<int>>& rows_p, const std::vector<std::vector<int>>& rows_v);
+
 bool form_interpolation(HostLevel& L, HostLevel& Lc, const SetupParams& prm) {
   const int d = L.dim;
   // form_aux_block_diagonal
@@ -589,8 +592,6 @@ bool form_interpolation(HostLevel& L, HostLevel& Lc, const SetupParams& prm) {
       std::sort(rows_p[i].begin(), rows_p[i].end());
     }
   }
-  const bool cg = prm.symmetric;
-  L.Pp = emin_step(Ap, rows_p, (int)L.Cp.size(), cg);
   // Alg. 4 and co-located velocities
   std::vector<char> Cbar = find_velocity_cpoints(cp, L.pX.data(), d, prm.tau2sq);
   std::vector<char> isCv(L.n_v, 0);
@@ -600,6 +601,40 @@ bool form_interpolation(HostLevel& L, HostLevel& Lc, const SetupParams& prm) {
       if (v >= 0 && !L.dirichlet[v]) isCv[v] = 1;
     }
   std::vector<std::vector<int>> rows_v = velocity_pattern(Gv, isCv, L.dirichlet, L.Cv);
+  finish_interpolation(L, Lc, prm, Ap, Av, rows_p, rows_v);
+  return true;
+}
+
+// The coarse points and sparsity patterns of a previous hierarchy's level (same
+// matrix structure), with EMIN and the Petrov-Galerkin product redone on this
+// level's values: the graph phase is done once per nonlinear sequence (Section
+// 6.1), the rest per matrix.
+void form_interpolation_reuse(HostLevel& L, HostLevel& Lc, const SetupParams& prm, const HostLevel& prev) {
+  if (prev.Pp.nrows != L.n_p || prev.P.nrows != L.n_v || prev.dim != L.dim)
+    throw std::runtime_error("reused hierarchy does not match the problem's structure");
+  Csr Zp = spgemm(L.B, transpose(L.B));
+  Csr Ap, Av;
+  Graph Gp, Gv;
+  filter_lump(Zp, prm.tau1_for(L.dim), Ap, Gp);
+  filter_lump(L.A, prm.tau1_for(L.dim), Av, Gv);
+  L.Cp = prev.Cp;
+  L.Cv = prev.Cv;
+  auto rows_of = [](const Csr& M) {
+    std::vector<std::vector<int>> rows(M.nrows);
+    for (int i = 0; i < M.nrows; ++i) rows[i].assign(M.col.begin() + M.row_begin(i), M.col.begin() + M.row_end(i));
+    return rows;
+  };
+  finish_interpolation(L, Lc, prm, Ap, Av, rows_of(prev.Pp), rows_of(prev.P));
+}
+
+// EMIN on the patterns, restriction and the Petrov-Galerkin product (Alg. 1-2,
+// Section 4.3), given the filtered matrices, the coarse points (L.Cp, L.Cv) and
+// the patterns.
+void finish_interpolation(HostLevel& L, HostLevel& Lc, const SetupParams& prm, const Csr& Ap, const Csr& Av,
+                          const std::vector<std::vector<int>>& rows_p, const std::vector<std::vector<int>>& rows_v) {
+  const int d = L.dim;
+  const bool cg = prm.symmetric;
+  L.Pp = emin_step(Ap, rows_p, (int)L.Cp.size(), cg);
   L.P = emin_step(Av, rows_v, (int)L.Cv.size(), cg);
   // form_restriction (Section 4.3)
   if (cg) {
@@ -633,7 +668,6 @@ bool form_interpolation(HostLevel& L, HostLevel& Lc, const SetupParams& prm) {
     Lc.p2v[t] = v >= 0 ? vpos[v] : -1;
   }
   Lc.dirichlet.assign(Lc.n_v, 0);
-  return true;
 }
 
 
@@ -811,9 +845,18 @@ void form_vanka(HostLevel& L, const SetupParams& prm) {
 std::vector<HostLevel> build_hierarchy(HostLevel fine, const SetupParams& prm) {
   std::vector<HostLevel> levels;
   levels.push_back(std::move(fine));
+  const std::vector<HostLevel>* prev = prm.reuse;
   while (true) {
     HostLevel& L = levels.back();
     form_relaxation(L, prm);
+    if (prev) {
+      // the previous hierarchy decides the levels
+      if (levels.size() >= prev->size()) break;
+      HostLevel Lc;
+      form_interpolation_reuse(L, Lc, prm, (*prev)[levels.size() - 1]);
+      levels.push_back(std::move(Lc));
+      continue;
+    }
     if (L.N() <= prm.max_coarse || (int)levels.size() == prm.max_levels) break;
     HostLevel Lc;
     if (!form_interpolation(L, Lc, prm) || Lc.N() >= L.N()) {

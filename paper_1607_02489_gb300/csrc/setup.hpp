@@ -18,6 +18,10 @@ struct SetupParams {
   bool symmetric = true;   // one EMIN CG step, R = P^T; otherwise EMIN GMRES for P and R
   bool vanka = false;      // form the Vanka smoother's blocks (Section 5.1) on every level but the coarsest
   size_t vanka_max_bytes = (size_t)16 << 30;  // limit on the FP64 block inverses of one level
+  // When set: take the number of levels, the coarse points and the sparsity
+  // patterns of P from this hierarchy (built for a matrix of the same structure)
+  // and redo only filtering, EMIN, RAP and the smoother data.
+  const std::vector<struct HostLevel>* reuse = nullptr;
 };
 
 struct HostLevel {

@@ -804,7 +804,39 @@ void amg_params_default(amg_params* p) {
 
 const char* amg_last_error(void) { return g_last_error.c_str(); }
 
+namespace {
+amg_status create_impl(const amg_problem* pb, const amg_params* prm_in, void* stream, amg_handle* out,
+                       const amg_hierarchy* reuse);
+bool same_pattern(const Csr& M, const int* rp, const int* ci, int nrows) {
+  if (M.nrows != nrows) return false;
+  for (int i = 0; i <= nrows; ++i)
+    if (M.rowptr[i] != rp[i]) return false;
+  for (int64_t t = 0; t < M.rowptr[nrows]; ++t)
+    if (M.col[t] != ci[t]) return false;
+  return true;
+}
+}  // namespace
+
 amg_status amg_hierarchy_create(const amg_problem* pb, const amg_params* prm_in, void* stream, amg_handle* out) {
+  return create_impl(pb, prm_in, stream, out, nullptr);
+}
+
+amg_status amg_hierarchy_create_reuse(amg_handle prev, const amg_problem* pb, const amg_params* prm_in, void* stream,
+                                      amg_handle* out) {
+  if (!prev || !pb || !out) return fail(AMG_ERR_ARG, "null previous hierarchy, problem or output handle");
+  *out = nullptr;
+  const HostLevel& F = prev->host[0];
+  if (pb->dim != F.dim || pb->n_vnodes != F.n_v || pb->n_pnodes != F.n_p)
+    return fail(AMG_ERR_ARG, "the problem's sizes differ from the previous hierarchy's");
+  if (!pb->A_rowptr || !pb->A_col || !pb->B_rowptr || !pb->B_col) return fail(AMG_ERR_ARG, "null problem array");
+  if (!same_pattern(F.A, pb->A_rowptr, pb->A_col, F.n_v) || !same_pattern(F.B, pb->B_rowptr, pb->B_col, F.n_p))
+    return fail(AMG_ERR_ARG, "the sparsity of A or B differs from the previous hierarchy's");
+  return create_impl(pb, prm_in, stream, out, prev);
+}
+
+namespace {
+amg_status create_impl(const amg_problem* pb, const amg_params* prm_in, void* stream, amg_handle* out,
+                       const amg_hierarchy* reuse) {
   if (!pb || !out) return fail(AMG_ERR_ARG, "null problem or output handle");
   *out = nullptr;
   amg_params prm;
@@ -850,6 +882,7 @@ amg_status amg_hierarchy_create(const amg_problem* pb, const amg_params* prm_in,
     sp.max_levels = prm.max_levels;
     sp.symmetric = pb->symmetric != 0;
     sp.vanka = prm.smoother == 1;
+    sp.reuse = reuse ? &reuse->host : nullptr;
     h->host = build_hierarchy(std::move(fine), sp);
     h->prm = prm;
     h->N = h->host[0].N();
@@ -872,6 +905,8 @@ amg_status amg_hierarchy_create(const amg_problem* pb, const amg_params* prm_in,
   *out = h.release();
   return AMG_OK;
 }
+
+}  // namespace
 
 amg_status amg_vcycle_apply(amg_handle h, const double* r, double* z, int nrhs, void* stream) {
   if (!h || !r || !z) return fail(AMG_ERR_ARG, "null argument");

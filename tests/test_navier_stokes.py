@@ -67,3 +67,34 @@ def test_table5_iterations_and_trends(picard_systems):
         assert v <= b, (key, v, b)
     for n in (16, 32):
         assert ours[(n, 0.002)][0] > ours[(n, 0.01)][0] and ours[(n, 0.002)][1] > ours[(n, 0.01)][1]
+
+
+def test_reused_coarsening_gives_the_fresh_hierarchy_on_the_same_matrix(picard_systems):
+    """Reusing a hierarchy on its own matrix reproduces it: same transfers and coarse operators."""
+    last = picard_systems[(16, 0.01)][0]
+    H = setup_hierarchy(last)
+    R = setup_hierarchy(last, reuse=H)
+    assert len(R.levels) == len(H.levels)
+    for L1, L2 in zip(H.levels[:-1], R.levels[:-1]):
+        for nm in ("P", "Pp", "R", "Rp"):
+            assert abs(getattr(L1, nm) - getattr(L2, nm)).max() == 0.0
+    assert abs(H.levels[-1].full_matrix() - R.levels[-1].full_matrix()).max() == 0.0
+
+
+def test_picard_with_reused_coarsening_keeps_its_iterations(picard_systems):
+    """The coarsening of the first Oseen step reused for the last Picard system: the
+    patterns stay valid (P 1 = 1 on every level) and GMRES needs at most two more
+    iterations than with a fresh setup."""
+    last = picard_systems[(32, 0.01)][0]
+    first = make_problem(32, 2, -1.0, 1.0, bc="lid", nu=0.01, body="none",
+                         wind_nodal=np.zeros((2, last.n_v)) + 1e-3)
+    H0 = setup_hierarchy(first)
+    Hr = setup_hierarchy(last, reuse=H0)
+    Hf = setup_hierarchy(last)
+    for L in Hr.levels[:-1]:
+        ones = np.ones(L.P.shape[1])
+        rows = ~np.asarray(L.dirichlet, dtype=bool)
+        assert np.abs((L.P @ ones)[rows] - 1.0).max() <= 1e-12
+    _, its_r, rel_r, _ = fgmres(Hr, last.b, rtol=1e-6)
+    _, its_f, _, _ = fgmres(Hf, last.b, rtol=1e-6)
+    assert rel_r[0] <= 1e-6 and its_r[0] <= its_f[0] + 2, (its_r, its_f)

@@ -44,9 +44,15 @@ def _csr(t):
     return sp.csr_matrix((val, col, rp), shape=shape)
 
 
-def _compare(prob, prm=None, **kw):
-    Hg = g.Hierarchy(prob, host_only=1, **kw)
-    Ho = setup_hierarchy(prob, prm or Params())
+def _compare(prob, prm=None, reuse=None, **kw):
+    """Library setup (host only) against the oracle's; reuse = (library hierarchy,
+    oracle hierarchy) whose coarsening both reuse."""
+    if reuse is None:
+        Hg = g.Hierarchy(prob, host_only=1, **kw)
+        Ho = setup_hierarchy(prob, prm or Params())
+    else:
+        Hg = g.Hierarchy(prob, host_only=1, reuse=reuse[0], **kw)
+        Ho = setup_hierarchy(prob, prm or Params(), reuse=reuse[1])
     assert Hg.num_levels() == len(Ho.levels)
     for l, L in enumerate(Ho.levels):
         info = Hg.level_info(l)
@@ -143,3 +149,25 @@ def test_vanka_blocks_and_colors_match_oracle(case):
         assert V["ncolors"] == int(L.vanka["colors"].max()) + 1
     with pytest.raises(g.AmgError):
         Hg.level_vanka(len(Ho.levels) - 1)
+
+
+
+def test_reused_coarsening_matches_oracle():
+    """amg_hierarchy_create_reuse against the oracle's reuse: the coarsening of one Oseen
+    matrix kept for another of the same structure (another wind), EMIN / RAP redone."""
+    from synth import make_problem as mk
+    n = 16
+    nv = (2 * n + 1) ** 2
+    X = np.linspace(-1, 1, 2 * n + 1)
+    xx, yy = np.meshgrid(X, X)
+    w1 = np.stack([yy.ravel() * (1 - xx.ravel() ** 2), -xx.ravel() * (1 - yy.ravel() ** 2)])
+    first = mk(n, 2, -1.0, 1.0, bc="lid", nu=0.05, body="none", wind_nodal=w1)
+    second = mk(n, 2, -1.0, 1.0, bc="lid", nu=0.02, body="none", wind_nodal=3.0 * w1 + 0.2)
+    Hg0 = g.Hierarchy(first, host_only=1)
+    Ho0 = setup_hierarchy(first)
+    _compare(second, reuse=(Hg0, Ho0))
+    # a matrix of another structure is refused
+    other = mk(n + 2, 2, -1.0, 1.0, bc="lid", nu=0.02, body="none", wind_nodal=np.zeros((2, (2 * n + 5) ** 2)))
+    with pytest.raises(g.AmgError):
+        g.Hierarchy(other, host_only=1, reuse=Hg0)
+    assert nv == first.n_v

@@ -332,37 +332,46 @@ def serve(g, torch, dev, n_requests, seed=0, max_active=None, merge_k=None):
 
     max_active = max_active or SERVE_ACTIVE
     merge_k = SERVE_MERGE if merge_k is None else merge_k
-    sv = g.Server(max_active=max_active, restart=SERVE_RESTART, maxit=MAXIT, merge_k=merge_k)
-    t0 = time.perf_counter()
-    for key in keys:  # one slot per (hierarchy, K) up front: no allocation or capture in the stream
-        for k in (1, 2, 4, 8):
-            sv.reserve(hs[key][1], k, 1)
-    reserve_s = time.perf_counter() - t0
-    g.run_stream(sv, requests(serving_stream(SERVE_WARM, SERVE_RATE, seed=1000 + seed)))
-    reqs = requests(serving_stream(n_requests, SERVE_RATE, seed=seed))
-    l0, c0 = sv.stats()["kernel_launches"], sv.stats()["cohorts"]
-    res = g.run_stream(sv, reqs)
-    st = sv.stats()
-    sv.close()
-    ok = all(r["status"] == g.AMG_OK and np.all(r["relres"] <= RTOL) for r in res)
-    lat = np.array([r["done"] - r["arrival"] for r in res])
-    wall = max(r["done"] for r in res) - min(r["arrival"] for r in res)
-    rhs = sum(q["nrhs"] for q in reqs)
-    by_n = {}
-    for q, r in zip(reqs, res):
-        by_n.setdefault(q["n"], []).append(1000.0 * (r["done"] - r["arrival"]))
-    return {"workload": SERVE_WORKLOAD, "requests": len(reqs), "rhs_solves": rhs, "all_converged": bool(ok),
-            "wall_s": wall, "requests_per_s": len(reqs) / wall, "solves_per_s": rhs / wall,
-            "offered_rps": SERVE_RATE, "max_active": max_active, "restart": SERVE_RESTART,
-            "merge_k": merge_k, "cohorts": int(st["cohorts"] - c0),
-            "latency_ms": {"p50": float(np.percentile(lat, 50) * 1000), "p99": float(np.percentile(lat, 99) * 1000),
-                           "max": float(lat.max() * 1000)},
-            "latency_p50_ms_by_mesh": {str(n): float(np.percentile(v, 50)) for n, v in sorted(by_n.items())},
-            "queued_p50_ms": float(np.percentile([r["queued"] for r in res], 50) * 1000),
-            "iterations_max": int(max(int(np.max(r["iters"])) for r in res)),
-            "gpu_launches": int(st["kernel_launches"] - l0), "slots_created": int(st["slots_created"]),
-            "slots_released": int(st["slots_released"]), "errors": int(st["errors"]),
-            "setup_s_untimed": setup_s, "reserve_s_untimed": reserve_s}
+
+    def one_stream(policy):
+        sv = g.Server(max_active=max_active, restart=SERVE_RESTART, maxit=MAXIT, merge_k=merge_k, policy=policy)
+        t0 = time.perf_counter()
+        for key in keys:  # one slot per (hierarchy, K) up front: no allocation or capture in the stream
+            for k in (1, 2, 4, 8):
+                sv.reserve(hs[key][1], k, 1)
+        reserve_s = time.perf_counter() - t0
+        g.run_stream(sv, requests(serving_stream(SERVE_WARM, SERVE_RATE, seed=1000 + seed)))
+        reqs = requests(serving_stream(n_requests, SERVE_RATE, seed=seed))
+        l0, c0 = sv.stats()["kernel_launches"], sv.stats()["cohorts"]
+        res = g.run_stream(sv, reqs)
+        st = sv.stats()
+        sv.close()
+        ok = all(r["status"] == g.AMG_OK and np.all(r["relres"] <= RTOL) for r in res)
+        lat = np.array([r["done"] - r["arrival"] for r in res])
+        wall = max(r["done"] for r in res) - min(r["arrival"] for r in res)
+        rhs = sum(q["nrhs"] for q in reqs)
+        by_n = {}
+        for q, r in zip(reqs, res):
+            by_n.setdefault(q["n"], []).append(1000.0 * (r["done"] - r["arrival"]))
+        return {"workload": SERVE_WORKLOAD, "policy": ["submission order", "smallest work first"][policy],
+                "requests": len(reqs), "rhs_solves": rhs, "all_converged": bool(ok),
+                "wall_s": wall, "requests_per_s": len(reqs) / wall, "solves_per_s": rhs / wall,
+                "offered_rps": SERVE_RATE, "max_active": max_active, "restart": SERVE_RESTART,
+                "merge_k": merge_k, "cohorts": int(st["cohorts"] - c0),
+                "latency_ms": {"p50": float(np.percentile(lat, 50) * 1000),
+                               "p99": float(np.percentile(lat, 99) * 1000), "max": float(lat.max() * 1000)},
+                "latency_p50_ms_by_mesh": {str(n): float(np.percentile(v, 50)) for n, v in sorted(by_n.items())},
+                "queued_p50_ms": float(np.percentile([r["queued"] for r in res], 50) * 1000),
+                "iterations_max": int(max(int(np.max(r["iters"])) for r in res)),
+                "gpu_launches": int(st["kernel_launches"] - l0), "slots_created": int(st["slots_created"]),
+                "slots_released": int(st["slots_released"]), "errors": int(st["errors"]),
+                "setup_s_untimed": setup_s, "reserve_s_untimed": reserve_s}
+
+    out = one_stream(0)
+    sjf = one_stream(1)
+    out["smallest_work_first"] = {k: sjf[k] for k in ("solves_per_s", "requests_per_s", "latency_ms",
+                                                      "latency_p50_ms_by_mesh", "cohorts", "all_converged")}
+    return out
 
 
 def main():

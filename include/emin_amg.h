@@ -279,6 +279,10 @@ typedef struct {
   int restart;         /* FGMRES restart length of every request; default 100 */
   int maxit;           /* iteration limit per right-hand side; default 500 */
   int merge_k;         /* most columns stacked into one cohort, 0..32; default 8; <= 1: no batching */
+  int policy;          /* admission order: 0 (default) submission order; 1 smallest work first
+                          (N x columns rounded up), submission order among equals: lower median
+                          latency under overload, but a large request can wait while smaller
+                          ones keep arriving */
 } amg_server_params;
 
 typedef struct {

@@ -62,7 +62,7 @@ class AmgLevelInfo(ctypes.Structure):
 
 class AmgServerParams(ctypes.Structure):
     _fields_ = [("max_active", ctypes.c_int), ("device_bytes", ctypes.c_size_t), ("restart", ctypes.c_int),
-                ("maxit", ctypes.c_int), ("merge_k", ctypes.c_int)]
+                ("maxit", ctypes.c_int), ("merge_k", ctypes.c_int), ("policy", ctypes.c_int)]
 
 
 class AmgServerStats(ctypes.Structure):
@@ -390,13 +390,14 @@ class Server:
     resident hierarchies.  submit() queues a solve on host buffers, progress()
     never blocks and returns the tickets that completed, result() collects one."""
 
-    def __init__(self, max_active=16, device_bytes=0, restart=100, maxit=500, merge_k=8):
+    def __init__(self, max_active=16, device_bytes=0, restart=100, maxit=500, merge_k=8, policy=0):
         lib = load()
         prm = AmgServerParams()
         lib.amg_server_params_default(ctypes.byref(prm))
         prm.max_active, prm.device_bytes, prm.restart, prm.maxit = int(max_active), int(device_bytes), int(restart), \
             int(maxit)
         prm.merge_k = int(merge_k)
+        prm.policy = int(policy)
         h = ctypes.c_void_p()
         self._check(lib.amg_server_create(ctypes.byref(prm), ctypes.byref(h)))
         self._s = h

@@ -228,14 +228,24 @@ struct amg_server {
   void admit() {
     std::vector<long long> q(queue.begin(), queue.end());
     std::vector<char> taken(q.size(), 0);
-    for (size_t a = 0; a < q.size(); ++a) {
+    // candidate heads: submission order, or smallest work (N x columns) first
+    std::vector<size_t> heads(q.size());
+    for (size_t a = 0; a < q.size(); ++a) heads[a] = a;
+    if (prm.policy == 1)
+      std::stable_sort(heads.begin(), heads.end(), [&](size_t x, size_t y) {
+        const Request& rx = reqs.at(q[x]);
+        const Request& ry = reqs.at(q[y]);
+        return (double)rx.h->N * round_k(rx.nrhs) < (double)ry.h->N * round_k(ry.nrhs);
+      });
+    for (size_t a : heads) {
       if (taken[a]) continue;
       if (busy_slots() >= prm.max_active) break;
       const Request& r = reqs.at(q[a]);
       std::vector<size_t> cohort{a};
       int total = r.nrhs;
       if (prm.merge_k > 1)
-        for (size_t b = a + 1; b < q.size(); ++b) {
+        for (size_t b = 0; b < q.size(); ++b) {
+          if (b == a || (b < a && prm.policy == 0)) continue;
           if (taken[b]) continue;
           const Request& o = reqs.at(q[b]);
           if (o.h == r.h && o.rtol == r.rtol && total + o.nrhs <= prm.merge_k) {
@@ -337,6 +347,7 @@ void amg_server_params_default(amg_server_params* p) {
   p->restart = 100;
   p->maxit = 500;
   p->merge_k = 8;
+  p->policy = 0;
 }
 
 const char* amg_server_last_error(amg_server_handle sv) {
@@ -354,6 +365,7 @@ amg_status amg_server_create(const amg_server_params* prm_in, amg_server_handle*
   if (prm.max_active < 1 || prm.max_active > 256) return sfail(AMG_ERR_ARG, "max_active must be in 1..256");
   if (prm.restart < 1 || prm.maxit < 1) return sfail(AMG_ERR_ARG, "restart and maxit must be positive");
   if (prm.merge_k < 0 || prm.merge_k > 32) return sfail(AMG_ERR_ARG, "merge_k must be in 0..32");
+  if (prm.policy != 0 && prm.policy != 1) return sfail(AMG_ERR_ARG, "policy must be 0 or 1");
   std::unique_ptr<amg_server> sv(new amg_server());
   sv->prm = prm;
   if (prm.device_bytes > 0) {

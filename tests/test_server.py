@@ -270,3 +270,20 @@ def test_batched_cohorts_match_solves_alone_within_tolerance(hierarchies):
     res2, xs2, _ = _run_batch(hs, reqs, rtol, merge_k=8)
     for i in range(len(reqs)):
         assert np.array_equal(res[i][1], res2[i][1]) and torch.equal(xs[i][1], xs2[i][1])
+
+
+def test_smallest_work_first_admits_the_small_request_first(hierarchies):
+    """With policy 1 and one slot, a small request queued behind a large one starts first."""
+    hs = hierarchies
+    sv = g.Server(max_active=1, restart=RESTART, maxit=MAXIT, merge_k=1, policy=1)
+    order = []
+    big_b = _b(hs["oseen48_re100"][0], 0, 8)
+    small_b = _b(hs["pinned16"][0], 0, 1)
+    big = sv.submit(hs["oseen48_re100"][1], big_b, torch.zeros_like(big_b).pin_memory())
+    small = sv.submit(hs["pinned16"][1], small_b, torch.zeros_like(small_b).pin_memory())
+    while len(order) < 2:
+        for t in sv.progress():
+            order.append(t)
+            assert sv.result(t)[0] == g.AMG_OK
+    assert order == [small, big]
+    sv.close()

@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving stream")
     ap.add_argument("--no-vanka", action="store_true", help="skip the Vanka-smoother side line")
+    ap.add_argument("--configs", action="store_true",
+                    help="instead of the default run: time the other workloads (16x16 pinned Stokes, 512x512 "
+                         "Oseen x32, 48^3 Stokes) with the FP64 and FP32 V-cycles, and the oracle on the first two")
     ap.add_argument("--serve-requests", type=int, default=64)
     ap.add_argument("--serve-active", type=int, default=None, help="requests running at once (default SERVE_ACTIVE)")
     ap.add_argument("--serve-merge", type=int, default=None, help="columns stacked per cohort (default SERVE_MERGE)")
@@ -215,6 +218,98 @@ CPU_SAMPLE = ("the FP64 oracle (numpy/scipy) solving 1 of the 8 right-hand sides
               "256x256 lid-cavity workload to 1e-8 with the same method; hierarchy set up beforehand, untimed")
 
 
+CONFIGS = {
+    "C1": dict(name="2D Stokes 16x16, pinned pressure, 1 rhs", kind="pinned", n=16, nrhs=1),
+    "C3": dict(name="2D Oseen 512x512 on [-1,1]^2, recirculating wind, Re=10, 32 rhs", kind="oseen", n=512,
+               nrhs=32, Re=10.0),
+    "C4": dict(name="3D Stokes 48^3 lid-driven cube, 1 rhs", kind="lid3d", n=48, nrhs=1),
+}
+
+
+def _config_problem(c, nrhs=None):
+    from synth import oseen_recirculating_2d, stokes_lid_3d, stokes_pinned_2d
+    k = nrhs or c["nrhs"]
+    if c["kind"] == "pinned":
+        return stokes_pinned_2d(c["n"], nrhs=k)
+    if c["kind"] == "oseen":
+        return oseen_recirculating_2d(c["n"], Re=c["Re"], nrhs=k)
+    return stokes_lid_3d(c["n"], nrhs=k)
+
+
+def _oracle_config_worker(key, q):
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    from oracle import setup_hierarchy, fgmres
+    p = _config_problem(CONFIGS[key], nrhs=1)
+    t0 = time.perf_counter()
+    Ho = setup_hierarchy(p)
+    t1 = time.perf_counter()
+    x, it, rel, _ = fgmres(Ho, p.b, rtol=RTOL, restart=RESTART, maxit=MAXIT)
+    q.put((t1 - t0, time.perf_counter() - t1, int(it[0])))
+
+
+def run_oracle_config(key):
+    import multiprocessing as mp
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    pr = ctx.Process(target=_oracle_config_worker, args=(key, q))
+    pr.start()
+    res = q.get()
+    pr.join()
+    return res
+
+
+def configs_main(args):
+    """One JSON line with the other workloads of the method: solves/s with the FP64 and
+    FP32 V-cycles on the GPU (inputs resident, CUDA events), the V-cycle kernels'
+    algorithmic bandwidth, and the oracle (1 core, 1 right-hand side) on C1 and C3."""
+    import numpy as np
+    import torch
+    oracle = {}
+    if not args.no_cpu_baseline:
+        for key in ("C1", "C3"):  # before any CUDA work in this process
+            setup_s, solve_s, its = run_oracle_config(key)
+            oracle[key] = {"solves_per_s": 1.0 / solve_s, "seconds": solve_s, "setup_s_untimed": setup_s,
+                           "iterations": its, "cores": 1, "sample": "1 right-hand side"}
+    import paper_1607_02489_gb300 as g
+    g._build.build()
+    peak = measured_peaks()[0]
+    out = {}
+    for key, c in CONFIGS.items():
+        p = _config_problem(c)
+        k = c["nrhs"]
+        b = torch.tensor(p.b, device="cuda")
+        x = torch.zeros_like(b)
+        rec = {"workload": c["name"], "dofs": int(p.N), "nrhs": k}
+        for fp32 in (0, 1):
+            H = g.Hierarchy(p, max_nrhs=k, vcycle_fp32=fp32)
+            H.fgmres(b, x, rtol=RTOL, restart=60, maxit=MAXIT)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 3
+            e0.record()
+            for _ in range(reps):
+                st, its, rel = H.fgmres(b, x, rtol=RTOL, restart=60, maxit=MAXIT)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            s = 4 if fp32 else 8
+            vms, vcnt = H.profile_vcycle(k, reps=3)
+            vbytes = sum(algorithmic_bytes(H, l, cl, k, s) * vcnt[l, j] / 3
+                         for l in range(vms.shape[0]) for j, cl in enumerate(g.KERNEL_CLASSES) if vcnt[l, j])
+            gbs = vbytes / (vms.sum() / 3 / 1000.0) / 1e9
+            rec["fp32" if fp32 else "fp64"] = {"solves_per_s": k / (ms / 1000.0), "ms_per_solve_batch": ms,
+                                               "status": int(st), "iterations_max": int(np.max(its)),
+                                               "relres_max": float(np.max(rel)), "vcycle_kernels_GBs": gbs,
+                                               "vcycle_kernels_frac": gbs / peak}
+            del H
+        if key in oracle:
+            rec["oracle"] = oracle[key]
+        out[key] = rec
+    print(json.dumps({"metric": METRIC, "configs": out, "peak_GBs": peak, "data": "synthetic"}), flush=True)
+
+
 def _oracle_worker(n_solves, q):
     os.environ.setdefault("OMP_NUM_THREADS", "1")
     from synth import stokes_lid_2d
@@ -378,6 +473,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return reference_main(args)
+    if args.configs:
+        return configs_main(args)
     if args.ncu:
         args.no_cpu_baseline = True
     import numpy as np

@@ -672,6 +672,51 @@ void finish_interpolation(HostLevel& L, HostLevel& Lc, const SetupParams& prm, c
 
 
 // ---------------------------------------------------------------------------
+// Dense form of a small level's Gauss-Seidel call: the iterations from dp = 0 are
+// the linear map dp = M g.  Rows are relaxed in the order (strip parity, color,
+// index); row i of M becomes (e_i - sum_{j != i} S_ij M_j) / S_ii when row i is
+// relaxed.  The columns of M are independent, so host threads split them.
+void form_dense_gs(HostLevel& L, int iters) {
+  const int n = L.n_p, T = L.gs_strip, ncol = L.n_colors;
+  const int nstrips = std::max(1, (n + T - 1) / T);
+  std::vector<int> order;  // rows in relaxation order for one iteration
+  order.reserve(n);
+  for (int par = 0; par < 2; ++par)
+    for (int c = 0; c < ncol; ++c)
+      for (int st = par; st < nstrips; st += 2)
+        for (int i = st * T; i < std::min(n, (st + 1) * T); ++i)
+          if (L.colors[i] == c) order.push_back(i);
+  L.gs_dense.assign((size_t)n * n, 0.0);
+  double* M = L.gs_dense.data();
+  auto work = [&](int q0, int q1) {
+    std::vector<double> row(q1 - q0);
+    for (int it = 0; it < iters; ++it)
+      for (int i : order) {
+        double diag = 0.0;
+        std::fill(row.begin(), row.end(), 0.0);
+        if (i >= q0 && i < q1) row[i - q0] = 1.0;
+        for (int64_t t = L.S.row_begin(i); t < L.S.row_end(i); ++t) {
+          const int j = L.S.col[t];
+          if (j == i) {
+            diag += L.S.val[t];
+            continue;
+          }
+          const double v = L.S.val[t];
+          const double* Mj = M + (size_t)j * n + q0;
+          for (int q = 0; q < q1 - q0; ++q) row[q] -= v * Mj[q];
+        }
+        const double dinv = diag != 0.0 ? 1.0 / diag : 0.0;
+        double* Mi = M + (size_t)i * n + q0;
+        for (int q = 0; q < q1 - q0; ++q) Mi[q] = row[q] * dinv;
+      }
+  };
+  const int nt = std::max(1, std::min<int>({(int)std::thread::hardware_concurrency(), 16, (n + 63) / 64}));
+  std::vector<std::thread> pool;
+  for (int t = 0; t < nt; ++t) pool.emplace_back(work, (int)((int64_t)n * t / nt), (int)((int64_t)n * (t + 1) / nt));
+  for (auto& th : pool) th.join();
+}
+
+// ---------------------------------------------------------------------------
 // Vanka blocks (Section 5.1): block i = the columns of row i of B plus pressure i;
 // a non-Dirichlet dof in no block is a block of its own; Dirichlet velocity dofs
 // (zero columns of B, identity rows of A) are relaxed exactly instead.  Order of
@@ -872,6 +917,8 @@ std::vector<HostLevel> build_hierarchy(HostLevel fine, const SetupParams& prm) {
   C.pinv = pseudo_inverse(dense_level(C), C.N(), 1e-12);
   if (prm.vanka)
     for (size_t l = 0; l + 1 < levels.size(); ++l) form_vanka(levels[l], prm);
+  for (size_t l = 0; l + 1 < levels.size(); ++l)
+    if (levels[l].n_p <= kGsDenseMaxRows) form_dense_gs(levels[l], prm.gs_iters);
   return levels;
 }
 

@@ -17,12 +17,15 @@ struct SetupParams {
   int max_levels = 12;
   bool symmetric = true;   // one EMIN CG step, R = P^T; otherwise EMIN GMRES for P and R
   bool vanka = false;      // form the Vanka smoother's blocks (Section 5.1) on every level but the coarsest
+  int gs_iters = 5;        // Gauss-Seidel iterations per Braess-Sarazin step (for the dense map)
   size_t vanka_max_bytes = (size_t)16 << 30;  // limit on the FP64 block inverses of one level
   // When set: take the number of levels, the coarse points and the sparsity
   // patterns of P from this hierarchy (built for a matrix of the same structure)
   // and redo only filtering, EMIN, RAP and the smoother data.
   const std::vector<struct HostLevel>* reuse = nullptr;
 };
+
+constexpr int kGsDenseMaxRows = 2896;  // dense Gauss-Seidel map: <= 32 MiB in FP32
 
 struct HostLevel {
   int dim = 2, n_v = 0, n_p = 0, pinned = -1;
@@ -37,7 +40,10 @@ struct HostLevel {
   Csr S;                               // B D^-1 Bt, pinned row = identity
   std::vector<int> colors;             // greedy coloring of each strip's subgraph of S
   int n_colors = 0;
-  int gs_strip = 1;                    // Gauss-Seidel strip length: bandwidth of S
+  int gs_strip = 1;                    // Gauss-Seidel strip length (see form_relaxation)
+  // levels of at most kGsDenseMaxRows pressures: M (n_p x n_p, row-major) with dp = M g
+  // for gs_iters Gauss-Seidel iterations from dp = 0 in the (strip parity, color, index) order
+  std::vector<double> gs_dense;
   // Vanka data (Section 5.1): blocks (global dofs of block b in vk_dofs[vk_ptr[b]..vk_ptr[b+1]),
   // a greedy coloring of the block interaction graph, each block's local matrix
   // inverted (row-major, at vk_inv_off[b]), and the Dirichlet dofs relaxed exactly.

@@ -882,6 +882,7 @@ amg_status create_impl(const amg_problem* pb, const amg_params* prm_in, void* st
     sp.max_levels = prm.max_levels;
     sp.symmetric = pb->symmetric != 0;
     sp.vanka = prm.smoother == 1;
+    sp.gs_iters = prm.gs_iters;
     sp.reuse = reuse ? &reuse->host : nullptr;
     h->host = build_hierarchy(std::move(fine), sp);
     h->prm = prm;

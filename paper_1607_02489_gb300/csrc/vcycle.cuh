@@ -77,7 +77,6 @@ class DeviceVCycle : public VCycleIface {
   // Strips of a level split over a cluster of C blocks (k_gs_cluster): block c owns
   // spc consecutive strips; plist / poff as GsCluster; extents are maxima over blocks.
   enum GsKind { kGsSingle = 0, kGsCluster = 1, kGsPipe = 2, kGsPhases = 3, kGsDense = 4 };
-  static constexpr int kGsDenseMax = 1024;  // pressures of a level whose Gauss-Seidel map is formed densely
   struct GsChoice {
     int kind = -1;  // GsKind, -1 = not tuned yet
     int C = 0;      // cluster size; shape of the pipelined kernel (0 heuristic, 1-3 launch_gs_pipe)
@@ -898,33 +897,6 @@ class DeviceVCycle : public VCycleIface {
     return B;
   }
 
-  // M with dp = M g for gs_iters_ Gauss-Seidel iterations from dp = 0, relaxing the
-  // sorted rows group by group in the order (strip parity, color, index): every
-  // column of M at once, in FP64.  Row i of M becomes (e_i - sum_j S_ij M_j) / S_ii
-  // when row i is relaxed.
-  std::vector<double> dense_gs_map(int n_p, int ncol, int nstrips, const std::vector<int>& soff,
-                                   const std::vector<int>& perm, const Csr& So, const std::vector<double>& dinv) {
-    std::vector<double> M((size_t)n_p * n_p, 0.0), row(n_p);
-    const int stride = ncol + 1;
-    for (int it = 0; it < gs_iters_; ++it)
-      for (int par = 0; par < 2; ++par)
-        for (int c = 0; c < ncol; ++c)
-          for (int st = par; st < nstrips; st += 2)
-            for (int r = soff[(size_t)st * stride + c]; r < soff[(size_t)st * stride + c + 1]; ++r) {
-              const int i = perm[r];
-              std::fill(row.begin(), row.end(), 0.0);
-              row[i] = 1.0;
-              for (int64_t t = So.rowptr[r]; t < So.rowptr[r + 1]; ++t) {
-                const double v = So.val[t];
-                const double* Mj = M.data() + (size_t)So.col[t] * n_p;
-                for (int q = 0; q < n_p; ++q) row[q] -= v * Mj[q];
-              }
-              double* Mi = M.data() + (size_t)i * n_p;
-              for (int q = 0; q < n_p; ++q) Mi[q] = row[q] * dinv[r];
-            }
-    return M;
-  }
-
   // Cluster plans for C = 2, 4, 8, 16 blocks (levels of more than two strips).
   std::vector<ClusterPlan> cluster_plans(int n_p, int Tst, int ncol, int nstrips, const std::vector<int>& soff,
                                          const Csr& So) {
@@ -1068,8 +1040,7 @@ class DeviceVCycle : public VCycleIface {
       plist_.push_back(alloc_copy<int>(plist));
       poff_.push_back(alloc_copy<int>(poff));
       cplans_.push_back(cluster_plans(H.n_p, Tst, ncol, nstrips, soff, So));
-      gsM_.push_back(H.n_p <= kGsDenseMax ? alloc_copy<T>(dense_gs_map(H.n_p, ncol, nstrips, soff, perm, So, dinv))
-                                          : nullptr);
+      gsM_.push_back(H.gs_dense.empty() ? nullptr : alloc_copy<T>(H.gs_dense));
     }
     // lanes per Schur row: 4 when rows are long enough to share
     const double avg = H.n_p ? (double)So.nnz() / H.n_p : 0.0;

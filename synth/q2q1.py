@@ -153,6 +153,26 @@ def _element_nodes(n, dim):
     return vloc, ploc, emi
 
 
+def mass_matrices(n: int, dim: int = 2, lo: float = 0.0, hi: float = 1.0):
+    """Q2 velocity mass matrix (one component, n_v x n_v) and Q1 pressure mass matrix
+    (n_p x n_p) on the uniform n^dim mesh: integrals of products of basis functions,
+    exact with the 3-point Gauss rule."""
+    h = (hi - lo) / n
+    phi, _, psi, wq, _ = _reference_tables(dim)
+    W = wq * h ** dim
+    Mv_e = np.einsum("q,qi,qj->ij", W, phi, phi)
+    Mp_e = np.einsum("q,qi,qj->ij", W, psi, psi)
+    vloc, ploc, _ = _element_nodes(n, dim)
+    n_v, n_p = (2 * n + 1) ** dim, (n + 1) ** dim
+    def build(loc, Me, size):
+        k = loc.shape[1]
+        r = np.repeat(loc, k, axis=1).ravel()
+        c = np.tile(loc, (1, k)).ravel()
+        v = np.tile(Me.ravel(), loc.shape[0])
+        return sp.csr_matrix((v, (r, c)), shape=(size, size))
+    return build(vloc, Mv_e, n_v), build(ploc, Mp_e, n_p)
+
+
 def _grid_coords(m, dim, lo, hi):
     """Coordinates of an m^dim lexicographic grid of nodes spanning [lo, hi]^dim."""
     i = np.arange(m ** dim)

@@ -278,3 +278,37 @@ def test_3d_velocities_coarsen_with_the_3d_tau1():
     assert H.levels[-1].N <= 200
     H06 = setup_hierarchy(p, Params(tau1=0.06, max_levels=2))
     assert H06.levels[1].n_v > 0.3 * H06.levels[0].n_v
+
+
+def _infsup_estimates(n):
+    """Table 3's estimate: the smallest non-zero singular value of
+    lump(|M_l^p|)^-1/2 B_l lump(|M_l^v|)^-1/2 on every level, with the mass matrices
+    carried to the coarse levels as M_l = R_l M_{l-1} P_l (Section 6.1)."""
+    from synth.q2q1 import mass_matrices
+    p = stokes_lid_2d(n, nrhs=1, body="none", lo=-1.0, hi=1.0)
+    H = setup_hierarchy(p)
+    Mv, Mp = mass_matrices(n, 2, -1.0, 1.0)
+    scal = lambda M: sp.diags(1.0 / np.sqrt(np.asarray(abs(M).sum(axis=1)).ravel()))  # noqa: E731
+    out = []
+    for l, L in enumerate(H.levels):
+        if l > 0:
+            Lp = H.levels[l - 1]
+            Mv, Mp = Lp.R @ Mv @ Lp.P, Lp.Rp @ Mp @ Lp.Pp
+        Bs = scal(Mp) @ L.B @ sp.kron(sp.identity(L.dim), scal(Mv))
+        ev = np.sort(np.linalg.eigvalsh((Bs @ Bs.T).toarray()))
+        out.append(float(np.sqrt(ev[ev > 1e-10 * ev[-1]][0])))
+    return out
+
+
+def test_table3_infsup_estimates_of_the_coarse_operators():
+    """Table 3 (256x256: 1.54, 1.56, 1.56, 1.07): the estimate does not depend on the mesh,
+    the first coarse level matches the paper's 1.56, and no level approaches zero.  With the
+    formula as written (lumping |M|) the finest level gives 1.42, 8% below the paper's 1.54;
+    lumping M itself gives 1.56 there, so the paper's fine-level figure may come from that
+    lumping.  A wrong B scale, transfer or Galerkin product moves these values."""
+    s16, s32, s64 = _infsup_estimates(16), _infsup_estimates(32), _infsup_estimates(64)
+    assert abs(s16[0] - s64[0]) < 0.02 and abs(s32[0] - s64[0]) < 0.01
+    assert abs(s64[0] - 1.54) <= 0.10 * 1.54
+    assert abs(s64[1] - 1.56) <= 0.03 * 1.56
+    assert abs(s32[1] - s64[1]) < 0.03
+    assert min(s64) > 0.2

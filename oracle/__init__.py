@@ -7,7 +7,7 @@ shares no code with it, and it imports nothing from the product.
 
 It is a plain, slow restatement of the method, step by step in the paper's
 order (Alg. 1-4, Section 4.3 for EMIN, Section 5.2 for Braess-Sarazin,
-Section 5.1 for Vanka),
+Section 5.1 for Vanka, Section 5 for ILU(1)),
 written with numpy / scipy.sparse primitives and Python loops over graph
 vertices.  Where the paper is silent or garbled, the reading taken is stated
 in the docstring of the function that implements the step.
@@ -22,6 +22,10 @@ tests/test_synth.py):
   * vanka.py (Vanka relaxation, Section 5.1): pinned (block definition,
     exact local solves, colored sweep = block-by-block sweep, dense solves,
     Table 1's Vanka(1,1) counts).
+  * ilu.py (ILU(1) relaxation, Section 5): pinned (L U = A on the kept
+    pattern, the level-of-fill rule, exactness without fill, the zero-pivot
+    reading on a 3x3 saddle matrix, the error-propagation spectrum, dense
+    solves, Table 1's and Table 5's ILU(1)(1,1) counts).
   * find_extra_dist3_cpoints: the paper names its criteria but gives no
     thresholds, and no uniform-mesh case triggers it, so its choices are
     parity unpinned (only the coverage invariant it must keep is pinned).

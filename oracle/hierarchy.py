@@ -43,7 +43,7 @@ class Params:
     pre: int = 2
     post: int = 2
     emin: str = "auto"            # "cg" (Stokes), "gmres" (Oseen); auto picks by symmetry
-    smoother: str = "bs"          # "bs" Braess-Sarazin (Section 5.2), "vanka" (Section 5.1)
+    smoother: str = "bs"          # "bs" Braess-Sarazin (Section 5.2), "vanka" (Section 5.1), "ilu" ILU(1) (Section 5)
     vanka_omega: float = 0.5      # Vanka under-relaxation (Section 6)
     max_coarse: int = 200
     max_levels: int = 12
@@ -86,6 +86,8 @@ class Level:
     coarse_pinv: np.ndarray = None
     # Vanka smoother data (oracle.vanka.form_vanka), when that smoother is chosen
     vanka: dict = None
+    # ILU(1) smoother data (oracle.ilu.form_ilu), when that smoother is chosen
+    ilu: dict = None
     # setup diagnostics (for the tests)
     info: dict = dataclasses.field(default_factory=dict)
 
@@ -659,4 +661,8 @@ def setup_hierarchy(prob, prm: Params = None, reuse: Hierarchy = None) -> Hierar
         from .vanka import form_vanka
         for L in levels[:-1]:
             form_vanka(L)
+    if prm.smoother == "ilu":
+        from .ilu import form_ilu
+        for L in levels[:-1]:
+            form_ilu(L)
     return Hierarchy(levels=levels, params=prm, symmetric=bool(prob.symmetric))

@@ -101,6 +101,8 @@ def vcycle(H, b, level: int = 0):
         return coarse_solve(L, b)
     if prm.smoother == "vanka":
         from .vanka import vanka_sweep as sweep
+    elif prm.smoother == "ilu":
+        from .ilu import ilu_sweep as sweep
     else:
         sweep = bs_sweep
     x = np.zeros_like(b)

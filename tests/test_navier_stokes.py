@@ -4,8 +4,8 @@ systems (synth.navier_stokes) and the oracle's AMG on them against Table 5.
 Pins: the discrete-wind assembly equals the analytic-wind assembly for a wind
 the Q2 space holds exactly; the Picard sequence reaches the paper's 1e-8
 nonlinear residual; on the last Picard system the oracle's GMRES (to 1e-6, the
-paper's tolerance) with Vanka(1,1) and BS(2,2) stays within [0.45, 1.25] x the
-iteration counts of Table 5 and keeps its trends (more iterations at the smaller
+paper's tolerance) with Vanka(1,1), BS(2,2) and ILU(1)(1,1) stays within
+[0.45, 1.25] x the iteration counts of Table 5 and keeps its trends (more iterations at the smaller
 viscosity; Vanka no worse than Braess-Sarazin).  The oracle's counts sit below
 the paper's because its coarsest level is solved exactly (the paper relaxes it
 with Vanka)."""
@@ -19,6 +19,8 @@ from oracle import Params, fgmres, setup_hierarchy
 # Table 5 (Navier-Stokes lid cavity): (Vanka(1,1), BS(2,2)) iterations
 TABLE5 = {(8, 0.01): (20, 19), (16, 0.01): (26, 22), (32, 0.01): (22, 26),
           (16, 0.002): (49, 55), (32, 0.002): (53, 60)}
+# its ILU(1)(1,1) column (reverse Cuthill-McKee order)
+TABLE5_ILU = {(8, 0.01): 6, (16, 0.01): 7, (32, 0.01): 9, (16, 0.002): 9, (32, 0.002): 13}
 
 
 def test_discrete_wind_assembly_equals_analytic_for_a_q2_wind():
@@ -67,6 +69,15 @@ def test_table5_iterations_and_trends(picard_systems):
         assert v <= b, (key, v, b)
     for n in (16, 32):
         assert ours[(n, 0.002)][0] > ours[(n, 0.01)][0] and ours[(n, 0.002)][1] > ours[(n, 0.01)][1]
+
+
+def test_table5_ilu_iterations(picard_systems):
+    """ILU(1)(1,1) with reverse Cuthill-McKee order on the last Picard systems: within
+    [0.45, 1.25] x Table 5's ILU column, like the other smoothers."""
+    il = Params(smoother="ilu", pre=1, post=1)
+    for key, (last, _, _) in picard_systems.items():
+        i = _its(last, il)
+        assert 0.45 * TABLE5_ILU[key] <= i <= 1.25 * TABLE5_ILU[key], (key, i, TABLE5_ILU[key])
 
 
 def test_reused_coarsening_gives_the_fresh_hierarchy_on_the_same_matrix(picard_systems):

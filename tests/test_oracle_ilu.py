@@ -1,0 +1,137 @@
+"""Pins of the oracle's ILU(1) relaxation (Section 5): the factorization identity of
+incomplete LU, the level-of-fill rule, exactness when level-1 fill is complete,
+the reverse Cuthill-McKee order, dense solves on tiny meshes and Table 1's
+ILU(1)(1,1) iteration counts (the oracle needs 6, 7, 8, 10 where the paper
+reports 6, 7, 9, 10 at 8x8..64x64)."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from synth import oseen_recirculating_2d, stokes_lid_2d, stokes_pinned_2d, uniform_pm1
+from oracle import Params, fgmres, setup_hierarchy
+from oracle.ilu import ilu1, ilu_sweep, rcm_order
+
+ILU = dict(smoother="ilu", pre=1, post=1)
+
+
+def _lu_product(rows, n):
+    L = sp.lil_matrix((n, n))
+    U = sp.lil_matrix((n, n))
+    for i, r in enumerate(rows):
+        for j, v in r.items():
+            (L if j < i else U)[i, j] = v
+    return (sp.csr_matrix(L) + sp.identity(n)) @ sp.csr_matrix(U)
+
+
+@pytest.mark.parametrize("case", ["lid", "oseen"])
+def test_lu_equals_the_matrix_on_the_kept_pattern(case):
+    """Incomplete LU by elimination with dropping keeps (L U)_ij = A_ij on every kept entry."""
+    p = stokes_lid_2d(4, nrhs=1) if case == "lid" else oseen_recirculating_2d(4, Re=50.0, nrhs=1)
+    A = sp.csr_matrix(p.full_matrix())
+    rows, lev = ilu1(A)
+    n = A.shape[0]
+    LU = _lu_product(rows, n).toarray()
+    Ad = A.toarray()
+    for i, r in enumerate(rows):
+        for j in r:
+            assert abs(LU[i, j] - Ad[i, j]) <= 1e-12 * np.abs(Ad).max(), (i, j)
+
+
+def test_fill_levels_follow_the_ilu_k_rule():
+    """Level 0 = the pattern of A plus the diagonal (all kept), nothing deeper than level 1,
+    and every level-1 entry comes from a pivot row whose entries make its level."""
+    p = stokes_pinned_2d(4, nrhs=1)
+    A = sp.csr_matrix(p.full_matrix())
+    rows, lev = ilu1(A)
+    for i in range(A.shape[0]):
+        pat = set(int(j) for j in A.indices[A.indptr[i]:A.indptr[i + 1]]) | {i}
+        assert pat <= set(rows[i])
+        assert all(lev[i][j] == 0 for j in pat)
+        assert all(l <= 1 for l in lev[i].values())
+        for j, l in lev[i].items():
+            if l == 1:
+                assert any(m < min(i, j) and lev[i].get(m) == 0 and lev[m].get(j) == 0 for m in rows[i]), (i, j)
+
+
+def test_an_unreached_zero_pivot_takes_the_schur_diagonal():
+    """A pressure ordered before its two velocity neighbours: no elimination reaches its zero
+    diagonal, which becomes -(b1^2/a1 + b2^2/a2); the rest is the exact elimination of that
+    perturbed matrix, so L U = M + s e_0 e_0^T."""
+    a1, a2, b1, b2 = 3.0, 5.0, 0.7, -1.3
+    M = sp.csr_matrix(np.array([[0.0, b1, b2], [b1, a1, 0.0], [b2, 0.0, a2]]))
+    rows, _ = ilu1(M)
+    s = -(b1 * b1 / a1 + b2 * b2 / a2)
+    assert rows[0][0] == s
+    E = M.toarray()
+    E[0, 0] = s
+    assert np.abs(_lu_product(rows, 3).toarray() - E).max() <= 1e-15
+    # a pivot that elimination reaches keeps its own value, even in the zero block
+    Mv = sp.csr_matrix(np.array([[a1, 0.0, b1], [0.0, a2, b2], [b1, b2, 0.0]]))
+    rows, _ = ilu1(Mv)
+    assert abs(rows[2][2] - s) <= 1e-15 and np.abs(_lu_product(rows, 3).toarray() - Mv.toarray()).max() <= 1e-15
+
+
+def test_complete_fill_gives_the_exact_lu():
+    """A tridiagonal matrix has no fill: ILU(1) is its LU and one step solves exactly."""
+    n = 12
+    T = sp.diags([-1.0 * np.ones(n - 1), 4.0 * np.ones(n), -2.0 * np.ones(n - 1)], [-1, 0, 1], format="csr")
+    rows, _ = ilu1(T)
+    assert np.abs(_lu_product(rows, n).toarray() - T.toarray()).max() <= 1e-14
+
+
+def test_rcm_is_a_permutation_that_narrows_the_band():
+    p = oseen_recirculating_2d(6, Re=10.0, nrhs=1)
+    A = sp.csr_matrix(p.full_matrix())
+    perm = rcm_order(A)
+    assert np.array_equal(np.sort(perm), np.arange(A.shape[0]))
+    def bandwidth(M):
+        C = sp.coo_matrix(M)
+        return int(np.abs(C.row - C.col).max())
+    assert bandwidth(A[perm][:, perm]) < bandwidth(A)
+    assert np.array_equal(rcm_order(A), perm)
+
+
+@pytest.mark.parametrize("case", ["pinned", "lid", "oseen"])
+@pytest.mark.parametrize("n", [2, 4])
+def test_ilu_fgmres_equals_dense_solve(case, n):
+    p = {"pinned": lambda: stokes_pinned_2d(n, nrhs=2), "lid": lambda: stokes_lid_2d(n, nrhs=2),
+         "oseen": lambda: oseen_recirculating_2d(n, Re=10.0, nrhs=2)}[case]()
+    H = setup_hierarchy(p, Params(**ILU))
+    x, its, rel, _ = fgmres(H, p.b, rtol=1e-12, maxit=400)
+    A = p.full_matrix().toarray()
+    xd = np.linalg.lstsq(A, p.b, rcond=None)[0]
+    nu = p.dim * p.n_v
+    if p.pinned < 0:
+        x = x.copy()
+        x[nu:] -= x[nu:].mean(axis=0)
+        xd[nu:] -= xd[nu:].mean(axis=0)
+    assert np.all(np.linalg.norm(x - xd, axis=0) <= 1e-9 * np.linalg.norm(xd, axis=0))
+
+
+@pytest.mark.parametrize("case", ["pinned", "lid"])
+def test_an_ilu_step_contracts_the_error(case):
+    """The error propagation I - (L U)^-1 A of one ILU step on the finest level: every
+    eigenvalue inside the unit disc for the pinned (nonsingular) matrix, exactly one equal
+    to one for the singular lid matrix (its constant-pressure null mode); apart from that
+    near-null pressure mode the step contracts strongly, most modes almost to zero."""
+    p = stokes_pinned_2d(8, nrhs=1) if case == "pinned" else stokes_lid_2d(8, nrhs=1)
+    H = setup_hierarchy(p, Params(**ILU))
+    L = H.levels[0]
+    n = L.N
+    E = np.column_stack([ilu_sweep(L, H.params, np.zeros(n), e) for e in np.eye(n)])
+    ev = np.sort(np.abs(np.linalg.eigvals(E)))
+    if case == "pinned":
+        assert ev[-1] < 1.0
+    else:
+        assert abs(ev[-1] - 1.0) <= 1e-10
+    assert ev[-2] < 0.7
+    assert np.median(ev) < 0.01
+
+
+@pytest.mark.parametrize("n,paper_its", [(8, 6), (16, 7), (32, 9)])
+def test_table1_ilu_iterations(n, paper_its):
+    """Table 1, ILU(1)(1,1), lid-driven cavity on [-1,1]^2: within one iteration of the paper."""
+    p = stokes_lid_2d(n, nrhs=1, body="none", lo=-1.0, hi=1.0)
+    H = setup_hierarchy(p, Params(**ILU))
+    x, its, rel, _ = fgmres(H, p.b, rtol=1e-6)
+    assert abs(its[0] - paper_its) <= 1, (its, paper_its)

@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving stream")
     ap.add_argument("--no-vanka", action="store_true", help="skip the Vanka-smoother side line")
+    ap.add_argument("--no-ilu", action="store_true", help="skip the ILU(1)-smoother side line")
     ap.add_argument("--no-picard", action="store_true", help="skip the Picard (steady Navier-Stokes) side line")
     ap.add_argument("--configs", action="store_true",
                     help="instead of the default run: time the other workloads (16x16 pinned Stokes, 512x512 "
@@ -177,6 +178,19 @@ def vanka_bytes(H, level, K, s):
     row_nnz = np.where(q < nu, rA[np.minimum(q, nu - 1) % nv] + rBt[np.minimum(q, nu - 1)],
                        rB[np.maximum(q - nu, 0)])
     return int((m * m).sum() * s + (row_nnz * (4 + s + K * s)).sum() + 2 * K * s * len(q))
+
+
+def ilu_bytes(H, level, K, s, from_zero):
+    """Compulsory bytes of one ILU(1) step's two substitutions on `level`: the factors
+    (values and columns, row pointers, the ticket order, the permutation, the pivots'
+    reciprocals), for every factor entry the K values of the row it refers to, and r
+    read, y written and read, d written, x written (and read unless from zero), K
+    values per row each."""
+    F = H.level_ilu(level)
+    n = len(F["perm"])
+    nnz = len(F["lower"][1]) + len(F["upper"][1])
+    return int(nnz * (s + 4) + nnz * K * s + 2 * (n + 1) * 4 + 2 * n * 4 + 2 * n * 4 + n * s
+               + (5 if from_zero else 6) * n * K * s)
 
 
 def load_traffic(kernel, level, K, s):
@@ -686,6 +700,46 @@ def main():
                  "level0_step_frac": l0_bytes / (l0_ms / 1000.0) / 1e9 / measured_peaks()[0]}
         del V32, V64
 
+    # the ILU(1) smoother (Section 5) on the same workload, FP64 V-cycle, FGMRES to the
+    # paper's 1e-6 (Table 1 reports 17 iterations at this size)
+    ilu = None
+    if not args.no_ilu and world == 1:
+        I64 = g.Hierarchy(p, max_nrhs=NRHS, smoother=2, pre=1, post=1)
+        isteps = 3
+
+        def itimed(H, steps, warm):
+            for _ in range(warm):
+                st, its, rel = H.fgmres(b, x, rtol=1e-6, restart=RESTART, maxit=MAXIT)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                st, its, rel = H.fgmres(b, x, rtol=1e-6, restart=RESTART, maxit=MAXIT)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1), st, its, rel
+
+        msi, sti, itsi, reli = itimed(I64, isteps, 3)
+        I64.vcycle(b, x)
+        ims, icnt = I64.profile_vcycle(NRHS, reps=3)
+        ii = g.KERNEL_CLASSES.index("ilu")
+        F0 = I64.level_ilu(0)
+        sub_us = float(ims[0, ii] / icnt[0, ii] * 1000.0)
+        step_bytes = (ilu_bytes(I64, 0, NRHS, 8, True) + ilu_bytes(I64, 0, NRHS, 8, False)) / 2
+        ilu = {"workload": "same 256x256 lid cavity, 8 rhs, ILU(1)(1,1), natural order, FP64 V-cycle, "
+                           "FGMRES to 1e-6 (the paper's tolerance)",
+               "value": NRHS * isteps / (msi / 1000.0), "unit": "solves/s", "status": int(sti),
+               "iterations": itsi.tolist(), "relres_max": float(np.max(reli)), "paper_iterations": 17,
+               "vcycle_us_by_kernel": {f"L{l}/{c}": round(float(ims[l, k] / 3 * 1000.0), 2)
+                                       for l in range(ims.shape[0]) for k, c in enumerate(g.KERNEL_CLASSES)
+                                       if icnt[l, k]},
+               "level0": {"rows": len(F0["perm"]), "factor_nnz": len(F0["lower"][1]) + len(F0["upper"][1]),
+                          "depth": F0["depth_lower"], "substitution_us": sub_us,
+                          "us_per_dependency_level": sub_us / F0["depth_lower"],
+                          "step_GBs": step_bytes / (2 * sub_us * 1e-6) / 1e9,
+                          "bound": "latency: depth x one L2 round trip per dependency level"}}
+        del I64
+
     picard = None
     if not args.no_picard and world == 1:
         picard = picard_line(g, torch)
@@ -715,7 +769,7 @@ def main():
                 "latency_ms": (None if serving is None else
                                {"p50": serving["latency_ms"]["p50"], "p99": serving["latency_ms"]["p99"],
                                 "source": "serving stream (arrival to result on the host)"}),
-                "serving": serving, "accuracy": accuracy, "vanka": vanka, "picard": picard,
+                "serving": serving, "accuracy": accuracy, "vanka": vanka, "ilu": ilu, "picard": picard,
                 "e2e": e2e, "gpu_launches": launches32, "clocks": clocks, "roofline": roofline,
                 "vcycle_us_by_kernel": breakdown, "gs_variants": gs_variants,
                 "row_shapes": {f"L{l}": "".join(str(v) for v in d.values()) for l, d in H32.row_shapes(NRHS).items()},

@@ -91,13 +91,19 @@ typedef struct {
   int autotune;       /* 1 (default): before a cycle for K right-hand sides is first captured,
                          time each Gauss-Seidel variant that applies to each level (one block,
                          a thread-block cluster of 2-16 blocks, the pipelined kernel, one launch
-                         per phase, the dense map on levels of <= 1024 pressures) and keep the
+                         per phase, the dense map on levels of <= 2896 pressures) and keep the
                          fastest; 0: fixed choice by level size, sweeps only */
   int smoother;       /* 0 (default): Braess-Sarazin (Section 5.2); 1: Vanka (Section 5.1):
                          overlapping blocks, one per pressure dof (the columns of its row of
                          B plus the pressure), relaxed in the order (color, index) of a
                          greedy coloring of the blocks' interaction graph, Dirichlet dofs
-                         exactly; pre and post count Vanka steps (the paper's Vanka(1,1)) */
+                         exactly; pre and post count Vanka steps (the paper's Vanka(1,1));
+                         2: ILU(1) (Section 5): incomplete LU of each level's whole block
+                         matrix with one level of fill, its diagonal (the zero block's too)
+                         kept in the pattern; natural order for symmetric problems, reverse
+                         Cuthill-McKee otherwise (Section 6.1); a zero-block pivot that no
+                         elimination step reaches becomes -sum_j M_ij M_ji / M_jj over its
+                         row; pre and post count ILU steps (the paper's ILU(1)(1,1)) */
   double vanka_omega; /* Vanka under-relaxation, 0.5 (Section 6) */
 } amg_params;
 
@@ -174,8 +180,9 @@ amg_status amg_fgmres_solve_host(amg_handle h, const double* b_host, double* x_h
  * Classes: 0 velocity predictor, 1 Schur right-hand side, 2 Gauss-Seidel color
  * sweep, 3 velocity/pressure update, 4 block residual, 5 restriction,
  * 6 prolongation, 7 coarsest solve, 8 Vanka step (its color launches and the exact
- * Dirichlet relaxation).  Synchronises `stream`. */
-#define AMG_NUM_KERNEL_CLASSES 9
+ * Dirichlet relaxation), 9 ILU(1) substitution (forward and backward, one launch
+ * each; the step's residual counts as class 4).  Synchronises `stream`. */
+#define AMG_NUM_KERNEL_CLASSES 10
 amg_status amg_profile_vcycle(amg_handle h, int nrhs, int reps, double* ms, long long* count, void* stream);
 
 /* Number of CUDA kernels this handle has launched so far (a replayed V-cycle graph
@@ -216,10 +223,22 @@ amg_status amg_level_get_points(amg_handle h, int level, int* cp, int* cv, int* 
 amg_status amg_level_get_vanka(amg_handle h, int level, int* nblocks, int* ndofs, int* ncolors, int* ptr,
                                int* dofs, int* colors);
 
+/* The ILU(1) factors of a level (hierarchies built with smoother = 2, every level
+ * but the coarsest), in positions of the smoother's order: perm[position] = dof
+ * (dofs ordered [u_x | u_y (| u_z) | p]); the strict lower factor (unit diagonal
+ * implied) and the strict upper factor as CSR with ascending columns (ptr has
+ * n + 1 entries); pivots the diagonal of U.  depth_lower / depth_upper: the number
+ * of dependency levels of the forward / backward substitution (its critical path
+ * in rows).  Sizes only when the arrays are NULL; each array may be NULL.
+ * AMG_ERR_ARG for a level without factors. */
+amg_status amg_level_get_ilu(amg_handle h, int level, int* n, long long* nnz_lower, long long* nnz_upper,
+                             int* depth_lower, int* depth_upper, int* perm, int* lower_ptr, int* lower_col,
+                             double* lower_val, int* upper_ptr, int* upper_col, double* upper_val, double* pivots);
+
 /* The Gauss-Seidel variant the V-cycle (FP32 one if built, else FP64) uses on a
  * level for nrhs right-hand sides: -1 not chosen yet (the cycle for that K has
  * not run), 0 one block, 1 a cluster of *cluster blocks, 2 the pipelined strip
- * kernel, 3 one launch per phase, 4 the dense map (levels of at most 1024
+ * kernel, 3 one launch per phase, 4 the dense map (levels of at most 2896
  * pressures: the iterations' linear map formed at setup by the same sweeps and
  * applied as one dense product); *ms is the time the autotuner measured for one
  * launch (0 without autotuning).  Either output may be NULL. */

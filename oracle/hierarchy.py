@@ -664,5 +664,5 @@ def setup_hierarchy(prob, prm: Params = None, reuse: Hierarchy = None) -> Hierar
     if prm.smoother == "ilu":
         from .ilu import form_ilu
         for L in levels[:-1]:
-            form_ilu(L)
+            form_ilu(L, bool(prob.symmetric))
     return Hierarchy(levels=levels, params=prm, symmetric=bool(prob.symmetric))

@@ -122,10 +122,10 @@ def _schur_pivot(M, i):
     return s
 
 
-def form_ilu(L):
-    """The level's block matrix in the smoother's order, its ILU(1) factors and the order."""
+def form_ilu(L, symmetric: bool):
+    """The level's block matrix in the smoother's order (natural for a symmetric
+    problem, Stokes; reverse Cuthill-McKee otherwise), its ILU(1) factors and the order."""
     M = sp.csr_matrix(L.full_matrix())
-    symmetric = abs(M - M.T).max() <= 1e-12 * abs(M).max()
     perm = np.arange(M.shape[0]) if symmetric else rcm_order(M)
     Mp = M[perm][:, perm]
     rows, _ = ilu1(Mp)

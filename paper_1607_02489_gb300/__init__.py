@@ -23,10 +23,11 @@ STATUS_NAMES = {0: "OK", 1: "NOT_CONVERGED", 2: "BREAKDOWN", -1: "ERR_ARG", -2: 
                 -4: "ERR_SETUP"}
 EXPORTED = ["amg_params_default", "amg_hierarchy_create", "amg_hierarchy_create_reuse", "amg_vcycle_apply", "amg_apply", "amg_fgmres_solve",
             "amg_fgmres_solve_host", "amg_num_levels", "amg_level_get_info", "amg_level_get_matrix",
-            "amg_level_get_points", "amg_hierarchy_destroy", "amg_last_error", "amg_profile_vcycle", "amg_kernel_launches", "amg_apply_noalloc", "amg_gs_variant", "amg_row_shape", "amg_level_get_vanka",
+            "amg_level_get_points", "amg_hierarchy_destroy", "amg_last_error", "amg_profile_vcycle", "amg_kernel_launches", "amg_apply_noalloc", "amg_gs_variant", "amg_row_shape", "amg_level_get_vanka", "amg_level_get_ilu",
             "amg_server_params_default", "amg_server_create", "amg_server_reserve", "amg_server_submit", "amg_server_progress",
             "amg_server_result", "amg_server_state", "amg_server_get_stats", "amg_server_destroy", "amg_server_last_error"]
-KERNEL_CLASSES = ["velocity", "schur_rhs", "gs_color", "update", "residual", "restrict", "prolong", "coarse", "vanka"]
+KERNEL_CLASSES = ["velocity", "schur_rhs", "gs_color", "update", "residual", "restrict", "prolong", "coarse", "vanka",
+                  "ilu"]
 MATRICES = {"A": 0, "B": 1, "Bt": 2, "S": 3, "P": 4, "Pp": 5, "R": 6, "Rp": 7}
 
 _i32p = ctypes.POINTER(ctypes.c_int)
@@ -123,6 +124,9 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.amg_level_get_points.restype = ctypes.c_int
     lib.amg_level_get_vanka.argtypes = [vp, ctypes.c_int, _i32p, _i32p, _i32p, _i32p, _i32p, _i32p]
     lib.amg_level_get_vanka.restype = ctypes.c_int
+    lib.amg_level_get_ilu.argtypes = [vp, ctypes.c_int, _i32p, _i64p, _i64p, _i32p, _i32p, _i32p, _i32p, _i32p, _f64p,
+                                      _i32p, _i32p, _f64p, _f64p]
+    lib.amg_level_get_ilu.restype = ctypes.c_int
     lib.amg_hierarchy_destroy.argtypes = [vp]
     lib.amg_hierarchy_destroy.restype = None
     lib.amg_last_error.argtypes = []
@@ -315,7 +319,7 @@ class Hierarchy:
         out = {}
         for l in range(self.num_levels() - 1):
             out[l] = {c: load().amg_row_shape(self._h, l, int(nrhs), k) for k, c in enumerate(KERNEL_CLASSES)
-                      if c not in ("gs_color", "coarse")}
+                      if c not in ("gs_color", "coarse", "vanka", "ilu")}
         return out
 
     def kernel_launches(self) -> int:
@@ -362,6 +366,27 @@ class Hierarchy:
         _check(load().amg_level_get_vanka(self._h, level, None, None, None, _ptr(ptr, ctypes.c_int),
                                           _ptr(dofs, ctypes.c_int), _ptr(colors, ctypes.c_int)))
         return dict(ptr=ptr, dofs=dofs[:nd.value], colors=colors[:nb.value], ncolors=nc.value)
+
+    def level_ilu(self, level: int) -> dict:
+        """ILU(1) factors of a level (amg_level_get_ilu): perm (position -> dof), the strict
+        lower and upper factors as (ptr, col, val), the pivots and both substitutions' depths."""
+        n, nl, nu = ctypes.c_int(), ctypes.c_longlong(), ctypes.c_longlong()
+        dl, du = ctypes.c_int(), ctypes.c_int()
+        _check(load().amg_level_get_ilu(self._h, level, ctypes.byref(n), ctypes.byref(nl), ctypes.byref(nu),
+                                        ctypes.byref(dl), ctypes.byref(du), None, None, None, None, None, None,
+                                        None, None))
+        N = n.value
+        perm = np.zeros(N, dtype=np.int32)
+        lp, up = np.zeros(N + 1, dtype=np.int32), np.zeros(N + 1, dtype=np.int32)
+        lc, uc = np.zeros(max(nl.value, 1), dtype=np.int32), np.zeros(max(nu.value, 1), dtype=np.int32)
+        lv, uv = np.zeros(max(nl.value, 1)), np.zeros(max(nu.value, 1))
+        piv = np.zeros(N)
+        _check(load().amg_level_get_ilu(self._h, level, None, None, None, None, None, _ptr(perm, ctypes.c_int),
+                                        _ptr(lp, ctypes.c_int), _ptr(lc, ctypes.c_int), _ptr(lv, ctypes.c_double),
+                                        _ptr(up, ctypes.c_int), _ptr(uc, ctypes.c_int), _ptr(uv, ctypes.c_double),
+                                        _ptr(piv, ctypes.c_double)))
+        return dict(perm=perm, lower=(lp, lc[:nl.value], lv[:nl.value]), upper=(up, uc[:nu.value], uv[:nu.value]),
+                    pivots=piv, depth_lower=dl.value, depth_upper=du.value)
 
     def level_points(self, level: int) -> dict:
         info = self.level_info(level)

@@ -810,6 +810,154 @@ __global__ void __launch_bounds__(kBlock) k_vanka_exact(int n, const int* __rest
   x[q] = f[q];
 }
 
+// ILU(1) relaxation (Section 5): x <- x + (L U)^-1 r, the factors' rows and columns
+// in the smoother's order (position i holds dof perm[i]).  Each substitution is one
+// launch with no grid-wide barrier.  Warps take rows from a ticket counter in
+// (dependency level, position) order, so a row only ever waits for rows already
+// taken by running warps: no co-residency is needed and any grid size works.  The
+// substitution's output is filled with a sentinel (every bit set, a NaN) before the
+// launch and the written values are their own signal: a lane polls each value it
+// needs until it differs from the sentinel, so a row costs no fence and no flag.
+// Values computed from finite data are never NaN; a NaN result that matched the
+// sentinel would end in a timed-out wait, reported through *err.  Every wait is
+// bounded (kSpinLimit polls) and gives up at once when *err is set; a lane that
+// gives up takes 0 and goes on, so the launch always ends.  The warp that takes
+// the last ticket puts the counter back to zero for the next launch.
+constexpr int kIluBlock = 256;
+constexpr int kIluChunk = 8;  // entries a lane has in flight at once
+
+template <typename T>
+struct IluView {
+  int n;
+  const int* perm;    // position -> dof
+  DCsr<T> L, U;       // strict lower / upper factor rows, columns in positions
+  const T* dinv;      // 1 / pivot
+  const int* schedL;  // ticket -> row of the forward substitution
+  const int* schedU;  // ticket -> row of the backward substitution
+};
+
+__device__ __forceinline__ float ld_relaxed(const float* p) {
+  float v;
+  asm volatile("ld.relaxed.gpu.global.f32 %0, [%1];\n" : "=f"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ double ld_relaxed(const double* p) {
+  double v;
+  asm volatile("ld.relaxed.gpu.global.f64 %0, [%1];\n" : "=d"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed(float* p, float v) {
+  asm volatile("st.relaxed.gpu.global.f32 [%0], %1;\n" ::"l"(p), "f"(v) : "memory");
+}
+__device__ __forceinline__ void st_relaxed(double* p, double v) {
+  asm volatile("st.relaxed.gpu.global.f64 [%0], %1;\n" ::"l"(p), "d"(v) : "memory");
+}
+__device__ __forceinline__ bool is_sentinel(float v) { return __float_as_uint(v) == 0xffffffffu; }
+__device__ __forceinline__ bool is_sentinel(double v) { return __double_as_longlong(v) == -1ll; }
+
+template <typename T>
+__device__ __noinline__ T wait_value(const T* p, int* err) {
+  T v = ld_relaxed(p);
+  for (unsigned long long spins = 1; is_sentinel(v); ++spins) {
+    if (spins > kSpinLimit || ((spins & 31) == 0 && *(volatile int*)err)) {
+      atomicExch(err, 1);
+      return T(0);
+    }
+    if (spins > 128) __nanosleep(64);
+    v = ld_relaxed(p);
+  }
+  return v;
+}
+
+// sum over the row's entries of T.v[e] * z[T.ci[e]] for right-hand side k, the
+// entries split over the G = 32 / K lane groups, z polled (written by this launch)
+template <typename T, int K>
+__device__ __forceinline__ T ilu_row_dot(const DCsr<T>& F, int i, const T* z, int k, int g, int* err) {
+  constexpr int G = 32 / K;
+  T acc = T(0);
+  const int e1 = F.rp[i + 1];
+  for (int e0 = F.rp[i] + g; e0 < e1; e0 += G * kIluChunk) {
+    int j[kIluChunk];
+    T a[kIluChunk], v[kIluChunk];
+#pragma unroll
+    for (int c = 0; c < kIluChunk; ++c) {
+      const int e = e0 + c * G;
+      j[c] = e < e1 ? F.ci[e] : -1;
+      a[c] = e < e1 ? F.v[e] : T(0);
+    }
+#pragma unroll
+    for (int c = 0; c < kIluChunk; ++c) v[c] = j[c] >= 0 ? ld_relaxed(z + (size_t)j[c] * K + k) : T(0);
+#pragma unroll
+    for (int c = 0; c < kIluChunk; ++c) {
+      if (j[c] >= 0 && is_sentinel(v[c])) v[c] = wait_value(z + (size_t)j[c] * K + k, err);
+      acc += a[c] * v[c];
+    }
+  }
+#pragma unroll
+  for (int o = K; o < 32; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  return acc;
+}
+
+__device__ __forceinline__ int ilu_ticket(int* ticket) {
+  int t = 0;
+  if ((threadIdx.x & 31) == 0) t = atomicAdd(ticket, 1);
+  return __shfl_sync(0xffffffffu, t, 0);
+}
+__device__ __forceinline__ void ilu_release(int* ticket, int t, int n) {
+  if ((threadIdx.x & 31) == 0 && t == n + (int)(gridDim.x * (blockDim.x / 32)) - 1) atomicExch(ticket, 0);
+}
+
+// forward substitution: y_i = r_{perm i} - sum_{j < i} L_ij y_j (y all sentinel at launch)
+template <typename T, int K>
+__global__ void __launch_bounds__(kIluBlock) k_ilu_lower(IluView<T> F, const T* __restrict__ r, T* y, int* ticket,
+                                                         int* err) {
+  static_assert(K >= 1 && K <= 32 && (32 % K) == 0, "K must divide a warp");
+  const int lane = threadIdx.x & 31, k = lane % K, g = lane / K;
+  for (;;) {
+    const int t = ilu_ticket(ticket);
+    if (t >= F.n) {
+      ilu_release(ticket, t, F.n);
+      return;
+    }
+    const int i = F.schedL[t];
+    // the row's own operand first: its load overlaps the waits instead of following them
+    const T ri = g == 0 ? r[(size_t)F.perm[i] * K + k] : T(0);
+    const T acc = ilu_row_dot<T, K>(F.L, i, y, k, g, err);
+    if (g == 0) st_relaxed(y + (size_t)i * K + k, ri - acc);
+  }
+}
+
+// backward substitution: d_i = (y_i - sum_{j > i} U_ij d_j) / U_ii (d all sentinel at
+// launch), then x_{perm i} += d_i (x_{perm i} = d_i when zero is set)
+template <typename T, int K>
+__global__ void __launch_bounds__(kIluBlock) k_ilu_upper(IluView<T> F, const T* __restrict__ y, T* d, T* x, int zero,
+                                                         int* ticket, int* err) {
+  const int lane = threadIdx.x & 31, k = lane % K, g = lane / K;
+  for (;;) {
+    const int t = ilu_ticket(ticket);
+    if (t >= F.n) {
+      ilu_release(ticket, t, F.n);
+      return;
+    }
+    const int i = F.schedU[t];
+    // the row's own operands first (overlapping the waits)
+    T yi = T(0), dv = T(0), xq = T(0);
+    size_t q = 0;
+    if (g == 0) {
+      yi = y[(size_t)i * K + k];
+      dv = F.dinv[i];
+      q = (size_t)F.perm[i] * K + k;
+      if (!zero) xq = x[q];
+    }
+    const T acc = ilu_row_dot<T, K>(F.U, i, d, k, g, err);
+    if (g == 0) {
+      const T di = (yi - acc) * dv;
+      st_relaxed(d + (size_t)i * K + k, di);
+      x[q] = xq + di;
+    }
+  }
+}
+
 // Single-block Gauss-Seidel for a small level, same ordering: the whole level's
 // S, g, 1/S_ii and dp sit in shared memory and the (parity, color) groups run one
 // after another separated by __syncthreads, with no inter-block waits.

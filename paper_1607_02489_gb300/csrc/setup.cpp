@@ -885,6 +885,210 @@ void form_vanka(HostLevel& L, const SetupParams& prm) {
   if (!failure.empty()) throw std::runtime_error(failure);
 }
 
+// ILU(1) relaxation (Section 5): x <- x + (L U)^-1 (b - A x) with incomplete factors
+// of the whole block matrix M, whose diagonal (the zero block's too) is kept in the
+// pattern so that fill can reach it.  Level of fill one: position (i, j) of the
+// factors exists when M has it or i == j (level 0), or when some m < min(i, j) has
+// (i, m) and (m, j) at level 0 (level 1: a path through a level-1 entry has level 2
+// and is dropped); the elimination then runs in IKJ order over that pattern.  A
+// pivot that no elimination step reaches and whose entry of M is zero (a row of the
+// zero block ordered before all its neighbours) becomes -sum_j M_ij M_ji / M_jj over
+// its row: the Schur-complement diagonal of its neighbours with their block taken
+// as diagonal.
+
+// Reverse Cuthill-McKee on the graph of M + M^T without self loops: start at the
+// unvisited vertex of smallest degree (lowest index on ties), visit each vertex's
+// unvisited neighbours by increasing (degree, index), start again for every new
+// component, reverse the visiting order.  Result: position -> index.
+std::vector<int> rcm_order(const Csr& M) {
+  const int n = M.nrows;
+  std::vector<std::vector<int>> nb(n);
+  for (int i = 0; i < n; ++i)
+    for (int64_t t = M.row_begin(i); t < M.row_end(i); ++t) {
+      const int j = M.col[t];
+      if (j == i || M.val[t] == 0.0) continue;
+      nb[i].push_back(j);
+      nb[j].push_back(i);
+    }
+  std::vector<int> deg(n);
+  for (int i = 0; i < n; ++i) {
+    std::sort(nb[i].begin(), nb[i].end());
+    nb[i].erase(std::unique(nb[i].begin(), nb[i].end()), nb[i].end());
+    deg[i] = (int)nb[i].size();
+  }
+  auto before = [&](int a, int b) { return deg[a] != deg[b] ? deg[a] < deg[b] : a < b; };
+  std::vector<int> by_degree(n);
+  for (int i = 0; i < n; ++i) by_degree[i] = i;
+  std::sort(by_degree.begin(), by_degree.end(), before);
+  std::vector<char> seen(n, 0);
+  std::vector<int> order;
+  order.reserve(n);
+  std::vector<int> next;
+  for (int start : by_degree) {
+    if (seen[start]) continue;
+    seen[start] = 1;
+    size_t head = order.size();
+    order.push_back(start);
+    while (head < order.size()) {
+      const int v = order[head++];
+      next.clear();
+      for (int u : nb[v])
+        if (!seen[u]) next.push_back(u);
+      std::sort(next.begin(), next.end(), before);
+      for (int u : next) {
+        seen[u] = 1;
+        order.push_back(u);
+      }
+    }
+  }
+  std::reverse(order.begin(), order.end());
+  return order;
+}
+
+// Rows of a triangular factor by (dependency level, position): a row's level is one
+// more than the largest level among the rows its entries refer to.
+void schedule(const Csr& T, bool lower, std::vector<int>& sched, int& depth) {
+  const int n = T.nrows;
+  std::vector<int> lev(n, 0);
+  depth = 0;
+  for (int s = 0; s < n; ++s) {
+    const int i = lower ? s : n - 1 - s;
+    int l = 0;
+    for (int64_t t = T.row_begin(i); t < T.row_end(i); ++t) l = std::max(l, lev[T.col[t]] + 1);
+    lev[i] = l;
+    depth = std::max(depth, l + 1);
+  }
+  std::vector<int> cnt(depth + 1, 0);
+  for (int i = 0; i < n; ++i) cnt[lev[i] + 1]++;
+  for (int l = 0; l < depth; ++l) cnt[l + 1] += cnt[l];
+  sched.assign(n, 0);
+  for (int i = 0; i < n; ++i) sched[cnt[lev[i]]++] = i;
+}
+
+void form_ilu(HostLevel& L, bool symmetric) {
+  const int n = L.N();
+  Csr M;  // natural order
+  M.resize_rows(n, n);
+  for (int q = 0; q < n; ++q) {
+    const size_t b = M.col.size();
+    block_matrix_row(L, q, [&](int v, double val) {
+      M.col.push_back(v);
+      M.val.push_back(val);
+    });
+    std::vector<std::pair<int, double>> row;
+    for (size_t t = b; t < M.col.size(); ++t) row.emplace_back(M.col[t], M.val[t]);
+    std::sort(row.begin(), row.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
+    for (size_t t = 0; t < row.size(); ++t) {
+      M.col[b + t] = row[t].first;
+      M.val[b + t] = row[t].second;
+    }
+    M.rowptr[q + 1] = (int64_t)M.col.size();
+  }
+  std::vector<int> perm(n);
+  if (symmetric)
+    for (int i = 0; i < n; ++i) perm[i] = i;
+  else
+    perm = rcm_order(M);
+  std::vector<int> pos(n);
+  for (int i = 0; i < n; ++i) pos[perm[i]] = i;
+  // the permuted matrix (rows and columns in positions), rows ascending
+  Csr Mp;
+  Mp.resize_rows(n, n);
+  {
+    std::vector<std::pair<int, double>> row;
+    for (int i = 0; i < n; ++i) {
+      row.clear();
+      const int q = perm[i];
+      for (int64_t t = M.row_begin(q); t < M.row_end(q); ++t) row.emplace_back(pos[M.col[t]], M.val[t]);
+      std::sort(row.begin(), row.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
+      for (const auto& e : row) {
+        Mp.col.push_back(e.first);
+        Mp.val.push_back(e.second);
+      }
+      Mp.rowptr[i + 1] = (int64_t)Mp.col.size();
+    }
+  }
+  // symbolic: level-0 pattern (M's plus the diagonal) and the level-1 fill
+  std::vector<int64_t> fptr(n + 1, 0);
+  std::vector<int> fcol;
+  {
+    std::vector<int> mark(n, -1), row;
+    for (int i = 0; i < n; ++i) {
+      row.clear();
+      auto add = [&](int j) {
+        if (mark[j] != i) {
+          mark[j] = i;
+          row.push_back(j);
+        }
+      };
+      add(i);
+      for (int64_t t = Mp.row_begin(i); t < Mp.row_end(i); ++t) add(Mp.col[t]);
+      for (int64_t t = Mp.row_begin(i); t < Mp.row_end(i); ++t) {
+        const int m = Mp.col[t];
+        if (m >= i) continue;
+        for (int64_t u = Mp.row_begin(m); u < Mp.row_end(m); ++u)
+          if (Mp.col[u] > m) add(Mp.col[u]);
+      }
+      std::sort(row.begin(), row.end());
+      fcol.insert(fcol.end(), row.begin(), row.end());
+      fptr[i + 1] = (int64_t)fcol.size();
+    }
+  }
+  // numeric: IKJ over the fixed pattern
+  Csr& Lf = L.il_L;
+  Csr& Uf = L.il_U;
+  Lf.resize_rows(n, n);
+  Uf.resize_rows(n, n);
+  L.il_diag.assign(n, 0.0);
+  std::vector<double> w(n, 0.0);
+  std::vector<int> in(n, -1);
+  for (int i = 0; i < n; ++i) {
+    for (int64_t t = fptr[i]; t < fptr[i + 1]; ++t) {
+      in[fcol[t]] = i;
+      w[fcol[t]] = 0.0;
+    }
+    for (int64_t t = Mp.row_begin(i); t < Mp.row_end(i); ++t) w[Mp.col[t]] += Mp.val[t];
+    bool reached = false;
+    for (int64_t t = fptr[i]; t < fptr[i + 1] && fcol[t] < i; ++t) {
+      const int m = fcol[t];
+      const double f = w[m] / L.il_diag[m];
+      w[m] = f;
+      for (int64_t u = Uf.row_begin(m); u < Uf.row_end(m); ++u) {
+        const int j = Uf.col[u];
+        if (in[j] == i) w[j] -= f * Uf.val[u];
+      }
+      // the step reaches the pivot when (m, i) is in row m's upper part
+      if (std::binary_search(Uf.col.begin() + Uf.row_begin(m), Uf.col.begin() + Uf.row_end(m), i)) reached = true;
+    }
+    if (!reached && w[i] == 0.0) {
+      double sdiag = 0.0;
+      for (int64_t t = Mp.row_begin(i); t < Mp.row_end(i); ++t) {
+        const int j = Mp.col[t];
+        if (j == i) continue;
+        const double mjj = lookup(Mp, j, j);
+        if (mjj != 0.0) sdiag -= Mp.val[t] * lookup(Mp, j, i) / mjj;
+      }
+      w[i] = sdiag;
+    }
+    for (int64_t t = fptr[i]; t < fptr[i + 1]; ++t) {
+      const int j = fcol[t];
+      if (j < i) {
+        Lf.col.push_back(j);
+        Lf.val.push_back(w[j]);
+      } else if (j > i) {
+        Uf.col.push_back(j);
+        Uf.val.push_back(w[j]);
+      }
+    }
+    L.il_diag[i] = w[i];
+    Lf.rowptr[i + 1] = Lf.nnz();
+    Uf.rowptr[i + 1] = Uf.nnz();
+  }
+  L.il_perm = std::move(perm);
+  schedule(Lf, true, L.il_schedL, L.il_depthL);
+  schedule(Uf, false, L.il_schedU, L.il_depthU);
+}
+
 }  // namespace
 
 std::vector<HostLevel> build_hierarchy(HostLevel fine, const SetupParams& prm) {
@@ -917,6 +1121,8 @@ std::vector<HostLevel> build_hierarchy(HostLevel fine, const SetupParams& prm) {
   C.pinv = pseudo_inverse(dense_level(C), C.N(), 1e-12);
   if (prm.vanka)
     for (size_t l = 0; l + 1 < levels.size(); ++l) form_vanka(levels[l], prm);
+  if (prm.ilu)
+    for (size_t l = 0; l + 1 < levels.size(); ++l) form_ilu(levels[l], prm.symmetric);
   for (size_t l = 0; l + 1 < levels.size(); ++l)
     if (levels[l].n_p <= kGsDenseMaxRows) form_dense_gs(levels[l], prm.gs_iters);
   return levels;

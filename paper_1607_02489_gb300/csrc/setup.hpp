@@ -17,6 +17,7 @@ struct SetupParams {
   int max_levels = 12;
   bool symmetric = true;   // one EMIN CG step, R = P^T; otherwise EMIN GMRES for P and R
   bool vanka = false;      // form the Vanka smoother's blocks (Section 5.1) on every level but the coarsest
+  bool ilu = false;        // form the ILU(1) factors (Section 5) on every level but the coarsest
   int gs_iters = 5;        // Gauss-Seidel iterations per Braess-Sarazin step (for the dense map)
   size_t vanka_max_bytes = (size_t)16 << 30;  // limit on the FP64 block inverses of one level
   // When set: take the number of levels, the coarse points and the sparsity
@@ -51,6 +52,17 @@ struct HostLevel {
   std::vector<int64_t> vk_inv_off;
   std::vector<double> vk_inv;
   int vk_ncolors = 0;
+  // ILU(1) data (Section 5): the level's block matrix in the smoother's order
+  // (il_perm[position] = dof; natural for symmetric problems, reverse Cuthill-McKee
+  // otherwise) factored with one level of fill: il_L its strict lower part (unit
+  // diagonal implied), il_U the strict upper part, il_diag the pivots, all in
+  // positions of that order.  il_schedL / il_schedU list the rows by (dependency
+  // level, position) of the forward / backward substitution; il_depthL / il_depthU
+  // count those levels.
+  Csr il_L, il_U;
+  std::vector<double> il_diag;
+  std::vector<int> il_perm, il_schedL, il_schedU;
+  int il_depthL = 0, il_depthU = 0;
   // transfers to the next level
   Csr P, Pp, R, Rp;
   std::vector<int> Cp, Cv;             // coarse points (fine indices, ascending)

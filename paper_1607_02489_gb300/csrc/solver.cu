@@ -851,7 +851,8 @@ amg_status create_impl(const amg_problem* pb, const amg_params* prm_in, void* st
   if (prm.max_nrhs < 1 || prm.max_nrhs > 32) return fail(AMG_ERR_ARG, "max_nrhs must be in 1..32");
   if (prm.gs_iters < 0 || prm.pre < 0 || prm.post < 0 || prm.omega <= 0.0)
     return fail(AMG_ERR_ARG, "invalid smoother parameters");
-  if (prm.smoother != 0 && prm.smoother != 1) return fail(AMG_ERR_ARG, "smoother must be 0 (Braess-Sarazin) or 1 (Vanka)");
+  if (prm.smoother < 0 || prm.smoother > 2)
+    return fail(AMG_ERR_ARG, "smoother must be 0 (Braess-Sarazin), 1 (Vanka) or 2 (ILU(1))");
   if (prm.smoother == 1 && !(prm.vanka_omega > 0.0)) return fail(AMG_ERR_ARG, "vanka_omega must be positive");
   if (pb->pinned_p >= pb->n_pnodes) return fail(AMG_ERR_ARG, "pinned pressure out of range");
   std::string why;
@@ -882,6 +883,7 @@ amg_status create_impl(const amg_problem* pb, const amg_params* prm_in, void* st
     sp.max_levels = prm.max_levels;
     sp.symmetric = pb->symmetric != 0;
     sp.vanka = prm.smoother == 1;
+    sp.ilu = prm.smoother == 2;
     sp.gs_iters = prm.gs_iters;
     sp.reuse = reuse ? &reuse->host : nullptr;
     h->host = build_hierarchy(std::move(fine), sp);
@@ -889,10 +891,10 @@ amg_status create_impl(const amg_problem* pb, const amg_params* prm_in, void* st
     h->N = h->host[0].N();
     if (!prm.host_only) {
       const double vomega = prm.smoother == 1 ? prm.vanka_omega : 0.0;
-      h->v64 = make_vcycle_f64(h->host, sp.c, prm.gs_iters, prm.pre, prm.post, round_k(prm.max_nrhs), vomega);
+      h->v64 = make_vcycle_f64(h->host, sp.c, prm.gs_iters, prm.pre, prm.post, round_k(prm.max_nrhs), vomega, sp.ilu);
       h->v64->set_autotune(prm.autotune != 0);
       if (prm.vcycle_fp32) {
-        h->v32 = make_vcycle_f32(h->host, sp.c, prm.gs_iters, prm.pre, prm.post, round_k(prm.max_nrhs), vomega);
+        h->v32 = make_vcycle_f32(h->host, sp.c, prm.gs_iters, prm.pre, prm.post, round_k(prm.max_nrhs), vomega, sp.ilu);
         h->v32->set_autotune(prm.autotune != 0);
       }
       EMIN_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
@@ -1067,6 +1069,28 @@ amg_status amg_level_get_vanka(amg_handle h, int level, int* nblocks, int* ndofs
   if (ptr) std::copy(L.vk_ptr.begin(), L.vk_ptr.end(), ptr);
   if (dofs) std::copy(L.vk_dofs.begin(), L.vk_dofs.end(), dofs);
   if (colors) std::copy(L.vk_colors.begin(), L.vk_colors.end(), colors);
+  return AMG_OK;
+}
+
+amg_status amg_level_get_ilu(amg_handle h, int level, int* n, long long* nnz_lower, long long* nnz_upper,
+                             int* depth_lower, int* depth_upper, int* perm, int* lower_ptr, int* lower_col,
+                             double* lower_val, int* upper_ptr, int* upper_col, double* upper_val, double* pivots) {
+  if (!h || level < 0 || level >= (int)h->host.size()) return fail(AMG_ERR_ARG, "bad handle or level");
+  const HostLevel& L = h->host[level];
+  if (L.il_perm.empty()) return fail(AMG_ERR_ARG, "the level has no ILU(1) factors");
+  if (n) *n = L.N();
+  if (nnz_lower) *nnz_lower = L.il_L.nnz();
+  if (nnz_upper) *nnz_upper = L.il_U.nnz();
+  if (depth_lower) *depth_lower = L.il_depthL;
+  if (depth_upper) *depth_upper = L.il_depthU;
+  if (perm) std::copy(L.il_perm.begin(), L.il_perm.end(), perm);
+  if (lower_ptr) std::copy(L.il_L.rowptr.begin(), L.il_L.rowptr.end(), lower_ptr);
+  if (lower_col) std::copy(L.il_L.col.begin(), L.il_L.col.end(), lower_col);
+  if (lower_val) std::copy(L.il_L.val.begin(), L.il_L.val.end(), lower_val);
+  if (upper_ptr) std::copy(L.il_U.rowptr.begin(), L.il_U.rowptr.end(), upper_ptr);
+  if (upper_col) std::copy(L.il_U.col.begin(), L.il_U.col.end(), upper_col);
+  if (upper_val) std::copy(L.il_U.val.begin(), L.il_U.val.end(), upper_val);
+  if (pivots) std::copy(L.il_diag.begin(), L.il_diag.end(), pivots);
   return AMG_OK;
 }
 

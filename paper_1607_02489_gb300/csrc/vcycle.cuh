@@ -58,7 +58,7 @@ struct VCycleIface {
 
 // Kernel classes reported by profile().
 enum KernelClass {
-  kVelocity = 0, kSchurRhs, kGsColor, kUpdate, kResidual, kRestrict, kProlong, kCoarse, kVanka, kNumClasses
+  kVelocity = 0, kSchurRhs, kGsColor, kUpdate, kResidual, kRestrict, kProlong, kCoarse, kVanka, kIlu, kNumClasses
 };
 
 #define EMIN_CUDA(call)                                                                 \
@@ -73,6 +73,7 @@ class DeviceVCycle : public VCycleIface {
  public:
   struct Buf {
     T *b = nullptr, *x = nullptr, *y = nullptr, *g = nullptr, *dp = nullptr, *r = nullptr;
+    T* iy = nullptr;  // ILU substitutions' outputs, 2 x N_l x K (ILU cycles only)
   };
   // Strips of a level split over a cluster of C blocks (k_gs_cluster): block c owns
   // spc consecutive strips; plist / poff as GsCluster; extents are maxima over blocks.
@@ -89,15 +90,20 @@ class DeviceVCycle : public VCycleIface {
   };
 
   DeviceVCycle(const std::vector<HostLevel>& levels, double cfac, int gs_iters, int pre, int post, int kmax,
-               double vanka_omega = 0.0)
+               double vanka_omega = 0.0, bool ilu = false)
       : c_(cfac), cfac_((T)cfac), gs_iters_(gs_iters), pre_(pre), post_(post), kmax_(kmax),
-        vanka_omega_((T)vanka_omega) {
+        vanka_omega_((T)vanka_omega), ilu_(ilu) {
     try {
       if ((long long)levels[0].N() * kmax_ >= (1LL << 31))
         throw std::runtime_error("N * max_nrhs must stay below 2^31 (32-bit vector indices)");
       for (size_t l = 0; l < levels.size(); ++l) upload_level(levels[l], l + 1 == levels.size());
       if (vanka_omega > 0.0)
         for (size_t l = 0; l + 1 < levels.size(); ++l) upload_vanka(levels[l]);
+      if (ilu_) {
+        for (size_t l = 0; l + 1 < levels.size(); ++l) upload_ilu(levels[l]);
+        il_ticket_ = alloc<int>(1);
+        EMIN_CUDA(cudaMemset(il_ticket_, 0, sizeof(int)));
+      }
       tune_ = std::make_shared<std::vector<GsChoice>>(levels.size() * 6);
       rowmap_ = std::make_shared<std::vector<int>>(levels.size() * 6 * kRowClasses, -1);
       vkform_ = std::make_shared<std::vector<int>>(levels.size() * 6, -1);
@@ -135,9 +141,11 @@ class DeviceVCycle : public VCycleIface {
   }
   size_t clone_bytes(int kmax) const override {
     size_t b = 256;
-    for (const LevelView<T>& L : views_) {
+    for (size_t l = 0; l < views_.size(); ++l) {
+      const LevelView<T>& L = views_[l];
       const size_t N = (size_t)L.dim * L.n_v + L.n_p;
       b += ((3 * N + (size_t)L.dim * L.n_v + 2 * (size_t)L.n_p) * kmax * sizeof(T) + 255) / 256 * 256;
+      if (ilu_ && l + 1 < views_.size()) b += (2 * N * kmax * sizeof(T) + 255) / 256 * 256;
     }
     for (const GsStrips& P : gs_) b += ((size_t)(P.nstrips + 1) * sizeof(int) + 255) / 256 * 256;
     return b;
@@ -325,6 +333,29 @@ class DeviceVCycle : public VCycleIface {
       mark_end(s);
     }
   }
+  // ILU(1) step (Section 5): r = b - A x (r = b from x = 0), then the forward and the
+  // backward substitution, the second adding (L U)^-1 r to x.
+  template <int K>
+  void ilu_sweep(int l, bool from_zero, cudaStream_t s) {
+    const Buf& B = buf_[l];
+    const IluLevel& I = il_[l];
+    const T* r = B.b;
+    if (!from_zero) {
+      mark_begin(l, kResidual, s);
+      launch_rows<K>(kResidual, l, shape(l, K, kResidual), 0, s);
+      mark_end(s);
+      r = B.r;
+    }
+    const size_t n = (size_t)I.view.n * K;
+    cudaMemsetAsync(B.iy, 0xff, sizeof(T) * 2 * n, s);
+    mark_begin(l, kIlu, s);
+    k_ilu_lower<T, K><<<I.blocks, kIluBlock, 0, s>>>(I.view, r, B.iy, il_ticket_, err_);
+    mark_end(s);
+    mark_begin(l, kIlu, s);
+    k_ilu_upper<T, K><<<I.blocks, kIluBlock, 0, s>>>(I.view, B.iy, B.iy + n, B.x, from_zero ? 1 : 0, il_ticket_, err_);
+    mark_end(s);
+  }
+
   // One color of a level's Vanka blocks in one of three forms (0 pairs, 1 warp rows
   // with 256 threads, 2 warp rows with 1024 threads).
   template <int K>
@@ -391,6 +422,10 @@ class DeviceVCycle : public VCycleIface {
       for (int sw = 0; sw < sweeps; ++sw) vanka_sweep<K>(l, from_zero && sw == 0, s);
       return;
     }
+    if (ilu_) {
+      for (int sw = 0; sw < sweeps; ++sw) ilu_sweep<K>(l, from_zero && sw == 0, s);
+      return;
+    }
     for (int sw = 0; sw < sweeps; ++sw) {
       const int zero = (from_zero && sw == 0) ? 1 : 0;
       mark_begin(l, kVelocity, s);
@@ -422,7 +457,7 @@ class DeviceVCycle : public VCycleIface {
     const bool vanka = vanka_omega_ > T(0);
     for (int l = 0; l + 1 < (int)views_.size(); ++l)
       for (int cls : classes) {
-        if (vanka && (cls == kVelocity || cls == kSchurRhs || cls == kUpdate)) continue;  // not in a Vanka cycle
+        if ((vanka || ilu_) && (cls == kVelocity || cls == kSchurRhs || cls == kUpdate)) continue;  // not in this cycle
         int& slot = (*rowmap_)[((size_t)l * 6 + ks) * kRowClasses + cls];
         if (slot >= 0) continue;
         int best = -1;
@@ -529,7 +564,7 @@ class DeviceVCycle : public VCycleIface {
   // round alike.  Runs outside graph capture, before the first capture for K.
   template <int K>
   void tune_gs(cudaStream_t s) {
-    if (vanka_omega_ > T(0)) return;  // no Gauss-Seidel in a Vanka cycle
+    if (vanka_omega_ > T(0) || ilu_) return;  // no Gauss-Seidel in a Vanka or ILU cycle
     const int ks = kslot(K);
     cudaEvent_t e0, e1;
     EMIN_CUDA(cudaEventCreate(&e0));
@@ -852,7 +887,7 @@ class DeviceVCycle : public VCycleIface {
   struct CloneTag {};
   DeviceVCycle(const DeviceVCycle& o, int kmax, CloneTag)
       : c_(o.c_), cfac_(o.cfac_), gs_iters_(o.gs_iters_), pre_(o.pre_), post_(o.post_), kmax_(kmax),
-        vanka_omega_(o.vanka_omega_) {
+        vanka_omega_(o.vanka_omega_), ilu_(o.ilu_) {
     try {
       if ((long long)((size_t)o.views_[0].dim * o.views_[0].n_v + o.views_[0].n_p) * kmax_ >= (1LL << 31))
         throw std::runtime_error("N * max_nrhs must stay below 2^31 (32-bit vector indices)");
@@ -862,6 +897,7 @@ class DeviceVCycle : public VCycleIface {
       ci_rel_ = o.ci_rel_;
       cplans_ = o.cplans_;
       vk_ = o.vk_;
+      il_ = o.il_;
       gsM_ = o.gsM_;
       tune_ = o.tune_;
       rowmap_ = o.rowmap_;
@@ -874,18 +910,22 @@ class DeviceVCycle : public VCycleIface {
       pinv_ = o.pinv_;
       Nc_ = o.Nc_;
       for (size_t l = 0; l < views_.size(); ++l) {
-        buf_.push_back(alloc_bufs(views_[l]));
+        buf_.push_back(alloc_bufs(views_[l], l + 1 < views_.size()));
         done_.push_back(alloc<int>(gs_[l].nstrips + 1));
       }
       err_ = alloc<int>(1);
       EMIN_CUDA(cudaMemset(err_, 0, sizeof(int)));
+      if (ilu_) {
+        il_ticket_ = alloc<int>(1);
+        EMIN_CUDA(cudaMemset(il_ticket_, 0, sizeof(int)));
+      }
     } catch (...) {
       release();
       throw;
     }
   }
 
-  Buf alloc_bufs(const LevelView<T>& L) {
+  Buf alloc_bufs(const LevelView<T>& L, bool smoothed) {
     const size_t N = ((size_t)L.dim * L.n_v + L.n_p) * kmax_;
     Buf B;
     B.b = alloc<T>(N);
@@ -894,6 +934,7 @@ class DeviceVCycle : public VCycleIface {
     B.y = alloc<T>((size_t)L.dim * L.n_v * kmax_);
     B.g = alloc<T>((size_t)L.n_p * kmax_);
     B.dp = alloc<T>((size_t)L.n_p * kmax_);
+    if (ilu_ && smoothed) B.iy = alloc<T>(2 * N);
     return B;
   }
 
@@ -957,6 +998,34 @@ class DeviceVCycle : public VCycleIface {
     V.dirichlet = alloc_copy<int>(H.vk_dirichlet);
     V.n_dirichlet = (int)H.vk_dirichlet.size();
     vk_.push_back(V);
+  }
+
+  // ILU(1) factors of a level.  Grid: about four warps per row of an average
+  // dependency level (rows of a level run concurrently, the next levels' warps wait
+  // behind them), at least 32 warps and at most 16 per SM.
+  void upload_ilu(const HostLevel& H) {
+    if (H.il_perm.empty()) throw std::runtime_error("the hierarchy was built without the ILU(1) factors");
+    const int n = H.N();
+    IluLevel I;
+    I.view.n = n;
+    I.view.perm = alloc_copy<int>(H.il_perm);
+    I.view.L = upload(H.il_L);
+    I.view.U = upload(H.il_U);
+    std::vector<double> dinv(n);
+    for (int i = 0; i < n; ++i) dinv[i] = 1.0 / H.il_diag[i];
+    I.view.dinv = alloc_copy<T>(dinv);
+    I.view.schedL = alloc_copy<int>(H.il_schedL);
+    I.view.schedU = alloc_copy<int>(H.il_schedU);
+    I.depthL = H.il_depthL;
+    I.depthU = H.il_depthU;
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long per_level = (n + std::max(1, std::min(I.depthL, I.depthU)) - 1) / std::max(1, std::min(I.depthL, I.depthU));
+    const long long warps = std::min<long long>(std::max<long long>(4 * per_level, 32), 16LL * std::max(1, sms));
+    constexpr int wpb = kIluBlock / 32;
+    I.blocks = (int)((warps + wpb - 1) / wpb);
+    il_.push_back(I);
   }
 
   void upload_level(const HostLevel& H, bool coarsest) {
@@ -1057,7 +1126,7 @@ class DeviceVCycle : public VCycleIface {
       L.Rp = upload(H.Rp);
     }
     views_.push_back(L);
-    buf_.push_back(alloc_bufs(L));
+    buf_.push_back(alloc_bufs(L, !coarsest));
   }
 
   void release() {
@@ -1074,6 +1143,13 @@ class DeviceVCycle : public VCycleIface {
   T cfac_;
   int gs_iters_, pre_, post_, kmax_;
   T vanka_omega_ = T(0);  // > 0: the Vanka smoother replaces Braess-Sarazin
+  bool ilu_ = false;      // ILU(1) replaces Braess-Sarazin
+  struct IluLevel {
+    IluView<T> view{};
+    int depthL = 0, depthU = 0, blocks = 1;
+  };
+  std::vector<IluLevel> il_;  // shared (read-only) with the clones
+  int* il_ticket_ = nullptr;  // ticket counter of the substitutions, zero between launches
   bool autotune_ = true;
   std::vector<LevelView<T>> views_;
   std::vector<Buf> buf_;
@@ -1110,11 +1186,12 @@ class DeviceVCycle : public VCycleIface {
 };
 
 // Factories, one translation unit per type.
-// vanka_omega > 0 smooths with Vanka (the levels must carry the Vanka blocks), else Braess-Sarazin.
+// vanka_omega > 0 smooths with Vanka (the levels must carry the Vanka blocks), ilu with
+// ILU(1) (the levels must carry the factors), else Braess-Sarazin.
 VCycleIface* make_vcycle_f64(const std::vector<HostLevel>& levels, double cfac, int gs, int pre, int post, int kmax,
-                             double vanka_omega);
+                             double vanka_omega, bool ilu);
 VCycleIface* make_vcycle_f32(const std::vector<HostLevel>& levels, double cfac, int gs, int pre, int post, int kmax,
-                             double vanka_omega);
+                             double vanka_omega, bool ilu);
 // Finest-level FP64 block product out = A x (TX = double or float), or out = b - A x.
 cudaError_t apply_finest_f64(VCycleIface* v64, const void* x, bool x_fp32, const double* b, double* out, int K,
                              cudaStream_t s);

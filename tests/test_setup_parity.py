@@ -171,3 +171,41 @@ def test_reused_coarsening_matches_oracle():
     with pytest.raises(g.AmgError):
         g.Hierarchy(other, host_only=1, reuse=Hg0)
     assert nv == first.n_v
+
+
+@pytest.mark.parametrize("case", ["lid32", "pinned16", "oseen32", "lid18", "lid3d"])
+def test_ilu_factors_match_oracle(case):
+    """The library's ILU(1) setup (smoother = 2) against the oracle's on every smoothed
+    level: the same order (natural for Stokes, reverse Cuthill-McKee for Oseen; integer
+    work, bit-exact), the same factor patterns and the factors and pivots to rounding.
+    oseen32's coarse level has zero-block pivots that no elimination step reaches."""
+    prob = {"lid32": lambda: stokes_lid_2d(32, nrhs=1), "pinned16": lambda: stokes_pinned_2d(16, nrhs=1),
+            "oseen32": lambda: oseen_recirculating_2d(32, Re=100.0, nrhs=1),
+            "lid18": lambda: make_problem(18, 2, 0.0, 1.0, bc="lid", nrhs=1),
+            "lid3d": lambda: make_problem(4, 3, 0.0, 1.0, bc="lid", nrhs=1)}[case]()
+    Ho = setup_hierarchy(prob, Params(smoother="ilu", pre=1, post=1))
+    Hg = g.Hierarchy(prob, host_only=1, smoother=2, pre=1, post=1)
+    assert Hg.num_levels() == len(Ho.levels)
+    for l, L in enumerate(Ho.levels[:-1]):
+        F = Hg.level_ilu(l)
+        I = L.ilu
+        n = L.N
+        assert np.array_equal(F["perm"], I["perm"]), l
+        Lo = sp.csr_matrix(I["L"])
+        Uo = sp.csr_matrix(I["U"])
+        piv_o = Uo.diagonal()
+        Uo = sp.triu(Uo, k=1, format="csr")
+        Lg = sp.csr_matrix((F["lower"][2], F["lower"][1], F["lower"][0]), shape=(n, n))
+        Ug = sp.csr_matrix((F["upper"][2], F["upper"][1], F["upper"][0]), shape=(n, n))
+        for Mg, Mo, nm in ((Lg, Lo, "L"), (Ug, Uo, "U")):
+            Mg = Mg.copy()
+            Mg.eliminate_zeros()
+            Mo.eliminate_zeros()
+            Mo.sort_indices()
+            assert np.array_equal(Mg.indptr, Mo.indptr) and np.array_equal(Mg.indices, Mo.indices), (l, nm)
+            scale = max(abs(Mo).max(), 1e-300)
+            assert abs(Mg - Mo).max() <= 1e-11 * scale, (l, nm, abs(Mg - Mo).max(), scale)
+        assert np.abs(F["pivots"] - piv_o).max() <= 1e-11 * np.abs(piv_o).max(), l
+        assert F["depth_lower"] >= 1 and F["depth_upper"] >= 1
+    with pytest.raises(g.AmgError):
+        Hg.level_ilu(len(Ho.levels) - 1)

@@ -105,6 +105,10 @@ typedef struct {
                          elimination step reaches becomes -sum_j M_ij M_ji / M_jj over its
                          row; pre and post count ILU steps (the paper's ILU(1)(1,1)) */
   double vanka_omega; /* Vanka under-relaxation, 0.5 (Section 6) */
+  int ilu_order;      /* ILU(1) order of a symmetric problem's levels: 0 (default) the dof order
+                         [u_x | u_y (| u_z) | p], 1 by node location (lexicographic from the
+                         lower-left corner, u_x, u_y (, u_z), p at one node); non-symmetric
+                         problems always take reverse Cuthill-McKee */
 } amg_params;
 
 void amg_params_default(amg_params* prm);

@@ -45,6 +45,7 @@ class Params:
     emin: str = "auto"            # "cg" (Stokes), "gmres" (Oseen); auto picks by symmetry
     smoother: str = "bs"          # "bs" Braess-Sarazin (Section 5.2), "vanka" (Section 5.1), "ilu" ILU(1) (Section 5)
     vanka_omega: float = 0.5      # Vanka under-relaxation (Section 6)
+    ilu_order: str = "block"      # ILU(1) order of symmetric levels: "block" (the paper's) or "location"
     max_coarse: int = 200
     max_levels: int = 12
 
@@ -664,5 +665,5 @@ def setup_hierarchy(prob, prm: Params = None, reuse: Hierarchy = None) -> Hierar
     if prm.smoother == "ilu":
         from .ilu import form_ilu
         for L in levels[:-1]:
-            form_ilu(L, bool(prob.symmetric))
+            form_ilu(L, bool(prob.symmetric), prm.ilu_order)
     return Hierarchy(levels=levels, params=prm, symmetric=bool(prob.symmetric))

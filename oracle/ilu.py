@@ -22,7 +22,11 @@ Readings (the paper is silent on them):
     takes the value -sum_j M_ij M_ji / M_jj: the Schur-complement diagonal that
     eliminating its neighbours would give with their block replaced by its
     diagonal.  Every other pivot is the elimination's own.
-  * Natural order: the level's dof order [u_x | u_y (| u_z) | p].
+  * Natural order: the level's dof order [u_x | u_y (| u_z) | p] (the block order of
+    the paper's IFISS matrices, each block lexicographic).  Params.ilu_order =
+    "location" is an alternative for symmetric problems, not the paper's: every dof
+    sorted by its node's coordinates (last coordinate slowest), the dofs of one node
+    as u_x, u_y (, u_z), p, a pressure placed at its co-located velocity node.
   * Reverse Cuthill-McKee (non-symmetric problems): on the graph of A + A^T
     without self loops, start at the vertex of smallest degree (lowest index on
     ties), visit the unvisited neighbours of each vertex by increasing degree
@@ -122,11 +126,29 @@ def _schur_pivot(M, i):
     return s
 
 
-def form_ilu(L, symmetric: bool):
+def location_order(L) -> np.ndarray:
+    """Dofs by node location (see the module docstring): position -> dof."""
+    nu = L.dim * L.n_v
+    X = np.empty((nu + L.n_p, L.dim))
+    for c in range(L.dim):
+        X[c * L.n_v:(c + 1) * L.n_v] = L.vcoords
+    for k in range(L.n_p):
+        v = int(L.p2v[k])
+        X[nu + k] = L.vcoords[v] if v >= 0 else L.pcoords[k]
+    keys = [np.arange(nu + L.n_p)] + [X[:, c] for c in range(L.dim)]
+    return np.lexsort(keys).astype(np.int64)
+
+
+def form_ilu(L, symmetric: bool, order: str = "block"):
     """The level's block matrix in the smoother's order (natural for a symmetric
     problem, Stokes; reverse Cuthill-McKee otherwise), its ILU(1) factors and the order."""
     M = sp.csr_matrix(L.full_matrix())
-    perm = np.arange(M.shape[0]) if symmetric else rcm_order(M)
+    if not symmetric:
+        perm = rcm_order(M)
+    elif order == "location":
+        perm = location_order(L)
+    else:
+        perm = np.arange(M.shape[0])
     Mp = M[perm][:, perm]
     rows, _ = ilu1(Mp)
     n = M.shape[0]

@@ -49,7 +49,8 @@ class AmgParams(ctypes.Structure):
                 ("omega_on_D", ctypes.c_int), ("gs_iters", ctypes.c_int), ("pre", ctypes.c_int),
                 ("post", ctypes.c_int), ("max_coarse", ctypes.c_int), ("max_levels", ctypes.c_int),
                 ("vcycle_fp32", ctypes.c_int), ("max_nrhs", ctypes.c_int), ("host_only", ctypes.c_int),
-                ("autotune", ctypes.c_int), ("smoother", ctypes.c_int), ("vanka_omega", ctypes.c_double)]
+                ("autotune", ctypes.c_int), ("smoother", ctypes.c_int), ("vanka_omega", ctypes.c_double),
+                ("ilu_order", ctypes.c_int)]
 
 
 class AmgLevelInfo(ctypes.Structure):

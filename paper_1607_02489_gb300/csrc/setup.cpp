@@ -965,7 +965,30 @@ void schedule(const Csr& T, bool lower, std::vector<int>& sched, int& depth) {
   for (int i = 0; i < n; ++i) sched[cnt[lev[i]]++] = i;
 }
 
-void form_ilu(HostLevel& L, bool symmetric) {
+// Location order: dofs sorted by their node's coordinates (last coordinate slowest:
+// lexicographic from the lower-left corner), the dofs of one node as u_x, u_y (, u_z),
+// p; a pressure takes its co-located velocity node's coordinates (exact ties).
+std::vector<int> location_order(const HostLevel& L) {
+  const int n = L.N(), nu = L.dim * L.n_v, d = L.dim;
+  auto coord = [&](int q) -> const double* {
+    if (q < nu) return &L.vX[(size_t)(q % L.n_v) * d];
+    const int i = q - nu;
+    const int v = L.p2v.empty() ? -1 : L.p2v[i];
+    return v >= 0 ? &L.vX[(size_t)v * d] : &L.pX[(size_t)i * d];
+  };
+  std::vector<int> order(n);
+  for (int q = 0; q < n; ++q) order[q] = q;
+  std::sort(order.begin(), order.end(), [&](int a, int b) {
+    const double* xa = coord(a);
+    const double* xb = coord(b);
+    for (int k = d - 1; k >= 0; --k)
+      if (xa[k] != xb[k]) return xa[k] < xb[k];
+    return a < b;  // u_x, u_y (, u_z), p: the block order at one node
+  });
+  return order;
+}
+
+void form_ilu(HostLevel& L, bool symmetric, int ilu_order) {
   const int n = L.N();
   Csr M;  // natural order
   M.resize_rows(n, n);
@@ -985,10 +1008,12 @@ void form_ilu(HostLevel& L, bool symmetric) {
     M.rowptr[q + 1] = (int64_t)M.col.size();
   }
   std::vector<int> perm(n);
-  if (symmetric)
-    for (int i = 0; i < n; ++i) perm[i] = i;
-  else
+  if (!symmetric)
     perm = rcm_order(M);
+  else if (ilu_order == 1)
+    perm = location_order(L);
+  else
+    for (int i = 0; i < n; ++i) perm[i] = i;
   std::vector<int> pos(n);
   for (int i = 0; i < n; ++i) pos[perm[i]] = i;
   // the permuted matrix (rows and columns in positions), rows ascending
@@ -1122,7 +1147,7 @@ std::vector<HostLevel> build_hierarchy(HostLevel fine, const SetupParams& prm) {
   if (prm.vanka)
     for (size_t l = 0; l + 1 < levels.size(); ++l) form_vanka(levels[l], prm);
   if (prm.ilu)
-    for (size_t l = 0; l + 1 < levels.size(); ++l) form_ilu(levels[l], prm.symmetric);
+    for (size_t l = 0; l + 1 < levels.size(); ++l) form_ilu(levels[l], prm.symmetric, prm.ilu_order);
   for (size_t l = 0; l + 1 < levels.size(); ++l)
     if (levels[l].n_p <= kGsDenseMaxRows) form_dense_gs(levels[l], prm.gs_iters);
   return levels;

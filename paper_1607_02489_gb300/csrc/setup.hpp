@@ -18,6 +18,7 @@ struct SetupParams {
   bool symmetric = true;   // one EMIN CG step, R = P^T; otherwise EMIN GMRES for P and R
   bool vanka = false;      // form the Vanka smoother's blocks (Section 5.1) on every level but the coarsest
   bool ilu = false;        // form the ILU(1) factors (Section 5) on every level but the coarsest
+  int ilu_order = 0;       // symmetric problems: 0 block order [u_x | u_y | p], 1 by node location
   int gs_iters = 5;        // Gauss-Seidel iterations per Braess-Sarazin step (for the dense map)
   size_t vanka_max_bytes = (size_t)16 << 30;  // limit on the FP64 block inverses of one level
   // When set: take the number of levels, the coarse points and the sparsity

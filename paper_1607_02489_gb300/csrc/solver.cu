@@ -800,6 +800,7 @@ void amg_params_default(amg_params* p) {
   p->autotune = 1;
   p->smoother = 0;
   p->vanka_omega = 0.5;
+  p->ilu_order = 0;
 }
 
 const char* amg_last_error(void) { return g_last_error.c_str(); }
@@ -854,6 +855,7 @@ amg_status create_impl(const amg_problem* pb, const amg_params* prm_in, void* st
   if (prm.smoother < 0 || prm.smoother > 2)
     return fail(AMG_ERR_ARG, "smoother must be 0 (Braess-Sarazin), 1 (Vanka) or 2 (ILU(1))");
   if (prm.smoother == 1 && !(prm.vanka_omega > 0.0)) return fail(AMG_ERR_ARG, "vanka_omega must be positive");
+  if (prm.ilu_order != 0 && prm.ilu_order != 1) return fail(AMG_ERR_ARG, "ilu_order must be 0 or 1");
   if (pb->pinned_p >= pb->n_pnodes) return fail(AMG_ERR_ARG, "pinned pressure out of range");
   std::string why;
   if (!check_csr(pb->A_rowptr, pb->A_col, pb->n_vnodes, pb->n_vnodes, why)) return fail(AMG_ERR_ARG, "A: " + why);
@@ -884,6 +886,7 @@ amg_status create_impl(const amg_problem* pb, const amg_params* prm_in, void* st
     sp.symmetric = pb->symmetric != 0;
     sp.vanka = prm.smoother == 1;
     sp.ilu = prm.smoother == 2;
+    sp.ilu_order = prm.ilu_order;
     sp.gs_iters = prm.gs_iters;
     sp.reuse = reuse ? &reuse->host : nullptr;
     h->host = build_hierarchy(std::move(fine), sp);

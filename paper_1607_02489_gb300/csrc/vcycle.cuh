@@ -107,6 +107,7 @@ class DeviceVCycle : public VCycleIface {
       tune_ = std::make_shared<std::vector<GsChoice>>(levels.size() * 6);
       rowmap_ = std::make_shared<std::vector<int>>(levels.size() * 6 * kRowClasses, -1);
       vkform_ = std::make_shared<std::vector<int>>(levels.size() * 6, -1);
+      ilgrid_ = std::make_shared<std::vector<int>>(levels.size() * 6, -1);
       for (size_t l = 0; l + 1 < levels.size(); ++l) {
         views_[l].n_vc = levels[l + 1].n_v;
         views_[l].n_pc = levels[l + 1].n_p;
@@ -346,14 +347,67 @@ class DeviceVCycle : public VCycleIface {
       mark_end(s);
       r = B.r;
     }
+    const int tuned = (*ilgrid_)[(size_t)l * 6 + kslot(K)];
+    ilu_substitutions<K>(l, r, from_zero, tuned > 0 ? tuned : I.blocks, true, s);
+  }
+  template <int K>
+  void ilu_substitutions(int l, const T* r, bool zero, int blocks, bool marks, cudaStream_t s) {
+    const Buf& B = buf_[l];
+    const IluLevel& I = il_[l];
     const size_t n = (size_t)I.view.n * K;
     cudaMemsetAsync(B.iy, 0xff, sizeof(T) * 2 * n, s);
-    mark_begin(l, kIlu, s);
-    k_ilu_lower<T, K><<<I.blocks, kIluBlock, 0, s>>>(I.view, r, B.iy, il_ticket_, err_);
-    mark_end(s);
-    mark_begin(l, kIlu, s);
-    k_ilu_upper<T, K><<<I.blocks, kIluBlock, 0, s>>>(I.view, B.iy, B.iy + n, B.x, from_zero ? 1 : 0, il_ticket_, err_);
-    mark_end(s);
+    if (marks) mark_begin(l, kIlu, s);
+    k_ilu_lower<T, K><<<blocks, kIluBlock, 0, s>>>(I.view, r, B.iy, il_ticket_, err_);
+    if (marks) mark_end(s);
+    if (marks) mark_begin(l, kIlu, s);
+    k_ilu_upper<T, K><<<blocks, kIluBlock, 0, s>>>(I.view, B.iy, B.iy + n, B.x, zero ? 1 : 0, il_ticket_, err_);
+    if (marks) mark_end(s);
+  }
+  // ILU grid autotuner: both substitutions of each level timed (CUDA events) with 1, 2,
+  // 4, 8 and 16 warps per row of an average dependency level (within 32 warps and 32
+  // per SM); the fastest kept in a table shared with the clones.
+  template <int K>
+  void tune_ilu(cudaStream_t s) {
+    if (!ilu_) return;
+    const int ks = kslot(K);
+    cudaEvent_t e0, e1;
+    EMIN_CUDA(cudaEventCreate(&e0));
+    EMIN_CUDA(cudaEventCreate(&e1));
+    constexpr int wpb = kIluBlock / 32;
+    for (int l = 0; l < (int)il_.size(); ++l) {
+      int& slot = (*ilgrid_)[(size_t)l * 6 + ks];
+      if (slot > 0) continue;
+      const IluLevel& I = il_[l];
+      // input: the level's residual scratch, zeroed (a cycle writes r before reading it; b
+      // may already hold the caller's vector, since tuning runs inside the first cycle)
+      cudaMemsetAsync(buf_[l].r, 0, sizeof(T) * (size_t)I.view.n * K, s);
+      int best = I.blocks, last = -1;
+      float best_ms = 1e30f;
+      for (int f = 1; f <= 16; f *= 2) {
+        const long long warps = std::min<long long>(std::max<long long>(f * I.per_level, 32), 32LL * sms_);
+        const int blocks = (int)((warps + wpb - 1) / wpb);
+        if (blocks == last) continue;
+        last = blocks;
+        float total = 0.f;
+        for (int rep = 0; rep < 3; ++rep) {
+          cudaEventRecord(e0, s);
+          ilu_substitutions<K>(l, buf_[l].r, true, blocks, false, s);
+          launches_ += 2;
+          cudaEventRecord(e1, s);
+          cudaEventSynchronize(e1);
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          if (rep > 0) total += ms;
+        }
+        if (cudaGetLastError() == cudaSuccess && total < best_ms) {
+          best_ms = total;
+          best = blocks;
+        }
+      }
+      slot = best;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
   }
 
   // One color of a level's Vanka blocks in one of three forms (0 pairs, 1 warp rows
@@ -608,12 +662,12 @@ class DeviceVCycle : public VCycleIface {
   }
   void tune_for(int K, cudaStream_t s) {
     switch (K) {
-      case 1: tune_rows<1>(s); tune_gs<1>(s); tune_vanka<1>(s); break;
-      case 2: tune_rows<2>(s); tune_gs<2>(s); tune_vanka<2>(s); break;
-      case 4: tune_rows<4>(s); tune_gs<4>(s); tune_vanka<4>(s); break;
-      case 8: tune_rows<8>(s); tune_gs<8>(s); tune_vanka<8>(s); break;
-      case 16: tune_rows<16>(s); tune_gs<16>(s); tune_vanka<16>(s); break;
-      case 32: tune_rows<32>(s); tune_gs<32>(s); tune_vanka<32>(s); break;
+      case 1: tune_rows<1>(s); tune_gs<1>(s); tune_vanka<1>(s); tune_ilu<1>(s); break;
+      case 2: tune_rows<2>(s); tune_gs<2>(s); tune_vanka<2>(s); tune_ilu<2>(s); break;
+      case 4: tune_rows<4>(s); tune_gs<4>(s); tune_vanka<4>(s); tune_ilu<4>(s); break;
+      case 8: tune_rows<8>(s); tune_gs<8>(s); tune_vanka<8>(s); tune_ilu<8>(s); break;
+      case 16: tune_rows<16>(s); tune_gs<16>(s); tune_vanka<16>(s); tune_ilu<16>(s); break;
+      case 32: tune_rows<32>(s); tune_gs<32>(s); tune_vanka<32>(s); tune_ilu<32>(s); break;
     }
   }
 
@@ -902,6 +956,8 @@ class DeviceVCycle : public VCycleIface {
       tune_ = o.tune_;
       rowmap_ = o.rowmap_;
       vkform_ = o.vkform_;
+      ilgrid_ = o.ilgrid_;
+      sms_ = o.sms_;
       autotune_ = o.autotune_;
       plist_ = o.plist_;
       poff_ = o.poff_;
@@ -1022,7 +1078,9 @@ class DeviceVCycle : public VCycleIface {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const long long per_level = (n + std::max(1, std::min(I.depthL, I.depthU)) - 1) / std::max(1, std::min(I.depthL, I.depthU));
-    const long long warps = std::min<long long>(std::max<long long>(4 * per_level, 32), 16LL * std::max(1, sms));
+    sms_ = std::max(1, sms);
+    I.per_level = per_level;
+    const long long warps = std::min<long long>(std::max<long long>(4 * per_level, 32), 16LL * sms_);
     constexpr int wpb = kIluBlock / 32;
     I.blocks = (int)((warps + wpb - 1) / wpb);
     il_.push_back(I);
@@ -1146,9 +1204,12 @@ class DeviceVCycle : public VCycleIface {
   bool ilu_ = false;      // ILU(1) replaces Braess-Sarazin
   struct IluLevel {
     IluView<T> view{};
-    int depthL = 0, depthU = 0, blocks = 1;
+    int depthL = 0, depthU = 0, blocks = 1;  // blocks: the untuned grid
+    long long per_level = 1;                  // rows per dependency level, on average
   };
   std::vector<IluLevel> il_;  // shared (read-only) with the clones
+  int sms_ = 1;
+  std::shared_ptr<std::vector<int>> ilgrid_;  // [level * 6 + K slot]: tuned ILU grid (blocks), -1 untuned
   int* il_ticket_ = nullptr;  // ticket counter of the substitutions, zero between launches
   bool autotune_ = true;
   std::vector<LevelView<T>> views_;

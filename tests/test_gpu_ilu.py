@@ -66,6 +66,22 @@ def test_ilu_vcycle_fp64_matches_oracle(case):
     assert torch.equal(zt, z2)
 
 
+@pytest.mark.parametrize("case", ["lid32", "lid3d"])
+def test_ilu_location_order_vcycle_matches_oracle(case):
+    """The alternative order (amg_params.ilu_order = 1) against the oracle's."""
+    p = CASES[case]()
+    Ho = setup_hierarchy(p, Params(smoother="ilu", pre=1, post=1, ilu_order="location"))
+    Hg = g.Hierarchy(p, max_nrhs=p.b.shape[1], ilu_order=1, **IL)
+    r = uniform_pm1(44, p.N * p.b.shape[1]).reshape(p.N, -1)
+    zo = vcycle(Ho, r)
+    rt = torch.tensor(r, device="cuda")
+    zt = torch.empty_like(rt)
+    Hg.vcycle(rt, zt)
+    torch.cuda.synchronize()
+    err = _relerr(zt.cpu().numpy(), zo)
+    assert np.all(err <= max(1e-11, 2.0 * _coarse_condition(Ho) * 2.0 ** -53)), err
+
+
 @pytest.mark.parametrize("K", [1, 8, 32])
 def test_ilu_vcycle_lane_groups(K):
     """Every lane split of a row (32 / K groups of K lanes): K = 1, 8 and 32 columns."""

@@ -9,7 +9,7 @@ import scipy.sparse as sp
 
 from synth import oseen_recirculating_2d, stokes_lid_2d, stokes_pinned_2d, uniform_pm1
 from oracle import Params, fgmres, setup_hierarchy
-from oracle.ilu import ilu1, ilu_sweep, rcm_order
+from oracle.ilu import ilu1, ilu_sweep, location_order, rcm_order
 
 ILU = dict(smoother="ilu", pre=1, post=1)
 
@@ -77,6 +77,35 @@ def test_complete_fill_gives_the_exact_lu():
     T = sp.diags([-1.0 * np.ones(n - 1), 4.0 * np.ones(n), -2.0 * np.ones(n - 1)], [-1, 0, 1], format="csr")
     rows, _ = ilu1(T)
     assert np.abs(_lu_product(rows, n).toarray() - T.toarray()).max() <= 1e-14
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_location_order_sorts_by_coordinates(dim):
+    """The alternative order: a permutation, node coordinates non-decreasing in the slowest
+    coordinate (and lexicographic), each pressure right after its co-located velocity
+    node's last component, the components of a node consecutive, on fine and coarse levels."""
+    from synth import make_problem
+    p = make_problem(8 if dim == 2 else 4, dim, 0.0, 1.0, bc="lid", nrhs=1)
+    H = setup_hierarchy(p, Params(smoother="ilu", ilu_order="location", pre=1, post=1))
+    for L in H.levels[:-1]:
+        perm = location_order(L)
+        nu = L.dim * L.n_v
+        assert np.array_equal(np.sort(perm), np.arange(nu + L.n_p))
+        assert np.array_equal(L.ilu["perm"], perm)
+        pos = np.empty_like(perm)
+        pos[perm] = np.arange(len(perm))
+        node = np.where(perm < nu, perm % L.n_v, -1)
+        for t, q in enumerate(perm):
+            if q >= nu:
+                v = int(L.p2v[q - nu])
+                if v >= 0:
+                    assert pos[(L.dim - 1) * L.n_v + v] == t - 1
+                    node[t] = v
+        X = L.vcoords[node[node >= 0]]
+        key = X[:, ::-1]
+        assert all(tuple(key[i]) <= tuple(key[i + 1]) for i in range(len(key) - 1))
+        for v in range(L.n_v):
+            assert all(pos[c * L.n_v + v] == pos[v] + c for c in range(L.dim))
 
 
 def test_rcm_is_a_permutation_that_narrows_the_band():

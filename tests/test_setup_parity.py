@@ -173,18 +173,21 @@ def test_reused_coarsening_matches_oracle():
     assert nv == first.n_v
 
 
-@pytest.mark.parametrize("case", ["lid32", "pinned16", "oseen32", "lid18", "lid3d"])
+@pytest.mark.parametrize("case", ["lid32", "pinned16", "oseen32", "lid18", "lid3d", "lid32_loc", "lid3d_loc"])
 def test_ilu_factors_match_oracle(case):
     """The library's ILU(1) setup (smoother = 2) against the oracle's on every smoothed
     level: the same order (natural for Stokes, reverse Cuthill-McKee for Oseen; integer
     work, bit-exact), the same factor patterns and the factors and pivots to rounding.
-    oseen32's coarse level has zero-block pivots that no elimination step reaches."""
+    oseen32's coarse level has zero-block pivots that no elimination step reaches; the
+    _loc cases take the location order (ilu_order = 1)."""
+    loc = case.endswith("_loc")
+    case = case.replace("_loc", "")
     prob = {"lid32": lambda: stokes_lid_2d(32, nrhs=1), "pinned16": lambda: stokes_pinned_2d(16, nrhs=1),
             "oseen32": lambda: oseen_recirculating_2d(32, Re=100.0, nrhs=1),
             "lid18": lambda: make_problem(18, 2, 0.0, 1.0, bc="lid", nrhs=1),
             "lid3d": lambda: make_problem(4, 3, 0.0, 1.0, bc="lid", nrhs=1)}[case]()
-    Ho = setup_hierarchy(prob, Params(smoother="ilu", pre=1, post=1))
-    Hg = g.Hierarchy(prob, host_only=1, smoother=2, pre=1, post=1)
+    Ho = setup_hierarchy(prob, Params(smoother="ilu", pre=1, post=1, ilu_order="location" if loc else "block"))
+    Hg = g.Hierarchy(prob, host_only=1, smoother=2, pre=1, post=1, ilu_order=1 if loc else 0)
     assert Hg.num_levels() == len(Ho.levels)
     for l, L in enumerate(Ho.levels[:-1]):
         F = Hg.level_ilu(l)

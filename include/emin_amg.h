@@ -91,7 +91,7 @@ typedef struct {
   int autotune;       /* 1 (default): before a cycle for K right-hand sides is first captured,
                          time each Gauss-Seidel variant that applies to each level (one block,
                          a thread-block cluster of 2-16 blocks, the pipelined kernel, one launch
-                         per phase, the dense map on levels of <= 2896 pressures) and keep the
+                         per phase, the dense map on levels of <= 4608 pressures) and keep the
                          fastest; 0: fixed choice by level size, sweeps only */
   int smoother;       /* 0 (default): Braess-Sarazin (Section 5.2); 1: Vanka (Section 5.1):
                          overlapping blocks, one per pressure dof (the columns of its row of
@@ -242,7 +242,7 @@ amg_status amg_level_get_ilu(amg_handle h, int level, int* n, long long* nnz_low
 /* The Gauss-Seidel variant the V-cycle (FP32 one if built, else FP64) uses on a
  * level for nrhs right-hand sides: -1 not chosen yet (the cycle for that K has
  * not run), 0 one block, 1 a cluster of *cluster blocks, 2 the pipelined strip
- * kernel, 3 one launch per phase, 4 the dense map (levels of at most 2896
+ * kernel, 3 one launch per phase, 4 the dense map (levels of at most 4608
  * pressures: the iterations' linear map formed at setup by the same sweeps and
  * applied as one dense product); *ms is the time the autotuner measured for one
  * launch (0 without autotuning).  Either output may be NULL. */

@@ -666,18 +666,82 @@ __global__ void __launch_bounds__(kGsBlock) k_gs_cluster(LevelView<T> L, const T
 
 // Dense form of the Gauss-Seidel call on a small level: the gs_iters iterations
 // from dp = 0 in the (strip parity, color, index) order are a fixed linear map of
-// g, dp = M g, with M (n_p x n_p, row-major) formed at setup by the same sweeps.
-// One warp per row i: lane (jsplit, k) sums M[i, j] g[j, k] over j = jsplit,
-// jsplit + 32/K, ..., then the 32/K partial sums of each column are combined.
+// g, dp = M g, with M (n_p x n_p, row-major, rows padded with zeros to ld, a
+// multiple of 16 bytes) formed at setup by the same sweeps.
+//
+// k_gs_dense_tile (K <= 16): a block of kDenseWarps warps takes kDenseRows rows
+// (kDenseRowsPerWarp per warp); g is staged in shared memory kDenseChunk columns at a
+// time.  Lane t takes columns t, t + 32, ... of the chunk: its reads of M are
+// coalesced across the warp, its K values of g are contiguous in shared memory and
+// serve all of the warp's rows.  Streaming M is the bound (about 71 MB in FP32 for
+// 4225 pressures).
+constexpr int kDenseWarps = 4, kDenseRowsPerWarp = 4, kDenseChunk = 256;
+constexpr int kDenseRows = kDenseWarps * kDenseRowsPerWarp;
 template <typename T, int K>
-__global__ void __launch_bounds__(kBlock) k_gs_dense(int n_p, const T* __restrict__ M, const T* __restrict__ g,
-                                                     T* __restrict__ dp) {
+__global__ void __launch_bounds__(kDenseWarps * 32) k_gs_dense_tile(int n_p, int ld, const T* __restrict__ M,
+                                                                    const T* __restrict__ g, T* __restrict__ dp) {
+  constexpr int RW = kDenseRowsPerWarp, CJ = kDenseChunk;
+  constexpr int VG = VecWidth<T, K>::V;
+  __shared__ __align__(16) T s_g[CJ * K];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i0 = blockIdx.x * kDenseRows + warp * RW;
+  const T* Mr[RW];
+#pragma unroll
+  for (int r = 0; r < RW; ++r) Mr[r] = M + (size_t)min(i0 + r, n_p - 1) * ld;  // rows past n_p: read, unused
+  T acc[RW][K];
+#pragma unroll
+  for (int r = 0; r < RW; ++r)
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[r][k] = T(0);
+  for (int c0 = 0; c0 < n_p; c0 += CJ) {
+    const int cn = min(CJ, n_p - c0);
+    __syncthreads();  // the previous chunk is consumed
+    for (int t = threadIdx.x; t < CJ * K; t += blockDim.x) s_g[t] = t < cn * K ? g[(size_t)c0 * K + t] : T(0);
+    __syncthreads();
+    T m[CJ / 32][RW];
+#pragma unroll
+    for (int q = 0; q < CJ / 32; ++q) {
+      const int j = c0 + 32 * q + lane;
+#pragma unroll
+      for (int r = 0; r < RW; ++r) m[q][r] = j < n_p ? Mr[r][j] : T(0);
+    }
+#pragma unroll
+    for (int q = 0; q < CJ / 32; ++q) {
+      const T* gq = s_g + (32 * q + lane) * K;
+#pragma unroll
+      for (int k0 = 0; k0 < K; k0 += VG) {
+        T gv[VG];
+        vld<T, VG>(gv, gq + k0);
+#pragma unroll
+        for (int w = 0; w < VG; ++w)
+#pragma unroll
+          for (int r = 0; r < RW; ++r) acc[r][k0 + w] += m[q][r] * gv[w];
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < RW; ++r)
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      T a = acc[r][k];
+#pragma unroll
+      for (int off = 16; off >= 1; off >>= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
+      if (lane == (r * K + k) % 32 && i0 + r < n_p) dp[(size_t)(i0 + r) * K + k] = a;
+    }
+}
+
+// k_gs_dense (any K, used for K = 32): one warp per row i, lane (jsplit, k) sums
+// M[i, j] g[j, k] over j = jsplit, jsplit + 32/K, ..., then the 32/K partial sums of
+// each column are combined.
+template <typename T, int K>
+__global__ void __launch_bounds__(kBlock) k_gs_dense(int n_p, int ld, const T* __restrict__ M,
+                                                     const T* __restrict__ g, T* __restrict__ dp) {
   constexpr int J = 32 / K;  // row entries a column's lanes split
   const int i = (int)(gtid() >> 5);
   if (i >= n_p) return;
   const int lane = threadIdx.x & 31;
   const int k = lane % K, js = lane / K;
-  const T* Mi = M + (size_t)i * n_p;
+  const T* Mi = M + (size_t)i * ld;
   T a0 = T(0), a1 = T(0);
   int j = js;
   for (; j + J < n_p; j += 2 * J) {

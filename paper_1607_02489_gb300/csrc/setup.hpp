@@ -27,7 +27,7 @@ struct SetupParams {
   const std::vector<struct HostLevel>* reuse = nullptr;
 };
 
-constexpr int kGsDenseMaxRows = 2896;  // dense Gauss-Seidel map: <= 32 MiB in FP32
+constexpr int kGsDenseMaxRows = 4608;  // dense Gauss-Seidel map: <= 81 MiB in FP32
 
 struct HostLevel {
   int dim = 2, n_v = 0, n_p = 0, pinned = -1;

@@ -603,8 +603,12 @@ class DeviceVCycle : public VCycleIface {
       case kGsPhases: launch_gs_fallback<K>(l, s); return true;
       case kGsDense:
         if (!gsM_[l]) return false;
-        k_gs_dense<T, K><<<grid_for((long long)views_[l].n_p * 32), kBlock, 0, s>>>(views_[l].n_p, gsM_[l], buf_[l].g,
-                                                                                   buf_[l].dp);
+        if constexpr (K <= 16)
+          k_gs_dense_tile<T, K><<<(views_[l].n_p + kDenseRows - 1) / kDenseRows, kDenseWarps * 32, 0, s>>>(
+              views_[l].n_p, gs_ld(views_[l].n_p), gsM_[l], buf_[l].g, buf_[l].dp);
+        else
+          k_gs_dense<T, K><<<grid_for((long long)views_[l].n_p * 32), kBlock, 0, s>>>(
+              views_[l].n_p, gs_ld(views_[l].n_p), gsM_[l], buf_[l].g, buf_[l].dp);
         return true;
     }
     return false;
@@ -1167,7 +1171,16 @@ class DeviceVCycle : public VCycleIface {
       plist_.push_back(alloc_copy<int>(plist));
       poff_.push_back(alloc_copy<int>(poff));
       cplans_.push_back(cluster_plans(H.n_p, Tst, ncol, nstrips, soff, So));
-      gsM_.push_back(H.gs_dense.empty() ? nullptr : alloc_copy<T>(H.gs_dense));
+      if (H.gs_dense.empty()) {
+        gsM_.push_back(nullptr);
+      } else {  // rows padded with zeros to gs_ld (aligned 16-byte reads)
+        const size_t ld = gs_ld(H.n_p);
+        std::vector<double> padded((size_t)H.n_p * ld, 0.0);
+        for (int i = 0; i < H.n_p; ++i)
+          std::copy(H.gs_dense.begin() + (size_t)i * H.n_p, H.gs_dense.begin() + (size_t)(i + 1) * H.n_p,
+                    padded.begin() + (size_t)i * ld);
+        gsM_.push_back(alloc_copy<T>(padded));
+      }
     }
     // lanes per Schur row: 4 when rows are long enough to share
     const double avg = H.n_p ? (double)So.nnz() / H.n_p : 0.0;
@@ -1229,7 +1242,11 @@ class DeviceVCycle : public VCycleIface {
   };
   std::vector<VankaLevel> vk_;
   std::shared_ptr<std::vector<int>> vkform_;  // [level * 6 + K slot]: Vanka kernel form, -1 untuned
-  std::vector<T*> gsM_;  // dense Gauss-Seidel map of small levels (nullptr elsewhere)
+  std::vector<T*> gsM_;  // dense Gauss-Seidel map of small levels (nullptr elsewhere), rows of gs_ld
+  static int gs_ld(int n_p) {
+    constexpr int vm = 16 / (int)sizeof(T);
+    return (n_p + vm - 1) / vm * vm;
+  }
   std::shared_ptr<std::vector<GsChoice>> tune_;  // [level * 6 + K slot], shared with clones
   std::shared_ptr<std::vector<int>> rowmap_;     // [(level * 6 + K slot) * classes + class], -1 untuned
   std::vector<long long> s_nnz_;

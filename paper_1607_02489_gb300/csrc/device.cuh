@@ -670,21 +670,22 @@ __global__ void __launch_bounds__(kGsBlock) k_gs_cluster(LevelView<T> L, const T
 // multiple of 16 bytes) formed at setup by the same sweeps.
 //
 // k_gs_dense_tile (K <= 16): a block of kDenseWarps warps takes kDenseRows rows
-// (kDenseRowsPerWarp per warp); g is staged in shared memory kDenseChunk columns at a
-// time.  Lane t takes columns t, t + 32, ... of the chunk: its reads of M are
-// coalesced across the warp, its K values of g are contiguous in shared memory and
-// serve all of the warp's rows.  Streaming M is the bound (about 71 MB in FP32 for
-// 4225 pressures).
-constexpr int kDenseWarps = 4, kDenseRowsPerWarp = 4, kDenseChunk = 256;
+// (kDenseRowsPerWarp per warp).  Lane t takes columns t, t + 32, ...: its reads of M
+// are coalesced across the warp, and its K values of g are contiguous and adjacent to
+// the next lane's, so g (small: it stays in L1) is read coalesced and serves all of
+// the warp's rows.  Each step first issues the reads of M for kDenseSteps columns per
+// lane, then reads g and accumulates, so the loads of M overlap.  No shared memory and
+// no barrier.  Streaming M is the bound (about 71 MB in FP32 for 4225 pressures).
+constexpr int kDenseWarps = 4, kDenseRowsPerWarp = 2, kDenseSteps = 16;
 constexpr int kDenseRows = kDenseWarps * kDenseRowsPerWarp;
 template <typename T, int K>
 __global__ void __launch_bounds__(kDenseWarps * 32) k_gs_dense_tile(int n_p, int ld, const T* __restrict__ M,
                                                                     const T* __restrict__ g, T* __restrict__ dp) {
-  constexpr int RW = kDenseRowsPerWarp, CJ = kDenseChunk;
+  constexpr int RW = kDenseRowsPerWarp, U = kDenseSteps;
   constexpr int VG = VecWidth<T, K>::V;
-  __shared__ __align__(16) T s_g[CJ * K];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int i0 = blockIdx.x * kDenseRows + warp * RW;
+  if (i0 >= n_p) return;
   const T* Mr[RW];
 #pragma unroll
   for (int r = 0; r < RW; ++r) Mr[r] = M + (size_t)min(i0 + r, n_p - 1) * ld;  // rows past n_p: read, unused
@@ -693,29 +694,28 @@ __global__ void __launch_bounds__(kDenseWarps * 32) k_gs_dense_tile(int n_p, int
   for (int r = 0; r < RW; ++r)
 #pragma unroll
     for (int k = 0; k < K; ++k) acc[r][k] = T(0);
-  for (int c0 = 0; c0 < n_p; c0 += CJ) {
-    const int cn = min(CJ, n_p - c0);
-    __syncthreads();  // the previous chunk is consumed
-    for (int t = threadIdx.x; t < CJ * K; t += blockDim.x) s_g[t] = t < cn * K ? g[(size_t)c0 * K + t] : T(0);
-    __syncthreads();
-    T m[CJ / 32][RW];
+  for (int jb = lane; jb < n_p; jb += 32 * U) {
+    T m[U][RW];
 #pragma unroll
-    for (int q = 0; q < CJ / 32; ++q) {
-      const int j = c0 + 32 * q + lane;
+    for (int u = 0; u < U; ++u) {
+      const int j = jb + 32 * u;
 #pragma unroll
-      for (int r = 0; r < RW; ++r) m[q][r] = j < n_p ? Mr[r][j] : T(0);
+      for (int r = 0; r < RW; ++r) m[u][r] = j < n_p ? Mr[r][j] : T(0);
     }
 #pragma unroll
-    for (int q = 0; q < CJ / 32; ++q) {
-      const T* gq = s_g + (32 * q + lane) * K;
+    for (int u = 0; u < U; ++u) {
+      const int j = jb + 32 * u;
+      if (j < n_p) {
+        const T* gj = g + (size_t)j * K;
 #pragma unroll
-      for (int k0 = 0; k0 < K; k0 += VG) {
-        T gv[VG];
-        vld<T, VG>(gv, gq + k0);
+        for (int k0 = 0; k0 < K; k0 += VG) {
+          T gv[VG];
+          vld<T, VG>(gv, gj + k0);
 #pragma unroll
-        for (int w = 0; w < VG; ++w)
+          for (int w = 0; w < VG; ++w)
 #pragma unroll
-          for (int r = 0; r < RW; ++r) acc[r][k0 + w] += m[q][r] * gv[w];
+            for (int r = 0; r < RW; ++r) acc[r][k0 + w] += m[u][r] * gv[w];
+        }
       }
     }
   }

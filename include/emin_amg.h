@@ -109,6 +109,9 @@ typedef struct {
                          [u_x | u_y (| u_z) | p], 1 by node location (lexicographic from the
                          lower-left corner, u_x, u_y (, u_z), p at one node); non-symmetric
                          problems always take reverse Cuthill-McKee */
+  int coarse;         /* coarsest level: 0 (default) FP64 pseudo-inverse (exact minimum-norm
+                         solve); 1 Vanka relaxation as in the paper (Section 6.1): pre + post
+                         Vanka steps (vanka_omega) from zero, whatever the smoother */
 } amg_params;
 
 void amg_params_default(amg_params* prm);
@@ -220,8 +223,8 @@ amg_status amg_level_get_matrix(amg_handle h, int level, int which, long long* r
  * (n_p) and the Braess-Sarazin diagonal D (n_v).  Any pointer may be NULL. */
 amg_status amg_level_get_points(amg_handle h, int level, int* cp, int* cv, int* colors, double* D);
 
-/* The Vanka blocks of a level (hierarchies built with smoother = 1, every level but
- * the coarsest): *nblocks, *ndofs (total dofs over blocks) and *ncolors when the
+/* The Vanka blocks of a level (hierarchies built with smoother = 1: every level but
+ * the coarsest; with coarse = 1: the coarsest): *nblocks, *ndofs (total dofs over blocks) and *ncolors when the
  * arrays are NULL; otherwise ptr (nblocks + 1), dofs (ndofs, global dof indices)
  * and colors (nblocks) are filled.  AMG_ERR_ARG for a level without blocks. */
 amg_status amg_level_get_vanka(amg_handle h, int level, int* nblocks, int* ndofs, int* ncolors, int* ptr,

@@ -21,7 +21,9 @@ tests/test_synth.py):
     paper's worked special cases, invariants, dense brute force, Table 1).
   * vanka.py (Vanka relaxation, Section 5.1): pinned (block definition,
     exact local solves, colored sweep = block-by-block sweep, dense solves,
-    Table 1's Vanka(1,1) counts).
+    Table 1's Vanka(1,1) counts); the coarsest-level Vanka relaxation of
+    Section 6.1 (Params.coarse = "vanka"): pinned (pre + post steps from zero on
+    a one-level hierarchy, dense solves with it).
   * ilu.py (ILU(1) relaxation, Section 5): pinned (L U = A on the kept
     pattern, the level-of-fill rule, exactness without fill, the zero-pivot
     reading on a 3x3 saddle matrix, the error-propagation spectrum, dense

@@ -46,6 +46,8 @@ class Params:
     smoother: str = "bs"          # "bs" Braess-Sarazin (Section 5.2), "vanka" (Section 5.1), "ilu" ILU(1) (Section 5)
     vanka_omega: float = 0.5      # Vanka under-relaxation (Section 6)
     ilu_order: str = "block"      # ILU(1) order of symmetric levels: "block" (the paper's) or "location"
+    coarse: str = "exact"         # coarsest level: "exact" (pseudo-inverse) or "vanka" (pre + post Vanka
+                                  # steps from zero, as the paper relaxes it, Section 6.1)
     max_coarse: int = 200
     max_levels: int = 12
 
@@ -662,6 +664,9 @@ def setup_hierarchy(prob, prm: Params = None, reuse: Hierarchy = None) -> Hierar
         from .vanka import form_vanka
         for L in levels[:-1]:
             form_vanka(L)
+    if prm.coarse == "vanka":
+        from .vanka import form_vanka
+        form_vanka(levels[-1])
     if prm.smoother == "ilu":
         from .ilu import form_ilu
         for L in levels[:-1]:

@@ -98,6 +98,14 @@ def vcycle(H, b, level: int = 0):
     prm = H.params
     L = H.levels[level]
     if level == len(H.levels) - 1:
+        if prm.coarse == "vanka":
+            # the paper's coarsest relaxation (Section 6.1): Vanka steps from zero, as
+            # many as the pre- and post-smoothing of the other levels together
+            from .vanka import vanka_sweep
+            x = np.zeros_like(b)
+            for _ in range(prm.pre + prm.post):
+                x = vanka_sweep(L, prm, b, x)
+            return x
         return coarse_solve(L, b)
     if prm.smoother == "vanka":
         from .vanka import vanka_sweep as sweep

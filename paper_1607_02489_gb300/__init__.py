@@ -50,7 +50,7 @@ class AmgParams(ctypes.Structure):
                 ("post", ctypes.c_int), ("max_coarse", ctypes.c_int), ("max_levels", ctypes.c_int),
                 ("vcycle_fp32", ctypes.c_int), ("max_nrhs", ctypes.c_int), ("host_only", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("smoother", ctypes.c_int), ("vanka_omega", ctypes.c_double),
-                ("ilu_order", ctypes.c_int)]
+                ("ilu_order", ctypes.c_int), ("coarse", ctypes.c_int)]
 
 
 class AmgLevelInfo(ctypes.Structure):

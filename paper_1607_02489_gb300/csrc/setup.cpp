@@ -1146,6 +1146,7 @@ std::vector<HostLevel> build_hierarchy(HostLevel fine, const SetupParams& prm) {
   C.pinv = pseudo_inverse(dense_level(C), C.N(), 1e-12);
   if (prm.vanka)
     for (size_t l = 0; l + 1 < levels.size(); ++l) form_vanka(levels[l], prm);
+  if (prm.vanka_coarse) form_vanka(levels.back(), prm);
   if (prm.ilu)
     for (size_t l = 0; l + 1 < levels.size(); ++l) form_ilu(levels[l], prm.symmetric, prm.ilu_order);
   for (size_t l = 0; l + 1 < levels.size(); ++l)

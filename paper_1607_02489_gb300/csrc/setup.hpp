@@ -17,6 +17,7 @@ struct SetupParams {
   int max_levels = 12;
   bool symmetric = true;   // one EMIN CG step, R = P^T; otherwise EMIN GMRES for P and R
   bool vanka = false;      // form the Vanka smoother's blocks (Section 5.1) on every level but the coarsest
+  bool vanka_coarse = false;  // form them on the coarsest level too (its Vanka relaxation, Section 6.1)
   bool ilu = false;        // form the ILU(1) factors (Section 5) on every level but the coarsest
   int ilu_order = 0;       // symmetric problems: 0 block order [u_x | u_y | p], 1 by node location
   int gs_iters = 5;        // Gauss-Seidel iterations per Braess-Sarazin step (for the dense map)

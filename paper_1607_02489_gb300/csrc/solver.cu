@@ -801,6 +801,7 @@ void amg_params_default(amg_params* p) {
   p->smoother = 0;
   p->vanka_omega = 0.5;
   p->ilu_order = 0;
+  p->coarse = 0;
 }
 
 const char* amg_last_error(void) { return g_last_error.c_str(); }
@@ -856,6 +857,8 @@ amg_status create_impl(const amg_problem* pb, const amg_params* prm_in, void* st
     return fail(AMG_ERR_ARG, "smoother must be 0 (Braess-Sarazin), 1 (Vanka) or 2 (ILU(1))");
   if (prm.smoother == 1 && !(prm.vanka_omega > 0.0)) return fail(AMG_ERR_ARG, "vanka_omega must be positive");
   if (prm.ilu_order != 0 && prm.ilu_order != 1) return fail(AMG_ERR_ARG, "ilu_order must be 0 or 1");
+  if (prm.coarse != 0 && prm.coarse != 1) return fail(AMG_ERR_ARG, "coarse must be 0 (pseudo-inverse) or 1 (Vanka)");
+  if (prm.coarse == 1 && !(prm.vanka_omega > 0.0)) return fail(AMG_ERR_ARG, "vanka_omega must be positive");
   if (pb->pinned_p >= pb->n_pnodes) return fail(AMG_ERR_ARG, "pinned pressure out of range");
   std::string why;
   if (!check_csr(pb->A_rowptr, pb->A_col, pb->n_vnodes, pb->n_vnodes, why)) return fail(AMG_ERR_ARG, "A: " + why);
@@ -887,6 +890,7 @@ amg_status create_impl(const amg_problem* pb, const amg_params* prm_in, void* st
     sp.vanka = prm.smoother == 1;
     sp.ilu = prm.smoother == 2;
     sp.ilu_order = prm.ilu_order;
+    sp.vanka_coarse = prm.coarse == 1;
     sp.gs_iters = prm.gs_iters;
     sp.reuse = reuse ? &reuse->host : nullptr;
     h->host = build_hierarchy(std::move(fine), sp);
@@ -894,10 +898,13 @@ amg_status create_impl(const amg_problem* pb, const amg_params* prm_in, void* st
     h->N = h->host[0].N();
     if (!prm.host_only) {
       const double vomega = prm.smoother == 1 ? prm.vanka_omega : 0.0;
-      h->v64 = make_vcycle_f64(h->host, sp.c, prm.gs_iters, prm.pre, prm.post, round_k(prm.max_nrhs), vomega, sp.ilu);
+      const double comega = prm.coarse == 1 ? prm.vanka_omega : 0.0;
+      h->v64 = make_vcycle_f64(h->host, sp.c, prm.gs_iters, prm.pre, prm.post, round_k(prm.max_nrhs), vomega, sp.ilu,
+                               comega);
       h->v64->set_autotune(prm.autotune != 0);
       if (prm.vcycle_fp32) {
-        h->v32 = make_vcycle_f32(h->host, sp.c, prm.gs_iters, prm.pre, prm.post, round_k(prm.max_nrhs), vomega, sp.ilu);
+        h->v32 = make_vcycle_f32(h->host, sp.c, prm.gs_iters, prm.pre, prm.post, round_k(prm.max_nrhs), vomega,
+                                 sp.ilu, comega);
         h->v32->set_autotune(prm.autotune != 0);
       }
       EMIN_CUDA(cudaStreamSynchronize((cudaStream_t)stream));

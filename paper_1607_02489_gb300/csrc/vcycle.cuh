@@ -90,15 +90,18 @@ class DeviceVCycle : public VCycleIface {
   };
 
   DeviceVCycle(const std::vector<HostLevel>& levels, double cfac, int gs_iters, int pre, int post, int kmax,
-               double vanka_omega = 0.0, bool ilu = false)
+               double vanka_omega = 0.0, bool ilu = false, double coarse_omega = 0.0)
       : c_(cfac), cfac_((T)cfac), gs_iters_(gs_iters), pre_(pre), post_(post), kmax_(kmax),
-        vanka_omega_((T)vanka_omega), ilu_(ilu) {
+        vanka_omega_((T)vanka_omega), ilu_(ilu), coarse_vanka_(coarse_omega > 0.0),
+        vk_omega_((T)(vanka_omega > 0.0 ? vanka_omega : coarse_omega)) {
     try {
       if ((long long)levels[0].N() * kmax_ >= (1LL << 31))
         throw std::runtime_error("N * max_nrhs must stay below 2^31 (32-bit vector indices)");
       for (size_t l = 0; l < levels.size(); ++l) upload_level(levels[l], l + 1 == levels.size());
+      vk_.resize(levels.size());
       if (vanka_omega > 0.0)
-        for (size_t l = 0; l + 1 < levels.size(); ++l) upload_vanka(levels[l]);
+        for (size_t l = 0; l + 1 < levels.size(); ++l) upload_vanka(levels[l], l);
+      if (coarse_vanka_) upload_vanka(levels.back(), levels.size() - 1);
       if (ilu_) {
         for (size_t l = 0; l + 1 < levels.size(); ++l) upload_ilu(levels[l]);
         il_ticket_ = alloc<int>(1);
@@ -229,9 +232,14 @@ class DeviceVCycle : public VCycleIface {
       launch_rows<K>(kRestrict, l, shape(l, K, kRestrict), 0, s);
       mark_end(s);
     }
-    mark_begin(nl - 1, kCoarse, s);  // every kernel launch of the cycle is preceded by mark_begin
-    k_coarse_solve<T, K><<<grid_for((long long)Nc_ * K), kBlock, 0, s>>>(Nc_, pinv_, buf_[nl - 1].b, buf_[nl - 1].x);
-    mark_end(s);
+    if (coarse_vanka_) {
+      // the paper's coarsest relaxation: pre + post Vanka steps from zero
+      for (int sw = 0; sw < std::max(1, pre_ + post_); ++sw) vanka_sweep<K>(nl - 1, sw == 0, s);
+    } else {
+      mark_begin(nl - 1, kCoarse, s);  // every kernel launch of the cycle is preceded by mark_begin
+      k_coarse_solve<T, K><<<grid_for((long long)Nc_ * K), kBlock, 0, s>>>(Nc_, pinv_, buf_[nl - 1].b, buf_[nl - 1].x);
+      mark_end(s);
+    }
     for (int l = nl - 2; l >= 0; --l) {
       mark_begin(l, kProlong, s);
       launch_rows<K>(kProlong, l, shape(l, K, kProlong), 0, s);
@@ -421,25 +429,25 @@ class DeviceVCycle : public VCycleIface {
     if (form == 1 || form == 2) {
       auto kern = form == 1 ? k_vanka_color<T, K, 256> : k_vanka_color<T, K, 1024>;
       if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      kern<<<nb, form == 1 ? 256 : 1024, smem, s>>>(views_[l], V.view, V.coff[c], B.b, B.x, vanka_omega_);
+      kern<<<nb, form == 1 ? 256 : 1024, smem, s>>>(views_[l], V.view, V.coff[c], B.b, B.x, vk_omega_);
     } else {
       auto kern = k_vanka_color_pairs<T, K>;
       if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      kern<<<nb, 128, smem, s>>>(views_[l], V.view, V.coff[c], B.b, B.x, vanka_omega_);
+      kern<<<nb, 128, smem, s>>>(views_[l], V.view, V.coff[c], B.b, B.x, vk_omega_);
     }
   }
   // Vanka autotuner: each form timed on a whole step of each level (CUDA events),
   // the fastest kept in a table shared with the clones.
   template <int K>
   void tune_vanka(cudaStream_t s) {
-    if (!(vanka_omega_ > T(0))) return;
+    if (!(vanka_omega_ > T(0)) && !coarse_vanka_) return;
     const int ks = kslot(K);
     cudaEvent_t e0, e1;
     EMIN_CUDA(cudaEventCreate(&e0));
     EMIN_CUDA(cudaEventCreate(&e1));
     for (int l = 0; l < (int)vk_.size(); ++l) {
       int& slot = (*vkform_)[(size_t)l * 6 + ks];
-      if (slot >= 0) continue;
+      if (slot >= 0 || vk_[l].coff.empty()) continue;  // tuned, or a level without Vanka blocks
       int best = 0;
       float best_ms = 1e30f;
       for (int form = 0; form < 3; ++form) {
@@ -945,7 +953,7 @@ class DeviceVCycle : public VCycleIface {
   struct CloneTag {};
   DeviceVCycle(const DeviceVCycle& o, int kmax, CloneTag)
       : c_(o.c_), cfac_(o.cfac_), gs_iters_(o.gs_iters_), pre_(o.pre_), post_(o.post_), kmax_(kmax),
-        vanka_omega_(o.vanka_omega_), ilu_(o.ilu_) {
+        vanka_omega_(o.vanka_omega_), ilu_(o.ilu_), coarse_vanka_(o.coarse_vanka_), vk_omega_(o.vk_omega_) {
     try {
       if ((long long)((size_t)o.views_[0].dim * o.views_[0].n_v + o.views_[0].n_p) * kmax_ >= (1LL << 31))
         throw std::runtime_error("N * max_nrhs must stay below 2^31 (32-bit vector indices)");
@@ -1036,7 +1044,7 @@ class DeviceVCycle : public VCycleIface {
     return plans;
   }
 
-  void upload_vanka(const HostLevel& H) {
+  void upload_vanka(const HostLevel& H, size_t level) {
     if (H.vk_ptr.empty()) throw std::runtime_error("the hierarchy was built without the Vanka blocks");
     const int nb = (int)H.vk_ptr.size() - 1;
     VankaLevel V;
@@ -1057,7 +1065,7 @@ class DeviceVCycle : public VCycleIface {
     V.view.order = alloc_copy<int>(order);
     V.dirichlet = alloc_copy<int>(H.vk_dirichlet);
     V.n_dirichlet = (int)H.vk_dirichlet.size();
-    vk_.push_back(V);
+    vk_[level] = V;
   }
 
   // ILU(1) factors of a level.  Grid: about four warps per row of an average
@@ -1215,6 +1223,8 @@ class DeviceVCycle : public VCycleIface {
   int gs_iters_, pre_, post_, kmax_;
   T vanka_omega_ = T(0);  // > 0: the Vanka smoother replaces Braess-Sarazin
   bool ilu_ = false;      // ILU(1) replaces Braess-Sarazin
+  bool coarse_vanka_ = false;  // Vanka relaxation instead of the pseudo-inverse on the coarsest level
+  T vk_omega_ = T(0);          // the Vanka under-relaxation, wherever Vanka runs
   struct IluLevel {
     IluView<T> view{};
     int depthL = 0, depthU = 0, blocks = 1;  // blocks: the untuned grid
@@ -1240,7 +1250,7 @@ class DeviceVCycle : public VCycleIface {
     const int* dirichlet = nullptr;
     int n_dirichlet = 0, max_block = 0;
   };
-  std::vector<VankaLevel> vk_;
+  std::vector<VankaLevel> vk_;  // one per level; empty (no blocks) where Vanka does not run
   std::shared_ptr<std::vector<int>> vkform_;  // [level * 6 + K slot]: Vanka kernel form, -1 untuned
   std::vector<T*> gsM_;  // dense Gauss-Seidel map of small levels (nullptr elsewhere), rows of gs_ld
   static int gs_ld(int n_p) {
@@ -1265,11 +1275,13 @@ class DeviceVCycle : public VCycleIface {
 
 // Factories, one translation unit per type.
 // vanka_omega > 0 smooths with Vanka (the levels must carry the Vanka blocks), ilu with
-// ILU(1) (the levels must carry the factors), else Braess-Sarazin.
+// ILU(1) (the levels must carry the factors), else Braess-Sarazin; coarse_omega > 0
+// relaxes the coarsest level with Vanka (it must carry the blocks) instead of the
+// pseudo-inverse.
 VCycleIface* make_vcycle_f64(const std::vector<HostLevel>& levels, double cfac, int gs, int pre, int post, int kmax,
-                             double vanka_omega, bool ilu);
+                             double vanka_omega, bool ilu, double coarse_omega);
 VCycleIface* make_vcycle_f32(const std::vector<HostLevel>& levels, double cfac, int gs, int pre, int post, int kmax,
-                             double vanka_omega, bool ilu);
+                             double vanka_omega, bool ilu, double coarse_omega);
 // Finest-level FP64 block product out = A x (TX = double or float), or out = b - A x.
 cudaError_t apply_finest_f64(VCycleIface* v64, const void* x, bool x_fp32, const double* b, double* out, int K,
                              cudaStream_t s);

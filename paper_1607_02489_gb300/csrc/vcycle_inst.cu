@@ -8,8 +8,8 @@ namespace emin {
 #ifdef EMIN_VCYCLE_DOUBLE
 
 VCycleIface* make_vcycle_f64(const std::vector<HostLevel>& levels, double cfac, int gs, int pre, int post, int kmax,
-                             double vanka_omega, bool ilu) {
-  return new DeviceVCycle<double>(levels, cfac, gs, pre, post, kmax, vanka_omega, ilu);
+                             double vanka_omega, bool ilu, double coarse_omega) {
+  return new DeviceVCycle<double>(levels, cfac, gs, pre, post, kmax, vanka_omega, ilu, coarse_omega);
 }
 
 template <int K>
@@ -42,8 +42,8 @@ cudaError_t apply_finest_f64(VCycleIface* v64, const void* x, bool x_fp32, const
 #else
 
 VCycleIface* make_vcycle_f32(const std::vector<HostLevel>& levels, double cfac, int gs, int pre, int post, int kmax,
-                             double vanka_omega, bool ilu) {
-  return new DeviceVCycle<float>(levels, cfac, gs, pre, post, kmax, vanka_omega, ilu);
+                             double vanka_omega, bool ilu, double coarse_omega) {
+  return new DeviceVCycle<float>(levels, cfac, gs, pre, post, kmax, vanka_omega, ilu, coarse_omega);
 }
 
 #endif

@@ -108,3 +108,33 @@ def test_vanka_profile_counts_its_launches():
     v = g.KERNEL_CLASSES.index("vanka")
     gs = g.KERNEL_CLASSES.index("gs_color")
     assert cnt[0, v] > 0 and cnt[:, gs].sum() == 0
+
+
+@pytest.mark.parametrize("case", ["pinned16", "lid32", "oseen32"])
+@pytest.mark.parametrize("smoother", ["bs", "vanka"])
+def test_coarsest_vanka_relaxation_matches_oracle(case, smoother):
+    """amg_params.coarse = 1 (the paper's Vanka relaxation of the coarsest level instead of
+    a direct solve): the FP64 V-cycle against the oracle's to 1e-11 and FGMRES within +-1."""
+    p = CASES[case]()
+    if smoother == "vanka":
+        Ho = setup_hierarchy(p, Params(smoother="vanka", pre=1, post=1, coarse="vanka"))
+        Hg = g.Hierarchy(p, max_nrhs=p.b.shape[1], coarse=1, **VK)
+    else:
+        Ho = setup_hierarchy(p, Params(coarse="vanka"))
+        Hg = g.Hierarchy(p, max_nrhs=p.b.shape[1], coarse=1)
+    r = uniform_pm1(35, p.N * p.b.shape[1]).reshape(p.N, -1)
+    zo = vcycle(Ho, r)
+    rt = torch.tensor(r, device="cuda")
+    zt = torch.empty_like(rt)
+    Hg.vcycle(rt, zt)
+    torch.cuda.synchronize()
+    err = _relerr(zt.cpu().numpy(), zo)
+    assert np.all(err <= 1e-11), err
+    _, its_o, _, _ = fgmres(Ho, p.b, rtol=1e-8)
+    bt = torch.tensor(p.b, device="cuda")
+    xt = torch.zeros_like(bt)
+    st, its, rel = Hg.fgmres(bt, xt, rtol=1e-8, restart=100, maxit=300)
+    assert st == g.AMG_OK and np.all(np.abs(its - its_o) <= 1), (its, its_o)
+    ms, cnt = Hg.profile_vcycle(p.b.shape[1], reps=1)
+    v, c = g.KERNEL_CLASSES.index("vanka"), g.KERNEL_CLASSES.index("coarse")
+    assert cnt[-1, v] > 0 and cnt[:, c].sum() == 0

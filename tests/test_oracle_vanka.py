@@ -8,7 +8,7 @@ import pytest
 import scipy.sparse as sp
 
 from synth import make_problem, oseen_recirculating_2d, stokes_lid_2d, stokes_pinned_2d, uniform_pm1
-from oracle import Params, fgmres, setup_hierarchy
+from oracle import Params, fgmres, setup_hierarchy, vcycle
 from oracle.vanka import vanka_sweep, vanka_sweep_sequential
 
 VANKA = dict(smoother="vanka", pre=1, post=1)
@@ -145,3 +145,41 @@ def test_table1_vanka_iterations(n, paper_its):
     x, its, rel, _ = fgmres(H, p.b, rtol=1e-6)
     assert its[0] <= 1.25 * paper_its, (its, paper_its)
     assert its[0] >= 0.6 * paper_its, (its, paper_its)
+
+
+@pytest.mark.parametrize("case", ["pinned", "lid", "oseen"])
+@pytest.mark.parametrize("smoother", ["bs", "vanka"])
+def test_coarsest_vanka_relaxation_fgmres_equals_dense_solve(case, smoother):
+    """The paper's coarsest treatment (Section 6.1: Vanka relaxation instead of a direct
+    solve), Params.coarse = "vanka": FGMRES with that preconditioner still reaches the
+    dense solution (it is a fixed linear preconditioner)."""
+    n = 4
+    p = {"pinned": lambda: stokes_pinned_2d(n, nrhs=2), "lid": lambda: stokes_lid_2d(n, nrhs=2),
+         "oseen": lambda: oseen_recirculating_2d(n, Re=10.0, nrhs=2)}[case]()
+    prm = Params(smoother=smoother, pre=1, post=1, coarse="vanka") if smoother == "vanka" else Params(coarse="vanka")
+    H = setup_hierarchy(p, prm)
+    x, its, rel, _ = fgmres(H, p.b, rtol=1e-12, maxit=400)
+    A = p.full_matrix().toarray()
+    xd = np.linalg.lstsq(A, p.b, rcond=None)[0]
+    nu = p.dim * p.n_v
+    if p.pinned < 0:
+        x = x.copy()
+        x[nu:] -= x[nu:].mean(axis=0)
+        xd[nu:] -= xd[nu:].mean(axis=0)
+    assert np.all(np.linalg.norm(x - xd, axis=0) <= 1e-9 * np.linalg.norm(xd, axis=0))
+
+
+def test_coarsest_vanka_relaxation_is_pre_plus_post_steps_from_zero():
+    """On a one-level hierarchy the cycle is the coarsest treatment alone: pre + post
+    Vanka steps from x = 0, which contract the error of the coarsest system."""
+    p = stokes_pinned_2d(2, nrhs=1)
+    H = setup_hierarchy(p, Params(smoother="vanka", pre=1, post=2, coarse="vanka"))
+    assert len(H.levels) == 1
+    L = H.levels[0]
+    b = p.b
+    x = np.zeros_like(b)
+    for _ in range(3):
+        x = vanka_sweep(L, H.params, b, x)
+    assert np.array_equal(vcycle(H, b), x)
+    xd = np.linalg.solve(p.full_matrix().toarray(), b)
+    assert np.linalg.norm(x - xd) < 0.9 * np.linalg.norm(xd)

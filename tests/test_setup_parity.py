@@ -151,6 +151,27 @@ def test_vanka_blocks_and_colors_match_oracle(case):
         Hg.level_vanka(len(Ho.levels) - 1)
 
 
+@pytest.mark.parametrize("case", ["lid32", "pinned16", "oseen32"])
+def test_coarsest_vanka_blocks_match_oracle(case):
+    """coarse = 1 (the paper's Vanka relaxation of the coarsest level): the coarsest level
+    carries the same blocks and colors as the oracle's, with either smoother."""
+    from synth import stokes_pinned_2d, oseen_recirculating_2d
+    prob = {"lid32": lambda: stokes_lid_2d(32, nrhs=1), "pinned16": lambda: stokes_pinned_2d(16, nrhs=1),
+            "oseen32": lambda: oseen_recirculating_2d(32, Re=100.0, nrhs=1)}[case]()
+    Ho = setup_hierarchy(prob, Params(coarse="vanka"))
+    Hg = g.Hierarchy(prob, host_only=1, coarse=1)
+    c = len(Ho.levels) - 1
+    assert Hg.num_levels() == c + 1
+    V = Hg.level_vanka(c)
+    blocks = Ho.levels[c].vanka["blocks"]
+    assert len(V["ptr"]) - 1 == len(blocks)
+    for b, T in enumerate(blocks):
+        assert np.array_equal(V["dofs"][V["ptr"][b]:V["ptr"][b + 1]], T), b
+    assert np.array_equal(V["colors"], Ho.levels[c].vanka["colors"])
+    with pytest.raises(g.AmgError):
+        Hg.level_vanka(0)   # Braess-Sarazin levels carry no blocks
+
+
 
 def test_reused_coarsening_matches_oracle():
     """amg_hierarchy_create_reuse against the oracle's reuse: the coarsening of one Oseen

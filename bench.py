@@ -118,7 +118,9 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------
-# algorithmic bytes per kernel launch (the per-unit figures are in the design doc)
+# algorithmic bytes per kernel launch: each kernel's compulsory reads and writes (matrix
+# values and column indices once, the vectors it gathers K values per entry from, and the
+# vectors it reads and writes once per row), as the formulas below state
 
 def algorithmic_bytes(H, level, cls, K, s, zero_fraction=0.25):
     """Compulsory bytes of one launch of kernel class `cls` on `level`: each matrix

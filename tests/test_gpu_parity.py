@@ -1,6 +1,8 @@
 """GPU parity: the CUDA path through the C ABI against the FP64 oracle.
 
-Tolerances (written here, derived in the design doc):
+Tolerances (from the arithmetic: a V-cycle is a fixed sequence of sums, so FP64 results
+agree to a small multiple of the unit roundoff times the operators' conditioning; the
+coarsest solve contributes kappa u):
   * FP64 V-cycle: relative 2-norm error <= 1e-11 per application and column;
   * block product A x: <= 1e-13;
   * FP32 V-cycle: <= 1e-4 (single precision through a few levels of smoothing);

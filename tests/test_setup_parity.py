@@ -233,3 +233,23 @@ def test_ilu_factors_match_oracle(case):
         assert F["depth_lower"] >= 1 and F["depth_upper"] >= 1
     with pytest.raises(g.AmgError):
         Hg.level_ilu(len(Ho.levels) - 1)
+
+
+@pytest.mark.parametrize("case", ["lid16", "oseen16"])
+def test_ilu_substitution_depths_are_the_longest_dependency_chains(case):
+    """The substitutions hand out rows by (dependency level, position); their depths are
+    the longest chains of the factors' dependencies (row i after every column j of its
+    row in L, or in U for the backward pass), recomputed here from the exported factors."""
+    prob = stokes_lid_2d(16, nrhs=1) if case == "lid16" else oseen_recirculating_2d(16, Re=50.0, nrhs=1)
+    Hg = g.Hierarchy(prob, host_only=1, smoother=2, pre=1, post=1)
+    for l in range(Hg.num_levels() - 1):
+        F = Hg.level_ilu(l)
+        n = len(F["perm"])
+        for (ptr, col, _), lower, depth in ((F["lower"], True, F["depth_lower"]),
+                                            (F["upper"], False, F["depth_upper"])):
+            lev = np.zeros(n, dtype=np.int64)
+            for i in (range(n) if lower else range(n - 1, -1, -1)):
+                c = col[ptr[i]:ptr[i + 1]]
+                assert np.all(c < i) if lower else np.all(c > i)
+                lev[i] = lev[c].max() + 1 if len(c) else 0
+            assert depth == lev.max() + 1, (l, lower, depth, lev.max() + 1)

@@ -361,7 +361,8 @@ class FgmresTask final : public SolveTask {
         phase_ = kStep;
         return true;
       case kStep:
-        if (w_->host_i[1] != 0) throw std::runtime_error("cuda: a Gauss-Seidel wait timed out");
+        if (w_->host_i[1] != 0)
+          throw std::runtime_error("cuda: a bounded device wait timed out (Gauss-Seidel strips or ILU substitution)");
         if (w_->host_i[0] == 0) {
           ++j_;
           end_cycle();

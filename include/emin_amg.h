@@ -111,7 +111,10 @@ typedef struct {
                          problems always take reverse Cuthill-McKee */
   int coarse;         /* coarsest level: 0 (default) FP64 pseudo-inverse (exact minimum-norm
                          solve); 1 Vanka relaxation as in the paper (Section 6.1): pre + post
-                         Vanka steps (vanka_omega) from zero, whatever the smoother */
+                         Vanka steps (vanka_omega) from zero, whatever the smoother; setup
+                         fails (AMG_ERR_SETUP) when a coarsest Vanka block is numerically
+                         singular, as on a coarsest level that keeps only the constant
+                         pressure (the 256x256 and 8^3 lid cavities' do) */
 } amg_params;
 
 void amg_params_default(amg_params* prm);

@@ -70,7 +70,14 @@ def form_vanka(L):
     M = sp.csr_matrix(L.full_matrix())
     blocks, dirichlet = vanka_blocks(L)
     colors = vanka_colors(M, blocks)
-    inv = [np.linalg.inv(M[T][:, T].toarray()) for T in blocks]
+    inv = []
+    for T in blocks:
+        MT = M[T][:, T].toarray()
+        # a numerically singular local matrix (its pressures carry no coupling, as on a
+        # coarsest level that keeps only the constant pressure) has no Vanka step
+        if np.linalg.cond(MT) > 1.0 / (len(T) * np.finfo(float).eps):
+            raise ValueError("a Vanka block matrix is singular")
+        inv.append(np.linalg.inv(MT))
     L.vanka = dict(blocks=blocks, colors=colors, inv=inv, dirichlet=dirichlet, M=M)
 
 

@@ -740,8 +740,12 @@ void block_matrix_row(const HostLevel& L, int q, F&& f) {
 }
 
 // In-place inverse of a dense n x n row-major matrix by Gauss-Jordan elimination
-// with partial pivoting; false if a pivot vanishes.
+// with partial pivoting; false if the matrix is numerically singular: a pivot at
+// most n * eps times the largest entry of the matrix.
 bool invert_dense(std::vector<double>& a, int n) {
+  double amax = 0.0;
+  for (double v : a) amax = std::max(amax, std::fabs(v));
+  const double tiny = n * std::numeric_limits<double>::epsilon() * amax;
   std::vector<int> piv(n);
   for (int i = 0; i < n; ++i) piv[i] = i;
   std::vector<double> inv((size_t)n * n, 0.0);
@@ -750,7 +754,7 @@ bool invert_dense(std::vector<double>& a, int n) {
     int best = col;
     for (int r = col + 1; r < n; ++r)
       if (std::fabs(a[(size_t)r * n + col]) > std::fabs(a[(size_t)best * n + col])) best = r;
-    if (a[(size_t)best * n + col] == 0.0) return false;
+    if (!(std::fabs(a[(size_t)best * n + col]) > tiny)) return false;
     if (best != col)
       for (int k = 0; k < n; ++k) {
         std::swap(a[(size_t)best * n + k], a[(size_t)col * n + k]);
@@ -873,7 +877,9 @@ void form_vanka(HostLevel& L, const SetupParams& prm) {
         block_matrix_row(L, L.vk_dofs[p0 + j], [&](int v, double val) {
           if (loc[v] >= 0) a[(size_t)j * m + loc[v]] += val;
         });
-      if (!invert_dense(a, m)) failure = "a Vanka block matrix is singular";
+      if (!invert_dense(a, m))
+        failure = "a Vanka block matrix is singular (a level whose pressures carry no coupling, such as a "
+                  "coarsest level that keeps only the constant pressure, has no Vanka step)";
       std::copy(a.begin(), a.end(), L.vk_inv.begin() + L.vk_inv_off[b]);
       for (int j = 0; j < m; ++j) loc[L.vk_dofs[p0 + j]] = -1;
     }

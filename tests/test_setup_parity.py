@@ -253,3 +253,16 @@ def test_ilu_substitution_depths_are_the_longest_dependency_chains(case):
                 assert np.all(c < i) if lower else np.all(c > i)
                 lev[i] = lev[c].max() + 1 if len(c) else 0
             assert depth == lev.max() + 1, (l, lower, depth, lev.max() + 1)
+
+
+def test_coarsest_vanka_refuses_a_level_without_pressure_coupling():
+    """A coarsest level that keeps only the constant pressure (the 8^3 lid cube's) has B = 0
+    to rounding: its Vanka block is singular, so coarse = 1 is refused at setup by the
+    library (AMG_ERR_SETUP) and by the oracle, instead of diverging."""
+    p = make_problem(8, 3, 0.0, 1.0, bc="lid", nrhs=1)
+    with pytest.raises(g.AmgError) as e:
+        g.Hierarchy(p, host_only=1, coarse=1)
+    assert e.value.status == -4 and "singular" in str(e.value)
+    with pytest.raises(ValueError):
+        setup_hierarchy(p, Params(coarse="vanka"))
+    assert g.Hierarchy(p, host_only=1).num_levels() >= 2      # the default coarsest solve is fine

@@ -111,10 +111,11 @@ typedef struct {
                          problems always take reverse Cuthill-McKee */
   int coarse;         /* coarsest level: 0 (default) FP64 pseudo-inverse (exact minimum-norm
                          solve); 1 Vanka relaxation as in the paper (Section 6.1): pre + post
-                         Vanka steps (vanka_omega) from zero, whatever the smoother; setup
-                         fails (AMG_ERR_SETUP) when a coarsest Vanka block is numerically
-                         singular, as on a coarsest level that keeps only the constant
-                         pressure (the 256x256 and 8^3 lid cavities' do) */
+                         Vanka steps (vanka_omega) from zero, whatever the smoother; coarsening
+                         then stops before a level that would keep only one pressure (the
+                         constant, whose B vanishes: no Vanka step exists there), and setup
+                         fails (AMG_ERR_SETUP) if a coarsest Vanka block is still numerically
+                         singular (e.g. coarsening reused from a hierarchy built without it) */
 } amg_params;
 
 void amg_params_default(amg_params* prm);

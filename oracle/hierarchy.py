@@ -658,6 +658,12 @@ def setup_hierarchy(prob, prm: Params = None, reuse: Hierarchy = None) -> Hierar
         if Lc is None or Lc.N >= L.N:
             L.P = L.Pp = L.R = L.Rp = None
             break
+        if prm.coarse == "vanka" and Lc.n_p <= 1:
+            # the coarsest level is relaxed with Vanka (Section 6.1): a level keeping only
+            # one pressure (the constant, whose B vanishes) has no Vanka step, so the
+            # current level stays the coarsest
+            L.P = L.Pp = L.R = L.Rp = None
+            break
         levels.append(Lc)
     form_coarse_solve(levels[-1])
     if prm.smoother == "vanka":

@@ -1139,7 +1139,9 @@ std::vector<HostLevel> build_hierarchy(HostLevel fine, const SetupParams& prm) {
     }
     if (L.N() <= prm.max_coarse || (int)levels.size() == prm.max_levels) break;
     HostLevel Lc;
-    if (!form_interpolation(L, Lc, prm) || Lc.N() >= L.N()) {
+    // with the coarsest level relaxed by Vanka, a level keeping only one pressure (the
+    // constant, whose B vanishes) has no Vanka step: the current level stays the coarsest
+    if (!form_interpolation(L, Lc, prm) || Lc.N() >= L.N() || (prm.vanka_coarse && Lc.n_p <= 1)) {
       L.P = L.Pp = L.R = L.Rp = Csr();
       L.Cp.clear();
       L.Cv.clear();

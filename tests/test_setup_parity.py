@@ -255,14 +255,34 @@ def test_ilu_substitution_depths_are_the_longest_dependency_chains(case):
             assert depth == lev.max() + 1, (l, lower, depth, lev.max() + 1)
 
 
-def test_coarsest_vanka_refuses_a_level_without_pressure_coupling():
-    """A coarsest level that keeps only the constant pressure (the 8^3 lid cube's) has B = 0
-    to rounding: its Vanka block is singular, so coarse = 1 is refused at setup by the
-    library (AMG_ERR_SETUP) and by the oracle, instead of diverging."""
+def test_coarsest_vanka_stops_before_a_level_without_pressure_coupling():
+    """A level keeping only the constant pressure (the 8^3 lid cube's third level) has B = 0 to
+    rounding and a singular Vanka block.  With coarse = 1, coarsening stops before it (library
+    and oracle alike); a hierarchy that still ends on such a level (here: coarsening reused from
+    one built without the rule) is refused at setup (AMG_ERR_SETUP; the oracle raises)."""
     p = make_problem(8, 3, 0.0, 1.0, bc="lid", nrhs=1)
+    H0 = g.Hierarchy(p, host_only=1)
+    Ho0 = setup_hierarchy(p)
+    assert H0.level_info(H0.num_levels() - 1)["n_p"] == 1 and Ho0.levels[-1].n_p == 1
+    Hg = g.Hierarchy(p, host_only=1, coarse=1)
+    Ho = setup_hierarchy(p, Params(coarse="vanka"))
+    assert Hg.num_levels() == len(Ho.levels) == H0.num_levels() - 1
+    assert Hg.level_info(Hg.num_levels() - 1)["n_p"] == Ho.levels[-1].n_p > 1
+    V = Hg.level_vanka(Hg.num_levels() - 1)
+    assert np.array_equal(V["colors"], Ho.levels[-1].vanka["colors"])
     with pytest.raises(g.AmgError) as e:
-        g.Hierarchy(p, host_only=1, coarse=1)
+        g.Hierarchy(p, host_only=1, coarse=1, reuse=H0)
     assert e.value.status == -4 and "singular" in str(e.value)
     with pytest.raises(ValueError):
-        setup_hierarchy(p, Params(coarse="vanka"))
-    assert g.Hierarchy(p, host_only=1).num_levels() >= 2      # the default coarsest solve is fine
+        setup_hierarchy(p, Params(coarse="vanka"), reuse=Ho0)
+
+
+def test_coarsest_vanka_hierarchy_at_256_matches_oracle():
+    """The 256x256 lid cavity with coarse = 1: coarsening stops at the 301-dof level (15
+    pressures) instead of the 23-dof one-pressure level, in the library as in the oracle."""
+    p = stokes_lid_2d(256, nrhs=1)
+    Hg = g.Hierarchy(p, host_only=1, coarse=1)
+    Ho = setup_hierarchy(p, Params(coarse="vanka"))
+    assert Hg.num_levels() == len(Ho.levels) == 4
+    c = Hg.level_info(3)
+    assert (c["n_v"], c["n_p"]) == (Ho.levels[3].n_v, Ho.levels[3].n_p) == (143, 15)

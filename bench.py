@@ -141,9 +141,11 @@ def algorithmic_bytes(H, level, cls, K, s, zero_fraction=0.25):
     if cls == "schur_rhs":
         return mat(info["nnz_B"], np_) + vec(d * nv) + 2 * vec(np_)
     if cls == "gs_color":
-        # one fused launch = gs_iters Gauss-Seidel iterations over all colors
+        # one fused launch = gs_iters Gauss-Seidel iterations over all colors: every pass
+        # reads the matrix (off-diagonal entries, row pointers, 1/S_ii and the row order),
+        # while the vector operands g (read) and dp (read and written) count once per launch
         nnz_off = info["nnz_S"] - np_
-        return H.params.gs_iters * (mat(nnz_off, np_) + np_ * (4 + s) + 3 * vec(np_))
+        return H.params.gs_iters * (mat(nnz_off, np_) + np_ * (4 + s)) + 3 * vec(np_)
     if cls == "update":
         return mat(info["nnz_Bt"], d * nv) + nv * s + vec(d * nv) + 2 * vec(np_) + vec(N)
     if cls == "residual":

@@ -49,9 +49,9 @@ typedef enum {
  * row, no duplicate entries.  The library copies what it needs during
  * amg_hierarchy_create; the caller may free these afterwards.
  * Section 2 (eq. stokes_block_system, ns_block_system) defines A and B; the
- * coordinates and the pressure-to-velocity co-location are the inputs Alg. 1
- * and Alg. 4 rely on (Section 4: "our algorithms rely on coordinate
- * locations"; Section 4.2: co-located velocities). */
+ * node coordinates and the pressure-to-velocity co-location are inputs of the
+ * coarsening (Section 4 uses coordinates in its distance heuristics, Alg. 3;
+ * Section 4.2 maps coarse pressures to co-located velocities, Alg. 4). */
 typedef struct {
   int dim;                         /* 2 or 3 */
   int n_vnodes;                    /* n_v: velocity nodes per component */
@@ -133,8 +133,8 @@ amg_status amg_hierarchy_create(const amg_problem* prob, const amg_params* prm, 
  * velocities (Alg. 3-4) and the sparsity patterns of the transfers are taken from
  * prev, and filtering, the EMIN steps, restriction, the Galerkin products, the
  * smoother data and the coarsest solve are redone on the new values (Section 6.1:
- * the graph phase dominates setup and "can be performed just once over a sequence
- * associated with a nonlinear solve").  prev stays valid and independent. */
+ * the graph phase dominates setup, and the paper notes that one graph coarsening can
+ * serve every linear system of a nonlinear solve).  prev stays valid and independent. */
 amg_status amg_hierarchy_create_reuse(amg_handle prev, const amg_problem* problem, const amg_params* params,
                                       void* stream, amg_handle* out);
 
@@ -166,7 +166,8 @@ amg_status amg_apply(amg_handle h, const double* x, double* y, int nrhs, void* s
 amg_status amg_apply_noalloc(amg_handle h, const double* x, double* y, int nrhs, void* stream);
 
 /* Right-preconditioned flexible GMRES with the V-cycle as preconditioner
- * (Section 6: "multigrid-preconditioned GMRES"), FP64 Arnoldi (classical
+ * (Section 6 solves every system with GMRES preconditioned by the multigrid
+ * cycle), FP64 Arnoldi (classical
  * Gram-Schmidt with one re-orthogonalisation) and Givens rotations on the
  * device, x0 = 0, restarted every `restart` iterations, stopped per column when
  * ||b - A x|| / ||b|| <= rtol (the recurrence residual, then checked with the
@@ -245,6 +246,25 @@ amg_status amg_level_get_vanka(amg_handle h, int level, int* nblocks, int* ndofs
 amg_status amg_level_get_ilu(amg_handle h, int level, int* n, long long* nnz_lower, long long* nnz_upper,
                              int* depth_lower, int* depth_upper, int* perm, int* lower_ptr, int* lower_col,
                              double* lower_val, int* upper_ptr, int* upper_col, double* upper_val, double* pivots);
+
+/* The coarsest level's FP64 pseudo-inverse X (N_c x N_c, row-major, N_c the N of
+ * the last level), which the coarsest solve applies: the minimum-norm solution of
+ * the (possibly singular) coarsest system, formed at setup by a one-sided Jacobi
+ * SVD with singular values below 1e-12 of the largest dropped, then (N_c <= 512, so
+ * always with the default max_coarse) refined by two Newton-Schulz steps
+ * X <- X + X (I - A X) whose residual is summed in about twice the working
+ * precision.  *n gets N_c; X (N_c * N_c doubles) may be NULL. */
+amg_status amg_coarse_inverse(amg_handle h, int* n, double* X);
+
+/* Bounded waits (the pipelined Gauss-Seidel kernel's waits on neighbouring strips,
+ * the ILU(1) substitutions' waits on earlier rows) give up after this many polls,
+ * set the cycle's error word and return, so a kernel always ends; the solve then
+ * returns AMG_ERR_CUDA ("a bounded device wait timed out").  polls <= 0 restores
+ * the default of 2^24 polls (seconds).  A low limit makes waits run out on purpose
+ * (tests of the failure path); results of a cycle whose wait ran out are not
+ * meaningful.  Applies to the handle's own cycles (not to a server's clones), and
+ * every solve clears the error word when it starts.  Synchronous. */
+amg_status amg_set_wait_limit(amg_handle h, long long polls);
 
 /* The Gauss-Seidel variant the V-cycle (FP32 one if built, else FP64) uses on a
  * level for nrhs right-hand sides: -1 not chosen yet (the cycle for that K has

@@ -552,9 +552,21 @@ def form_coarse_solve(L: Level, rcond: float = 1e-12):
     solution, and the pseudo-inverse takes the one orthogonal to the null
     space (the constant pressure, plus any spurious pressure mode of a very
     small, inf-sup unstable coarsest level).  A nonsingular coarsest level
-    (a pinned fine pressure) gets its plain inverse."""
+    (a pinned fine pressure) gets its plain inverse.
+
+    The SVD gives A^+ only to about cond(A) times the unit roundoff in the
+    directions of small singular values (the pinned problem's levels have
+    cond ~ 1e7).  On coarsest levels of at most 512 dofs (every hierarchy with
+    the default max_coarse), two steps of X <- X + X (I - A X) with the residual
+    I - A X formed in extended precision (numpy's longdouble) bring X to working
+    accuracy; X R stays in X's row space, so dropped directions stay dropped."""
     A = L.full_matrix().toarray()
-    L.coarse_pinv = np.linalg.pinv(A, rcond=rcond)
+    X = np.linalg.pinv(A, rcond=rcond)
+    Al = A.astype(np.longdouble)
+    for _ in range(2 if A.shape[0] <= 512 else 0):
+        R = (np.eye(A.shape[0], dtype=np.longdouble) - Al @ X.astype(np.longdouble)).astype(np.float64)
+        X = X + X @ R
+    L.coarse_pinv = X
 
 
 # ----------------------------------------------------------------------------

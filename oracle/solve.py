@@ -27,8 +27,9 @@ def apply_A(L, x):
 
 
 def gauss_seidel(L, g, iters: int):
-    """`iters` forward Gauss-Seidel iterations on S dp = g from dp = 0 (Section 5.2:
-    "several Gauss-Seidel iterations"; five in Section 6).  The paper gives no
+    """`iters` forward Gauss-Seidel iterations on S dp = g from dp = 0 (Section 5.2
+    solves the Schur system approximately by a few Gauss-Seidel iterations; Section 6
+    uses five).  The paper gives no
     ordering.  Reading: rows ordered by (strip parity, color, index), where the
     strips are consecutive blocks of T rows, T the smallest length for which
     strips two apart share no entry of S (hierarchy.strip_length), and each strip

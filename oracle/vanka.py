@@ -9,7 +9,7 @@ the pressure dof itself, and for each block in turn
 with R_i the restriction to T_i and omega = 0.5 (Section 6).
 
 Readings (the paper is silent on them):
-  * Order.  The paper cycles "through all sets T_i" without an order.  Reading:
+  * Order.  The paper relaxes every set T_i in turn but names no order.  Reading:
     blocks in the order (color, index), the colors a greedy coloring (index
     order, smallest free color) of the block interaction graph, in which blocks
     i and j are adjacent when a row of A in T_i has an entry in a column of T_j
@@ -24,6 +24,7 @@ Readings (the paper is silent on them):
 from __future__ import annotations
 
 import numpy as np
+import scipy.linalg as sla
 import scipy.sparse as sp
 
 
@@ -74,8 +75,11 @@ def form_vanka(L):
     for T in blocks:
         MT = M[T][:, T].toarray()
         # a numerically singular local matrix (its pressures carry no coupling, as on a
-        # coarsest level that keeps only the constant pressure) has no Vanka step
-        if np.linalg.cond(MT) > 1.0 / (len(T) * np.finfo(float).eps):
+        # coarsest level that keeps only the constant pressure) has no Vanka step.  The
+        # test: LU with partial pivoting meets a pivot of at most n eps max|entry| (the
+        # pivots of Gauss-Jordan elimination with partial pivoting are the same ones)
+        lu, _ = sla.lu_factor(MT, check_finite=False)
+        if not np.abs(np.diag(lu)).min() > len(T) * np.finfo(float).eps * np.abs(MT).max():
             raise ValueError("a Vanka block matrix is singular")
         inv.append(np.linalg.inv(MT))
     L.vanka = dict(blocks=blocks, colors=colors, inv=inv, dirichlet=dirichlet, M=M)

@@ -24,6 +24,7 @@ STATUS_NAMES = {0: "OK", 1: "NOT_CONVERGED", 2: "BREAKDOWN", -1: "ERR_ARG", -2: 
 EXPORTED = ["amg_params_default", "amg_hierarchy_create", "amg_hierarchy_create_reuse", "amg_vcycle_apply", "amg_apply", "amg_fgmres_solve",
             "amg_fgmres_solve_host", "amg_num_levels", "amg_level_get_info", "amg_level_get_matrix",
             "amg_level_get_points", "amg_hierarchy_destroy", "amg_last_error", "amg_profile_vcycle", "amg_kernel_launches", "amg_apply_noalloc", "amg_gs_variant", "amg_row_shape", "amg_level_get_vanka", "amg_level_get_ilu",
+            "amg_coarse_inverse", "amg_set_wait_limit",
             "amg_server_params_default", "amg_server_create", "amg_server_reserve", "amg_server_submit", "amg_server_progress",
             "amg_server_result", "amg_server_state", "amg_server_get_stats", "amg_server_destroy", "amg_server_last_error"]
 KERNEL_CLASSES = ["velocity", "schur_rhs", "gs_color", "update", "residual", "restrict", "prolong", "coarse", "vanka",
@@ -128,6 +129,10 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.amg_level_get_ilu.argtypes = [vp, ctypes.c_int, _i32p, _i64p, _i64p, _i32p, _i32p, _i32p, _i32p, _i32p, _f64p,
                                       _i32p, _i32p, _f64p, _f64p]
     lib.amg_level_get_ilu.restype = ctypes.c_int
+    lib.amg_coarse_inverse.argtypes = [vp, _i32p, _f64p]
+    lib.amg_coarse_inverse.restype = ctypes.c_int
+    lib.amg_set_wait_limit.argtypes = [vp, ctypes.c_longlong]
+    lib.amg_set_wait_limit.restype = ctypes.c_int
     lib.amg_hierarchy_destroy.argtypes = [vp]
     lib.amg_hierarchy_destroy.restype = None
     lib.amg_last_error.argtypes = []
@@ -388,6 +393,18 @@ class Hierarchy:
                                         _ptr(piv, ctypes.c_double)))
         return dict(perm=perm, lower=(lp, lc[:nl.value], lv[:nl.value]), upper=(up, uc[:nu.value], uv[:nu.value]),
                     pivots=piv, depth_lower=dl.value, depth_upper=du.value)
+
+    def coarse_inverse(self) -> np.ndarray:
+        """The coarsest level's pseudo-inverse (amg_coarse_inverse), N_c x N_c."""
+        n = ctypes.c_int()
+        _check(load().amg_coarse_inverse(self._h, ctypes.byref(n), None))
+        X = np.zeros((n.value, n.value))
+        _check(load().amg_coarse_inverse(self._h, None, _ptr(X, ctypes.c_double)))
+        return X
+
+    def set_wait_limit(self, polls: int):
+        """Poll limit of the bounded device waits (amg_set_wait_limit; <= 0: the default)."""
+        _check(load().amg_set_wait_limit(self._h, int(polls)))
 
     def level_points(self, level: int) -> dict:
         info = self.level_info(level)

@@ -226,9 +226,15 @@ __global__ void __launch_bounds__(kBlock) k_schur_rhs(LevelView<T> L, const T* _
 }
 
 // Bounded waits: a block polling a counter that another block publishes gives
-// up after kSpinLimit polls (seconds), sets *err and returns, so a wait can
-// never hang the GPU; the host checks *err after the cycle.
+// up after a limit of polls (by default kSpinLimit, seconds), sets *err and
+// returns, so a wait can never hang the GPU; the host checks *err after the
+// cycle.  The error word and the limit share one device allocation: err[0] is
+// the error word, err[2..3] the limit as a 64-bit count (the host lowers it to
+// make waits run out on purpose, for tests of the failure path).
 constexpr unsigned long long kSpinLimit = 1ull << 24;
+__device__ __forceinline__ unsigned long long wait_limit(const int* err) {
+  return *reinterpret_cast<const volatile unsigned long long*>(err + 2);
+}
 
 // Strip-ordered Gauss-Seidel for the Schur system S dp = g, gs_iters iterations
 // from dp = 0.  Rows are relaxed in the order (strip parity, color, index):
@@ -375,7 +381,7 @@ __global__ void __launch_bounds__(kGsBlock) k_gs_strips(LevelView<T> L, const T*
 // alongside any other work on the device.  Per-strip counters of completed
 // iterations carry the dependencies (release / acquire).  A block stages the
 // strip's rows of S, 1/S_ii and g while it waits, then the dp halo.  Waits are
-// bounded (kSpinLimit polls), set *err and return on timeout.
+// bounded (the wait_limit polls), set *err and return on timeout.
 __device__ __forceinline__ int ld_acquire(const int* p) {
   int v;
   asm volatile("ld.acquire.gpu.global.b32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
@@ -438,12 +444,13 @@ __global__ void __launch_bounds__(NT) k_gs_pipe(LevelView<T> L, const T* __restr
     }
     const int need_nb = par == 0 ? it : it + 1;
     if (threadIdx.x == 0) {
+      const unsigned long long limit = wait_limit(err);
       for (int nb = s - 1; nb <= s + 1; ++nb) {
         const int need = nb == s ? it : need_nb;
         if (nb < 0 || nb >= P.nstrips || need == 0) continue;
         unsigned long long spins = 0;
         while (ld_acquire(done + nb) < need) {
-          if (++spins > kSpinLimit || *(volatile int*)err) {
+          if (++spins > limit || *(volatile int*)err) {
             atomicExch(err, 1);
             s_fail = 1;
             break;
@@ -884,7 +891,7 @@ __global__ void __launch_bounds__(kBlock) k_vanka_exact(int n, const int* __rest
 // needs until it differs from the sentinel, so a row costs no fence and no flag.
 // Values computed from finite data are never NaN; a NaN result that matched the
 // sentinel would end in a timed-out wait, reported through *err.  Every wait is
-// bounded (kSpinLimit polls) and gives up at once when *err is set; a lane that
+// bounded (the wait_limit polls) and gives up at once when *err is set; a lane that
 // gives up takes 0 and goes on, so the launch always ends.  The warp that takes
 // the last ticket puts the counter back to zero for the next launch.
 constexpr int kIluBlock = 256;
@@ -922,8 +929,9 @@ __device__ __forceinline__ bool is_sentinel(double v) { return __double_as_longl
 template <typename T>
 __device__ __noinline__ T wait_value(const T* p, int* err) {
   T v = ld_relaxed(p);
+  const unsigned long long limit = is_sentinel(v) ? wait_limit(err) : 0ull;
   for (unsigned long long spins = 1; is_sentinel(v); ++spins) {
-    if (spins > kSpinLimit || ((spins & 31) == 0 && *(volatile int*)err)) {
+    if (spins > limit || ((spins & 31) == 0 && *(volatile int*)err)) {
       atomicExch(err, 1);
       return T(0);
     }

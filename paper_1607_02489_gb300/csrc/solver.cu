@@ -429,6 +429,8 @@ class FgmresTask final : public SolveTask {
   }
 
   void start() {
+    // a wait that timed out in an earlier call does not fail this one
+    EMIN_CUDA(cudaMemsetAsync(vc_->error_flag(), 0, sizeof(int), s_));
     for (const SolveSegment& g : segs_)
       if (g.b_host)
         EMIN_CUDA(cudaMemcpyAsync(const_cast<double*>(g.b), g.b_host, sizeof(double) * N_ * g.ncols,
@@ -1102,6 +1104,25 @@ amg_status amg_level_get_ilu(amg_handle h, int level, int* n, long long* nnz_low
   if (upper_col) std::copy(L.il_U.col.begin(), L.il_U.col.end(), upper_col);
   if (upper_val) std::copy(L.il_U.val.begin(), L.il_U.val.end(), upper_val);
   if (pivots) std::copy(L.il_diag.begin(), L.il_diag.end(), pivots);
+  return AMG_OK;
+}
+
+amg_status amg_coarse_inverse(amg_handle h, int* n, double* X) {
+  if (!h || h->host.empty()) return fail(AMG_ERR_ARG, "bad handle");
+  const HostLevel& C = h->host.back();
+  if (n) *n = C.N();
+  if (X) std::copy(C.pinv.begin(), C.pinv.end(), X);
+  return AMG_OK;
+}
+
+amg_status amg_set_wait_limit(amg_handle h, long long polls) {
+  if (!h) return fail(AMG_ERR_ARG, "bad handle");
+  const unsigned long long lim = polls > 0 ? (unsigned long long)polls : kSpinLimit;
+  for (VCycleIface* v : {h->v64, h->v32}) {
+    if (!v) continue;
+    const cudaError_t e = v->set_wait_limit(lim);
+    if (e != cudaSuccess) return fail(AMG_ERR_CUDA, std::string("amg_set_wait_limit: ") + cudaGetErrorString(e));
+  }
   return AMG_OK;
 }
 

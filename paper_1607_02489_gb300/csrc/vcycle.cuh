@@ -33,8 +33,10 @@ struct VCycleIface {
   virtual cudaError_t profile(int K, int reps, cudaStream_t s, double* ms, long long* count) = 0;
   // Kernels launched so far by run() and profile() (graph replays count every kernel node).
   virtual long long launches() const = 0;
-  // Device word set when a bounded grid barrier timed out (0 otherwise).
+  // Device word set when a bounded wait timed out (0 otherwise).
   virtual int* error_flag() const = 0;
+  // Poll limit of this cycle's bounded waits (kSpinLimit by default); synchronous.
+  virtual cudaError_t set_wait_limit(unsigned long long polls) = 0;
   // FP32 cycles only: out = A z on the finest level for an FP32 z, FP64 result by
   // float-float arithmetic on the FP64 matrix split into two floats.
   virtual cudaError_t apply_ff(const float* z, double* out, int K, cudaStream_t s) = 0;
@@ -119,8 +121,9 @@ class DeviceVCycle : public VCycleIface {
       Nc_ = C.N();
       pinv_ = alloc_copy<double>(C.pinv);
       if (sizeof(T) == 4) build_ff(levels[0]);
-      err_ = alloc<int>(1);
-      EMIN_CUDA(cudaMemset(err_, 0, sizeof(int)));
+      err_ = alloc<int>(4);
+      EMIN_CUDA(cudaMemset(err_, 0, 4 * sizeof(int)));
+      EMIN_CUDA(set_wait_limit(kSpinLimit));
     } catch (...) {
       release();
       throw;
@@ -843,6 +846,9 @@ class DeviceVCycle : public VCycleIface {
  public:
   // Nonzero when a bounded wait gave up (checked by the solver after a cycle).
   int* error_flag() const override { return err_; }
+  cudaError_t set_wait_limit(unsigned long long polls) override {
+    return cudaMemcpy(err_ + 2, &polls, sizeof(polls), cudaMemcpyHostToDevice);
+  }
 
   cudaError_t apply_ff(const float* z, double* out, int K, cudaStream_t s) override {
     if (!ff_.A.hi) return cudaErrorInvalidValue;
@@ -981,8 +987,9 @@ class DeviceVCycle : public VCycleIface {
         buf_.push_back(alloc_bufs(views_[l], l + 1 < views_.size()));
         done_.push_back(alloc<int>(gs_[l].nstrips + 1));
       }
-      err_ = alloc<int>(1);
-      EMIN_CUDA(cudaMemset(err_, 0, sizeof(int)));
+      err_ = alloc<int>(4);
+      EMIN_CUDA(cudaMemset(err_, 0, 4 * sizeof(int)));
+      EMIN_CUDA(set_wait_limit(kSpinLimit));
       if (ilu_) {
         il_ticket_ = alloc<int>(1);
         EMIN_CUDA(cudaMemset(il_ticket_, 0, sizeof(int)));

@@ -2,7 +2,7 @@
 C ABI against the oracle's ILU V-cycle and FGMRES.
 
 Tolerances as for the other smoothers (test_gpu_parity.py): FP64 V-cycle relative
-2-norm error <= max(1e-11, 2 kappa u) per column; FP32 V-cycle <= 1e-4; FGMRES
+2-norm error <= 1e-11 per column; FP32 V-cycle <= 1e-4; FGMRES
 iterations within +-1 (FP64 cycle), true residual re-checked on the host.  The
 substitutions are sync-free (rows wait on the values they need), but each row's
 sum runs in a fixed lane order, so a cycle is deterministic."""
@@ -40,12 +40,6 @@ def _relerr(a, b):
     return np.linalg.norm(a - b, axis=0) / np.maximum(np.linalg.norm(b, axis=0), 1e-300)
 
 
-def _coarse_condition(Ho):
-    s = np.linalg.svd(Ho.levels[-1].full_matrix().toarray(), compute_uv=False)
-    s = s[s > 1e-12 * s[0]]
-    return s[0] / s[-1]
-
-
 @pytest.mark.parametrize("case", list(CASES))
 def test_ilu_vcycle_fp64_matches_oracle(case):
     p = CASES[case]()
@@ -57,9 +51,9 @@ def test_ilu_vcycle_fp64_matches_oracle(case):
     zt = torch.empty_like(rt)
     Hg.vcycle(rt, zt)
     torch.cuda.synchronize()
-    tol = max(1e-11, 2.0 * _coarse_condition(Ho) * 2.0 ** -53)
     err = _relerr(zt.cpu().numpy(), zo)
-    assert np.all(err <= tol), (err, tol)
+    print(f"\nFP64 ILU(1) V-cycle vs oracle, {case}: max relative error {err.max():.2e}")
+    assert np.all(err <= 1e-11), err
     z2 = torch.empty_like(rt)
     Hg.vcycle(rt, z2)
     torch.cuda.synchronize()
@@ -79,7 +73,7 @@ def test_ilu_location_order_vcycle_matches_oracle(case):
     Hg.vcycle(rt, zt)
     torch.cuda.synchronize()
     err = _relerr(zt.cpu().numpy(), zo)
-    assert np.all(err <= max(1e-11, 2.0 * _coarse_condition(Ho) * 2.0 ** -53)), err
+    assert np.all(err <= 1e-11), err
 
 
 @pytest.mark.parametrize("K", [1, 8, 32])
@@ -95,7 +89,7 @@ def test_ilu_vcycle_lane_groups(K):
     Hg.vcycle(rt, zt)
     torch.cuda.synchronize()
     err = _relerr(zt.cpu().numpy(), zo)
-    assert np.all(err <= max(1e-11, 2.0 * _coarse_condition(Ho) * 2.0 ** -53)), err
+    assert np.all(err <= 1e-11), err
 
 
 @pytest.mark.parametrize("case", ["lid32", "oseen32"])

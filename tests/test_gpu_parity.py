@@ -2,7 +2,7 @@
 
 Tolerances (from the arithmetic: a V-cycle is a fixed sequence of sums, so FP64 results
 agree to a small multiple of the unit roundoff times the operators' conditioning; the
-coarsest solve contributes kappa u):
+coarsest solve applies a pseudo-inverse that both sides refine to working accuracy):
   * FP64 V-cycle: relative 2-norm error <= 1e-11 per application and column;
   * block product A x: <= 1e-13;
   * FP32 V-cycle: <= 1e-4 (single precision through a few levels of smoothing);
@@ -46,18 +46,14 @@ def _relerr(a, b):
     return np.linalg.norm(a - b, axis=0) / np.maximum(np.linalg.norm(b, axis=0), 1e-300)
 
 
-def _coarse_condition(Ho):
-    """Condition number of the coarsest operator on the complement of its exact null space."""
-    s = np.linalg.svd(Ho.levels[-1].full_matrix().toarray(), compute_uv=False)
-    s = s[s > 1e-12 * s[0]]
-    return s[0] / s[-1]
-
-
 @pytest.mark.parametrize("case", list(CASES))
 def test_vcycle_fp64_matches_oracle(case):
-    """Relative error <= max(1e-11, 2 kappa u): the coarsest solve of any FP64 method is only
-    accurate to its condition number kappa times the unit roundoff u = 2^-53, and the
-    pinned problem's coarsest level is nearly singular (kappa ~ 7.5e6)."""
+    """Relative error <= 1e-11 per column.  The pinned problem's coarsest level has
+    cond ~ 7.5e6, so an SVD alone would give its inverse only to cond * u; both the
+    library and the oracle refine their pseudo-inverse to working accuracy (the CPU
+    test test_pinned_coarse_inverse_is_refined_beyond_cond_u pins the agreement of
+    the two inverses), which keeps the comparison at 1e-11.  The measured error is
+    printed (pytest -s)."""
     p = CASES[case]()
     Ho = setup_hierarchy(p)
     Hg = g.Hierarchy(p, max_nrhs=p.b.shape[1])
@@ -68,8 +64,9 @@ def test_vcycle_fp64_matches_oracle(case):
     zt = torch.empty_like(rt)
     Hg.vcycle(rt, zt)
     torch.cuda.synchronize()
-    tol = max(1e-11, 2.0 * _coarse_condition(Ho) * 2.0 ** -53)
-    assert np.all(_relerr(zt.cpu().numpy(), zo) <= tol), (_relerr(zt.cpu().numpy(), zo), tol)
+    err = _relerr(zt.cpu().numpy(), zo)
+    print(f"\nFP64 V-cycle vs oracle, {case}: max relative error {err.max():.2e}")
+    assert np.all(err <= 1e-11), err
     # a second application reuses the captured graph and gives the same result
     z2 = torch.empty_like(rt)
     Hg.vcycle(rt, z2)

@@ -2,7 +2,7 @@
 the C ABI against the oracle's Vanka V-cycle and FGMRES.
 
 Tolerances as for Braess-Sarazin (test_gpu_parity.py): FP64 V-cycle relative
-2-norm error <= max(1e-11, 2 kappa u) per column; FP32 V-cycle <= 1e-4; FGMRES
+2-norm error <= 1e-11 per column; FP32 V-cycle <= 1e-4; FGMRES
 iterations within +-1 (FP64 cycle), true residual re-checked on the host."""
 import numpy as np
 import pytest
@@ -37,12 +37,6 @@ def _relerr(a, b):
     return np.linalg.norm(a - b, axis=0) / np.maximum(np.linalg.norm(b, axis=0), 1e-300)
 
 
-def _coarse_condition(Ho):
-    s = np.linalg.svd(Ho.levels[-1].full_matrix().toarray(), compute_uv=False)
-    s = s[s > 1e-12 * s[0]]
-    return s[0] / s[-1]
-
-
 @pytest.mark.parametrize("case", list(CASES))
 def test_vanka_vcycle_fp64_matches_oracle(case):
     p = CASES[case]()
@@ -54,9 +48,9 @@ def test_vanka_vcycle_fp64_matches_oracle(case):
     zt = torch.empty_like(rt)
     Hg.vcycle(rt, zt)
     torch.cuda.synchronize()
-    tol = max(1e-11, 2.0 * _coarse_condition(Ho) * 2.0 ** -53)
     err = _relerr(zt.cpu().numpy(), zo)
-    assert np.all(err <= tol), (err, tol)
+    print(f"\nFP64 Vanka V-cycle vs oracle, {case}: max relative error {err.max():.2e}")
+    assert np.all(err <= 1e-11), err
     z2 = torch.empty_like(rt)
     Hg.vcycle(rt, z2)
     torch.cuda.synchronize()
@@ -138,3 +132,30 @@ def test_coarsest_vanka_relaxation_matches_oracle(case, smoother):
     ms, cnt = Hg.profile_vcycle(p.b.shape[1], reps=1)
     v, c = g.KERNEL_CLASSES.index("vanka"), g.KERNEL_CLASSES.index("coarse")
     assert cnt[-1, v] > 0 and cnt[:, c].sum() == 0
+
+
+@pytest.mark.parametrize("fp32", [0, 1])
+def test_coarsest_vanka_solve_at_256(fp32):
+    """The 256x256 lid cavity with the paper's Vanka relaxation of the coarsest level
+    (coarse = 1): coarsening stops at the 301-dof level with 15 pressures (the level
+    below keeps one pressure and has no Vanka step), and FGMRES reaches 1e-8 in the
+    oracle's iteration count (+-1 with the FP64 cycle, at most 2 more with the FP32
+    one) on the first right-hand side; the true residual is re-checked on the host."""
+    p = stokes_lid_2d(256, nrhs=2)
+    Ho = setup_hierarchy(p, Params(coarse="vanka"))
+    assert Ho.levels[-1].N == 301 and Ho.levels[-1].n_p == 15
+    _, its_o, _, _ = fgmres(Ho, p.b[:, :1], rtol=1e-8)
+    Hg = g.Hierarchy(p, max_nrhs=2, coarse=1, vcycle_fp32=fp32)
+    assert Hg.num_levels() == len(Ho.levels)
+    bt = torch.tensor(p.b, device="cuda")
+    xt = torch.zeros_like(bt)
+    st, its, rel = Hg.fgmres(bt, xt, rtol=1e-8, restart=100, maxit=300)
+    print(f"\ncoarsest Vanka at 256x256 (fp32={fp32}): iterations {its.tolist()}, oracle {its_o.tolist()}")
+    assert st == g.AMG_OK and np.all(rel <= 1e-8)
+    if fp32:
+        assert its[0] <= its_o[0] + 2, (its, its_o)
+    else:
+        assert abs(int(its[0]) - int(its_o[0])) <= 1, (its, its_o)
+    A = p.full_matrix()
+    x = xt.cpu().numpy()
+    assert np.all(np.linalg.norm(p.b - A @ x, axis=0) <= 1.01e-8 * np.linalg.norm(p.b, axis=0))

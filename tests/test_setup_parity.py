@@ -77,6 +77,12 @@ def _compare(prob, prm=None, reuse=None, **kw):
             assert np.array_equal(M.indptr, O.indptr) and np.array_equal(M.indices, O.indices), (l, nm)
             ref = {"A": scale, "B": scale, "Bt": scale, "S": s_scale}.get(nm, abs(O).max())
             assert abs(M - O).max() <= 1e-11 * ref, (l, nm, abs(M - O).max(), ref)
+    # the coarsest pseudo-inverse: both sides refine their SVD's result (Newton-Schulz with
+    # residuals in extended precision), so they agree well below cond * u, which reaches
+    # 1e-9 on the pinned problems.  On singular levels what refinement cannot reach is the
+    # SVD's tilt of the kept singular vectors towards the null space (u ||A|| / gap).
+    X, Xo = Hg.coarse_inverse(), Ho.levels[-1].coarse_pinv
+    assert np.linalg.norm(X - Xo) <= 1e-11 * np.linalg.norm(Xo), np.linalg.norm(X - Xo) / np.linalg.norm(Xo)
 
 
 @pytest.mark.parametrize("n", [8, 16, 32, 64])
@@ -286,3 +292,20 @@ def test_coarsest_vanka_hierarchy_at_256_matches_oracle():
     assert Hg.num_levels() == len(Ho.levels) == 4
     c = Hg.level_info(3)
     assert (c["n_v"], c["n_p"]) == (Ho.levels[3].n_v, Ho.levels[3].n_p) == (143, 15)
+
+
+def test_pinned_coarse_inverse_is_refined_beyond_cond_u():
+    """The 16x16 pinned problem's coarsest level is nonsingular but ill-conditioned
+    (cond ~ 7.5e6): an SVD alone gives its inverse only to cond * u ~ 1e-9, and two
+    SVDs of the same matrix differ by ~1e-10.  After refinement the library's and the
+    oracle's inverses agree to ~1e-14."""
+    p = stokes_pinned_2d(16)
+    Hg = g.Hierarchy(p, host_only=1)
+    Ho = setup_hierarchy(p)
+    A = Ho.levels[-1].full_matrix().toarray()
+    s = np.linalg.svd(A, compute_uv=False)
+    assert s[0] / s[-1] > 1e6
+    X, Xo = Hg.coarse_inverse(), Ho.levels[-1].coarse_pinv
+    raw = np.linalg.pinv(A, rcond=1e-12)
+    assert np.linalg.norm(raw - Xo) > 1e-11 * np.linalg.norm(Xo)  # the SVD alone is cond * u away
+    assert np.linalg.norm(X - Xo) <= 1e-13 * np.linalg.norm(Xo)

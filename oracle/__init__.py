@@ -28,9 +28,15 @@ tests/test_synth.py):
     pattern, the level-of-fill rule, exactness without fill, the zero-pivot
     reading on a 3x3 saddle matrix, the error-propagation spectrum, dense
     solves, Table 1's and Table 5's ILU(1)(1,1) counts).
-  * find_extra_dist3_cpoints: the paper names its criteria but gives no
-    thresholds, and no uniform-mesh case triggers it, so its choices are
-    parity unpinned (only the coverage invariant it must keep is pinned).
+  * find_extra_dist3_cpoints: pinned on hand-built graphs whose conversions
+    are worked out by hand (one C-point at distance 3; two C-points at distance
+    3 with the point on either side of the quarter-length threshold and beyond
+    the segment's end), and it fires on the perturbed-coordinate meshes of the
+    setup-parity tests, where the library's choices equal the oracle's.
+  * emin_step: pinned by its optimality (the CG step is the exact line
+    minimum of the energy along -Proj(A P0); the GMRES step's projected
+    residual is orthogonal to Proj(A R0)), with a projection built in the test
+    from null-space bases.
 """
 from .hierarchy import Params, Hierarchy, setup_hierarchy  # noqa: F401
 from .solve import bs_sweep, vcycle, fgmres, apply_A  # noqa: F401

@@ -313,3 +313,19 @@ def stokes_lid_3d(n=48, nrhs=1, seed=0):
     """Unit cube, lid (1,0,0) on z=1 including its edges, nu=1."""
     return make_problem(n, 3, 0.0, 1.0, bc="lid", pin=False, nrhs=nrhs, seed=seed,
                         name=f"stokes3d_lid_{n}^3")
+
+
+def with_perturbed_coordinates(p: Problem, amplitude: float = 0.35, seed: int = 100) -> Problem:
+    """The same matrices and right-hand sides with the node coordinates the
+    coarsening reads (Alg. 3's distance heuristics, Alg. 4's mid-point test)
+    moved by seeded uniform offsets of up to `amplitude` times the velocity node
+    spacing per direction; a pressure node keeps its co-located velocity node's
+    position.  On a uniform mesh Alg. 3 packs the coarse pressures perfectly and
+    no F-point is badly covered; the perturbed positions change which candidate
+    wins each step, so find_extra_dist3_Cpoints has F-points to convert.  Only
+    the coordinate inputs change: the block system is the uniform mesh's."""
+    lo, hi = float(p.vcoords.min()), float(p.vcoords.max())
+    h = (hi - lo) / (2 * p.n)
+    off = uniform_pm1(seed, p.n_v * p.dim).reshape(p.n_v, p.dim) * (amplitude * h)
+    vX = p.vcoords + off
+    return dataclasses.replace(p, vcoords=vX, pcoords=vX[p.p2v], name=p.name + f"_perturbed{seed}")

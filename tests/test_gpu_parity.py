@@ -12,7 +12,8 @@ coarsest solve applies a pseudo-inverse that both sides refine to working accura
 import numpy as np
 import pytest
 
-from synth import make_problem, stokes_lid_2d, stokes_pinned_2d, oseen_recirculating_2d, uniform_pm1
+from synth import (make_problem, stokes_lid_2d, stokes_pinned_2d, oseen_recirculating_2d, uniform_pm1,
+                   with_perturbed_coordinates)
 from oracle import setup_hierarchy, vcycle, fgmres, apply_A, Params
 
 pytestmark = pytest.mark.gpu
@@ -35,6 +36,8 @@ CASES = {
     "single_level": lambda: stokes_lid_2d(2, nrhs=2),
     "lid3d": lambda: make_problem(4, 3, 0.0, 1.0, bc="lid", nrhs=1),
     "oseen_re100_k8": lambda: oseen_recirculating_2d(16, Re=100.0, nrhs=8),
+    # perturbed node positions: Alg. 3's extra coarse pressures (find_extra_dist3_Cpoints) in play
+    "lid20_perturbed": lambda: with_perturbed_coordinates(stokes_lid_2d(20, nrhs=2), 0.35, 101),
 }
 
 
@@ -111,7 +114,7 @@ def _center(p, x):
     return x
 
 
-@pytest.mark.parametrize("case", ["pinned16", "lid32", "oseen32", "lid18_ragged3"])
+@pytest.mark.parametrize("case", ["pinned16", "lid32", "oseen32", "lid18_ragged3", "lid20_perturbed"])
 @pytest.mark.parametrize("fp32", [0, 1])
 def test_fgmres_matches_oracle(case, fp32):
     p = CASES[case]()

@@ -3,12 +3,24 @@ systems (synth.navier_stokes) and the oracle's AMG on them against Table 5.
 
 Pins: the discrete-wind assembly equals the analytic-wind assembly for a wind
 the Q2 space holds exactly; the Picard sequence reaches the paper's 1e-8
-nonlinear residual; on the last Picard system the oracle's GMRES (to 1e-6, the
-paper's tolerance) with Vanka(1,1), BS(2,2) and ILU(1)(1,1) stays within
-[0.45, 1.25] x the iteration counts of Table 5 and keeps its trends (more iterations at the smaller
-viscosity; Vanka no worse than Braess-Sarazin).  The oracle's counts sit below
-the paper's because its coarsest level is solved exactly (the paper relaxes it
-with Vanka)."""
+nonlinear residual; on the last Picard system the oracle's GMRES (to a relative
+1e-6, the paper's tolerance) with Vanka(1,1), BS(2,2) and ILU(1)(1,1) needs at
+most 1.25 x the iteration counts of Table 5; with BS(2,2) at least as many as
+Table 1 shows for the Stokes problem on the same mesh (the paper's Navier-Stokes
+counts exceed its Stokes counts everywhere); and it keeps Table 5's trends (more
+iterations at the smaller viscosity; Vanka no worse than Braess-Sarazin; ILU(1)
+no worse than Braess-Sarazin).
+
+There is no lower band tied to Table 5: the oracle's counts sit at 45-75% of the
+paper's (its Vanka counts at nu = 0.01, 13-14, do not even rise above its Stokes
+ones as the paper's do), and neither of the two explanations at hand closes
+that gap.  The
+coarsest level (exact here, Vanka in the paper) moves them by at most 3.  The
+stopping test matters more: the paper names a residual tolerance of 1e-6 without
+saying relative; read as an absolute ||r|| <= 1e-6 (||b|| is 4-8 on these
+systems) the counts rise by 15-25% (Vanka 16/16/16/31 and BS 18/19/18/47 on
+8x8-32x32 at nu = 0.01 and 16x16 at nu = 0.002, against 20/26/22/49 and
+19/22/26/55), still below the paper's."""
 import numpy as np
 import pytest
 
@@ -16,6 +28,8 @@ from synth import make_problem, picard_lid_cavity
 from synth.q2q1 import assemble
 from oracle import Params, fgmres, setup_hierarchy
 
+# Table 1 (Stokes lid cavity): (Vanka(1,1), BS(2,2)) iterations per mesh (BS used)
+TABLE1 = {8: (11, 9), 16: (12, 10), 32: (14, 14)}
 # Table 5 (Navier-Stokes lid cavity): (Vanka(1,1), BS(2,2)) iterations
 TABLE5 = {(8, 0.01): (20, 19), (16, 0.01): (26, 22), (32, 0.01): (22, 26),
           (16, 0.002): (49, 55), (32, 0.002): (53, 60)}
@@ -64,20 +78,23 @@ def test_table5_iterations_and_trends(picard_systems):
         v, b = _its(last, vk), _its(last, bs)
         ours[key] = (v, b)
         pv, pb = TABLE5[key]
-        assert 0.45 * pv <= v <= 1.25 * pv, (key, v, pv)
-        assert 0.45 * pb <= b <= 1.25 * pb, (key, b, pb)
+        sb = TABLE1[key[0]][1]
+        assert v <= 1.25 * pv, (key, v, pv)
+        assert sb <= b <= 1.25 * pb, (key, b, pb, sb)
         assert v <= b, (key, v, b)
     for n in (16, 32):
         assert ours[(n, 0.002)][0] > ours[(n, 0.01)][0] and ours[(n, 0.002)][1] > ours[(n, 0.01)][1]
 
 
 def test_table5_ilu_iterations(picard_systems):
-    """ILU(1)(1,1) with reverse Cuthill-McKee order on the last Picard systems: within
-    [0.45, 1.25] x Table 5's ILU column, like the other smoothers."""
+    """ILU(1)(1,1) with reverse Cuthill-McKee order on the last Picard systems: at most
+    1.25 x Table 5's ILU column and no more iterations than Braess-Sarazin(2,2) on the
+    same system (the paper's ILU column is the smallest of Table 5's rows)."""
     il = Params(smoother="ilu", pre=1, post=1)
     for key, (last, _, _) in picard_systems.items():
         i = _its(last, il)
-        assert 0.45 * TABLE5_ILU[key] <= i <= 1.25 * TABLE5_ILU[key], (key, i, TABLE5_ILU[key])
+        assert 1 <= i <= 1.25 * TABLE5_ILU[key], (key, i, TABLE5_ILU[key])
+        assert i <= _its(last, Params()), key
 
 
 def test_reused_coarsening_gives_the_fresh_hierarchy_on_the_same_matrix(picard_systems):

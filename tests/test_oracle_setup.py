@@ -312,3 +312,219 @@ def test_table3_infsup_estimates_of_the_coarse_operators():
     assert abs(s64[1] - 1.56) <= 0.03 * 1.56
     assert abs(s32[1] - s64[1]) < 0.03
     assert min(s64) > 0.2
+
+
+# ----------------------------------------------------------------------------
+# find_extra_dist3_Cpoints (Alg. 3's last step) on hand-built graphs whose
+# coarse points and S sets are worked out by hand in the docstrings
+
+def _path_graph(n):
+    return [[j for j in (i - 1, i + 1) if 0 <= j < n] for i in range(n)]
+
+
+def test_extra_cpoint_for_an_fpoint_covered_once_at_distance_three():
+    """Path 0-1-...-7 on the x axis.  Alg. 3 starts at 0 (C); 1, 2, 3 become F and 4,
+    at distance 4, the only candidate, becomes the next C; 5, 6, 7 become F.  Then
+    S_7 = {4: 3}: one C-point at graph distance 3, so 7 is converted (|S_j| = 1 rule),
+    while 1 (S = {0: 1, 4: 3}), 2, 3, 5, 6 are not.  The conversion adds 7 to the S
+    sets of the vertices within distance 3 of it (4, 5, 6), and the pattern rows
+    use the coarse numbering of C = {0, 4, 7}."""
+    from oracle.hierarchy import find_extra_dist3_cpoints
+    adj = _path_graph(8)
+    X = np.array([[float(i), 0.0] for i in range(8)])
+    state, S, order = find_coarse_pressures(adj, X, [])
+    assert order == [0, 4]
+    assert [int(s) for s in state] == [CPT, FPT, FPT, FPT, CPT, FPT, FPT, FPT]
+    assert S[7] == {4: 3} and S[1] == {0: 1, 4: 3} and S[5] == {4: 1}
+    added = find_extra_dist3_cpoints(adj, X, state, S)
+    assert added == [7] and state[7] == CPT
+    assert S[6] == {4: 2, 7: 1} and S[5] == {4: 1, 7: 2} and S[4] == {4: 0, 7: 3}
+    rows = pressure_pattern(state, S, [0, 4, 7])
+    assert rows[7] == [2] and rows[6] == [1, 2] and rows[1] == [0, 1]
+
+
+def _two_cpoint_graph(jxy):
+    """a = 0 at (0, 0) and b = 4 at (4, 0) joined by the path 0-1-2-3-4 on the x axis;
+    j = 5 joined to a by 0-6-7-5 and to b by 4-8-9-5 (distance 3 from both).  The
+    coordinates of 6-9 are placed far away so that b (h1 = 16), not 9 (also at graph
+    distance 4 from a), is the closest candidate after a."""
+    adj = [[1, 6], [0, 2], [1, 3], [2, 4], [3, 8], [7, 9], [0, 7], [6, 5], [4, 9], [8, 5]]
+    X = np.array([[0, 0], [1, 0], [2, 0], [3, 0], [4, 0], list(jxy), [-5, 9], [-5, 10], [9, -9], [9, -10]],
+                 dtype=float)
+    return adj, X
+
+
+@pytest.mark.parametrize("jxy, convert", [((2.0, 2.0), True), ((2.0, 0.5), False), ((2.0, 1.01), True),
+                                          ((2.0, 0.99), False), ((5.0, 0.5), True)])
+def test_extra_cpoint_for_an_fpoint_between_two_distant_cpoints(jxy, convert):
+    """Alg. 3 gives C = {a, b} = {0, 4} and S_j = {0: 3, 4: 3}.  The reading converts j when
+    its distance to the segment [a, b] exceeds a quarter of |ab| = 1: (2, 2), (2, 1.01)
+    are converted, (2, 0.5) and (2, 0.99) are not; (5, 0.5) lies 0.5 from the line but
+    1.118 from the segment's end b, so it is converted (segment, not line)."""
+    from oracle.hierarchy import find_extra_dist3_cpoints
+    adj, X = _two_cpoint_graph(jxy)
+    state, S, order = find_coarse_pressures(adj, X, [])
+    assert order == [0, 4]
+    assert S[5] == {0: 3, 4: 3}
+    assert all(len(S[v]) != 1 or 3 not in S[v].values() for v in range(10) if state[v] == FPT)
+    added = find_extra_dist3_cpoints(adj, X, state, S)
+    assert added == ([5] if convert else [])
+
+
+def test_extra_cpoints_fire_on_perturbed_meshes_and_keep_the_coverage():
+    """With perturbed node positions (synth.with_perturbed_coordinates) Alg. 3's packing is
+    irregular and some F-points end up badly covered (one C-point at distance 3, or two
+    far from the segment between them); they are converted, and every remaining F-point
+    stays within graph distance 3 of a C-point (the coverage Section 4.1 states)."""
+    from synth import with_perturbed_coordinates
+    p = with_perturbed_coordinates(stokes_lid_2d(16, nrhs=1), 0.35, 100)
+    H = setup_hierarchy(p, Params(max_levels=2))
+    L0 = H.levels[0]
+    extra = L0.info["extra_p"]
+    assert len(extra) >= 2
+    state, S = L0.info["state"], L0.info["S"]
+    for j in extra:
+        assert state[j] == CPT
+    for v in range(L0.n_p):
+        if state[v] == FPT:
+            assert any(d <= 3 for c, d in S[v].items() if state[c] == CPT)
+
+
+# ----------------------------------------------------------------------------
+# EMIN step (eq. min_problem, Section 4.3): optimality along its search direction,
+# checked with a projection built here from a null-space basis of each row's
+# constraint (not the oracle's mean subtraction)
+
+def _test_projection(G, rows, ncols):
+    """Orthogonal projection of G onto {X : X_ij = 0 off the pattern, X 1 = 0}, row by
+    row through an orthonormal basis of the null space of the row's all-ones vector."""
+    import scipy.linalg as sla
+    G = sp.csr_matrix(G)
+    out = np.zeros((len(rows), ncols))
+    for i, cols in enumerate(rows):
+        if len(cols) < 2:
+            continue
+        g = np.asarray(G[i, cols].todense()).ravel()
+        Q = sla.null_space(np.ones((1, len(cols))))
+        out[i, cols] = Q @ (Q.T @ g)
+    return out
+
+
+def _emin_case(kind):
+    if kind == "stokes_pressure":
+        p = stokes_lid_2d(16, nrhs=1)
+        H = setup_hierarchy(p, Params(max_levels=2))
+        info = H.levels[0].info
+        return info["Ap_filtered"], pressure_pattern(info["state"], info["S"], info["Cp"]), len(info["Cp"])
+    if kind == "stokes_velocity":
+        p = stokes_lid_2d(16, nrhs=1)
+        H = setup_hierarchy(p, Params(max_levels=2))
+        L = H.levels[0]
+        P = L.P
+        rows = [list(P.indices[P.indptr[i]:P.indptr[i + 1]]) for i in range(P.shape[0])]
+        return L.info["Av_filtered"], rows, P.shape[1]
+    p = oseen_recirculating_2d(16, Re=100.0, nrhs=1)
+    H = setup_hierarchy(p, Params(max_levels=2))
+    L = H.levels[0]
+    P = L.P
+    rows = [list(P.indices[P.indptr[i]:P.indptr[i + 1]]) for i in range(P.shape[0])]
+    return L.info["Av_filtered"], rows, P.shape[1]
+
+
+@pytest.mark.parametrize("kind", ["stokes_pressure", "stokes_velocity"])
+def test_emin_cg_step_is_the_exact_line_minimum(kind):
+    """One CG step of min tr(P^T A P) over {pattern, P 1 = 1} from P0 = pattern / row
+    count: P1 - P0 is a multiple of the projected negative gradient R0 = -Proj(A P0), and
+    P1 minimises the energy on that line, i.e. <R0, A P1>_F = 0 (the directional
+    derivative vanishes), which fixes the step length; the energy is larger a little
+    before and after P1 on the line."""
+    A, rows, nc = _emin_case(kind)
+    A = sp.csr_matrix(A)
+    n = len(rows)
+    P0 = np.zeros((n, nc))
+    for i, cols in enumerate(rows):
+        if cols:
+            P0[i, cols] = 1.0 / len(cols)
+    R0 = -_test_projection(A @ sp.csr_matrix(P0), rows, nc)
+    P1 = emin_step(A, rows, nc, "cg").toarray()
+    D = P1 - P0
+    a = np.sum(D * R0) / np.sum(R0 * R0)
+    assert a > 0 and np.linalg.norm(D - a * R0) <= 1e-12 * np.linalg.norm(D)
+    g0 = np.sum(R0 * (A @ P0))
+    g1 = np.sum(R0 * (A @ P1))
+    assert abs(g1) <= 1e-10 * abs(g0)
+    energy = lambda P: np.sum(P * (A @ P))  # noqa: E731
+    e1 = energy(P1)
+    assert energy(P1 + 0.05 * a * R0) > e1 and energy(P1 - 0.05 * a * R0) > e1
+
+
+def test_emin_gmres_step_minimises_the_projected_residual():
+    """One GMRES step (Oseen, Section 4.3): P1 = P0 + alpha R0 minimises the Frobenius
+    norm of the projected residual Proj(A P) on the line P0 + t R0, so the residual at P1
+    is orthogonal to Q = Proj(A R0)."""
+    A, rows, nc = _emin_case("oseen_velocity")
+    A = sp.csr_matrix(A)
+    n = len(rows)
+    P0 = np.zeros((n, nc))
+    for i, cols in enumerate(rows):
+        if cols:
+            P0[i, cols] = 1.0 / len(cols)
+    R0 = -_test_projection(A @ sp.csr_matrix(P0), rows, nc)
+    Q = _test_projection(A @ sp.csr_matrix(R0), rows, nc)
+    P1 = emin_step(A, rows, nc, "gmres").toarray()
+    D = P1 - P0
+    a = np.sum(D * R0) / np.sum(R0 * R0)
+    assert np.linalg.norm(D - a * R0) <= 1e-12 * np.linalg.norm(D)
+    res1 = _test_projection(A @ sp.csr_matrix(P1), rows, nc)
+    res0 = _test_projection(A @ sp.csr_matrix(P0), rows, nc)
+    assert abs(np.sum(Q * res1)) <= 1e-10 * abs(np.sum(Q * res0))
+    nrm = lambda t: np.linalg.norm(_test_projection(A @ sp.csr_matrix(P0 + t * R0), rows, nc))  # noqa: E731
+    assert nrm(1.05 * a) > np.linalg.norm(res1) and nrm(0.95 * a) > np.linalg.norm(res1)
+
+
+# ----------------------------------------------------------------------------
+# Hierarchy shape at 592,387 dofs (Section 6.1, Tables 2 and 3)
+
+@pytest.fixture(scope="module")
+def lid256():
+    p = stokes_lid_2d(256, nrhs=1, body="none", lo=-1.0, hi=1.0)
+    return setup_hierarchy(p, Params(max_levels=4))
+
+
+def test_first_coarse_level_in_the_papers_tau1_band(lid256):
+    """Section 6.1 (Table 2 discussion): the first coarse matrix of the 592,387-dof lid
+    cavity has between 28,088 rows (tau1 = 0) and 74,428 rows (tau1 = 0.25); tau1 = 0.06
+    lies between.  The perfect distance-4 coarsening gives 65^2 pressures and 127^2
+    interior velocities per component: 36,483 rows."""
+    assert lid256.levels[0].N == 592387
+    assert 28088 <= lid256.levels[1].N <= 74428
+    assert lid256.levels[1].N == 36483
+
+
+@pytest.mark.xfail(strict=True, reason="reading 5's coarsening misses the paper's coarse levels below level 1: "
+                   "level 2 has 4,629 rows (paper 2,199-2,739) and level 3 15 pressures (paper 150); on level 1 "
+                   "tau1 = 0.06 keeps only the diagonal couplings of B B^T (axis neighbours scale to 0.009)")
+def test_second_and_third_levels_match_tables_2_and_3(lid256):
+    """Section 6.1: the level-2 matrix of the 592,387-dof problem has 2,199 (tau2 = 0.4) to
+    2,739 rows; Table 3's coarsest operator shown (level 3) has 150 pressure dofs."""
+    assert 2199 <= lid256.levels[2].N <= 2739
+    assert abs(lid256.levels[3].n_p - 150) <= 30
+
+
+def test_level_one_pressure_graph_keeps_only_diagonal_neighbours(lid256):
+    """Why the coarser levels miss Tables 2-3 (measured, reading 5 of the design notes): on the
+    Galerkin level 1 the scaled couplings |z_ij| / sqrt(z_ii z_jj) of Z = B_1 B_1^T are
+    ~0.14 to the diagonal neighbours but ~0.009 to the axis neighbours and ~0.056 two
+    apart, so tau1 = 0.06 leaves an interior node only its four diagonal neighbours (the
+    graph splits into the two checkerboard classes) and Alg. 3 keeps 497 of the 4,225
+    pressures where a perfect coarsening keeps 17^2 = 289."""
+    from oracle.hierarchy import spgemm
+    L1 = lid256.levels[1]
+    adj = L1.info["adjp"]
+    m = 65
+    X = L1.pcoords
+    h = X[1, 0] - X[0, 0]
+    for c in (32 * m + 32, 20 * m + 40):
+        offs = sorted(tuple(np.round((X[j] - X[c]) / h).astype(int)) for j in adj[c])
+        assert offs == [(-1, -1), (-1, 1), (1, -1), (1, 1)]
+    assert L1.info["n_cp"] == 497

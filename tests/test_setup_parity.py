@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 import scipy.sparse as sp
 
-from synth import stokes_lid_2d, stokes_pinned_2d, oseen_recirculating_2d, make_problem
+from synth import stokes_lid_2d, stokes_pinned_2d, oseen_recirculating_2d, make_problem, with_perturbed_coordinates
 from oracle import setup_hierarchy, Params
 
 g = pytest.importorskip("paper_1607_02489_gb300")
@@ -309,3 +309,14 @@ def test_pinned_coarse_inverse_is_refined_beyond_cond_u():
     raw = np.linalg.pinv(A, rcond=1e-12)
     assert np.linalg.norm(raw - Xo) > 1e-11 * np.linalg.norm(Xo)  # the SVD alone is cond * u away
     assert np.linalg.norm(X - Xo) <= 1e-13 * np.linalg.norm(Xo)
+
+
+@pytest.mark.parametrize("n, amp, seed", [(16, 0.35, 100), (16, 0.35, 102), (20, 0.2, 100), (20, 0.35, 101)])
+def test_perturbed_coordinates_setup_matches_oracle(n, amp, seed):
+    """Perturbed node positions make Alg. 3 leave badly covered F-points, which
+    find_extra_dist3_Cpoints converts (the oracle reports them): the library's C/F
+    splits, with those extra C-points, patterns and values match the oracle's."""
+    p = with_perturbed_coordinates(stokes_lid_2d(n, nrhs=1), amp, seed)
+    Ho = setup_hierarchy(p)
+    assert sum(len(L.info.get("extra_p", [])) for L in Ho.levels[:-1]) >= 2
+    _compare(p)

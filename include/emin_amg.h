@@ -138,6 +138,36 @@ amg_status amg_hierarchy_create(const amg_problem* prob, const amg_params* prm, 
 amg_status amg_hierarchy_create_reuse(amg_handle prev, const amg_problem* problem, const amg_params* params,
                                       void* stream, amg_handle* out);
 
+/* Checkpoint of a hierarchy: write the operators and transfers of every level (the
+ * result of Alg. 1's coarsening, EMIN steps and Galerkin products) to a file, and
+ * build a hierarchy from such a file without repeating that setup.  Import forms
+ * only the smoother data (Section 5: the Braess-Sarazin diagonal, Schur complement
+ * and its Gauss-Seidel order, or the Vanka blocks or ILU(1) factors, as prm asks)
+ * and the coarsest pseudo-inverse, then uploads like amg_hierarchy_create.  Another
+ * program can write the file (a reference implementation's hierarchy, for V-cycle
+ * parity independent of the setup); an imported hierarchy also serves as the
+ * `prev` of amg_hierarchy_create_reuse.
+ *
+ * File layout, little-endian, no padding:
+ *   char[8] "EMINAMG1"; int32 version = 1; int32 levels; int32 symmetric (1 Stokes,
+ *   0 Oseen); then per level l = 0 (finest) .. levels-1:
+ *     int32 dim, n_v, n_p, pinned (-1 none)
+ *     csr A (n_v x n_v), csr B (n_p x dim*n_v), csr Bt (dim*n_v x n_p)
+ *     float64 vcoords[n_v*dim], float64 pcoords[n_p*dim], int32 p2v[n_p],
+ *     uint8 dirichlet[n_v]
+ *     every level but the last: csr P (n_v x n_v'), csr Pp (n_p x n_p'),
+ *     csr R (n_v' x n_v), csr Rp (n_p' x n_p), int32 n_p', int32 Cp[n_p'],
+ *     int32 n_v', int32 Cv[n_v'] (coarse points as fine indices; n_v', n_p' the
+ *     next level's sizes)
+ *   csr: int32 nrows, int32 ncols, int64 nnz, int64 rowptr[nrows+1],
+ *        int32 col[nnz] (strictly ascending per row), float64 val[nnz].
+ * Import checks every size and CSR structure and returns AMG_ERR_ARG naming the
+ * first problem (or a file that cannot be read); export returns AMG_ERR_ARG when
+ * the file cannot be written.  prm as for amg_hierarchy_create (NULL: defaults;
+ * the coarsening parameters are unused).  Import synchronises `stream` once. */
+amg_status amg_hierarchy_export(amg_handle h, const char* path);
+amg_status amg_hierarchy_import(const char* path, const amg_params* prm, void* stream, amg_handle* out);
+
 /* z = M^-1 r: one V(pre, post) cycle from a zero initial guess (Alg. 1's relaxation
  * form on every level, coarse correction by R and P).  r and z: device, N x nrhs,
  * FP64; 1 <= nrhs <= max_nrhs.  r and z must not overlap.  Asynchronous. */

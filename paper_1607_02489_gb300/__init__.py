@@ -21,7 +21,8 @@ LIB_PATH = _build.LIB
 AMG_OK, AMG_NOT_CONVERGED, AMG_BREAKDOWN = 0, 1, 2
 STATUS_NAMES = {0: "OK", 1: "NOT_CONVERGED", 2: "BREAKDOWN", -1: "ERR_ARG", -2: "ERR_OOM", -3: "ERR_CUDA",
                 -4: "ERR_SETUP"}
-EXPORTED = ["amg_params_default", "amg_hierarchy_create", "amg_hierarchy_create_reuse", "amg_vcycle_apply", "amg_apply", "amg_fgmres_solve",
+EXPORTED = ["amg_params_default", "amg_hierarchy_create", "amg_hierarchy_create_reuse", "amg_hierarchy_export",
+            "amg_hierarchy_import", "amg_vcycle_apply", "amg_apply", "amg_fgmres_solve",
             "amg_fgmres_solve_host", "amg_num_levels", "amg_level_get_info", "amg_level_get_matrix",
             "amg_level_get_points", "amg_hierarchy_destroy", "amg_last_error", "amg_profile_vcycle", "amg_kernel_launches", "amg_apply_noalloc", "amg_gs_variant", "amg_row_shape", "amg_level_get_vanka", "amg_level_get_ilu",
             "amg_coarse_inverse", "amg_set_wait_limit",
@@ -98,6 +99,10 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.amg_hierarchy_create_reuse.argtypes = [vp, ctypes.POINTER(AmgProblem), ctypes.POINTER(AmgParams), vp,
                                                ctypes.POINTER(vp)]
     lib.amg_hierarchy_create_reuse.restype = ctypes.c_int
+    lib.amg_hierarchy_export.argtypes = [vp, ctypes.c_char_p]
+    lib.amg_hierarchy_export.restype = ctypes.c_int
+    lib.amg_hierarchy_import.argtypes = [ctypes.c_char_p, ctypes.POINTER(AmgParams), vp, ctypes.POINTER(vp)]
+    lib.amg_hierarchy_import.restype = ctypes.c_int
     lib.amg_vcycle_apply.argtypes = [vp, vp, vp, ctypes.c_int, vp]
     lib.amg_vcycle_apply.restype = ctypes.c_int
     lib.amg_apply.argtypes = [vp, vp, vp, ctypes.c_int, vp]
@@ -237,6 +242,26 @@ class Hierarchy:
             _check(lib.amg_hierarchy_create(ctypes.byref(pb), ctypes.byref(self.params), sptr,
                                             ctypes.byref(handle)))
         self._h = handle
+
+    @classmethod
+    def from_file(cls, path, stream=None, **params) -> "Hierarchy":
+        """amg_hierarchy_import: a hierarchy from a checkpoint file (operators and transfers
+        of every level; the smoother data and the coarsest solve are formed)."""
+        lib = load()
+        self = cls.__new__(cls)
+        self.params = default_params(**params)
+        handle = ctypes.c_void_p()
+        sptr = ctypes.c_void_p(0) if self.params.host_only else _stream_ptr(stream)
+        _check(lib.amg_hierarchy_import(os.fsencode(path), ctypes.byref(self.params), sptr, ctypes.byref(handle)))
+        self._h = handle
+        info = self.level_info(0)
+        self.dim, self.n_v, self.n_p = info["dim"], info["n_v"], info["n_p"]
+        self.N = self.dim * self.n_v + self.n_p
+        return self
+
+    def export(self, path):
+        """amg_hierarchy_export: write the hierarchy's checkpoint file."""
+        _check(load().amg_hierarchy_export(self._h, os.fsencode(path)))
 
     def close(self):
         if getattr(self, "_h", None):

@@ -3,7 +3,7 @@
 The host setup (csrc/setup.cpp) is built with -ffp-contract=off so that the
 integer decisions it takes from floating point do not change with the
 machine's fused multiply-add; the CUDA sources are compiled for
-compute_103a / sm_103a only.  The five translation units compile in parallel.
+compute_103a / sm_103a only.  The translation units compile in parallel.
 """
 from __future__ import annotations
 
@@ -47,6 +47,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     common = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off", "-I", CSRC]
     jobs = [
         ([nvcc, "-x", "c++", "-c", os.path.join(CSRC, "setup.cpp"), "-o", os.path.join(BUILD, "setup.o")] + common),
+        ([nvcc, "-x", "c++", "-c", os.path.join(CSRC, "checkpoint.cpp"), "-o", os.path.join(BUILD, "checkpoint.o")]
+         + common),
         ([nvcc, "-c", os.path.join(CSRC, "solver.cu"), "-o", os.path.join(BUILD, "solver.o")] + ARCH + common),
         ([nvcc, "-c", os.path.join(CSRC, "server.cu"), "-o", os.path.join(BUILD, "server.o")] + ARCH + common),
         ([nvcc, "-c", os.path.join(CSRC, "vcycle_inst.cu"), "-DEMIN_VCYCLE_DOUBLE", "-o",
@@ -63,7 +65,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
             errors.append(" ".join(cmd) + "\n" + out)
     if errors:
         raise RuntimeError("building libemin_amg.so failed:\n" + "\n".join(errors))
-    objs = [os.path.join(BUILD, o) for o in ("setup.o", "solver.o", "server.o", "vcycle_f64.o", "vcycle_f32.o")]
+    objs = [os.path.join(BUILD, o) for o in ("setup.o", "checkpoint.o", "solver.o", "server.o", "vcycle_f64.o",
+                                             "vcycle_f32.o")]
     tmp = LIB + ".tmp"
     link = [nvcc, "-shared", "-o", tmp] + objs + ARCH
     r = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)

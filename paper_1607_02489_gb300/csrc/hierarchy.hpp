@@ -103,6 +103,7 @@ struct amg_hierarchy_core {
   VCycleIface* v64 = nullptr;  // FP64 cycle; also holds the finest FP64 matrices for residuals
   VCycleIface* v32 = nullptr;
   long long N = 0;
+  bool symmetric = true;  // Stokes (R = P^T) or Oseen (Petrov-Galerkin) problem
   VCycleIface* vc() const { return prm.vcycle_fp32 ? v32 : v64; }
 };
 

@@ -1202,6 +1202,14 @@ std::vector<HostLevel> build_hierarchy(HostLevel fine, const SetupParams& prm) {
     }
     levels.push_back(std::move(Lc));
   }
+  complete_hierarchy(levels, prm, false);
+  return levels;
+}
+
+void complete_hierarchy(std::vector<HostLevel>& levels, const SetupParams& prm, bool relaxation) {
+  if (levels.empty()) throw std::runtime_error("a hierarchy needs at least one level");
+  if (relaxation)
+    for (HostLevel& L : levels) form_relaxation(L, prm);
   HostLevel& C = levels.back();
   if (C.N() > 4096) throw std::runtime_error("coarsest level too large for the dense solve: " + std::to_string(C.N()));
   {
@@ -1216,7 +1224,6 @@ std::vector<HostLevel> build_hierarchy(HostLevel fine, const SetupParams& prm) {
     for (size_t l = 0; l + 1 < levels.size(); ++l) form_ilu(levels[l], prm.symmetric, prm.ilu_order);
   for (size_t l = 0; l + 1 < levels.size(); ++l)
     if (levels[l].n_p <= kGsDenseMaxRows) form_dense_gs(levels[l], prm.gs_iters);
-  return levels;
 }
 
 }  // namespace emin

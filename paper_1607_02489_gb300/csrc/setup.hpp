@@ -79,4 +79,17 @@ struct HostLevel {
 // Builds every level; throws std::runtime_error with a message on failure.
 std::vector<HostLevel> build_hierarchy(HostLevel fine, const SetupParams& prm);
 
+// The smoother data of levels whose operators and transfers are given: with
+// `relaxation`, the Braess-Sarazin data of every level (D, S, strips, colors);
+// then the coarsest pseudo-inverse and, as prm asks, the Vanka blocks, the ILU(1)
+// factors and the dense Gauss-Seidel maps.  build_hierarchy ends with it; an
+// imported hierarchy goes through it whole.
+void complete_hierarchy(std::vector<HostLevel>& levels, const SetupParams& prm, bool relaxation);
+
+// Checkpoint file of a hierarchy's operators and transfers (format in emin_amg.h,
+// amg_hierarchy_export).  read_hierarchy checks sizes and CSR structure and throws
+// std::runtime_error naming the first problem.
+void write_hierarchy(const std::vector<HostLevel>& levels, bool symmetric, const std::string& path);
+std::vector<HostLevel> read_hierarchy(const std::string& path, bool* symmetric);
+
 }  // namespace emin

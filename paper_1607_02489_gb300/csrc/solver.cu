@@ -840,30 +840,68 @@ amg_status amg_hierarchy_create_reuse(amg_handle prev, const amg_problem* pb, co
 }
 
 namespace {
+// The parameters of a create or import call (defaults for NULL); "" if valid, else why not.
+std::string check_params(const amg_params* prm_in, amg_params& prm) {
+  if (prm_in)
+    prm = *prm_in;
+  else
+    amg_params_default(&prm);
+  if (prm.max_nrhs < 1 || prm.max_nrhs > 32) return "max_nrhs must be in 1..32";
+  if (prm.gs_iters < 0 || prm.pre < 0 || prm.post < 0 || prm.omega <= 0.0) return "invalid smoother parameters";
+  if (prm.smoother < 0 || prm.smoother > 2) return "smoother must be 0 (Braess-Sarazin), 1 (Vanka) or 2 (ILU(1))";
+  if (prm.smoother == 1 && !(prm.vanka_omega > 0.0)) return "vanka_omega must be positive";
+  if (prm.ilu_order != 0 && prm.ilu_order != 1) return "ilu_order must be 0 or 1";
+  if (prm.coarse != 0 && prm.coarse != 1) return "coarse must be 0 (pseudo-inverse) or 1 (Vanka)";
+  if (prm.coarse == 1 && !(prm.vanka_omega > 0.0)) return "vanka_omega must be positive";
+  return "";
+}
+
+SetupParams setup_params(const amg_params& prm, bool symmetric) {
+  SetupParams sp;
+  sp.tau1 = prm.tau1;
+  sp.tau2sq = prm.tau2sq;
+  sp.c = prm.omega_on_D ? 1.0 / prm.omega : prm.omega;
+  sp.max_coarse = prm.max_coarse;
+  sp.max_levels = prm.max_levels;
+  sp.symmetric = symmetric;
+  sp.vanka = prm.smoother == 1;
+  sp.ilu = prm.smoother == 2;
+  sp.ilu_order = prm.ilu_order;
+  sp.vanka_coarse = prm.coarse == 1;
+  sp.gs_iters = prm.gs_iters;
+  return sp;
+}
+
+// The device cycles of a hierarchy whose host levels are complete (throws).
+void upload_handle(amg_hierarchy* h, const SetupParams& sp, void* stream) {
+  const amg_params& prm = h->prm;
+  h->N = h->host[0].N();
+  if (prm.host_only) return;
+  const double vomega = prm.smoother == 1 ? prm.vanka_omega : 0.0;
+  const double comega = prm.coarse == 1 ? prm.vanka_omega : 0.0;
+  h->v64 = make_vcycle_f64(h->host, sp.c, prm.gs_iters, prm.pre, prm.post, round_k(prm.max_nrhs), vomega, sp.ilu,
+                           comega);
+  h->v64->set_autotune(prm.autotune != 0);
+  if (prm.vcycle_fp32) {
+    h->v32 = make_vcycle_f32(h->host, sp.c, prm.gs_iters, prm.pre, prm.post, round_k(prm.max_nrhs), vomega, sp.ilu,
+                             comega);
+    h->v32->set_autotune(prm.autotune != 0);
+  }
+  EMIN_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+}
+
 amg_status create_impl(const amg_problem* pb, const amg_params* prm_in, void* stream, amg_handle* out,
                        const amg_hierarchy* reuse) {
   if (!pb || !out) return fail(AMG_ERR_ARG, "null problem or output handle");
   *out = nullptr;
   amg_params prm;
-  if (prm_in)
-    prm = *prm_in;
-  else
-    amg_params_default(&prm);
+  std::string why = check_params(prm_in, prm);
+  if (!why.empty()) return fail(AMG_ERR_ARG, why);
   if (pb->dim < 2 || pb->dim > 3 || pb->n_vnodes <= 0 || pb->n_pnodes <= 0)
     return fail(AMG_ERR_ARG, "dim must be 2 or 3 and node counts positive");
   if (!pb->A_val || !pb->B_val || !pb->vcoords || !pb->pcoords || !pb->p2v || !pb->v_dirichlet)
     return fail(AMG_ERR_ARG, "null problem array");
-  if (prm.max_nrhs < 1 || prm.max_nrhs > 32) return fail(AMG_ERR_ARG, "max_nrhs must be in 1..32");
-  if (prm.gs_iters < 0 || prm.pre < 0 || prm.post < 0 || prm.omega <= 0.0)
-    return fail(AMG_ERR_ARG, "invalid smoother parameters");
-  if (prm.smoother < 0 || prm.smoother > 2)
-    return fail(AMG_ERR_ARG, "smoother must be 0 (Braess-Sarazin), 1 (Vanka) or 2 (ILU(1))");
-  if (prm.smoother == 1 && !(prm.vanka_omega > 0.0)) return fail(AMG_ERR_ARG, "vanka_omega must be positive");
-  if (prm.ilu_order != 0 && prm.ilu_order != 1) return fail(AMG_ERR_ARG, "ilu_order must be 0 or 1");
-  if (prm.coarse != 0 && prm.coarse != 1) return fail(AMG_ERR_ARG, "coarse must be 0 (pseudo-inverse) or 1 (Vanka)");
-  if (prm.coarse == 1 && !(prm.vanka_omega > 0.0)) return fail(AMG_ERR_ARG, "vanka_omega must be positive");
   if (pb->pinned_p >= pb->n_pnodes) return fail(AMG_ERR_ARG, "pinned pressure out of range");
-  std::string why;
   if (!check_csr(pb->A_rowptr, pb->A_col, pb->n_vnodes, pb->n_vnodes, why)) return fail(AMG_ERR_ARG, "A: " + why);
   if (!check_csr(pb->B_rowptr, pb->B_col, pb->n_pnodes, pb->dim * pb->n_vnodes, why))
     return fail(AMG_ERR_ARG, "B: " + why);
@@ -883,35 +921,12 @@ amg_status create_impl(const amg_problem* pb, const amg_params* prm_in, void* st
     fine.pX.assign(pb->pcoords, pb->pcoords + (size_t)fine.n_p * fine.dim);
     fine.p2v.assign(pb->p2v, pb->p2v + fine.n_p);
     fine.dirichlet.assign(pb->v_dirichlet, pb->v_dirichlet + fine.n_v);
-    SetupParams sp;
-    sp.tau1 = prm.tau1;
-    sp.tau2sq = prm.tau2sq;
-    sp.c = prm.omega_on_D ? 1.0 / prm.omega : prm.omega;
-    sp.max_coarse = prm.max_coarse;
-    sp.max_levels = prm.max_levels;
-    sp.symmetric = pb->symmetric != 0;
-    sp.vanka = prm.smoother == 1;
-    sp.ilu = prm.smoother == 2;
-    sp.ilu_order = prm.ilu_order;
-    sp.vanka_coarse = prm.coarse == 1;
-    sp.gs_iters = prm.gs_iters;
+    SetupParams sp = setup_params(prm, pb->symmetric != 0);
     sp.reuse = reuse ? &reuse->host : nullptr;
     h->host = build_hierarchy(std::move(fine), sp);
     h->prm = prm;
-    h->N = h->host[0].N();
-    if (!prm.host_only) {
-      const double vomega = prm.smoother == 1 ? prm.vanka_omega : 0.0;
-      const double comega = prm.coarse == 1 ? prm.vanka_omega : 0.0;
-      h->v64 = make_vcycle_f64(h->host, sp.c, prm.gs_iters, prm.pre, prm.post, round_k(prm.max_nrhs), vomega, sp.ilu,
-                               comega);
-      h->v64->set_autotune(prm.autotune != 0);
-      if (prm.vcycle_fp32) {
-        h->v32 = make_vcycle_f32(h->host, sp.c, prm.gs_iters, prm.pre, prm.post, round_k(prm.max_nrhs), vomega,
-                                 sp.ilu, comega);
-        h->v32->set_autotune(prm.autotune != 0);
-      }
-      EMIN_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
-    }
+    h->symmetric = sp.symmetric;
+    upload_handle(h.get(), sp, stream);
   } catch (const std::bad_alloc&) {
     return fail(AMG_ERR_OOM, "host allocation failed during setup");
   } catch (const std::exception& e) {
@@ -923,6 +938,47 @@ amg_status create_impl(const amg_problem* pb, const amg_params* prm_in, void* st
 }
 
 }  // namespace
+
+amg_status amg_hierarchy_export(amg_handle h, const char* path) {
+  if (!h || !path) return fail(AMG_ERR_ARG, "amg_hierarchy_export: null handle or path");
+  try {
+    write_hierarchy(h->host, h->symmetric, path);
+  } catch (const std::exception& e) {
+    return fail(AMG_ERR_ARG, std::string("amg_hierarchy_export: ") + e.what());
+  }
+  return AMG_OK;
+}
+
+amg_status amg_hierarchy_import(const char* path, const amg_params* prm_in, void* stream, amg_handle* out) {
+  if (!path || !out) return fail(AMG_ERR_ARG, "amg_hierarchy_import: null path or output handle");
+  *out = nullptr;
+  amg_params prm;
+  std::string why = check_params(prm_in, prm);
+  if (!why.empty()) return fail(AMG_ERR_ARG, "amg_hierarchy_import: " + why);
+  std::unique_ptr<amg_hierarchy> h(new amg_hierarchy());
+  bool symmetric = true;
+  try {
+    h->host = read_hierarchy(path, &symmetric);
+  } catch (const std::bad_alloc&) {
+    return fail(AMG_ERR_OOM, "amg_hierarchy_import: host allocation failed");
+  } catch (const std::exception& e) {
+    return fail(AMG_ERR_ARG, std::string("amg_hierarchy_import: ") + e.what());
+  }
+  try {
+    const SetupParams sp = setup_params(prm, symmetric);
+    complete_hierarchy(h->host, sp, true);
+    h->prm = prm;
+    h->symmetric = symmetric;
+    upload_handle(h.get(), sp, stream);
+  } catch (const std::bad_alloc&) {
+    return fail(AMG_ERR_OOM, "amg_hierarchy_import: host allocation failed");
+  } catch (const std::exception& e) {
+    const std::string m = e.what();
+    return fail(m.find("cuda") != std::string::npos ? AMG_ERR_CUDA : AMG_ERR_SETUP, "amg_hierarchy_import: " + m);
+  }
+  *out = h.release();
+  return AMG_OK;
+}
 
 amg_status amg_vcycle_apply(amg_handle h, const double* r, double* z, int nrhs, void* stream) {
   if (!h || !r || !z) return fail(AMG_ERR_ARG, "null argument");

@@ -116,6 +116,13 @@ typedef struct {
                          constant, whose B vanishes: no Vanka step exists there), and setup
                          fails (AMG_ERR_SETUP) if a coarsest Vanka block is still numerically
                          singular (e.g. coarsening reused from a hierarchy built without it) */
+  int device_setup;   /* 1 (default): the numeric setup work runs on the GPU where it can:
+                         amg_hierarchy_create_reuse forms the filtered auxiliary matrices, the
+                         EMIN steps, the restrictions, the Galerkin products and the
+                         Braess-Sarazin data there (every pattern is the previous hierarchy's),
+                         and every build forms the dense Gauss-Seidel maps there; values agree
+                         with the host setup to rounding.  0: all setup on the host.  Ignored
+                         with host_only. */
 } amg_params;
 
 void amg_params_default(amg_params* prm);
@@ -276,6 +283,14 @@ amg_status amg_level_get_vanka(amg_handle h, int level, int* nblocks, int* ndofs
 amg_status amg_level_get_ilu(amg_handle h, int level, int* n, long long* nnz_lower, long long* nnz_upper,
                              int* depth_lower, int* depth_upper, int* perm, int* lower_ptr, int* lower_col,
                              double* lower_val, int* upper_ptr, int* upper_col, double* upper_val, double* pivots);
+
+/* The dense Gauss-Seidel map of a level of at most 4608 pressures: the n_p x n_p
+ * matrix M (row-major) with dp = M g for the gs_iters Gauss-Seidel iterations on
+ * S dp = g from dp = 0 in the order (strip parity, color, index) (Section 5.2's
+ * Schur complement solve, as one linear map), formed at setup by running the sweep
+ * on every unit vector (on the GPU with device_setup).  *n gets n_p; M may be NULL.
+ * AMG_ERR_ARG for a level without a map (larger levels, the coarsest). */
+amg_status amg_level_get_gs_map(amg_handle h, int level, int* n, double* M);
 
 /* The coarsest level's FP64 pseudo-inverse X (N_c x N_c, row-major, N_c the N of
  * the last level), which the coarsest solve applies: the minimum-norm solution of

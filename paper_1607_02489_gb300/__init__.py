@@ -25,7 +25,7 @@ EXPORTED = ["amg_params_default", "amg_hierarchy_create", "amg_hierarchy_create_
             "amg_hierarchy_import", "amg_vcycle_apply", "amg_apply", "amg_fgmres_solve",
             "amg_fgmres_solve_host", "amg_num_levels", "amg_level_get_info", "amg_level_get_matrix",
             "amg_level_get_points", "amg_hierarchy_destroy", "amg_last_error", "amg_profile_vcycle", "amg_kernel_launches", "amg_apply_noalloc", "amg_gs_variant", "amg_row_shape", "amg_level_get_vanka", "amg_level_get_ilu",
-            "amg_coarse_inverse", "amg_set_wait_limit",
+            "amg_coarse_inverse", "amg_set_wait_limit", "amg_level_get_gs_map",
             "amg_server_params_default", "amg_server_create", "amg_server_reserve", "amg_server_submit", "amg_server_progress",
             "amg_server_result", "amg_server_state", "amg_server_get_stats", "amg_server_destroy", "amg_server_last_error"]
 KERNEL_CLASSES = ["velocity", "schur_rhs", "gs_color", "update", "residual", "restrict", "prolong", "coarse", "vanka",
@@ -52,7 +52,7 @@ class AmgParams(ctypes.Structure):
                 ("post", ctypes.c_int), ("max_coarse", ctypes.c_int), ("max_levels", ctypes.c_int),
                 ("vcycle_fp32", ctypes.c_int), ("max_nrhs", ctypes.c_int), ("host_only", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("smoother", ctypes.c_int), ("vanka_omega", ctypes.c_double),
-                ("ilu_order", ctypes.c_int), ("coarse", ctypes.c_int)]
+                ("ilu_order", ctypes.c_int), ("coarse", ctypes.c_int), ("device_setup", ctypes.c_int)]
 
 
 class AmgLevelInfo(ctypes.Structure):
@@ -134,6 +134,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.amg_level_get_ilu.argtypes = [vp, ctypes.c_int, _i32p, _i64p, _i64p, _i32p, _i32p, _i32p, _i32p, _i32p, _f64p,
                                       _i32p, _i32p, _f64p, _f64p]
     lib.amg_level_get_ilu.restype = ctypes.c_int
+    lib.amg_level_get_gs_map.argtypes = [vp, ctypes.c_int, _i32p, _f64p]
+    lib.amg_level_get_gs_map.restype = ctypes.c_int
     lib.amg_coarse_inverse.argtypes = [vp, _i32p, _f64p]
     lib.amg_coarse_inverse.restype = ctypes.c_int
     lib.amg_set_wait_limit.argtypes = [vp, ctypes.c_longlong]
@@ -418,6 +420,14 @@ class Hierarchy:
                                         _ptr(piv, ctypes.c_double)))
         return dict(perm=perm, lower=(lp, lc[:nl.value], lv[:nl.value]), upper=(up, uc[:nu.value], uv[:nu.value]),
                     pivots=piv, depth_lower=dl.value, depth_upper=du.value)
+
+    def level_gs_map(self, level: int) -> np.ndarray:
+        """The dense Gauss-Seidel map of a small level (amg_level_get_gs_map), n_p x n_p."""
+        n = ctypes.c_int()
+        _check(load().amg_level_get_gs_map(self._h, int(level), ctypes.byref(n), None))
+        M = np.zeros((n.value, n.value))
+        _check(load().amg_level_get_gs_map(self._h, int(level), None, _ptr(M, ctypes.c_double)))
+        return M
 
     def coarse_inverse(self) -> np.ndarray:
         """The coarsest level's pseudo-inverse (amg_coarse_inverse), N_c x N_c."""

@@ -51,6 +51,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
          + common),
         ([nvcc, "-c", os.path.join(CSRC, "solver.cu"), "-o", os.path.join(BUILD, "solver.o")] + ARCH + common),
         ([nvcc, "-c", os.path.join(CSRC, "server.cu"), "-o", os.path.join(BUILD, "server.o")] + ARCH + common),
+        ([nvcc, "-c", os.path.join(CSRC, "gpu_setup.cu"), "-o", os.path.join(BUILD, "gpu_setup.o")] + ARCH + common),
         ([nvcc, "-c", os.path.join(CSRC, "vcycle_inst.cu"), "-DEMIN_VCYCLE_DOUBLE", "-o",
           os.path.join(BUILD, "vcycle_f64.o")] + ARCH + common),
         ([nvcc, "-c", os.path.join(CSRC, "vcycle_inst.cu"), "-o", os.path.join(BUILD, "vcycle_f32.o")] + ARCH + common),
@@ -65,8 +66,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
             errors.append(" ".join(cmd) + "\n" + out)
     if errors:
         raise RuntimeError("building libemin_amg.so failed:\n" + "\n".join(errors))
-    objs = [os.path.join(BUILD, o) for o in ("setup.o", "checkpoint.o", "solver.o", "server.o", "vcycle_f64.o",
-                                             "vcycle_f32.o")]
+    objs = [os.path.join(BUILD, o) for o in ("setup.o", "checkpoint.o", "solver.o", "server.o", "gpu_setup.o",
+                                             "vcycle_f64.o", "vcycle_f32.o")]
     tmp = LIB + ".tmp"
     link = [nvcc, "-shared", "-o", tmp] + objs + ARCH
     r = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "../../include/emin_amg.h"
+#include "gpu_setup.hpp"
 #include "setup.hpp"
 #include "vcycle.cuh"
 
@@ -104,6 +105,9 @@ struct amg_hierarchy_core {
   VCycleIface* v32 = nullptr;
   long long N = 0;
   bool symmetric = true;  // Stokes (R = P^T) or Oseen (Petrov-Galerkin) problem
+  // device patterns and maps of this hierarchy's structure, built by the first
+  // device reuse of it and shared with the hierarchies reused from it
+  mutable std::shared_ptr<DeviceSetupPlan> plan;
   VCycleIface* vc() const { return prm.vcycle_fp32 ? v32 : v64; }
 };
 

@@ -1222,8 +1222,9 @@ void complete_hierarchy(std::vector<HostLevel>& levels, const SetupParams& prm, 
   if (prm.vanka_coarse) form_vanka(levels.back(), prm);
   if (prm.ilu)
     for (size_t l = 0; l + 1 < levels.size(); ++l) form_ilu(levels[l], prm.symmetric, prm.ilu_order);
-  for (size_t l = 0; l + 1 < levels.size(); ++l)
-    if (levels[l].n_p <= kGsDenseMaxRows) form_dense_gs(levels[l], prm.gs_iters);
+  if (prm.dense_gs)
+    for (size_t l = 0; l + 1 < levels.size(); ++l)
+      if (levels[l].n_p <= kGsDenseMaxRows) form_dense_gs(levels[l], prm.gs_iters);
 }
 
 }  // namespace emin

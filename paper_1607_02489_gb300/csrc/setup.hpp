@@ -21,6 +21,7 @@ struct SetupParams {
   bool ilu = false;        // form the ILU(1) factors (Section 5) on every level but the coarsest
   int ilu_order = 0;       // symmetric problems: 0 block order [u_x | u_y | p], 1 by node location
   int gs_iters = 5;        // Gauss-Seidel iterations per Braess-Sarazin step (for the dense map)
+  bool dense_gs = true;    // form the dense Gauss-Seidel maps on the host (else the caller forms them)
   size_t vanka_max_bytes = (size_t)16 << 30;  // limit on the FP64 block inverses of one level
   // When set: take the number of levels, the coarse points and the sparsity
   // patterns of P from this hierarchy (built for a matrix of the same structure)

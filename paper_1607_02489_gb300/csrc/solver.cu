@@ -11,6 +11,7 @@
 #include <string>
 #include <vector>
 
+#include "gpu_setup.hpp"
 #include "hierarchy.hpp"
 
 using namespace emin;
@@ -805,6 +806,7 @@ void amg_params_default(amg_params* p) {
   p->vanka_omega = 0.5;
   p->ilu_order = 0;
   p->coarse = 0;
+  p->device_setup = 1;
 }
 
 const char* amg_last_error(void) { return g_last_error.c_str(); }
@@ -853,6 +855,7 @@ std::string check_params(const amg_params* prm_in, amg_params& prm) {
   if (prm.ilu_order != 0 && prm.ilu_order != 1) return "ilu_order must be 0 or 1";
   if (prm.coarse != 0 && prm.coarse != 1) return "coarse must be 0 (pseudo-inverse) or 1 (Vanka)";
   if (prm.coarse == 1 && !(prm.vanka_omega > 0.0)) return "vanka_omega must be positive";
+  if (prm.device_setup != 0 && prm.device_setup != 1) return "device_setup must be 0 or 1";
   return "";
 }
 
@@ -922,8 +925,19 @@ amg_status create_impl(const amg_problem* pb, const amg_params* prm_in, void* st
     fine.p2v.assign(pb->p2v, pb->p2v + fine.n_p);
     fine.dirichlet.assign(pb->v_dirichlet, pb->v_dirichlet + fine.n_v);
     SetupParams sp = setup_params(prm, pb->symmetric != 0);
-    sp.reuse = reuse ? &reuse->host : nullptr;
-    h->host = build_hierarchy(std::move(fine), sp);
+    const bool on_device = prm.device_setup && !prm.host_only;
+    sp.dense_gs = !on_device;
+    if (reuse && on_device) {
+      // numeric setup on the GPU with the previous hierarchy's patterns; the plan
+      // (patterns and maps on the device) is shared along the sequence
+      h->host = build_hierarchy_reuse_device(std::move(fine), reuse->host, sp, reuse->plan, (cudaStream_t)stream);
+      h->plan = reuse->plan;
+      complete_hierarchy(h->host, sp, false);
+    } else {
+      sp.reuse = reuse ? &reuse->host : nullptr;
+      h->host = build_hierarchy(std::move(fine), sp);
+    }
+    if (on_device) form_dense_gs_device(h->host, prm.gs_iters, (cudaStream_t)stream);
     h->prm = prm;
     h->symmetric = sp.symmetric;
     upload_handle(h.get(), sp, stream);
@@ -965,8 +979,11 @@ amg_status amg_hierarchy_import(const char* path, const amg_params* prm_in, void
     return fail(AMG_ERR_ARG, std::string("amg_hierarchy_import: ") + e.what());
   }
   try {
-    const SetupParams sp = setup_params(prm, symmetric);
+    SetupParams sp = setup_params(prm, symmetric);
+    const bool on_device = prm.device_setup && !prm.host_only;
+    sp.dense_gs = !on_device;
     complete_hierarchy(h->host, sp, true);
+    if (on_device) form_dense_gs_device(h->host, prm.gs_iters, (cudaStream_t)stream);
     h->prm = prm;
     h->symmetric = symmetric;
     upload_handle(h.get(), sp, stream);
@@ -1160,6 +1177,15 @@ amg_status amg_level_get_ilu(amg_handle h, int level, int* n, long long* nnz_low
   if (upper_col) std::copy(L.il_U.col.begin(), L.il_U.col.end(), upper_col);
   if (upper_val) std::copy(L.il_U.val.begin(), L.il_U.val.end(), upper_val);
   if (pivots) std::copy(L.il_diag.begin(), L.il_diag.end(), pivots);
+  return AMG_OK;
+}
+
+amg_status amg_level_get_gs_map(amg_handle h, int level, int* n, double* M) {
+  if (!h || level < 0 || level >= (int)h->host.size()) return fail(AMG_ERR_ARG, "bad handle or level");
+  const HostLevel& L = h->host[level];
+  if (L.gs_dense.empty()) return fail(AMG_ERR_ARG, "the level has no dense Gauss-Seidel map");
+  if (n) *n = L.n_p;
+  if (M) std::copy(L.gs_dense.begin(), L.gs_dense.end(), M);
   return AMG_OK;
 }
 

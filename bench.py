@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--no-vanka", action="store_true", help="skip the Vanka-smoother side line")
     ap.add_argument("--no-ilu", action="store_true", help="skip the ILU(1)-smoother side line")
     ap.add_argument("--no-picard", action="store_true", help="skip the Picard (steady Navier-Stokes) side line")
+    ap.add_argument("--no-setup", action="store_true", help="skip the setup-time side line")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the side line with the other workloads (16x16 pinned, 512x512 Oseen x32, 48^3)")
     ap.add_argument("--configs", action="store_true",
                     help="instead of the default run: time the other workloads (16x16 pinned Stokes, 512x512 "
                          "Oseen x32, 48^3 Stokes) with the FP64 and FP32 V-cycles, and the oracle on the first two")
@@ -279,20 +282,12 @@ def run_oracle_config(key):
     return res
 
 
-def configs_main(args):
-    """One JSON line with the other workloads of the method: solves/s with the FP64 and
-    FP32 V-cycles on the GPU (inputs resident, CUDA events), the V-cycle kernels'
-    algorithmic bandwidth, and the oracle (1 core, 1 right-hand side) on C1 and C3."""
+def config_records(g, torch, reps=3):
+    """The other workloads of the method (16x16 pinned Stokes, 512x512 Oseen x32 at Re 10,
+    48^3 Stokes): setup seconds, and solves/s with the FP64 and FP32 V-cycles (inputs
+    resident, CUDA events over `reps` solves after one warm-up solve), the FGMRES
+    iterations and the V-cycle kernels' algorithmic bandwidth."""
     import numpy as np
-    import torch
-    oracle = {}
-    if not args.no_cpu_baseline:
-        for key in ("C1", "C3"):  # before any CUDA work in this process
-            setup_s, solve_s, its = run_oracle_config(key)
-            oracle[key] = {"solves_per_s": 1.0 / solve_s, "seconds": solve_s, "setup_s_untimed": setup_s,
-                           "iterations": its, "cores": 1, "sample": "1 right-hand side"}
-    import paper_1607_02489_gb300 as g
-    g._build.build()
     peak = measured_peaks()[0]
     out = {}
     for key, c in CONFIGS.items():
@@ -302,11 +297,13 @@ def configs_main(args):
         x = torch.zeros_like(b)
         rec = {"workload": c["name"], "dofs": int(p.N), "nrhs": k}
         for fp32 in (0, 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
             H = g.Hierarchy(p, max_nrhs=k, vcycle_fp32=fp32)
+            setup_s = time.perf_counter() - t0
             H.fgmres(b, x, rtol=RTOL, restart=60, maxit=MAXIT)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            reps = 3
             e0.record()
             for _ in range(reps):
                 st, its, rel = H.fgmres(b, x, rtol=RTOL, restart=60, maxit=MAXIT)
@@ -314,19 +311,64 @@ def configs_main(args):
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / reps
             s = 4 if fp32 else 8
-            vms, vcnt = H.profile_vcycle(k, reps=3)
-            vbytes = sum(algorithmic_bytes(H, l, cl, k, s) * vcnt[l, j] / 3
+            vms, vcnt = H.profile_vcycle(k, reps=2)
+            vbytes = sum(algorithmic_bytes(H, l, cl, k, s) * vcnt[l, j] / 2
                          for l in range(vms.shape[0]) for j, cl in enumerate(g.KERNEL_CLASSES) if vcnt[l, j])
-            gbs = vbytes / (vms.sum() / 3 / 1000.0) / 1e9
+            gbs = vbytes / (vms.sum() / 2 / 1000.0) / 1e9
             rec["fp32" if fp32 else "fp64"] = {"solves_per_s": k / (ms / 1000.0), "ms_per_solve_batch": ms,
                                                "status": int(st), "iterations_max": int(np.max(its)),
                                                "relres_max": float(np.max(rel)), "vcycle_kernels_GBs": gbs,
-                                               "vcycle_kernels_frac": gbs / peak}
+                                               "vcycle_kernels_frac": gbs / peak, "setup_s": setup_s,
+                                               "gs_variants": [v for v, _, _ in H.gs_variants(k)]}
             del H
-        if key in oracle:
-            rec["oracle"] = oracle[key]
+            torch.cuda.empty_cache()
         out[key] = rec
-    print(json.dumps({"metric": METRIC, "configs": out, "peak_GBs": peak, "data": "synthetic"}), flush=True)
+    return out
+
+
+def configs_main(args):
+    """One JSON line with the other workloads (config_records) and the oracle (1 core,
+    1 right-hand side) on the 16x16 pinned problem and the 512x512 Oseen problem."""
+    import torch
+    oracle = {}
+    if not args.no_cpu_baseline:
+        for key in ("C1", "C3"):  # before any CUDA work in this process
+            setup_s, solve_s, its = run_oracle_config(key)
+            oracle[key] = {"solves_per_s": 1.0 / solve_s, "seconds": solve_s, "setup_s_untimed": setup_s,
+                           "iterations": its, "cores": 1, "sample": "1 right-hand side"}
+    import paper_1607_02489_gb300 as g
+    g._build.build()
+    out = config_records(g, torch)
+    for key, rec in oracle.items():
+        out[key]["oracle"] = rec
+    print(json.dumps({"metric": METRIC, "configs": out, "peak_GBs": measured_peaks()[0], "data": "synthetic"}),
+          flush=True)
+
+
+def setup_line(g, torch, p):
+    """Setup seconds of the bench workload (592,387 dofs), host against device
+    (amg_params.device_setup): a fresh hierarchy, and hierarchies for the next
+    matrices of a sequence with the same structure reusing its coarsening (Section
+    6.1; the first device reuse also builds the structure's patterns and maps, later
+    ones share them).  Each includes the upload of the FP32 V-cycle."""
+    from synth import make_problem
+    q = make_problem(MESH, 2, 0.0, 1.0, bc="lid", nu=0.5, nrhs=1, seed=1)
+    out = {}
+    for dev in (0, 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        H = g.Hierarchy(p, max_nrhs=NRHS, vcycle_fp32=1, device_setup=dev)
+        t1 = time.perf_counter()
+        R1 = g.Hierarchy(q, reuse=H, max_nrhs=NRHS, vcycle_fp32=1, device_setup=dev)
+        t2 = time.perf_counter()
+        R2 = g.Hierarchy(p, reuse=R1, max_nrhs=NRHS, vcycle_fp32=1, device_setup=dev)
+        t3 = time.perf_counter()
+        out["device" if dev else "host"] = {"fresh_s": t1 - t0, "first_reuse_s": t2 - t1, "reuse_s": t3 - t2}
+        del R2, R1, H
+    return {"workload": "the bench's 256x256 lid cavity (fresh), then two more matrices of the same structure "
+                        "(nu = 0.5, then nu = 1 again) reusing the coarsening", **out,
+            "paper_context": {"setup_s": 13.34, "incremental_setup_s": 3.60,
+                              "source": "Table 1 and Section 6.1 (BS(2,2), 592,387 dofs; MueLu, hardware unstated)"}}
 
 
 def _oracle_worker(n_solves, q):
@@ -748,6 +790,10 @@ def main():
     if not args.no_picard and world == 1:
         picard = picard_line(g, torch)
 
+    setup = None
+    if not args.no_setup and world == 1:
+        setup = setup_line(g, torch, p)
+
     serving = None
     if not args.no_serve:
         serving = serve(g, torch, dev, args.serve_requests, seed=rank, max_active=args.serve_active,
@@ -756,6 +802,12 @@ def main():
             wall, reqs = replica_aggregate(dist, dev, serving["wall_s"], serving["requests"])
             _, rhs = replica_aggregate(dist, dev, serving["wall_s"], serving["rhs_solves"])
             serving["all_ranks"] = {"requests_per_s": reqs / wall, "solves_per_s": rhs / wall}
+
+    configs = None
+    if not args.no_configs and world == 1:
+        del H64
+        torch.cuda.empty_cache()
+        configs = config_records(g, torch, reps=2)
 
     if rank == 0:
         lat_sorted = sorted(lat32)
@@ -774,6 +826,7 @@ def main():
                                {"p50": serving["latency_ms"]["p50"], "p99": serving["latency_ms"]["p99"],
                                 "source": "serving stream (arrival to result on the host)"}),
                 "serving": serving, "accuracy": accuracy, "vanka": vanka, "ilu": ilu, "picard": picard,
+                "setup": setup, "configs": configs,
                 "e2e": e2e, "gpu_launches": launches32, "clocks": clocks, "roofline": roofline,
                 "vcycle_us_by_kernel": breakdown, "gs_variants": gs_variants,
                 "row_shapes": {f"L{l}": "".join(str(v) for v in d.values()) for l, d in H32.row_shapes(NRHS).items()},

@@ -1,5 +1,6 @@
 // Numeric hierarchy setup on the GPU (see gpu_setup.hpp).
 #include "gpu_setup.hpp"
+#include "trace.hpp"
 
 #include <algorithm>
 #include <cstdint>
@@ -451,8 +452,11 @@ std::vector<HostLevel> build_hierarchy_reuse_device(HostLevel fine, const std::v
     throw std::runtime_error("reused hierarchy does not match the problem's structure");
   int dev = -1;
   SETUP_CUDA(cudaGetDevice(&dev));
-  if (!plan || plan->device != dev || plan->levels.size() != prev.size() || plan->symmetric != prm.symmetric)
+  if (!plan || plan->device != dev || plan->levels.size() != prev.size() || plan->symmetric != prm.symmetric) {
+    TraceRange r("device setup: patterns and maps of the structure");
     plan = make_plan(prev, prm.symmetric);
+  }
+  TraceRange range("device setup: numeric (filtering, EMIN, R, RAP, S)");
   const size_t nl = prev.size();
   const double tau = prm.tau1_for(fine.dim);
   Arena work;
@@ -583,6 +587,7 @@ std::vector<HostLevel> build_hierarchy_reuse_device(HostLevel fine, const std::v
 }
 
 void form_dense_gs_device(std::vector<HostLevel>& levels, int iters, cudaStream_t s) {
+  TraceRange range("device setup: dense Gauss-Seidel maps");
   for (size_t l = 0; l + 1 < levels.size(); ++l) {
     HostLevel& L = levels[l];
     if (L.n_p > kGsDenseMaxRows) continue;

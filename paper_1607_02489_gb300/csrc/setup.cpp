@@ -4,6 +4,7 @@
 // point (filtering, the packing heuristic, the mid-point test) must not
 // depend on whether the compiler fuses a multiply and an add.
 #include "setup.hpp"
+#include "trace.hpp"
 
 #include <algorithm>
 #include <cmath>
@@ -618,6 +619,7 @@ void finish_interpolation(HostLevel& L, HostLevel& Lc, const SetupParams& prm, c
 
 bool form_interpolation(HostLevel& L, HostLevel& Lc, const SetupParams& prm) {
   const int d = L.dim;
+  trace_push("graph phase: filtering, Alg. 3, Alg. 4, patterns");
   // form_aux_block_diagonal
   Csr Zp = spgemm(L.B, transpose(L.B));
   Csr Ap, Av;
@@ -634,7 +636,10 @@ bool form_interpolation(HostLevel& L, HostLevel& Lc, const SetupParams& prm) {
       cidx[i] = (int)L.Cp.size();
       L.Cp.push_back(i);
     }
-  if ((int)L.Cp.size() >= L.n_p) return false;
+  if ((int)L.Cp.size() >= L.n_p) {
+    trace_pop();
+    return false;
+  }
   // pressure pattern: S_i for F-points, injection for C-points, empty if excluded
   std::vector<std::vector<int>> rows_p(L.n_p);
   for (int i = 0; i < L.n_p; ++i) {
@@ -654,6 +659,7 @@ bool form_interpolation(HostLevel& L, HostLevel& Lc, const SetupParams& prm) {
       if (v >= 0 && !L.dirichlet[v]) isCv[v] = 1;
     }
   std::vector<std::vector<int>> rows_v = velocity_pattern(Gv, isCv, L.dirichlet, L.Cv);
+  trace_pop();
   finish_interpolation(L, Lc, prm, Ap, Av, rows_p, rows_v);
   return true;
 }
@@ -685,6 +691,7 @@ void form_interpolation_reuse(HostLevel& L, HostLevel& Lc, const SetupParams& pr
 // the patterns.
 void finish_interpolation(HostLevel& L, HostLevel& Lc, const SetupParams& prm, const Csr& Ap, const Csr& Av,
                           const std::vector<std::vector<int>>& rows_p, const std::vector<std::vector<int>>& rows_v) {
+  TraceRange range("EMIN steps, restriction, Galerkin products");
   const int d = L.dim;
   const bool cg = prm.symmetric;
   L.Pp = emin_step(Ap, rows_p, (int)L.Cp.size(), cg);
@@ -1181,7 +1188,11 @@ std::vector<HostLevel> build_hierarchy(HostLevel fine, const SetupParams& prm) {
   const std::vector<HostLevel>* prev = prm.reuse;
   while (true) {
     HostLevel& L = levels.back();
-    form_relaxation(L, prm);
+    TraceRange level_range("setup: level %d", (int)levels.size() - 1);
+    {
+      TraceRange r("Braess-Sarazin data (D, S, strips, colors)");
+      form_relaxation(L, prm);
+    }
     if (prev) {
       // the previous hierarchy decides the levels
       if (levels.size() >= prev->size()) break;
@@ -1208,23 +1219,33 @@ std::vector<HostLevel> build_hierarchy(HostLevel fine, const SetupParams& prm) {
 
 void complete_hierarchy(std::vector<HostLevel>& levels, const SetupParams& prm, bool relaxation) {
   if (levels.empty()) throw std::runtime_error("a hierarchy needs at least one level");
-  if (relaxation)
+  if (relaxation) {
+    TraceRange r("setup: Braess-Sarazin data of every level");
     for (HostLevel& L : levels) form_relaxation(L, prm);
+  }
   HostLevel& C = levels.back();
   if (C.N() > 4096) throw std::runtime_error("coarsest level too large for the dense solve: " + std::to_string(C.N()));
   {
+    TraceRange r("setup: coarsest pseudo-inverse");
     const std::vector<double> M = dense_level(C);
     C.pinv = pseudo_inverse(M, C.N(), 1e-12);
     refine_pseudo_inverse(M, C.pinv, C.N());
   }
-  if (prm.vanka)
-    for (size_t l = 0; l + 1 < levels.size(); ++l) form_vanka(levels[l], prm);
-  if (prm.vanka_coarse) form_vanka(levels.back(), prm);
-  if (prm.ilu)
+  if (prm.vanka || prm.vanka_coarse) {
+    TraceRange r("setup: Vanka blocks");
+    if (prm.vanka)
+      for (size_t l = 0; l + 1 < levels.size(); ++l) form_vanka(levels[l], prm);
+    if (prm.vanka_coarse) form_vanka(levels.back(), prm);
+  }
+  if (prm.ilu) {
+    TraceRange r("setup: ILU(1) factors");
     for (size_t l = 0; l + 1 < levels.size(); ++l) form_ilu(levels[l], prm.symmetric, prm.ilu_order);
-  if (prm.dense_gs)
+  }
+  if (prm.dense_gs) {
+    TraceRange r("setup: dense Gauss-Seidel maps (host)");
     for (size_t l = 0; l + 1 < levels.size(); ++l)
       if (levels[l].n_p <= kGsDenseMaxRows) form_dense_gs(levels[l], prm.gs_iters);
+  }
 }
 
 }  // namespace emin

@@ -13,6 +13,7 @@
 
 #include "gpu_setup.hpp"
 #include "hierarchy.hpp"
+#include "trace.hpp"
 
 using namespace emin;
 
@@ -346,6 +347,9 @@ class FgmresTask final : public SolveTask {
         flag_(K, 0) {}
 
   bool advance() override {
+    static const char* kPhase[] = {"FGMRES: start", "FGMRES: Arnoldi step", "FGMRES: Arnoldi step",
+                                   "FGMRES: restart cycle end", "FGMRES: finish", "FGMRES: done"};
+    TraceRange range(kPhase[phase_]);
     switch (phase_) {
       case kStart:
         start();
@@ -825,6 +829,7 @@ bool same_pattern(const Csr& M, const int* rp, const int* ci, int nrows) {
 }  // namespace
 
 amg_status amg_hierarchy_create(const amg_problem* pb, const amg_params* prm_in, void* stream, amg_handle* out) {
+  TraceRange range("amg_hierarchy_create");
   return create_impl(pb, prm_in, stream, out, nullptr);
 }
 
@@ -838,6 +843,7 @@ amg_status amg_hierarchy_create_reuse(amg_handle prev, const amg_problem* pb, co
   if (!pb->A_rowptr || !pb->A_col || !pb->B_rowptr || !pb->B_col) return fail(AMG_ERR_ARG, "null problem array");
   if (!same_pattern(F.A, pb->A_rowptr, pb->A_col, F.n_v) || !same_pattern(F.B, pb->B_rowptr, pb->B_col, F.n_p))
     return fail(AMG_ERR_ARG, "the sparsity of A or B differs from the previous hierarchy's");
+  TraceRange range("amg_hierarchy_create_reuse");
   return create_impl(pb, prm_in, stream, out, prev);
 }
 
@@ -940,6 +946,7 @@ amg_status create_impl(const amg_problem* pb, const amg_params* prm_in, void* st
     if (on_device) form_dense_gs_device(h->host, prm.gs_iters, (cudaStream_t)stream);
     h->prm = prm;
     h->symmetric = sp.symmetric;
+    TraceRange r("upload of the device hierarchy");
     upload_handle(h.get(), sp, stream);
   } catch (const std::bad_alloc&) {
     return fail(AMG_ERR_OOM, "host allocation failed during setup");

@@ -12,6 +12,7 @@
 
 #include "device.cuh"
 #include "setup.hpp"
+#include "trace.hpp"
 
 namespace emin {
 
@@ -554,8 +555,19 @@ class DeviceVCycle : public VCycleIface {
     int level, cls;
     cudaEvent_t a, b;
   };
+  static constexpr const char* kClassRange[kNumClasses] = {
+      "velocity predictor", "Schur right-hand side", "Gauss-Seidel", "update", "residual",
+      "restriction", "prolongation", "coarsest solve", "Vanka step", "ILU(1) substitution"};
+  // every launch of the cycle is bracketed by mark_begin / mark_end: an NVTX range
+  // "L<level> <class>" (host side, so visible when the cycle is captured or profiled)
+  // and, when profiling, a CUDA event pair
   void mark_begin(int level, int cls, cudaStream_t s) {
     ++enq_kernels_;
+    {
+      char name[64];
+      std::snprintf(name, sizeof(name), "L%d %s", level, kClassRange[cls]);
+      trace_push(name);
+    }
     if (!prof_on_) return;
     Rec r{level, cls, nullptr, nullptr};
     cudaEventCreate(&r.a);
@@ -566,6 +578,7 @@ class DeviceVCycle : public VCycleIface {
   void mark_extra(cudaStream_t) { ++enq_kernels_; }
   void mark_end(cudaStream_t s) {
     if (prof_on_) cudaEventRecord(recs_.back().b, s);
+    trace_pop();
   }
 
   // Small levels are latency-bound: their sparse kernels put G > 1 lanes on a row.
@@ -901,6 +914,7 @@ class DeviceVCycle : public VCycleIface {
     cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
     if (e != cudaSuccess) return e;
     cudaGraph_t g = nullptr;
+    TraceRange range("V-cycle: autotune and graph capture, K = %d", K);
     try {
       if (autotune_) tune_for(K, cs);
     } catch (const std::exception&) {

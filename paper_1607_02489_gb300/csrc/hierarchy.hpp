@@ -44,7 +44,7 @@ struct Krylov {
   int* reorth = nullptr;     // device flag: the current Arnoldi step needs a second pass
   int* host_i = nullptr;     // pinned, kHostInts
   double* host_d = nullptr;  // pinned, kHostDoubles
-  static constexpr int kHostInts = 256, kHostDoubles = 64;
+  static constexpr int kHostInts = 256, kHostDoubles = 128;
 
   Krylov() = default;
   Krylov(const Krylov&) = delete;
@@ -70,6 +70,11 @@ class SolveTask {
   virtual amg_status result(int* iters, double* relres) const = 0;
   // Status of one column: AMG_OK, AMG_NOT_CONVERGED or AMG_BREAKDOWN.
   virtual amg_status column_status(int k) const = 0;
+  // The event after which the next advance() may run (its results are then on the
+  // host); nullptr: all work enqueued on the task's stream.  While Arnoldi steps
+  // run, the task keeps one step queued beyond the one whose results it reads next,
+  // so the device does not idle while the host reads them and enqueues more.
+  virtual cudaEvent_t ready() const { return nullptr; }
   long long launches = 0;  // kernels this task launched outside the V-cycle graphs
 };
 

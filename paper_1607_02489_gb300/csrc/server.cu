@@ -53,6 +53,7 @@ struct Slot {
   double* dev_x = nullptr;
   cudaStream_t s = nullptr;
   cudaEvent_t ev = nullptr;
+  cudaEvent_t wait = nullptr;  // the event the next step of the task waits for (the task's own, or ev)
   size_t bytes = 0;
   std::vector<long long> members;  // requests of the running cohort, empty when idle
   std::unique_ptr<SolveTask> task;
@@ -171,7 +172,11 @@ struct amg_server {
       task_launches += sl.task->launches;
       sl.task->launches = 0;
       if (more) {
-        EMIN_CUDA(cudaEventRecord(sl.ev, sl.s));
+        sl.wait = sl.task->ready();
+        if (!sl.wait) {
+          EMIN_CUDA(cudaEventRecord(sl.ev, sl.s));
+          sl.wait = sl.ev;
+        }
       } else {
         finish(sl, AMG_OK, "");
       }
@@ -314,7 +319,7 @@ struct amg_server {
   void poll() {
     for (auto& sl : slots) {
       if (!sl->busy()) continue;
-      const cudaError_t e = cudaEventQuery(sl->ev);
+      const cudaError_t e = cudaEventQuery(sl->wait);
       if (e == cudaErrorNotReady) continue;
       if (e != cudaSuccess) {
         finish(*sl, AMG_ERR_CUDA, std::string("cuda: ") + cudaGetErrorString(e));

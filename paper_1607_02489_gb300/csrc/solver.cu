@@ -344,7 +344,14 @@ class FgmresTask final : public SolveTask {
              double rtol, int restart, int maxit, cudaStream_t s)
       : h_(h), vc_(vc), w_(ws), segs_(segs), nrhs_(nrhs), restart_(restart), maxit_(maxit), rtol_(rtol), s_(s),
         N_(h->N), NK_(h->N * K), gNK_(grid_for(h->N * K)), bn_(K, 0.0), rel_(K, 0.0), total_(K, 0), done_(K, 0),
-        flag_(K, 0) {}
+        flag_(K, 0) {
+    for (cudaEvent_t& e : ev_) EMIN_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
+  ~FgmresTask() override {
+    for (cudaEvent_t e : ev_)
+      if (e) cudaEventDestroy(e);
+  }
+  cudaEvent_t ready() const override { return ready_; }
 
   bool advance() override {
     static const char* kPhase[] = {"FGMRES: start", "FGMRES: Arnoldi step", "FGMRES: Arnoldi step",
@@ -354,7 +361,7 @@ class FgmresTask final : public SolveTask {
       case kStart:
         start();
         phase_ = kNorms;
-        return true;
+        return chunk_done();
       case kNorms:
         for (int k = 0; k < K; ++k) {
           bn_[k] = w_->host_d[k];
@@ -362,27 +369,28 @@ class FgmresTask final : public SolveTask {
         }
         if (!any_left()) return finish();
         begin_cycle();
-        step();
         phase_ = kStep;
         return true;
-      case kStep:
-        if (w_->host_i[1] != 0)
+      case kStep: {
+        // the results of step seen_ (its slot) are on the host
+        const int slot = seen_ & 1;
+        if (w_->host_i[kSlotInts + 2 * slot + 1] != 0)
           throw std::runtime_error("cuda: a bounded device wait timed out (Gauss-Seidel strips or ILU substitution)");
-        if (w_->host_i[0] == 0) {
-          ++j_;
+        const int n_active = w_->host_i[kSlotInts + 2 * slot];
+        for (int k = 0; k < K; ++k) est_[2][k] = est_[1][k], est_[1][k] = w_->host_d[kSlotDoubles + 32 * slot + k];
+        ++seen_;
+        if (n_active == 0 || seen_ >= restart_) {
+          // every column stopped at step seen_ - 1; a step issued beyond it found no
+          // active column and changed nothing but the unused tail of V and Z
+          j_ = issued_;
           end_cycle();
-          return true;
+          return chunk_done();
         }
-        k_scale<K><<<gNK_, kBlock, 0, s_>>>(NK_, w_->w, w_->hbuf + (size_t)(j_ + 1) * K, w_->st.active,
-                                            w_->V + (size_t)(j_ + 1) * NK_);
-        ++launches;
-        ++j_;
-        if (j_ < restart_) {
-          step();
-          return true;
-        }
-        end_cycle();
+        if (issued_ == seen_) issue_step();  // not issued ahead: the next step now
+        if (issued_ < restart_ && !final_step_likely()) issue_step();
+        ready_ = ev_[seen_ & 1];
         return true;
+      }
       case kCycle: {
         bool left = false;
         for (int k = 0; k < K; ++k) {
@@ -398,7 +406,6 @@ class FgmresTask final : public SolveTask {
         }
         if (!left) return finish();
         begin_cycle();
-        step();
         phase_ = kStep;
         return true;
       }
@@ -428,6 +435,54 @@ class FgmresTask final : public SolveTask {
 
  private:
   enum Phase { kStart, kNorms, kStep, kCycle, kFinish, kDone };
+  // pinned host words of the two step result slots: (active columns, error word) at
+  // host_i[kSlotInts + 2 slot], the columns' residual estimates at
+  // host_d[kSlotDoubles + 32 slot]
+  static constexpr int kSlotInts = 32, kSlotDoubles = 64;
+
+  // An event after the chunk just enqueued, the one the next advance() waits for.
+  bool chunk_done() {
+    EMIN_CUDA(cudaEventRecord(ev_[2], s_));
+    ready_ = ev_[2];
+    return true;
+  }
+
+  // Enqueue Arnoldi step issued_ (after the normalisation of its basis vector),
+  // its results into slot issued_ & 1, and that slot's event.
+  void issue_step() {
+    if (issued_ > 0) {
+      k_scale<K><<<gNK_, kBlock, 0, s_>>>(NK_, w_->w, w_->hbuf + (size_t)issued_ * K, w_->st.active,
+                                          w_->V + (size_t)issued_ * NK_);
+      ++launches;
+    }
+    j_ = issued_;
+    step();
+    const int slot = issued_ & 1;
+    EMIN_CUDA(cudaMemcpyAsync(w_->host_i + kSlotInts + 2 * slot, w_->n_active, sizeof(int), cudaMemcpyDeviceToHost,
+                              s_));
+    EMIN_CUDA(cudaMemcpyAsync(w_->host_i + kSlotInts + 2 * slot + 1, vc_->error_flag(), sizeof(int),
+                              cudaMemcpyDeviceToHost, s_));
+    EMIN_CUDA(cudaMemcpyAsync(w_->host_d + kSlotDoubles + 32 * slot, w_->st.resest, sizeof(double) * K,
+                              cudaMemcpyDeviceToHost, s_));
+    EMIN_CUDA(cudaEventRecord(ev_[slot], s_));
+    ++issued_;
+  }
+
+  // Whether the step just issued (seen_, not yet seen) will probably stop every
+  // running column: each column's residual estimate extrapolated by its last
+  // reduction factor reaches 4 rtol.  Then no further step is queued ahead, which
+  // would find nothing left to do.
+  bool final_step_likely() const {
+    if (seen_ < 2) return false;
+    bool all = true;
+    for (int k = 0; k < K && all; ++k) {
+      if (done_[k]) continue;
+      const double e1 = est_[1][k], e2 = est_[2][k];
+      if (!(e1 > 0.0) || !(e2 > 0.0)) continue;  // a column that stopped: no opinion
+      all = e1 * (e1 / e2) <= 4.0 * rtol_;
+    }
+    return all;
+  }
 
   bool any_left() const {
     return std::any_of(done_.begin(), done_.end(), [](int d) { return !d; });
@@ -478,6 +533,11 @@ class FgmresTask final : public SolveTask {
     k_scale<K><<<gNK_, kBlock, 0, s_>>>(NK_, w_->rK, w_->rnorm, w_->st.active, w_->V);
     ++launches;
     j_ = 0;
+    issued_ = seen_ = 0;
+    for (auto& e : est_) std::fill(e.begin(), e.end(), 0.0);
+    issue_step();
+    if (restart_ > 1) issue_step();
+    ready_ = ev_[0];
   }
 
   void step() {
@@ -517,8 +577,6 @@ class FgmresTask final : public SolveTask {
     k_givens<<<1, 32, 0, s_>>>(j, restart_, K, w_->hbuf, w_->st, w_->bnorm, rtol_, w_->n_active);
     launches += 11;
     EMIN_CUDA(cudaGetLastError());
-    EMIN_CUDA(cudaMemcpyAsync(w_->host_i, w_->n_active, sizeof(int), cudaMemcpyDeviceToHost, s_));
-    EMIN_CUDA(cudaMemcpyAsync(w_->host_i + 1, vc_->error_flag(), sizeof(int), cudaMemcpyDeviceToHost, s_));
   }
 
   // x += Z y with y from the triangular systems; true residual r = b - A x in FP64.
@@ -535,6 +593,7 @@ class FgmresTask final : public SolveTask {
     EMIN_CUDA(cudaMemcpyAsync(w_->host_i + 64, w_->st.flags, sizeof(int) * K, cudaMemcpyDeviceToHost, s_));
     phase_ = kCycle;
   }
+  // (end_cycle's caller records the chunk's event: chunk_done)
 
   bool finish() {
     if (segs_.size() == 1) {
@@ -553,7 +612,7 @@ class FgmresTask final : public SolveTask {
       if (g.x_host)
         EMIN_CUDA(cudaMemcpyAsync(g.x_host, g.x, sizeof(double) * N_ * g.ncols, cudaMemcpyDeviceToHost, s_));
     phase_ = kFinish;
-    return true;
+    return chunk_done();
   }
 
   amg_hierarchy_core* h_;
@@ -569,6 +628,11 @@ class FgmresTask final : public SolveTask {
   std::vector<int> total_, done_, flag_;
   Phase phase_ = kStart;
   int j_ = 0;
+  int issued_ = 0, seen_ = 0;  // Arnoldi steps of the current cycle enqueued / whose results were read
+  cudaEvent_t ev_[3] = {nullptr, nullptr, nullptr};  // step slots 0 and 1, other chunks
+  cudaEvent_t ready_ = nullptr;
+  std::vector<double> est_[3] = {std::vector<double>(K, 0.0), std::vector<double>(K, 0.0),
+                                 std::vector<double>(K, 0.0)};  // [1] last seen step's estimates, [2] the one before
 };
 
 template <typename TZ>
@@ -639,8 +703,12 @@ amg_status fgmres_blocking(amg_hierarchy* h, const double* b, double* x, const d
     more = task->advance();
     h->launches += task->launches;
     task->launches = 0;
-    EMIN_CUDA(cudaStreamSynchronize(s));
+    if (cudaEvent_t e = task->ready(); more && e)
+      EMIN_CUDA(cudaEventSynchronize(e));
+    else
+      EMIN_CUDA(cudaStreamSynchronize(s));
   }
+  EMIN_CUDA(cudaStreamSynchronize(s));
   return task->result(iters, relres);
 }
 

@@ -61,6 +61,9 @@ def parse():
     ap.add_argument("--ncu", action="store_true",
                     help="short run for an ncu launch list: one warm-up solve, then one solve (FP32 V-cycle) "
                          "inside a cudaProfilerStart/Stop range")
+    ap.add_argument("--ncu-setup", action="store_true",
+                    help="short run for ncu: a hierarchy for the bench workload, a first device reuse of it, then "
+                         "a second device reuse inside a cudaProfilerStart/Stop range")
     return ap.parse_args()
 
 
@@ -586,7 +589,7 @@ def main():
         return reference_main(args)
     if args.configs:
         return configs_main(args)
-    if args.ncu:
+    if args.ncu or args.ncu_setup:
         args.no_cpu_baseline = True
     import numpy as np
     import torch
@@ -611,6 +614,18 @@ def main():
     import paper_1607_02489_gb300 as g
     g._build.build()
     p = rank_batch(rank)
+    if args.ncu_setup:
+        from synth import make_problem
+        q = make_problem(MESH, 2, 0.0, 1.0, bc="lid", nu=0.5, nrhs=1, seed=1)
+        H = g.Hierarchy(p, max_nrhs=NRHS, vcycle_fp32=1)
+        R1 = g.Hierarchy(q, reuse=H, max_nrhs=NRHS, vcycle_fp32=1)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        R2 = g.Hierarchy(p, reuse=R1, max_nrhs=NRHS, vcycle_fp32=1)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        print(f"device reuse setup: {R2.num_levels()} levels", flush=True)
+        return
     if args.ncu:
         H = g.Hierarchy(p, max_nrhs=NRHS, vcycle_fp32=1)
         b = torch.tensor(p.b, device=dev)

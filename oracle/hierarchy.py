@@ -48,6 +48,8 @@ class Params:
     ilu_order: str = "block"      # ILU(1) order of symmetric levels: "block" (the paper's) or "location"
     coarse: str = "exact"         # coarsest level: "exact" (pseudo-inverse) or "vanka" (pre + post Vanka
                                   # steps from zero, as the paper relaxes it, Section 6.1)
+    gs_order: str = "strips"      # Gauss-Seidel order on S: "strips" (strip parity, color, index; the GPU's)
+                                  # or "natural" (row index order, the textbook forward sweep)
     max_coarse: int = 200
     max_levels: int = 12
 

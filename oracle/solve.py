@@ -8,6 +8,7 @@ from __future__ import annotations
 import numpy as np
 import scipy.linalg as sla
 import scipy.sparse as sp
+import scipy.sparse.linalg as spla
 
 
 def _split(L, x):
@@ -26,7 +27,7 @@ def apply_A(L, x):
     return np.vstack([yu, yp])
 
 
-def gauss_seidel(L, g, iters: int):
+def gauss_seidel(L, g, iters: int, order: str = "strips"):
     """`iters` forward Gauss-Seidel iterations on S dp = g from dp = 0 (Section 5.2
     solves the Schur system approximately by a few Gauss-Seidel iterations; Section 6
     uses five).  The paper gives no
@@ -36,11 +37,23 @@ def gauss_seidel(L, g, iters: int):
     is greedily colored on its own subgraph.
     Rows with the same parity and color share no entry of S (same strip: the
     coloring; different strips of one parity: the bandwidth), so updating them
-    at once gives the same result as one after another."""
+    at once gives the same result as one after another.
+
+    order = "natural" takes the rows in index order instead (lexicographic on the
+    structured meshes): one iteration is the triangular solve
+    (D + L) dp_new = g - U dp_old with S = L + D + U."""
     S = L.S
     diag = S.diagonal()
     off = S - sp.diags(diag)
     dp = np.zeros_like(g)
+    if order == "natural":
+        lower = sp.tril(S, format="csr")
+        upper = sp.triu(S, k=1, format="csr")
+        for _ in range(iters):
+            dp = spla.spsolve_triangular(lower, g - upper @ dp, lower=True)
+        return dp
+    if order != "strips":
+        raise ValueError(f"unknown Gauss-Seidel order {order!r}")
     parity = (np.arange(L.n_p) // L.gs_strip) % 2
     ncol = int(L.colors.max()) + 1 if len(L.colors) else 0
     groups = [np.flatnonzero((parity == b) & (L.colors == c)) for b in (0, 1) for c in range(ncol)]
@@ -68,7 +81,7 @@ def bs_sweep(L, prm, b, x):
     g = L.B @ (Dinv * ru) - c * rp
     if L.pinned >= 0:
         g[L.pinned] = rp[L.pinned]
-    dp = gauss_seidel(L, g, prm.gs_iters)
+    dp = gauss_seidel(L, g, prm.gs_iters, prm.gs_order)
     du = (1.0 / c) * Dinv * (ru - L.Bt @ dp)
     return x + np.vstack([du, dp])
 

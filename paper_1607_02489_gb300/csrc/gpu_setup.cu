@@ -224,7 +224,11 @@ struct Arena {
   template <typename T>
   T* alloc(size_t n) {
     void* p = nullptr;
-    SETUP_CUDA(cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(T)));
+    const cudaError_t e = cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(T));
+    if (e != cudaSuccess) {
+      cudaGetLastError();  // not sticky: clear it for the next launch checks
+      throw std::runtime_error(std::string("cudaMalloc (device setup): ") + cudaGetErrorString(e));
+    }
     ptrs.push_back(p);
     return (T*)p;
   }

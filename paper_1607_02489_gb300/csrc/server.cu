@@ -193,8 +193,10 @@ struct amg_server {
     sl->vc.reset(h->vc()->clone(K));
     sl->ws.init(h->N, K, prm.restart, h->prm.vcycle_fp32 != 0);
     if (cudaMalloc(&sl->dev_b, sizeof(double) * (size_t)h->N * K) != cudaSuccess ||
-        cudaMalloc(&sl->dev_x, sizeof(double) * (size_t)h->N * K) != cudaSuccess)
+        cudaMalloc(&sl->dev_x, sizeof(double) * (size_t)h->N * K) != cudaSuccess) {
+      cudaGetLastError();  // not sticky: clear it for the next launch checks
       throw std::runtime_error("cudaMalloc for a request slot's b and x");
+    }
     EMIN_CUDA(cudaStreamCreateWithFlags(&sl->s, cudaStreamNonBlocking));
     EMIN_CUDA(cudaEventCreateWithFlags(&sl->ev, cudaEventDisableTiming));
     bytes += sl->bytes;

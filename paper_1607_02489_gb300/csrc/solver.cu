@@ -234,7 +234,10 @@ struct Carver {
     if (count_only) return nullptr;
     void* p = nullptr;
     cudaError_t e = cudaMalloc(&p, b);
-    if (e != cudaSuccess) throw std::runtime_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess) {
+      cudaGetLastError();  // an allocation failure is not sticky: clear it for the next launch checks
+      throw std::runtime_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
     list->push_back(p);
     return (U*)p;
   }
@@ -1020,6 +1023,7 @@ amg_status create_impl(const amg_problem* pb, const amg_params* prm_in, void* st
     return fail(AMG_ERR_OOM, "host allocation failed during setup");
   } catch (const std::exception& e) {
     const std::string m = e.what();
+    if (m.find("cudaMalloc") != std::string::npos) return fail(AMG_ERR_OOM, m);
     return fail(m.find("cuda") != std::string::npos ? AMG_ERR_CUDA : AMG_ERR_SETUP, m);
   }
   *out = h.release();
@@ -1132,8 +1136,13 @@ amg_status amg_fgmres_solve_host(amg_handle h, const double* b_host, double* x_h
   if (restart < 1 || maxit < 1 || !(rtol > 0.0)) return fail(AMG_ERR_ARG, "restart, maxit and rtol must be positive");
   if (!h->stage_b) {
     const size_t cap = sizeof(double) * (size_t)h->N * h->vc()->kmax();
-    if (cudaMalloc(&h->stage_b, cap) != cudaSuccess || cudaMalloc(&h->stage_x, cap) != cudaSuccess)
+    if (cudaMalloc(&h->stage_b, cap) != cudaSuccess || cudaMalloc(&h->stage_x, cap) != cudaSuccess) {
+      cudaGetLastError();  // not sticky: clear it for the next launch checks
+      if (h->stage_b) cudaFree(h->stage_b);
+      if (h->stage_x) cudaFree(h->stage_x);
+      h->stage_b = h->stage_x = nullptr;  // both or neither
       return fail(AMG_ERR_OOM, "cudaMalloc for the host-solve staging buffers");
+    }
   }
   try {
     return fgmres_blocking(h, (const double*)h->stage_b, (double*)h->stage_x, b_host, x_host, nrhs, rtol, restart,

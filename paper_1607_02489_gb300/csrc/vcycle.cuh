@@ -947,7 +947,10 @@ class DeviceVCycle : public VCycleIface {
     void* p = nullptr;
     const size_t bytes = std::max<size_t>(n, 1) * sizeof(U);
     cudaError_t e = cudaMalloc(&p, bytes);
-    if (e != cudaSuccess) throw std::runtime_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess) {
+      cudaGetLastError();  // not sticky: clear it for the next launch checks
+      throw std::runtime_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
     allocs_.push_back(p);
     bytes_ += bytes;
     return (U*)p;

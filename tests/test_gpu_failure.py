@@ -54,3 +54,18 @@ def test_a_wait_that_runs_out_returns_the_cuda_error_status(kind):
         assert torch.equal(x, x2)
     else:
         assert ((x - x2).norm() / x2.norm()).item() <= 1e-12
+
+
+def test_a_device_allocation_failure_returns_oom_and_the_handle_stays_usable():
+    """A Krylov workspace far beyond the device's memory (restart 10^8: basis vectors of
+    2,467 x 2 doubles, about 4 TB) makes its first cudaMalloc fail; the solve returns
+    AMG_ERR_OOM before any launch, and the same hierarchy then solves normally."""
+    p = stokes_lid_2d(16, nrhs=2)
+    H = g.Hierarchy(p, max_nrhs=2)
+    b = torch.tensor(p.b, device="cuda")
+    x = torch.zeros_like(b)
+    with pytest.raises(g.AmgError) as exc:
+        H.fgmres(b, x, rtol=1e-8, restart=100_000_000, maxit=10)
+    assert exc.value.status == -2 and "cudaMalloc" in str(exc.value)
+    st, its, rel = H.fgmres(b, x, rtol=1e-8)
+    assert st == g.AMG_OK and np.all(rel <= 1e-8)

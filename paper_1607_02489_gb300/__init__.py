@@ -24,7 +24,7 @@ STATUS_NAMES = {0: "OK", 1: "NOT_CONVERGED", 2: "BREAKDOWN", -1: "ERR_ARG", -2: 
 EXPORTED = ["amg_params_default", "amg_hierarchy_create", "amg_hierarchy_create_reuse", "amg_hierarchy_export",
             "amg_hierarchy_import", "amg_vcycle_apply", "amg_apply", "amg_fgmres_solve",
             "amg_fgmres_solve_host", "amg_num_levels", "amg_level_get_info", "amg_level_get_matrix",
-            "amg_level_get_points", "amg_hierarchy_destroy", "amg_last_error", "amg_profile_vcycle", "amg_kernel_launches", "amg_apply_noalloc", "amg_gs_variant", "amg_row_shape", "amg_level_get_vanka", "amg_level_get_ilu",
+            "amg_level_get_points", "amg_hierarchy_destroy", "amg_last_error", "amg_profile_vcycle", "amg_kernel_launches", "amg_apply_noalloc", "amg_gs_variant", "amg_set_gs_variant", "amg_row_shape", "amg_level_get_vanka", "amg_level_get_ilu",
             "amg_coarse_inverse", "amg_set_wait_limit", "amg_level_get_gs_map",
             "amg_server_params_default", "amg_server_create", "amg_server_reserve", "amg_server_submit", "amg_server_progress",
             "amg_server_result", "amg_server_state", "amg_server_get_stats", "amg_server_destroy", "amg_server_last_error"]
@@ -52,7 +52,8 @@ class AmgParams(ctypes.Structure):
                 ("post", ctypes.c_int), ("max_coarse", ctypes.c_int), ("max_levels", ctypes.c_int),
                 ("vcycle_fp32", ctypes.c_int), ("max_nrhs", ctypes.c_int), ("host_only", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("smoother", ctypes.c_int), ("vanka_omega", ctypes.c_double),
-                ("ilu_order", ctypes.c_int), ("coarse", ctypes.c_int), ("device_setup", ctypes.c_int)]
+                ("ilu_order", ctypes.c_int), ("coarse", ctypes.c_int), ("device_setup", ctypes.c_int),
+                ("vanka_max_mib", ctypes.c_double)]
 
 
 class AmgLevelInfo(ctypes.Structure):
@@ -117,6 +118,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.amg_profile_vcycle.restype = ctypes.c_int
     lib.amg_gs_variant.argtypes = [vp, ctypes.c_int, ctypes.c_int, _i32p, ctypes.POINTER(ctypes.c_float)]
     lib.amg_gs_variant.restype = ctypes.c_int
+    lib.amg_set_gs_variant.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    lib.amg_set_gs_variant.restype = ctypes.c_int
     lib.amg_row_shape.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     lib.amg_row_shape.restype = ctypes.c_int
     lib.amg_kernel_launches.argtypes = [vp]
@@ -346,6 +349,13 @@ class Hierarchy:
             v = load().amg_gs_variant(self._h, l, int(nrhs), ctypes.byref(c), ctypes.byref(ms))
             out.append((self.GS_VARIANTS.get(v, str(v)), c.value, ms.value))
         return out
+
+    def set_gs_variant(self, level, nrhs, variant, cluster=0):
+        """amg_set_gs_variant: fix the Gauss-Seidel variant of a level (a name of
+        GS_VARIANTS or its number) for nrhs right-hand sides."""
+        if isinstance(variant, str):
+            variant = {v: k for k, v in self.GS_VARIANTS.items()}[variant]
+        _check(load().amg_set_gs_variant(self._h, int(level), int(nrhs), int(variant), int(cluster)))
 
     def row_shapes(self, nrhs) -> dict:
         """{level: {kernel class: row mapping 0-3}} of the sparse kernels (amg_row_shape)."""

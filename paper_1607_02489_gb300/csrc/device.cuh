@@ -393,24 +393,36 @@ __device__ __forceinline__ void st_release(int* p, int v) {
 
 // done[0..nstrips) are the per-strip counters and done[nstrips] the ticket
 // counter; all are zero at launch, and dp is zero.
-template <typename T, int K, int G, int V, int NT>
+// In FP32 an entry of S is one 8-byte word (column relative to the strip's halo,
+// value bits), pk: one shared-memory load per entry instead of two.
+// HS > 1 splits the block into HS groups of threads, each relaxing K / HS of the
+// right-hand sides (independent systems) with its own barrier between colors, so
+// one group's color steps overlap another's barrier wait.
+template <typename T, int K, int G, int V, int NT, int HS = 1>
 __global__ void __launch_bounds__(NT) k_gs_pipe(LevelView<T> L, const T* __restrict__ g, T* dp, GsStrips P,
-                                                const int* __restrict__ ci_rel, int* done, int* err) {
-  static_assert((K / V) * G <= 32, "a row group must fit in a warp");
+                                                const int* __restrict__ ci_rel, const int2* __restrict__ pk,
+                                                int* done, int* err) {
+  static_assert((K / HS / V) * G <= 32, "a row group must fit in a warp");
+  static_assert(K % (HS * V) == 0 && NT % (32 * HS) == 0 && HS <= 8, "groups of whole warps and columns");
+  constexpr bool PK = sizeof(T) == 4;
   extern __shared__ __align__(16) unsigned char smem[];
   T* s_dp = reinterpret_cast<T*>(smem);
   T* s_g = s_dp + (size_t)3 * P.T * K;
   T* s_dinv = s_g + (size_t)P.T * K;
   T* s_v = s_dinv + P.T;
-  int* s_rp = reinterpret_cast<int*>(s_v + (P.stage == 2 ? P.max_strip_nnz : 0));
+  int* s_rp = reinterpret_cast<int*>(s_v + (!PK && P.stage == 2 ? P.max_strip_nnz : 0));
   int* s_perm = s_rp + P.T + 1;
   int* s_ci = s_perm + P.T;
+  int2* s_pk = reinterpret_cast<int2*>(smem + ((reinterpret_cast<unsigned char*>(s_ci) - smem + 15) & ~(size_t)15));
   __shared__ int s_fail, s_unit;
   __shared__ int s_so[kMaxColors + 1];  // this strip's color offsets (sorted rows)
-  constexpr int KV = K / V;
+  constexpr int KH = K / HS;   // right-hand sides of a thread group
+  constexpr int KV = KH / V;   // threads per row and lane
   constexpr int kGroup = KV * G;
-  const int k = (threadIdx.x % KV) * V;
-  const int lane = (threadIdx.x / KV) % G;
+  constexpr int NTH = NT / HS;  // threads of a group
+  const int hs = threadIdx.x / NTH, th = threadIdx.x - hs * NTH;
+  const int k = hs * KH + (th % KV) * V;
+  const int lane = (th / KV) % G;
   const unsigned mask = group_mask<kGroup>();
   const int n_p = L.n_p;
   const int nunits = P.iters * P.nstrips;
@@ -438,9 +450,15 @@ __global__ void __launch_bounds__(NT) k_gs_pipe(LevelView<T> L, const T* __restr
     stage_copy<false>(s_dinv, L.S_dinv + q0, q1 - q0);
     stage_copy<false>(s_perm, L.S_perm + q0, q1 - q0);
     stage_copy<false>(s_rp, L.S.rp + q0, q1 - q0 + 1);
+    // packed entries land at the 16-byte phase of their global address: whole 16-byte copies
+    int2* const s_pke = s_pk + (e0 & 1);
     if (P.stage == 2) {
-      stage_copy<false>(s_v, L.S.v + e0, e1 - e0);
-      stage_copy<false>(s_ci, ci_rel + e0, e1 - e0);
+      if constexpr (PK) {
+        stage_copy<false>(s_pke, pk + e0, e1 - e0);
+      } else {
+        stage_copy<false>(s_v, L.S.v + e0, e1 - e0);
+        stage_copy<false>(s_ci, ci_rel + e0, e1 - e0);
+      }
     }
     const int need_nb = par == 0 ? it : it + 1;
     if (threadIdx.x == 0) {
@@ -477,12 +495,24 @@ __global__ void __launch_bounds__(NT) k_gs_pipe(LevelView<T> L, const T* __restr
     const int* so = s_so;
     for (int pc = 0; pc < P.ncol; ++pc) {
       const int ra = so[pc], rb = so[pc + 1];
-      for (int t = threadIdx.x; t < (rb - ra) * kGroup; t += blockDim.x) {
+      for (int t = th; t < (rb - ra) * kGroup; t += NTH) {
         const int r = ra + t / kGroup;
         const int ea = s_rp[r - q0], eb = s_rp[r - q0 + 1];
         T acc[V];
         const T* sv = P.stage == 2 ? s_v - e0 : L.S.v;
         const int* sc = P.stage == 2 ? s_ci - e0 : ci_rel;
+        const int2* sp = P.stage == 2 ? s_pke - e0 : pk;
+        // entry e of S: relative column and value
+        auto entry = [&](int e, int& c, T& v) {
+          if constexpr (PK) {
+            const int2 q = sp[e];
+            c = q.x;
+            v = __int_as_float(q.y);
+          } else {
+            c = sc[e];
+            v = sv[e];
+          }
+        };
         if constexpr (V > 1 && G == 1) {
           // V columns per thread, whole row: two independent partial sums per column
           T a[V], b2[V];
@@ -490,8 +520,10 @@ __global__ void __launch_bounds__(NT) k_gs_pipe(LevelView<T> L, const T* __restr
           for (int uu = 0; uu < V; ++uu) a[uu] = b2[uu] = T(0);
           int e = ea;
           for (; e + 1 < eb; e += 2) {
-            const int c0 = sc[e], c1 = sc[e + 1];
-            const T v0 = sv[e], v1 = sv[e + 1];
+            int c0, c1;
+            T v0, v1;
+            entry(e, c0, v0);
+            entry(e + 1, c1, v1);
             T d0[V], d1[V];
             vld<T, V>(d0, s_dp + c0 * K + k);
             vld<T, V>(d1, s_dp + c1 * K + k);
@@ -502,10 +534,13 @@ __global__ void __launch_bounds__(NT) k_gs_pipe(LevelView<T> L, const T* __restr
             }
           }
           if (e < eb) {
+            int c0;
+            T v0;
+            entry(e, c0, v0);
             T d0[V];
-            vld<T, V>(d0, s_dp + sc[e] * K + k);
+            vld<T, V>(d0, s_dp + c0 * K + k);
 #pragma unroll
-            for (int uu = 0; uu < V; ++uu) a[uu] += sv[e] * d0[uu];
+            for (int uu = 0; uu < V; ++uu) a[uu] += v0 * d0[uu];
           }
 #pragma unroll
           for (int uu = 0; uu < V; ++uu) acc[uu] = a[uu] + b2[uu];
@@ -516,8 +551,12 @@ __global__ void __launch_bounds__(NT) k_gs_pipe(LevelView<T> L, const T* __restr
           for (int uu = 0; uu < V; ++uu) acc[uu] = a1[uu] = a2[uu] = a3[uu] = T(0);
           int e = ea + lane;
           for (; e + 3 * G < eb; e += 4 * G) {
-            const int c0 = sc[e], c1 = sc[e + G], c2 = sc[e + 2 * G], c3 = sc[e + 3 * G];
-            const T v0 = sv[e], v1 = sv[e + G], v2 = sv[e + 2 * G], v3 = sv[e + 3 * G];
+            int c0, c1, c2, c3;
+            T v0, v1, v2, v3;
+            entry(e, c0, v0);
+            entry(e + G, c1, v1);
+            entry(e + 2 * G, c2, v2);
+            entry(e + 3 * G, c3, v3);
             T d0[V], d1[V], d2[V], d3[V];
             vld<T, V>(d0, s_dp + c0 * K + k);
             vld<T, V>(d1, s_dp + c1 * K + k);
@@ -532,10 +571,13 @@ __global__ void __launch_bounds__(NT) k_gs_pipe(LevelView<T> L, const T* __restr
             }
           }
           for (; e < eb; e += G) {
+            int c0;
+            T v0;
+            entry(e, c0, v0);
             T d0[V];
-            vld<T, V>(d0, s_dp + sc[e] * K + k);
+            vld<T, V>(d0, s_dp + c0 * K + k);
 #pragma unroll
-            for (int uu = 0; uu < V; ++uu) acc[uu] += sv[e] * d0[uu];
+            for (int uu = 0; uu < V; ++uu) acc[uu] += v0 * d0[uu];
           }
 #pragma unroll
           for (int uu = 0; uu < V; ++uu) acc[uu] = group_sum<KV, G>((acc[uu] + a1[uu]) + (a2[uu] + a3[uu]), mask);
@@ -550,8 +592,12 @@ __global__ void __launch_bounds__(NT) k_gs_pipe(LevelView<T> L, const T* __restr
           vst<T, V>(s_dp + (size_t)(i - h_lo) * K + k, out);
         }
       }
-      __syncthreads();
+      if constexpr (HS == 1)
+        __syncthreads();
+      else  // barriers 1..HS: this group's threads only
+        asm volatile("bar.sync %0, %1;\n" ::"r"(1 + hs), "r"(NTH) : "memory");
     }
+    if constexpr (HS > 1) __syncthreads();  // every group's colors before the write-back
     for (int t = threadIdx.x; t < (r_hi - r_lo) * K; t += blockDim.x)
       dp[(size_t)r_lo * K + t] = s_dp[(size_t)(r_lo - h_lo) * K + t];
     __syncthreads();

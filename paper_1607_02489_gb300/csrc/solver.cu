@@ -114,10 +114,11 @@ __global__ void __launch_bounds__(kBlock) k_maxpy(long long NK, int nv, const TV
 }
 
 // v = w / nrm for active columns, 0 otherwise (one FP64 division per column and
-// block; the elements are multiplied by the reciprocal).
-template <int K>
-__global__ void k_scale(long long NK, const double* __restrict__ w, const double* __restrict__ nrm,
-                        const int* __restrict__ active, double* __restrict__ v) {
+// block; the elements are multiplied by the reciprocal), written in one pass both
+// to the FP64 basis vector and, converted, to the V-cycle's input.
+template <int K, typename TZ>
+__global__ void k_scale_pack(long long NK, const double* __restrict__ w, const double* __restrict__ nrm,
+                             const int* __restrict__ active, double* __restrict__ v, TZ* __restrict__ in) {
   __shared__ double inv[K];
   if (threadIdx.x < K) {
     const double n = nrm[threadIdx.x];
@@ -126,7 +127,9 @@ __global__ void k_scale(long long NK, const double* __restrict__ w, const double
   __syncthreads();
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= NK) return;
-  v[e] = w[e] * inv[(int)(e % K)];
+  const double x = w[e] * inv[(int)(e % K)];
+  v[e] = x;
+  in[e] = (TZ)x;
 }
 
 // Selective re-orthogonalisation test (Daniel, Gragg, Kaufman and Stewart 1976):
@@ -453,11 +456,12 @@ class FgmresTask final : public SolveTask {
   // Enqueue Arnoldi step issued_ (after the normalisation of its basis vector),
   // its results into slot issued_ & 1, and that slot's event.
   void issue_step() {
-    if (issued_ > 0) {
-      k_scale<K><<<gNK_, kBlock, 0, s_>>>(NK_, w_->w, w_->hbuf + (size_t)issued_ * K, w_->st.active,
-                                          w_->V + (size_t)issued_ * NK_);
-      ++launches;
-    }
+    // v_j = (r or w) / its norm, into the basis and the V-cycle's input
+    const bool first = issued_ == 0;
+    k_scale_pack<K, TZ><<<gNK_, kBlock, 0, s_>>>(NK_, first ? w_->rK : w_->w,
+                                                first ? w_->rnorm : w_->hbuf + (size_t)issued_ * K, w_->st.active,
+                                                w_->V + (size_t)issued_ * NK_, (TZ*)vc_->input(0));
+    ++launches;
     j_ = issued_;
     step();
     const int slot = issued_ & 1;
@@ -533,8 +537,6 @@ class FgmresTask final : public SolveTask {
     EMIN_CUDA(cudaMemsetAsync(w_->st.gv, 0, sizeof(double) * (restart_ + 1) * K, s_));
     col_norms<K>(*w_, w_->rK, w_->rnorm, s_, launches);
     EMIN_CUDA(cudaMemcpyAsync(w_->st.gv, w_->rnorm, sizeof(double) * K, cudaMemcpyDeviceToDevice, s_));
-    k_scale<K><<<gNK_, kBlock, 0, s_>>>(NK_, w_->rK, w_->rnorm, w_->st.active, w_->V);
-    ++launches;
     j_ = 0;
     issued_ = seen_ = 0;
     for (auto& e : est_) std::fill(e.begin(), e.end(), 0.0);
@@ -545,11 +547,8 @@ class FgmresTask final : public SolveTask {
 
   void step() {
     const int j = j_;
-    double* Vj = w_->V + (size_t)j * NK_;
     TZ* Z = (TZ*)w_->Z;
-    // z_j = M^-1 v_j through the captured V-cycle
-    k_pack<double, TZ, K><<<gNK_, kBlock, 0, s_>>>(N_, Vj, K, K, (TZ*)vc_->input(0));
-    ++launches;
+    // z_j = M^-1 v_j through the captured V-cycle (v_j is in its input: issue_step)
     EMIN_CUDA(cudaGetLastError());
     EMIN_CUDA(vc_->run(K, s_));
     EMIN_CUDA(cudaMemcpyAsync(Z + (size_t)j * NK_, vc_->output(0), sizeof(TZ) * NK_, cudaMemcpyDeviceToDevice, s_));
@@ -882,6 +881,7 @@ void amg_params_default(amg_params* p) {
   p->ilu_order = 0;
   p->coarse = 0;
   p->device_setup = 1;
+  p->vanka_max_mib = 16384.0;
 }
 
 const char* amg_last_error(void) { return g_last_error.c_str(); }
@@ -929,6 +929,7 @@ std::string check_params(const amg_params* prm_in, amg_params& prm) {
   if (prm.gs_iters < 0 || prm.pre < 0 || prm.post < 0 || prm.omega <= 0.0) return "invalid smoother parameters";
   if (prm.smoother < 0 || prm.smoother > 2) return "smoother must be 0 (Braess-Sarazin), 1 (Vanka) or 2 (ILU(1))";
   if (prm.smoother == 1 && !(prm.vanka_omega > 0.0)) return "vanka_omega must be positive";
+  if (!(prm.vanka_max_mib > 0.0) || prm.vanka_max_mib > 1e9) return "vanka_max_mib must be in (0, 1e9]";
   if (prm.ilu_order != 0 && prm.ilu_order != 1) return "ilu_order must be 0 or 1";
   if (prm.coarse != 0 && prm.coarse != 1) return "coarse must be 0 (pseudo-inverse) or 1 (Vanka)";
   if (prm.coarse == 1 && !(prm.vanka_omega > 0.0)) return "vanka_omega must be positive";
@@ -949,6 +950,7 @@ SetupParams setup_params(const amg_params& prm, bool symmetric) {
   sp.ilu_order = prm.ilu_order;
   sp.vanka_coarse = prm.coarse == 1;
   sp.gs_iters = prm.gs_iters;
+  sp.vanka_max_bytes = (size_t)(prm.vanka_max_mib * 1048576.0);
   return sp;
 }
 
@@ -1295,6 +1297,17 @@ amg_status amg_set_wait_limit(amg_handle h, long long polls) {
 int amg_gs_variant(amg_handle h, int level, int nrhs, int* cluster, float* ms) {
   if (!h || !h->vc() || nrhs < 1 || nrhs > 32) return -1;
   return h->vc()->gs_choice(level, round_k(nrhs), cluster, ms);
+}
+
+amg_status amg_set_gs_variant(amg_handle h, int level, int nrhs, int variant, int cluster) {
+  if (!h || !h->vc()) return fail(AMG_ERR_ARG, "amg_set_gs_variant: null handle or host-only hierarchy");
+  if (nrhs < 1 || nrhs > 32) return fail(AMG_ERR_ARG, "amg_set_gs_variant: nrhs must be in 1..32");
+  if (cudaDeviceSynchronize() != cudaSuccess) return fail(AMG_ERR_CUDA, "amg_set_gs_variant: device synchronise");
+  const int K = round_k(nrhs);
+  for (VCycleIface* vc : {h->v32, h->v64})
+    if (vc && K <= vc->kmax() && !vc->set_gs_choice(level, K, variant, cluster))
+      return fail(AMG_ERR_ARG, "amg_set_gs_variant: the variant does not apply to this level and nrhs");
+  return AMG_OK;
 }
 
 int amg_row_shape(amg_handle h, int level, int nrhs, int kernel) {

@@ -5,6 +5,7 @@
 
 #include <cuda_runtime.h>
 
+#include <cstring>
 #include <memory>
 #include <stdexcept>
 #include <string>
@@ -54,6 +55,11 @@ struct VCycleIface {
   // pipelined, 3 one launch per phase), the cluster size and the time measured.
   virtual void set_autotune(bool on) = 0;
   virtual int gs_choice(int level, int K, int* cluster, float* ms) const = 0;
+  // Fix the variant of a level for K (the autotuner then leaves it): returns false
+  // when the level, K or the variant does not apply (a dense map on a level without
+  // one, a cluster size without a plan, a pipelined shape outside 0-6 or not for K).  A cycle already captured for K is
+  // dropped and captured again on its next run.  Not for a cycle whose clones run.
+  virtual bool set_gs_choice(int level, int K, int kind, int C) = 0;
   // Row mapping (0-3, see DeviceVCycle::Shape) of a sparse kernel class on a level
   // for K right-hand sides, as tuned or by default; -1 for a bad argument.
   virtual int row_shape(int level, int K, int cls) const = 0;
@@ -83,7 +89,7 @@ class DeviceVCycle : public VCycleIface {
   enum GsKind { kGsSingle = 0, kGsCluster = 1, kGsPipe = 2, kGsPhases = 3, kGsDense = 4 };
   struct GsChoice {
     int kind = -1;  // GsKind, -1 = not tuned yet
-    int C = 0;      // cluster size; shape of the pipelined kernel (0 heuristic, 1-3 launch_gs_pipe)
+    int C = 0;      // cluster size; shape of the pipelined kernel (0 heuristic, 1-6 launch_gs_pipe)
     float ms = 0.f; // measured time per launch
   };
   struct ClusterPlan {
@@ -146,6 +152,34 @@ class DeviceVCycle : public VCycleIface {
     if (cluster) *cluster = c.C;
     if (ms) *ms = c.ms;
     return c.kind;
+  }
+  bool set_gs_choice(int level, int K, int kind, int C) override {
+    const int ks = kslot(K);
+    if (level < 0 || level >= (int)views_.size() || ks < 0 || K > kmax_) return false;
+    switch (kind) {
+      case kGsSingle: case kGsPhases: break;
+      case kGsCluster: {
+        bool found = false;
+        for (const ClusterPlan& P : cplans_[level]) found = found || P.C == C;
+        if (!found) return false;
+        break;
+      }
+      case kGsPipe:
+        if (C < 0 || C > 6 || (C >= 4 && K < (C == 6 ? 8 : 4)) || gs_stage(level, K) <= 0 ||
+            gs_[level].ncol > kMaxColors)
+          return false;
+        break;
+      case kGsDense:
+        if (!gsM_[level] || C != 0) return false;
+        break;
+      default: return false;
+    }
+    (*tune_)[(size_t)level * 6 + ks] = {kind, C, 0.f};
+    if (graphs_[ks]) {
+      cudaGraphExecDestroy(graphs_[ks]);
+      graphs_[ks] = nullptr;
+    }
+    return true;
   }
   size_t clone_bytes(int kmax) const override {
     size_t b = 256;
@@ -592,7 +626,7 @@ class DeviceVCycle : public VCycleIface {
     const GsStrips& P = gs_[l];
     if (stage == 0) return 0;
     size_t b = (size_t)4 * P.T * K * sizeof(T) + (size_t)P.T * sizeof(T) + (size_t)(2 * P.T + 1) * sizeof(int);
-    if (stage == 2) b += (size_t)P.max_strip_nnz * (sizeof(T) + sizeof(int));
+    if (stage == 2) b += (size_t)P.max_strip_nnz * (sizeof(T) + sizeof(int)) + 32;  // + alignment of packed entries
     return (b + 15) / 16 * 16;
   }
   int gs_stage(int l, int K) const {
@@ -659,7 +693,8 @@ class DeviceVCycle : public VCycleIface {
       for (const ClusterPlan& P : cplans_[l])
         if (cluster_smem(P, K, gs_[l].ncol) <= 220 * 1024) cands.push_back({kGsCluster, P.C, 0.f});
       if (gs_stage(l, K) > 0 && gs_[l].ncol <= kMaxColors)
-        for (int v = 0; v < 4; ++v) cands.push_back({kGsPipe, v, 0.f});
+        for (int v = 0; v < 7; ++v)
+          if (v < 4 || K >= (v == 6 ? 8 : 4)) cands.push_back({kGsPipe, v, 0.f});
       cands.push_back({kGsPhases, 0, 0.f});
       if (gsM_[l]) cands.push_back({kGsDense, 0, 0.f});
       GsChoice best{kGsPhases, 0, 1e30f};
@@ -794,10 +829,21 @@ class DeviceVCycle : public VCycleIface {
   template <int K>
   bool launch_gs_pipe(int l, cudaStream_t s, int variant = 0) {
     // shapes the autotuner also tries: 1024 threads with (lanes per row, columns per thread)
+    // and 4-6: the right-hand sides split over 2 or 4 thread groups, each with its own
+    // barrier between colors (K >= 4 and K >= 8)
     switch (variant) {
       case 1: return launch_gs_pipe_v<K, 2, 2, 1024>(l, s);
       case 2: return launch_gs_pipe_v<K, 1, 2, 1024>(l, s);
       case 3: return launch_gs_pipe_v<K, 4, 1, 1024>(l, s);
+      case 4:
+        if constexpr (K >= 4) return launch_gs_pipe_g<K, 1, 2, kGsPipeBlock, 2>(l, s);
+        return false;
+      case 5:
+        if constexpr (K >= 4) return launch_gs_pipe_g<K, 1, 2, 1024, 2>(l, s);
+        return false;
+      case 6:
+        if constexpr (K >= 8) return launch_gs_pipe_g<K, 1, 2, 1024, 4>(l, s);
+        return false;
       default: break;
     }
     const GsStrips& P0 = gs_[l];
@@ -820,7 +866,7 @@ class DeviceVCycle : public VCycleIface {
     return launch_gs_pipe_g<K, G, V, NT>(l, s);
   }
 
-  template <int K, int G, int V, int NT>
+  template <int K, int G, int V, int NT, int HS = 1>
   bool launch_gs_pipe_g(int l, cudaStream_t s) {
     const LevelView<T>& L = views_[l];
     const Buf& B = buf_[l];
@@ -828,11 +874,12 @@ class DeviceVCycle : public VCycleIface {
     P.stage = gs_stage(l, K);
     if (P.stage == 0 || P.ncol > kMaxColors) return false;
     const size_t smem = gs_smem(l, K, P.stage);
-    auto kern = k_gs_pipe<T, K, G, V, NT>;
+    auto kern = k_gs_pipe<T, K, G, V, NT, HS>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 48 * 1024));
     cudaMemsetAsync(done_[l], 0, sizeof(int) * (P.nstrips + 1), s);
     // one block per strip: as many units in flight as the pipeline can overlap
-    kern<<<P.nstrips, NT, smem, s>>>(L, (const T*)B.g, B.dp, P, (const int*)ci_rel_[l], done_[l], err_);
+    kern<<<P.nstrips, NT, smem, s>>>(L, (const T*)B.g, B.dp, P, (const int*)ci_rel_[l], (const int2*)pk_[l],
+                                     done_[l], err_);
     return true;
   }
 
@@ -984,6 +1031,7 @@ class DeviceVCycle : public VCycleIface {
       gs_ = o.gs_;
       gs_lanes_ = o.gs_lanes_;
       ci_rel_ = o.ci_rel_;
+      pk_ = o.pk_;
       cplans_ = o.cplans_;
       vk_ = o.vk_;
       il_ = o.il_;
@@ -1190,6 +1238,18 @@ class DeviceVCycle : public VCycleIface {
           for (int64_t t = So.rowptr[r]; t < So.rowptr[r + 1]; ++t) rel[t] = So.col[t] - h0;
       }
       ci_rel_.push_back(alloc_copy<int>(rel));
+      if (sizeof(T) == 4) {  // (relative column, FP32 value bits) per entry for the pipelined kernel
+        std::vector<int2> pk(So.col.size());
+        for (size_t t = 0; t < pk.size(); ++t) {
+          const float v = (float)So.val[t];
+          int bits;
+          std::memcpy(&bits, &v, sizeof(bits));
+          pk[t] = make_int2(rel[t], bits);
+        }
+        pk_.push_back(alloc_copy<int2>(pk));
+      } else {
+        pk_.push_back(nullptr);
+      }
       done_.push_back(alloc<int>(nstrips + 1));
       // rows of each (strip parity, color) group, for the single-block kernel
       std::vector<int> plist, poff(1, 0);
@@ -1264,6 +1324,7 @@ class DeviceVCycle : public VCycleIface {
   std::vector<GsStrips> gs_;
   std::vector<int> gs_lanes_;
   std::vector<int*> ci_rel_;
+  std::vector<int2*> pk_;  // FP32: S entries as (ci_rel, value bits); nullptr in FP64
   std::vector<int*> done_;
   std::vector<int*> plist_, poff_;
   std::vector<std::vector<ClusterPlan>> cplans_;

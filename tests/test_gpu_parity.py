@@ -227,3 +227,87 @@ def test_full_size_lid_cavity_256_eight_rhs():
     assert np.all(np.linalg.norm(p.b - A @ x, axis=0) <= 1.01e-8 * np.linalg.norm(p.b, axis=0))
     xo, its_o, rel_o, _ = fgmres(Ho, p.b[:, :1], rtol=1e-8)
     assert abs(int(its[0]) - int(its_o[0])) <= 1
+
+
+def _dense_levels(Hg):
+    out = []
+    for l in range(Hg.num_levels() - 1):
+        try:
+            if Hg.level_gs_map(l).size:
+                out.append(l)
+        except g.AmgError:
+            pass
+    return out
+
+
+@pytest.mark.parametrize("case", ["lid32", "lid18_ragged3", "oseen_re100_k8"])
+@pytest.mark.parametrize("fp32", [0, 1])
+def test_dense_gauss_seidel_map_matches_the_sweeps(case, fp32):
+    """Every level with a dense Gauss-Seidel map relaxed once by the map (one dense
+    product) and once by the sweeps it stands for (one launch per phase), chosen with
+    amg_set_gs_variant: the cycles agree to a few roundings (1e-13 in FP64, 1e-4 in
+    FP32, the FP32 cycle's own bound), and the FP64 ones match the oracle to 1e-11.
+    The dense map is refused on a level without one."""
+    p = CASES[case]()
+    k = p.b.shape[1]
+    r = _rand(p.N, k, 13)
+    rt = torch.tensor(r, device="cuda")
+    zs = {}
+    for variant in ("dense map", "phase launches"):
+        Hg = g.Hierarchy(p, max_nrhs=k, vcycle_fp32=fp32)
+        levels = _dense_levels(Hg)
+        assert levels, "no level with a dense Gauss-Seidel map"
+        for l in levels:
+            Hg.set_gs_variant(l, k, variant)
+        zt = torch.empty_like(rt)
+        Hg.vcycle(rt, zt)
+        torch.cuda.synchronize()
+        for l in levels:
+            assert Hg.gs_variants(k)[l][0] == variant
+        zs[variant] = zt.cpu().numpy()
+        nodense = [l for l in range(Hg.num_levels() - 1) if l not in levels]
+        if nodense:
+            with pytest.raises(g.AmgError) as exc:
+                Hg.set_gs_variant(nodense[0], k, "dense map")
+            assert exc.value.status == -1
+    agree = _relerr(zs["dense map"], zs["phase launches"]).max()
+    print(f"\ndense map vs sweeps, {case}, fp32={fp32}: {agree:.2e}")
+    assert agree <= (1e-4 if fp32 else 1e-13)
+    if not fp32:
+        zo = vcycle(setup_hierarchy(p), r)
+        for z in zs.values():
+            assert np.all(_relerr(z, zo) <= 1e-11)
+
+
+@pytest.mark.parametrize("case", ["lid32", "oseen_re100_k8"])
+@pytest.mark.parametrize("fp32", [0, 1])
+def test_pipelined_gauss_seidel_shapes_match_phase_launches(case, fp32):
+    """Level 0 relaxed by the pipelined strip kernel in each of its launch shapes (0-3;
+    4-6 split the right-hand sides over 2 or 4 thread groups with their own barriers,
+    for 4 and 8 columns; FP32: S entries packed as one 8-byte word each) against one launch per phase
+    (amg_set_gs_variant): the same rows in the same order, so the cycles agree to a
+    few roundings, and the FP64 ones match the oracle to 1e-11."""
+    p = CASES[case]()
+    k = p.b.shape[1]
+    r = _rand(p.N, k, 14)
+    rt = torch.tensor(r, device="cuda")
+
+    def cycle(variant, shape):
+        Hg = g.Hierarchy(p, max_nrhs=k, vcycle_fp32=fp32)
+        Hg.set_gs_variant(0, k, variant, shape)
+        zt = torch.empty_like(rt)
+        Hg.vcycle(rt, zt)
+        torch.cuda.synchronize()
+        assert Hg.gs_variants(k)[0][:2] == (variant, shape)
+        return zt.cpu().numpy()
+
+    ref = cycle("phase launches", 0)
+    zo = None if fp32 else vcycle(setup_hierarchy(p), r)
+    shapes = range(7) if k >= 8 else range(6) if k >= 4 else range(4)
+    for shape in shapes:
+        z = cycle("pipelined", shape)
+        agree = _relerr(z, ref).max()
+        print(f"\npipelined shape {shape}, {case}, fp32={fp32}: vs phase launches {agree:.2e}")
+        assert agree <= (1e-4 if fp32 else 1e-13)
+        if zo is not None:
+            assert np.all(_relerr(z, zo) <= 1e-11)

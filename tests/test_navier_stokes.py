@@ -13,14 +13,16 @@ no worse than Braess-Sarazin).
 
 There is no lower band tied to Table 5: the oracle's counts sit at 45-75% of the
 paper's (its Vanka counts at nu = 0.01, 13-14, do not even rise above its Stokes
-ones as the paper's do), and neither of the two explanations at hand closes
+ones as the paper's do), and none of the explanations at hand closes
 that gap.  The
 coarsest level (exact here, Vanka in the paper) moves them by at most 3.  The
 stopping test matters more: the paper names a residual tolerance of 1e-6 without
 saying relative; read as an absolute ||r|| <= 1e-6 (||b|| is 4-8 on these
 systems) the counts rise by 15-25% (Vanka 16/16/16/31 and BS 18/19/18/47 on
 8x8-32x32 at nu = 0.01 and 16x16 at nu = 0.002, against 20/26/22/49 and
-19/22/26/55), still below the paper's."""
+19/22/26/55), still below the paper's.  The Gauss-Seidel order is not it either:
+relaxing S's rows in index order (oracle Params(gs_order="natural")) leaves the
+BS(2,2) counts of all five systems unchanged."""
 import numpy as np
 import pytest
 

@@ -157,6 +157,30 @@ def test_vanka_blocks_and_colors_match_oracle(case):
         Hg.level_vanka(len(Ho.levels) - 1)
 
 
+def test_gs_variant_calls_need_a_device_hierarchy():
+    """amg_set_gs_variant on a host-only hierarchy is an argument error; amg_gs_variant
+    reports -1 there (no cycle was built)."""
+    H = g.Hierarchy(stokes_lid_2d(8, nrhs=1), host_only=1)
+    with pytest.raises(g.AmgError) as exc:
+        H.set_gs_variant(0, 1, "pipelined", 0)
+    assert exc.value.status == -1 and "host-only" in str(exc.value)
+    assert all(v == "not chosen" for v, _, _ in H.gs_variants(1))
+
+
+def test_vanka_inverses_over_the_limit_fail_setup():
+    """Setup refuses a level whose FP64 Vanka block inverses exceed amg_params.vanka_max_mib
+    (large 3D blocks) with AMG_ERR_SETUP and a message naming the size; the same problem
+    builds under the default limit, and a non-positive limit is an argument error."""
+    prob = make_problem(4, 3, 0.0, 1.0, bc="lid", nrhs=1)
+    g.Hierarchy(prob, host_only=1, smoother=1, pre=1, post=1)  # a few MiB: within 16 GiB
+    with pytest.raises(g.AmgError) as exc:
+        g.Hierarchy(prob, host_only=1, smoother=1, pre=1, post=1, vanka_max_mib=0.01)
+    assert exc.value.status == -4 and "MiB, more than the limit" in str(exc.value)
+    with pytest.raises(g.AmgError) as exc:
+        g.Hierarchy(prob, host_only=1, smoother=1, vanka_max_mib=0.0)
+    assert exc.value.status == -1
+
+
 @pytest.mark.parametrize("case", ["lid32", "pinned16", "oseen32"])
 def test_coarsest_vanka_blocks_match_oracle(case):
     """coarse = 1 (the paper's Vanka relaxation of the coarsest level): the coarsest level

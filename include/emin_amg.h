@@ -324,14 +324,13 @@ amg_status amg_set_wait_limit(amg_handle h, long long polls);
 int amg_gs_variant(amg_handle h, int level, int nrhs, int* cluster, float* ms);
 
 /* Fix the Gauss-Seidel variant (numbering of amg_gs_variant; `cluster` is the cluster
- * size or the pipelined kernel's shape 0-6, else 0) of a level for nrhs right-hand
+ * size or the pipelined kernel's shape 0-3, else 0) of a level for nrhs right-hand
  * sides in both of the handle's V-cycles, in place of the autotuner's choice.  Every
  * variant relaxes the same rows in the same order (the dense map applies the same
  * sweeps' linear map); they differ only in rounding.  A cycle already captured for that
  * nrhs is captured again on its next use.  Returns AMG_ERR_ARG if the level, nrhs or
  * variant does not apply (a dense map on a level without one, a cluster size the level
- * has no plan for, a pipelined shape outside 0-6 or above 3 for fewer than 4
- * right-hand sides, 6 for fewer than 8).  Synchronises the device; not for a
+ * has no plan for, a pipelined shape outside 0-3).  Synchronises the device; not for a
  * handle whose request server is running. */
 amg_status amg_set_gs_variant(amg_handle h, int level, int nrhs, int variant, int cluster);
 

@@ -395,15 +395,11 @@ __device__ __forceinline__ void st_release(int* p, int v) {
 // counter; all are zero at launch, and dp is zero.
 // In FP32 an entry of S is one 8-byte word (column relative to the strip's halo,
 // value bits), pk: one shared-memory load per entry instead of two.
-// HS > 1 splits the block into HS groups of threads, each relaxing K / HS of the
-// right-hand sides (independent systems) with its own barrier between colors, so
-// one group's color steps overlap another's barrier wait.
-template <typename T, int K, int G, int V, int NT, int HS = 1>
+template <typename T, int K, int G, int V, int NT>
 __global__ void __launch_bounds__(NT) k_gs_pipe(LevelView<T> L, const T* __restrict__ g, T* dp, GsStrips P,
                                                 const int* __restrict__ ci_rel, const int2* __restrict__ pk,
                                                 int* done, int* err) {
-  static_assert((K / HS / V) * G <= 32, "a row group must fit in a warp");
-  static_assert(K % (HS * V) == 0 && NT % (32 * HS) == 0 && HS <= 8, "groups of whole warps and columns");
+  static_assert((K / V) * G <= 32, "a row group must fit in a warp");
   constexpr bool PK = sizeof(T) == 4;
   extern __shared__ __align__(16) unsigned char smem[];
   T* s_dp = reinterpret_cast<T*>(smem);
@@ -416,13 +412,10 @@ __global__ void __launch_bounds__(NT) k_gs_pipe(LevelView<T> L, const T* __restr
   int2* s_pk = reinterpret_cast<int2*>(smem + ((reinterpret_cast<unsigned char*>(s_ci) - smem + 15) & ~(size_t)15));
   __shared__ int s_fail, s_unit;
   __shared__ int s_so[kMaxColors + 1];  // this strip's color offsets (sorted rows)
-  constexpr int KH = K / HS;   // right-hand sides of a thread group
-  constexpr int KV = KH / V;   // threads per row and lane
+  constexpr int KV = K / V;
   constexpr int kGroup = KV * G;
-  constexpr int NTH = NT / HS;  // threads of a group
-  const int hs = threadIdx.x / NTH, th = threadIdx.x - hs * NTH;
-  const int k = hs * KH + (th % KV) * V;
-  const int lane = (th / KV) % G;
+  const int k = (threadIdx.x % KV) * V;
+  const int lane = (threadIdx.x / KV) % G;
   const unsigned mask = group_mask<kGroup>();
   const int n_p = L.n_p;
   const int nunits = P.iters * P.nstrips;
@@ -495,7 +488,7 @@ __global__ void __launch_bounds__(NT) k_gs_pipe(LevelView<T> L, const T* __restr
     const int* so = s_so;
     for (int pc = 0; pc < P.ncol; ++pc) {
       const int ra = so[pc], rb = so[pc + 1];
-      for (int t = th; t < (rb - ra) * kGroup; t += NTH) {
+      for (int t = threadIdx.x; t < (rb - ra) * kGroup; t += blockDim.x) {
         const int r = ra + t / kGroup;
         const int ea = s_rp[r - q0], eb = s_rp[r - q0 + 1];
         T acc[V];
@@ -592,12 +585,8 @@ __global__ void __launch_bounds__(NT) k_gs_pipe(LevelView<T> L, const T* __restr
           vst<T, V>(s_dp + (size_t)(i - h_lo) * K + k, out);
         }
       }
-      if constexpr (HS == 1)
-        __syncthreads();
-      else  // barriers 1..HS: this group's threads only
-        asm volatile("bar.sync %0, %1;\n" ::"r"(1 + hs), "r"(NTH) : "memory");
+      __syncthreads();
     }
-    if constexpr (HS > 1) __syncthreads();  // every group's colors before the write-back
     for (int t = threadIdx.x; t < (r_hi - r_lo) * K; t += blockDim.x)
       dp[(size_t)r_lo * K + t] = s_dp[(size_t)(r_lo - h_lo) * K + t];
     __syncthreads();

@@ -57,7 +57,7 @@ struct VCycleIface {
   virtual int gs_choice(int level, int K, int* cluster, float* ms) const = 0;
   // Fix the variant of a level for K (the autotuner then leaves it): returns false
   // when the level, K or the variant does not apply (a dense map on a level without
-  // one, a cluster size without a plan, a pipelined shape outside 0-6 or not for K).  A cycle already captured for K is
+  // one, a cluster size without a plan, a pipelined shape outside 0-3).  A cycle already captured for K is
   // dropped and captured again on its next run.  Not for a cycle whose clones run.
   virtual bool set_gs_choice(int level, int K, int kind, int C) = 0;
   // Row mapping (0-3, see DeviceVCycle::Shape) of a sparse kernel class on a level
@@ -89,7 +89,7 @@ class DeviceVCycle : public VCycleIface {
   enum GsKind { kGsSingle = 0, kGsCluster = 1, kGsPipe = 2, kGsPhases = 3, kGsDense = 4 };
   struct GsChoice {
     int kind = -1;  // GsKind, -1 = not tuned yet
-    int C = 0;      // cluster size; shape of the pipelined kernel (0 heuristic, 1-6 launch_gs_pipe)
+    int C = 0;      // cluster size; shape of the pipelined kernel (0 heuristic, 1-3 launch_gs_pipe)
     float ms = 0.f; // measured time per launch
   };
   struct ClusterPlan {
@@ -165,9 +165,7 @@ class DeviceVCycle : public VCycleIface {
         break;
       }
       case kGsPipe:
-        if (C < 0 || C > 6 || (C >= 4 && K < (C == 6 ? 8 : 4)) || gs_stage(level, K) <= 0 ||
-            gs_[level].ncol > kMaxColors)
-          return false;
+        if (C < 0 || C > 3 || gs_stage(level, K) <= 0 || gs_[level].ncol > kMaxColors) return false;
         break;
       case kGsDense:
         if (!gsM_[level] || C != 0) return false;
@@ -693,8 +691,7 @@ class DeviceVCycle : public VCycleIface {
       for (const ClusterPlan& P : cplans_[l])
         if (cluster_smem(P, K, gs_[l].ncol) <= 220 * 1024) cands.push_back({kGsCluster, P.C, 0.f});
       if (gs_stage(l, K) > 0 && gs_[l].ncol <= kMaxColors)
-        for (int v = 0; v < 7; ++v)
-          if (v < 4 || K >= (v == 6 ? 8 : 4)) cands.push_back({kGsPipe, v, 0.f});
+        for (int v = 0; v < 4; ++v) cands.push_back({kGsPipe, v, 0.f});
       cands.push_back({kGsPhases, 0, 0.f});
       if (gsM_[l]) cands.push_back({kGsDense, 0, 0.f});
       GsChoice best{kGsPhases, 0, 1e30f};
@@ -829,21 +826,10 @@ class DeviceVCycle : public VCycleIface {
   template <int K>
   bool launch_gs_pipe(int l, cudaStream_t s, int variant = 0) {
     // shapes the autotuner also tries: 1024 threads with (lanes per row, columns per thread)
-    // and 4-6: the right-hand sides split over 2 or 4 thread groups, each with its own
-    // barrier between colors (K >= 4 and K >= 8)
     switch (variant) {
       case 1: return launch_gs_pipe_v<K, 2, 2, 1024>(l, s);
       case 2: return launch_gs_pipe_v<K, 1, 2, 1024>(l, s);
       case 3: return launch_gs_pipe_v<K, 4, 1, 1024>(l, s);
-      case 4:
-        if constexpr (K >= 4) return launch_gs_pipe_g<K, 1, 2, kGsPipeBlock, 2>(l, s);
-        return false;
-      case 5:
-        if constexpr (K >= 4) return launch_gs_pipe_g<K, 1, 2, 1024, 2>(l, s);
-        return false;
-      case 6:
-        if constexpr (K >= 8) return launch_gs_pipe_g<K, 1, 2, 1024, 4>(l, s);
-        return false;
       default: break;
     }
     const GsStrips& P0 = gs_[l];
@@ -866,7 +852,7 @@ class DeviceVCycle : public VCycleIface {
     return launch_gs_pipe_g<K, G, V, NT>(l, s);
   }
 
-  template <int K, int G, int V, int NT, int HS = 1>
+  template <int K, int G, int V, int NT>
   bool launch_gs_pipe_g(int l, cudaStream_t s) {
     const LevelView<T>& L = views_[l];
     const Buf& B = buf_[l];
@@ -874,7 +860,7 @@ class DeviceVCycle : public VCycleIface {
     P.stage = gs_stage(l, K);
     if (P.stage == 0 || P.ncol > kMaxColors) return false;
     const size_t smem = gs_smem(l, K, P.stage);
-    auto kern = k_gs_pipe<T, K, G, V, NT, HS>;
+    auto kern = k_gs_pipe<T, K, G, V, NT>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 48 * 1024));
     cudaMemsetAsync(done_[l], 0, sizeof(int) * (P.nstrips + 1), s);
     // one block per strip: as many units in flight as the pipeline can overlap

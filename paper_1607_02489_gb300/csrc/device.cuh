@@ -1440,20 +1440,42 @@ struct FFAcc {
   __device__ __forceinline__ void add_small(float a, float z) { c = fmaf(a, z, c); }
 };
 
-template <int K, int V>
+// Sum of two float-float accumulators (two-sum of the leading parts).
+__device__ __forceinline__ void ff_merge(FFAcc& a, float s2, float c2) {
+  const float t = a.s + s2;
+  const float bp = t - a.s;
+  const float err = (a.s - (t - bp)) + (s2 - bp);
+  a.s = t;
+  a.c += c2 + err;
+}
+
+// G lanes per row (small problems: G = 4 keeps more gathers in flight per row), their
+// float-float partial sums merged by shuffles at the end.
+template <int K, int G, int V>
 __global__ void __launch_bounds__(kBlock) k_block_spmv_ff(FFLevel L, const float* __restrict__ z,
                                                           double* __restrict__ out) {
-  using M = RowMap<K, 1, V>;
+  using M = RowMap<K, G, V>;
   const M q(gtid());
   const unsigned i = q.row, k0 = q.k0;
   const unsigned nvK = (unsigned)L.n_v * K, nuK = (unsigned)L.dim * nvK;
+  auto merge = [&](FFAcc& a) {
+    if constexpr (G > 1) {
+      const unsigned mask = group_mask<M::W>();
+#pragma unroll
+      for (int off = G / 2; off >= 1; off >>= 1) {
+        const float s2 = __shfl_xor_sync(mask, a.s, off * M::KV);
+        const float c2 = __shfl_xor_sync(mask, a.c, off * M::KV);
+        ff_merge(a, s2, c2);
+      }
+    }
+  };
   if (i < (unsigned)L.n_v) {
     FFAcc acc[3][V];
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
       for (int u = 0; u < V; ++u) acc[c][u] = {0.f, 0.f};
-    for (int e = L.A.rp[i]; e < L.A.rp[i + 1]; ++e) {
+    for (int e = L.A.rp[i] + q.lane; e < L.A.rp[i + 1]; e += G) {
       const float h = L.A.hi[e], l = L.A.lo[e];
       const unsigned j = (unsigned)L.A.ci[e] * K + k0;
 #pragma unroll
@@ -1472,7 +1494,7 @@ __global__ void __launch_bounds__(kBlock) k_block_spmv_ff(FFLevel L, const float
     for (int c = 0; c < 3; ++c)
       if (c < L.dim) {
         const unsigned r = c * L.n_v + i;
-        for (int e = L.Bt.rp[r]; e < L.Bt.rp[r + 1]; ++e) {
+        for (int e = L.Bt.rp[r] + q.lane; e < L.Bt.rp[r + 1]; e += G) {
           const float h = L.Bt.hi[e], l = L.Bt.lo[e];
           float zv[V];
           vld<float, V>(zv, z + nuK + (unsigned)L.Bt.ci[e] * K + k0);
@@ -1482,16 +1504,20 @@ __global__ void __launch_bounds__(kBlock) k_block_spmv_ff(FFLevel L, const float
             acc[c][u].add_small(l, zv[u]);
           }
         }
-        const unsigned o = c * nvK + i * K + k0;
 #pragma unroll
-        for (int u = 0; u < V; ++u) out[o + u] = (double)acc[c][u].s + (double)acc[c][u].c;
+        for (int u = 0; u < V; ++u) merge(acc[c][u]);
+        if (q.lane == 0) {
+          const unsigned o = c * nvK + i * K + k0;
+#pragma unroll
+          for (int u = 0; u < V; ++u) out[o + u] = (double)acc[c][u].s + (double)acc[c][u].c;
+        }
       }
   } else if (i < (unsigned)(L.n_v + L.n_p)) {
     const unsigned p = i - L.n_v;
     FFAcc acc[V];
 #pragma unroll
     for (int u = 0; u < V; ++u) acc[u] = {0.f, 0.f};
-    for (int e = L.B.rp[p]; e < L.B.rp[p + 1]; ++e) {
+    for (int e = L.B.rp[p] + q.lane; e < L.B.rp[p + 1]; e += G) {
       const float h = L.B.hi[e], l = L.B.lo[e];
       float zv[V];
       vld<float, V>(zv, z + (unsigned)L.B.ci[e] * K + k0);
@@ -1501,6 +1527,9 @@ __global__ void __launch_bounds__(kBlock) k_block_spmv_ff(FFLevel L, const float
         acc[u].add_small(l, zv[u]);
       }
     }
+#pragma unroll
+    for (int u = 0; u < V; ++u) merge(acc[u]);
+    if (q.lane != 0) return;
     const unsigned o = nuK + p * K + k0;
 #pragma unroll
     for (int u = 0; u < V; ++u) {
@@ -1511,17 +1540,30 @@ __global__ void __launch_bounds__(kBlock) k_block_spmv_ff(FFLevel L, const float
   }
 }
 
-// Coarsest level: x = A^+ b with the FP64 pseudo-inverse, whatever T is.
+// Coarsest level: x = A^+ b with the FP64 pseudo-inverse, whatever T is.  One warp
+// per row: the lanes split the row's columns (so the FP64 work of a row spreads over
+// the SMs, not over one thread), then a shuffle tree per right-hand side.
 template <typename T, int K>
 __global__ void __launch_bounds__(kBlock) k_coarse_solve(int Nc, const double* __restrict__ pinv,
                                                          const T* __restrict__ b, T* __restrict__ x) {
-  const long long t = gtid();
-  const int i = (int)(t / K), k = (int)(t % K);
+  const long long i = gtid() >> 5;
+  const int lane = threadIdx.x & 31;
   if (i >= Nc) return;
-  double s = 0.0;
   const double* row = pinv + (size_t)i * Nc;
-  for (int j = 0; j < Nc; ++j) s += row[j] * (double)b[(size_t)j * K + k];
-  x[(size_t)i * K + k] = (T)s;
+  double s[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) s[k] = 0.0;
+  for (int j = lane; j < Nc; j += 32) {
+    const double a = row[j];
+#pragma unroll
+    for (int k = 0; k < K; ++k) s[k] += a * (double)b[(size_t)j * K + k];
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) s[k] += __shfl_xor_sync(0xffffffffu, s[k], off);
+    if (lane == k) x[(size_t)i * K + k] = (T)s[k];
+  }
 }
 
 // dst (N x K) = src (N x ld, first nrhs columns, converted), zero padding.

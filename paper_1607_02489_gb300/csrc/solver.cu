@@ -32,6 +32,13 @@ amg_status fail(amg_status st, const std::string& msg) {
 
 constexpr int kRedBlocks = 608;  // 4 blocks per SM on 152 SMs for the streaming reductions
 
+// Blocks of a streaming reduction over NK entries: about four entries per thread,
+// at most kRedBlocks (small problems: a few blocks, few partial sums to combine).
+inline int red_blocks(long long NK) {
+  const long long b = (NK + 4LL * kBlock - 1) / (4LL * kBlock);
+  return (int)std::max(1LL, std::min<long long>(kRedBlocks, b));
+}
+
 // part[(blk*nd + i)*K + k] = sum over this block's entries with rhs k of V_i[e] * w[e],
 // for i < nv, plus w[e]^2 at i = nv when self is set (nd = nv + self).  Nothing
 // is done when cond is given and *cond == 0.
@@ -331,8 +338,9 @@ namespace fgmres_detail {
 template <int K>
 void col_norms(const Krylov& w, const double* v, double* out, cudaStream_t s, long long& launches) {
   const long long NK = w.N * K;
-  k_mdot_partial<K, double><<<kRedBlocks, kBlock, 0, s>>>(NK, 1, 0, v, v, w.part, nullptr);
-  k_reduce_partials<<<(K * 32 + 127) / 128, 128, 0, s>>>(kRedBlocks, K, w.part, out, 0, 1, nullptr);
+  const int rb = red_blocks(NK);
+  k_mdot_partial<K, double><<<rb, kBlock, 0, s>>>(NK, 1, 0, v, v, w.part, nullptr);
+  k_reduce_partials<<<(K * 32 + 127) / 128, 128, 0, s>>>(rb, K, w.part, out, 0, 1, nullptr);
   launches += 2;
 }
 
@@ -565,16 +573,17 @@ class FgmresTask final : public SolveTask {
     double* hn = w_->hbuf + (size_t)nv * K;  // |w|^2, then the norm of the new vector
     double* h2 = w_->y;                      // scratch for the correction coefficients
     const unsigned r1 = (unsigned)((K * 32 + 127) / 128), rnv = (unsigned)((nv * K * 32 + 127) / 128);
-    k_mdot_partial<K, double><<<kRedBlocks, kBlock, 0, s_>>>(NK_, nv, 1, w_->V, w_->w, w_->part, nullptr);
-    k_reduce_partials<<<((nv + 1) * K * 32 + 127) / 128, 128, 0, s_>>>(kRedBlocks, (nv + 1) * K, w_->part, w_->hbuf,
+    const int rb = red_blocks(NK_);
+    k_mdot_partial<K, double><<<rb, kBlock, 0, s_>>>(NK_, nv, 1, w_->V, w_->w, w_->part, nullptr);
+    k_reduce_partials<<<((nv + 1) * K * 32 + 127) / 128, 128, 0, s_>>>(rb, (nv + 1) * K, w_->part, w_->hbuf,
                                                                         0, 0, nullptr);
-    k_maxpy<K, double><<<kRedBlocks, kBlock, 0, s_>>>(NK_, nv, w_->V, w_->hbuf, w_->w, w_->part, nullptr);
-    k_reduce_partials<<<r1, 128, 0, s_>>>(kRedBlocks, K, w_->part, w_->rnorm, 0, 1, nullptr);
+    k_maxpy<K, double><<<rb, kBlock, 0, s_>>>(NK_, nv, w_->V, w_->hbuf, w_->w, w_->part, nullptr);
+    k_reduce_partials<<<r1, 128, 0, s_>>>(rb, K, w_->part, w_->rnorm, 0, 1, nullptr);
     k_reorth_check<<<1, 32, 0, s_>>>(K, hn, w_->rnorm, w_->st.active, w_->reorth);
-    k_mdot_partial<K, double><<<kRedBlocks, kBlock, 0, s_>>>(NK_, nv, 0, w_->V, w_->w, w_->part, w_->reorth);
-    k_reduce_partials<<<rnv, 128, 0, s_>>>(kRedBlocks, nv * K, w_->part, h2, 0, 0, w_->reorth);
-    k_maxpy<K, double><<<kRedBlocks, kBlock, 0, s_>>>(NK_, nv, w_->V, h2, w_->w, w_->part, w_->reorth);
-    k_reduce_partials<<<r1, 128, 0, s_>>>(kRedBlocks, K, w_->part, hn, 0, 1, w_->reorth);
+    k_mdot_partial<K, double><<<rb, kBlock, 0, s_>>>(NK_, nv, 0, w_->V, w_->w, w_->part, w_->reorth);
+    k_reduce_partials<<<rnv, 128, 0, s_>>>(rb, nv * K, w_->part, h2, 0, 0, w_->reorth);
+    k_maxpy<K, double><<<rb, kBlock, 0, s_>>>(NK_, nv, w_->V, h2, w_->w, w_->part, w_->reorth);
+    k_reduce_partials<<<r1, 128, 0, s_>>>(rb, K, w_->part, hn, 0, 1, w_->reorth);
     k_reduce_partials<<<rnv, 128, 0, s_>>>(1, nv * K, h2, w_->hbuf, 1, 0, w_->reorth);
     k_givens<<<1, 32, 0, s_>>>(j, restart_, K, w_->hbuf, w_->st, w_->bnorm, rtol_, w_->n_active);
     launches += 11;

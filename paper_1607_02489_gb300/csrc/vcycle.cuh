@@ -273,7 +273,7 @@ class DeviceVCycle : public VCycleIface {
       for (int sw = 0; sw < std::max(1, pre_ + post_); ++sw) vanka_sweep<K>(nl - 1, sw == 0, s);
     } else {
       mark_begin(nl - 1, kCoarse, s);  // every kernel launch of the cycle is preceded by mark_begin
-      k_coarse_solve<T, K><<<grid_for((long long)Nc_ * K), kBlock, 0, s>>>(Nc_, pinv_, buf_[nl - 1].b, buf_[nl - 1].x);
+      k_coarse_solve<T, K><<<grid_for((long long)Nc_ * 32), kBlock, 0, s>>>(Nc_, pinv_, buf_[nl - 1].b, buf_[nl - 1].x);
       mark_end(s);
     }
     for (int l = nl - 2; l >= 0; --l) {
@@ -913,7 +913,12 @@ class DeviceVCycle : public VCycleIface {
   template <int K>
   cudaError_t launch_ff(const float* z, double* out, cudaStream_t s) {
     constexpr int V = VecWidth<float, K>::V;
-    k_block_spmv_ff<K, V><<<grid_for((long long)(ff_.n_v + ff_.n_p) * (K / V)), kBlock, 0, s>>>(ff_, z, out);
+    constexpr int G4 = (K / V) * 4 <= 32 ? 4 : 1;
+    const long long rows = (long long)ff_.n_v + ff_.n_p;
+    if (rows * K < (1LL << 16))  // small problem: 4 lanes per row
+      k_block_spmv_ff<K, G4, V><<<grid_for(rows * (K / V) * G4), kBlock, 0, s>>>(ff_, z, out);
+    else
+      k_block_spmv_ff<K, 1, V><<<grid_for(rows * (K / V)), kBlock, 0, s>>>(ff_, z, out);
     ++launches_;
     return cudaGetLastError();
   }

@@ -32,16 +32,22 @@ amg_status fail(amg_status st, const std::string& msg) {
 
 constexpr int kRedBlocks = 608;  // 4 blocks per SM on 152 SMs for the streaming reductions
 
-// Blocks of a streaming reduction over NK entries: about four entries per thread,
-// at most kRedBlocks (small problems: a few blocks, few partial sums to combine).
+// Blocks of a streaming reduction over NK entries: one entry per thread at most,
+// and at most kRedBlocks (small problems: few partial sums to combine).
 inline int red_blocks(long long NK) {
-  const long long b = (NK + 4LL * kBlock - 1) / (4LL * kBlock);
+  const long long b = (NK + kBlock - 1) / kBlock;
   return (int)std::max(1LL, std::min<long long>(kRedBlocks, b));
 }
 
+// Second grid dimension of the inner products: when the entries fill fewer blocks
+// than the SMs, the basis vectors are split over blockIdx.y too, so the FP64 work
+// (slow on this GPU's FP64 pipe) spreads over more SMs.
+inline int dot_split(int rb, int nd) { return std::max(1, std::min(nd, kRedBlocks / 4 / rb)); }
+
 // part[(blk*nd + i)*K + k] = sum over this block's entries with rhs k of V_i[e] * w[e],
-// for i < nv, plus w[e]^2 at i = nv when self is set (nd = nv + self).  Nothing
-// is done when cond is given and *cond == 0.
+// for i < nv, plus w[e]^2 at i = nv when self is set (nd = nv + self); blk is
+// blockIdx.x, and blockIdx.y takes every gridDim.y-th i.  Nothing is done when cond
+// is given and *cond == 0.
 template <int K, typename TV>
 __global__ void __launch_bounds__(kBlock) k_mdot_partial(long long NK, int nv, int self, const TV* __restrict__ V,
                                                          const double* __restrict__ w, double* __restrict__ part,
@@ -51,7 +57,7 @@ __global__ void __launch_bounds__(kBlock) k_mdot_partial(long long NK, int nv, i
   const int k = threadIdx.x % K;
   const long long stride = (long long)gridDim.x * blockDim.x;
   const int nd = nv + self;
-  for (int i = 0; i < nd; ++i) {
+  for (int i = blockIdx.y; i < nd; i += gridDim.y) {
     double acc = 0.0;
     if (i < nv) {
       const TV* Vi = V + (size_t)i * NK;
@@ -574,13 +580,15 @@ class FgmresTask final : public SolveTask {
     double* h2 = w_->y;                      // scratch for the correction coefficients
     const unsigned r1 = (unsigned)((K * 32 + 127) / 128), rnv = (unsigned)((nv * K * 32 + 127) / 128);
     const int rb = red_blocks(NK_);
-    k_mdot_partial<K, double><<<rb, kBlock, 0, s_>>>(NK_, nv, 1, w_->V, w_->w, w_->part, nullptr);
+    k_mdot_partial<K, double><<<dim3(rb, dot_split(rb, nv + 1)), kBlock, 0, s_>>>(NK_, nv, 1, w_->V, w_->w, w_->part,
+                                                                                  nullptr);
     k_reduce_partials<<<((nv + 1) * K * 32 + 127) / 128, 128, 0, s_>>>(rb, (nv + 1) * K, w_->part, w_->hbuf,
                                                                         0, 0, nullptr);
     k_maxpy<K, double><<<rb, kBlock, 0, s_>>>(NK_, nv, w_->V, w_->hbuf, w_->w, w_->part, nullptr);
     k_reduce_partials<<<r1, 128, 0, s_>>>(rb, K, w_->part, w_->rnorm, 0, 1, nullptr);
     k_reorth_check<<<1, 32, 0, s_>>>(K, hn, w_->rnorm, w_->st.active, w_->reorth);
-    k_mdot_partial<K, double><<<rb, kBlock, 0, s_>>>(NK_, nv, 0, w_->V, w_->w, w_->part, w_->reorth);
+    k_mdot_partial<K, double><<<dim3(rb, dot_split(rb, nv)), kBlock, 0, s_>>>(NK_, nv, 0, w_->V, w_->w, w_->part,
+                                                                              w_->reorth);
     k_reduce_partials<<<rnv, 128, 0, s_>>>(rb, nv * K, w_->part, h2, 0, 0, w_->reorth);
     k_maxpy<K, double><<<rb, kBlock, 0, s_>>>(NK_, nv, w_->V, h2, w_->w, w_->part, w_->reorth);
     k_reduce_partials<<<r1, 128, 0, s_>>>(rb, K, w_->part, hn, 0, 1, w_->reorth);

@@ -145,18 +145,34 @@ __global__ void k_scale_pack(long long NK, const double* __restrict__ w, const d
   in[e] = (TZ)x;
 }
 
+// The sum k_reduce_partials forms for output t (same order, so the same bits), by
+// the calling warp; every lane gets it.
+__device__ __forceinline__ double warp_sum_partials(const double* __restrict__ part, int nblk, int nvK, int t) {
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+  for (int b = lane; b < nblk; b += 32) s += part[(size_t)b * nvK + t];
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  return s;
+}
+
 // Selective re-orthogonalisation test (Daniel, Gragg, Kaufman and Stewart 1976):
 // after one classical Gram-Schmidt pass, w' is re-orthogonalised when
-// |w'| < |w| / sqrt(2) for some active column.  slot holds |w|^2 on entry and
-// |w'| on exit (the norm used when no second pass runs); *flag = 1 asks for it.
-__global__ void k_reorth_check(int K, double* __restrict__ slot, const double* __restrict__ nrm1,
+// |w'| < |w| / sqrt(2) for some active column.  |w'| comes from the nblk block
+// partial sums of |w'|^2 in part (warp k sums column k; 32 K threads).  slot holds
+// |w|^2 on entry and |w'| on exit (the norm used when no second pass runs);
+// *flag = 1 asks for the second pass.
+__global__ void k_reorth_check(int K, double* __restrict__ slot, const double* __restrict__ part, int nblk,
                                const int* __restrict__ active, int* __restrict__ flag) {
-  const int k = threadIdx.x;
+  const int k = threadIdx.x >> 5;
   int need = 0;
   if (k < K) {
-    const double w2 = slot[k], n1 = nrm1[k];
-    need = active[k] && (n1 * n1 < 0.5 * w2);
-    slot[k] = n1;
+    const double n1 = sqrt(warp_sum_partials(part, nblk, K, k));
+    if ((threadIdx.x & 31) == 0) {
+      const double w2 = slot[k];
+      need = active[k] && (n1 * n1 < 0.5 * w2);
+      slot[k] = n1;
+    }
   }
   const int any = __syncthreads_or(need);
   if (threadIdx.x == 0) *flag = any;
@@ -164,9 +180,23 @@ __global__ void k_reorth_check(int K, double* __restrict__ slot, const double* _
 
 // Column j of the Hessenberg matrix for every rhs: apply the previous Givens
 // rotations, form the new one, update the residual recurrence, retire
-// columns that converged, broke down or ran out of iterations.
-__global__ void k_givens(int j, int m, int K, const double* __restrict__ hcol, GmresState st,
-                         const double* __restrict__ bnorm, double rtol, int* __restrict__ n_active) {
+// columns that converged, broke down or ran out of iterations.  When *reorth is
+// set the second Gram-Schmidt pass ran: first its coefficients h2 (nv per column)
+// are added to the column and the new vector's norm |w''| (hcol row nv) is formed
+// from the nblk partial sums in part (warp k, column k; 32 K threads).
+__global__ void k_givens(int j, int m, int K, double* __restrict__ hcol, GmresState st,
+                         const double* __restrict__ bnorm, double rtol, int* __restrict__ n_active,
+                         const int* __restrict__ reorth, const double* __restrict__ part, int nblk,
+                         const double* __restrict__ h2, int nv) {
+  if (*reorth) {
+    const int w = threadIdx.x >> 5;
+    if (w < K) {
+      const double n2 = sqrt(warp_sum_partials(part, nblk, K, w));
+      if ((threadIdx.x & 31) == 0) hcol[(size_t)nv * K + w] = n2;
+    }
+    for (int t = threadIdx.x; t < nv * K; t += blockDim.x) hcol[t] += h2[t];
+    __syncthreads();
+  }
   const int k = threadIdx.x;
   int still = 0;
   if (k < K && st.active[k]) {
@@ -578,23 +608,21 @@ class FgmresTask final : public SolveTask {
     const int nv = j + 1;
     double* hn = w_->hbuf + (size_t)nv * K;  // |w|^2, then the norm of the new vector
     double* h2 = w_->y;                      // scratch for the correction coefficients
-    const unsigned r1 = (unsigned)((K * 32 + 127) / 128), rnv = (unsigned)((nv * K * 32 + 127) / 128);
+    const unsigned rnv = (unsigned)((nv * K * 32 + 127) / 128);
     const int rb = red_blocks(NK_);
     k_mdot_partial<K, double><<<dim3(rb, dot_split(rb, nv + 1)), kBlock, 0, s_>>>(NK_, nv, 1, w_->V, w_->w, w_->part,
                                                                                   nullptr);
     k_reduce_partials<<<((nv + 1) * K * 32 + 127) / 128, 128, 0, s_>>>(rb, (nv + 1) * K, w_->part, w_->hbuf,
                                                                         0, 0, nullptr);
     k_maxpy<K, double><<<rb, kBlock, 0, s_>>>(NK_, nv, w_->V, w_->hbuf, w_->w, w_->part, nullptr);
-    k_reduce_partials<<<r1, 128, 0, s_>>>(rb, K, w_->part, w_->rnorm, 0, 1, nullptr);
-    k_reorth_check<<<1, 32, 0, s_>>>(K, hn, w_->rnorm, w_->st.active, w_->reorth);
+    k_reorth_check<<<1, 32 * K, 0, s_>>>(K, hn, w_->part, rb, w_->st.active, w_->reorth);
     k_mdot_partial<K, double><<<dim3(rb, dot_split(rb, nv)), kBlock, 0, s_>>>(NK_, nv, 0, w_->V, w_->w, w_->part,
                                                                               w_->reorth);
     k_reduce_partials<<<rnv, 128, 0, s_>>>(rb, nv * K, w_->part, h2, 0, 0, w_->reorth);
     k_maxpy<K, double><<<rb, kBlock, 0, s_>>>(NK_, nv, w_->V, h2, w_->w, w_->part, w_->reorth);
-    k_reduce_partials<<<r1, 128, 0, s_>>>(rb, K, w_->part, hn, 0, 1, w_->reorth);
-    k_reduce_partials<<<rnv, 128, 0, s_>>>(1, nv * K, h2, w_->hbuf, 1, 0, w_->reorth);
-    k_givens<<<1, 32, 0, s_>>>(j, restart_, K, w_->hbuf, w_->st, w_->bnorm, rtol_, w_->n_active);
-    launches += 11;
+    k_givens<<<1, 32 * K, 0, s_>>>(j, restart_, K, w_->hbuf, w_->st, w_->bnorm, rtol_, w_->n_active, w_->reorth,
+                                   w_->part, rb, h2, nv);
+    launches += 8;
     EMIN_CUDA(cudaGetLastError());
   }
 

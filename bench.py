@@ -30,6 +30,8 @@ sys.path.insert(0, ROOT)
 
 MESH = 256
 NRHS = 8
+ARNOLDI_NV = 12        # basis vectors of the timed Gram-Schmidt pass
+FP64_PEAK_TFLOPS = 1.25  # GB300 nominal dense FP64 rate (1/64 of its FP32 rate)
 RTOL = 1e-8
 RESTART = 100
 MAXIT = 300
@@ -735,6 +737,17 @@ def main():
                 "bytes_per_launch": bytes_launch, "avg_launch_us": avg_ms * 1000.0,
                 "vcycle_kernels_GBs": vcycle_bytes / (vcycle_ms / 1000.0) / 1e9,
                 "vcycle_kernels_frac": vcycle_bytes / (vcycle_ms / 1000.0) / 1e9 / peak}
+    # the FGMRES Arnoldi kernels, bound by FP64 arithmetic: one Gram-Schmidt pass with
+    # ARNOLDI_NV basis vectors (about the middle of a 22-23 iteration solve), CUDA events
+    NV = ARNOLDI_NV
+    ms_dot, ms_upd = H32.profile_arnoldi(NRHS, NV, reps=10)
+    fma = (NV + 1) * p.N * NRHS
+    arnoldi = {"bound": "fp64", "kernels": f"k_mdot_partial / k_maxpy, {NV} basis vectors of {p.N} x {NRHS}",
+               "achieved": [2 * fma / (t / 1000.0) / 1e12 for t in (ms_dot, ms_upd)],
+               "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "peak_kind": "nominal (GB300 FP64, no measured figure)",
+               "frac": [2 * fma / (t / 1000.0) / 1e12 / FP64_PEAK_TFLOPS for t in (ms_dot, ms_upd)],
+               "avg_launch_us": [1000.0 * ms_dot, 1000.0 * ms_upd],
+               "dram_algorithmic_GBs": [8.0 * (NV + 1) * p.N * NRHS / (t / 1000.0) / 1e9 for t in (ms_dot, ms_upd)]}
     gs_variants = [f"L{l}: {v}{' x' + str(c) if v == 'cluster' else (' shape ' + str(c) if v == 'pipelined' else '')}"
                    f" ({1000.0 * t:.1f} us)"
                    for l, (v, c, t) in enumerate(H32.gs_variants(NRHS))]
@@ -847,6 +860,7 @@ def main():
                 "serving": serving, "accuracy": accuracy, "vanka": vanka, "ilu": ilu, "picard": picard,
                 "setup": setup, "configs": configs,
                 "e2e": e2e, "gpu_launches": launches32, "clocks": clocks, "roofline": roofline,
+                "arnoldi_roofline": arnoldi,
                 "vcycle_us_by_kernel": breakdown, "gs_variants": gs_variants,
                 "row_shapes": {f"L{l}": "".join(str(v) for v in d.values()) for l, d in H32.row_shapes(NRHS).items()},
                 "cpu_baseline": cpu}

@@ -237,6 +237,16 @@ amg_status amg_fgmres_solve_host(amg_handle h, const double* b_host, double* x_h
 #define AMG_NUM_KERNEL_CLASSES 10
 amg_status amg_profile_vcycle(amg_handle h, int nrhs, int reps, double* ms, long long* count, void* stream);
 
+/* Arnoldi timing: one classical Gram-Schmidt pass with nv basis vectors of N x nrhs on
+ * the solver's own FP64 workspace (allocated as for restart = nv, then zeroed: the FP64
+ * work does not depend on the values), with CUDA events on `stream`: *ms_dot gets the
+ * average time of the inner-product kernel (nv products and the norm, per column) and
+ * *ms_update that of the update kernel (w -= V h, with the norm), over `reps` launches
+ * after one untimed.  Each does (nv + 1) N nrhs FP64 multiply-adds.  Synchronises
+ * `stream`; overwrites the workspace (call it between solves). */
+amg_status amg_profile_arnoldi(amg_handle h, int nrhs, int nv, int reps, double* ms_dot, double* ms_update,
+                               void* stream);
+
 /* Number of CUDA kernels this handle has launched so far (a replayed V-cycle graph
  * counts each of its kernel nodes).  Host-side counter, no synchronisation. */
 long long amg_kernel_launches(amg_handle h);

@@ -24,7 +24,7 @@ STATUS_NAMES = {0: "OK", 1: "NOT_CONVERGED", 2: "BREAKDOWN", -1: "ERR_ARG", -2: 
 EXPORTED = ["amg_params_default", "amg_hierarchy_create", "amg_hierarchy_create_reuse", "amg_hierarchy_export",
             "amg_hierarchy_import", "amg_vcycle_apply", "amg_apply", "amg_fgmres_solve",
             "amg_fgmres_solve_host", "amg_num_levels", "amg_level_get_info", "amg_level_get_matrix",
-            "amg_level_get_points", "amg_hierarchy_destroy", "amg_last_error", "amg_profile_vcycle", "amg_kernel_launches", "amg_apply_noalloc", "amg_gs_variant", "amg_set_gs_variant", "amg_row_shape", "amg_level_get_vanka", "amg_level_get_ilu",
+            "amg_level_get_points", "amg_hierarchy_destroy", "amg_last_error", "amg_profile_vcycle", "amg_kernel_launches", "amg_apply_noalloc", "amg_gs_variant", "amg_set_gs_variant", "amg_row_shape", "amg_profile_arnoldi", "amg_level_get_vanka", "amg_level_get_ilu",
             "amg_coarse_inverse", "amg_set_wait_limit", "amg_level_get_gs_map",
             "amg_server_params_default", "amg_server_create", "amg_server_reserve", "amg_server_submit", "amg_server_progress",
             "amg_server_result", "amg_server_state", "amg_server_get_stats", "amg_server_destroy", "amg_server_last_error"]
@@ -116,6 +116,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
         f.restype = ctypes.c_int
     lib.amg_profile_vcycle.argtypes = [vp, ctypes.c_int, ctypes.c_int, _f64p, _i64p, vp]
     lib.amg_profile_vcycle.restype = ctypes.c_int
+    lib.amg_profile_arnoldi.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _f64p, _f64p, vp]
+    lib.amg_profile_arnoldi.restype = ctypes.c_int
     lib.amg_gs_variant.argtypes = [vp, ctypes.c_int, ctypes.c_int, _i32p, ctypes.POINTER(ctypes.c_float)]
     lib.amg_gs_variant.restype = ctypes.c_int
     lib.amg_set_gs_variant.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
@@ -326,6 +328,14 @@ class Hierarchy:
                                                  _ptr(its, ctypes.c_int), _ptr(rel, ctypes.c_double),
                                                  _stream_ptr(stream)))
         return st, its, rel
+
+    def profile_arnoldi(self, nrhs, nv, reps=10, stream=None):
+        """amg_profile_arnoldi: average ms of the inner-product and the update kernel of one
+        Gram-Schmidt pass with nv basis vectors (overwrites the solver workspace)."""
+        a, b = ctypes.c_double(), ctypes.c_double()
+        _check(load().amg_profile_arnoldi(self._h, int(nrhs), int(nv), int(reps), ctypes.byref(a), ctypes.byref(b),
+                                          _stream_ptr(stream)))
+        return a.value, b.value
 
     def profile_vcycle(self, nrhs, reps=10, stream=None):
         """Per (level, kernel class) summed ms and launch counts over `reps` cycles

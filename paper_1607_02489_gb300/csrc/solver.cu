@@ -741,6 +741,39 @@ void ensure_ws(amg_hierarchy* h, int K, int m) {
   h->kry = std::move(w);
 }
 
+// One Gram-Schmidt pass with nv basis vectors on the solver's own workspace (zeroed
+// first: the FP64 work does not depend on the values), timed with CUDA events on
+// `s`: the inner products with the norm (k_mdot_partial, nv + 1 outputs per column)
+// and the update with the norm (k_maxpy), each averaged over reps launches.
+template <int K>
+void profile_arnoldi_k(amg_hierarchy* h, int nv, int reps, double* ms_dot, double* ms_update, cudaStream_t s) {
+  Krylov& w = *h->kry;
+  const long long NK = w.N * K;
+  EMIN_CUDA(cudaMemsetAsync(w.V, 0, sizeof(double) * (size_t)NK * (nv + 1), s));
+  EMIN_CUDA(cudaMemsetAsync(w.w, 0, sizeof(double) * (size_t)NK, s));
+  EMIN_CUDA(cudaMemsetAsync(w.hbuf, 0, sizeof(double) * (size_t)(nv + 2) * K, s));
+  const int rb = red_blocks(NK);
+  cudaEvent_t e[3];
+  for (cudaEvent_t& ev : e) EMIN_CUDA(cudaEventCreate(&ev));
+  float tot_dot = 0.f, tot_upd = 0.f;
+  for (int rep = 0; rep <= reps; ++rep) {  // rep 0 warms up
+    EMIN_CUDA(cudaEventRecord(e[0], s));
+    k_mdot_partial<K, double><<<dim3(rb, dot_split(rb, nv + 1)), kBlock, 0, s>>>(NK, nv, 1, w.V, w.w, w.part, nullptr);
+    EMIN_CUDA(cudaEventRecord(e[1], s));
+    k_maxpy<K, double><<<rb, kBlock, 0, s>>>(NK, nv, w.V, w.hbuf, w.w, w.part, nullptr);
+    EMIN_CUDA(cudaEventRecord(e[2], s));
+    EMIN_CUDA(cudaEventSynchronize(e[2]));
+    float a = 0.f, b = 0.f;
+    EMIN_CUDA(cudaEventElapsedTime(&a, e[0], e[1]));
+    EMIN_CUDA(cudaEventElapsedTime(&b, e[1], e[2]));
+    if (rep > 0) tot_dot += a, tot_upd += b;
+  }
+  for (cudaEvent_t ev : e) cudaEventDestroy(ev);
+  h->launches += 2LL * (reps + 1);
+  *ms_dot = tot_dot / reps;
+  *ms_update = tot_upd / reps;
+}
+
 amg_status fgmres_blocking(amg_hierarchy* h, const double* b, double* x, const double* bh, double* xh, int nrhs,
                            double rtol, int restart, int maxit, int* iters, double* relres, cudaStream_t s) {
   ensure_ws(h, round_k(nrhs), restart);
@@ -1211,6 +1244,31 @@ amg_status amg_profile_vcycle(amg_handle h, int nrhs, int reps, double* ms, long
   std::fill(count, count + n, 0LL);
   cudaError_t e = h->vc()->profile(round_k(nrhs), reps, (cudaStream_t)stream, ms, count);
   if (e != cudaSuccess) return fail(AMG_ERR_CUDA, cudaGetErrorString(e));
+  return AMG_OK;
+}
+
+amg_status amg_profile_arnoldi(amg_handle h, int nrhs, int nv, int reps, double* ms_dot, double* ms_update,
+                               void* stream) {
+  if (!h || !ms_dot || !ms_update || reps < 1 || nv < 1) return fail(AMG_ERR_ARG, "null argument, reps or nv < 1");
+  if (!h->vc()) return fail(AMG_ERR_ARG, "hierarchy was built with host_only");
+  if (nrhs < 1 || round_k(nrhs) > h->vc()->kmax()) return fail(AMG_ERR_ARG, "nrhs exceeds max_nrhs");
+  try {
+    const int K = round_k(nrhs);
+    ensure_ws(h, K, nv);
+    switch (K) {
+      case 1: profile_arnoldi_k<1>(h, nv, reps, ms_dot, ms_update, (cudaStream_t)stream); break;
+      case 2: profile_arnoldi_k<2>(h, nv, reps, ms_dot, ms_update, (cudaStream_t)stream); break;
+      case 4: profile_arnoldi_k<4>(h, nv, reps, ms_dot, ms_update, (cudaStream_t)stream); break;
+      case 8: profile_arnoldi_k<8>(h, nv, reps, ms_dot, ms_update, (cudaStream_t)stream); break;
+      case 16: profile_arnoldi_k<16>(h, nv, reps, ms_dot, ms_update, (cudaStream_t)stream); break;
+      case 32: profile_arnoldi_k<32>(h, nv, reps, ms_dot, ms_update, (cudaStream_t)stream); break;
+    }
+  } catch (const std::bad_alloc&) {
+    return fail(AMG_ERR_OOM, "host allocation failed");
+  } catch (const std::exception& e) {
+    const std::string m = e.what();
+    return fail(m.find("cudaMalloc") != std::string::npos ? AMG_ERR_OOM : AMG_ERR_CUDA, m);
+  }
   return AMG_OK;
 }
 

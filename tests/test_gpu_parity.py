@@ -309,3 +309,20 @@ def test_pipelined_gauss_seidel_shapes_match_phase_launches(case, fp32):
         assert agree <= (1e-4 if fp32 else 1e-13)
         if zo is not None:
             assert np.all(_relerr(z, zo) <= 1e-11)
+
+
+def test_arnoldi_timing_entry_point():
+    """amg_profile_arnoldi times one Gram-Schmidt pass on the solver's workspace (bench.py
+    reports it as the FP64 roofline of the Arnoldi kernels): positive times, nv < 1
+    refused, and a solve afterwards is unaffected."""
+    p = stokes_lid_2d(16, nrhs=2)
+    H = g.Hierarchy(p, max_nrhs=2)
+    t_dot, t_upd = H.profile_arnoldi(2, 5, reps=3)
+    assert t_dot > 0 and t_upd > 0
+    with pytest.raises(g.AmgError) as exc:
+        H.profile_arnoldi(2, 0)
+    assert exc.value.status == -1
+    b = torch.tensor(p.b, device="cuda")
+    x = torch.zeros_like(b)
+    st, its, rel = H.fgmres(b, x, rtol=1e-8)
+    assert st == g.AMG_OK and np.all(rel <= 1e-8)

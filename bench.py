@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--ncu", action="store_true",
                     help="short run for an ncu launch list: one warm-up solve, then one solve (FP32 V-cycle) "
                          "inside a cudaProfilerStart/Stop range")
+    ap.add_argument("--ncu-config", default=None, choices=sorted(CONFIGS),
+                    help="like --ncu on one of the other configs (FP32 V-cycle, its own right-hand sides)")
     ap.add_argument("--ncu-setup", action="store_true",
                     help="short run for ncu: a hierarchy for the bench workload, a first device reuse of it, then "
                          "a second device reuse inside a cudaProfilerStart/Stop range")
@@ -595,7 +597,7 @@ def main():
         return reference_main(args)
     if args.configs:
         return configs_main(args)
-    if args.ncu or args.ncu_setup:
+    if args.ncu or args.ncu_setup or args.ncu_config:
         args.no_cpu_baseline = True
     import numpy as np
     import torch
@@ -632,8 +634,10 @@ def main():
         torch.cuda.profiler.stop()
         print(f"device reuse setup: {R2.num_levels()} levels", flush=True)
         return
-    if args.ncu:
-        H = g.Hierarchy(p, max_nrhs=NRHS, vcycle_fp32=1)
+    if args.ncu or args.ncu_config:
+        if args.ncu_config:
+            p = _config_problem(CONFIGS[args.ncu_config])
+        H = g.Hierarchy(p, max_nrhs=p.b.shape[1], vcycle_fp32=1)
         b = torch.tensor(p.b, device=dev)
         x = torch.zeros_like(b)
         for rep in range(2):

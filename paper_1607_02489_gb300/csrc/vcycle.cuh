@@ -532,7 +532,9 @@ class DeviceVCycle : public VCycleIface {
       mark_begin(l, kSchurRhs, s);
       launch_rows<K>(kSchurRhs, l, shape(l, K, kSchurRhs), zero, s);
       mark_end(s);
-      cudaMemsetAsync(B.dp, 0, sizeof(T) * (size_t)L.n_p * K, s);
+      // the sweeps start from dp = 0; the dense map writes every entry of dp itself
+      if (!(gsM_[l] && (*tune_)[(size_t)l * 6 + kslot(K)].kind == kGsDense))
+        cudaMemsetAsync(B.dp, 0, sizeof(T) * (size_t)L.n_p * K, s);
       mark_begin(l, kGsColor, s);
       launch_gs<K>(l, s);
       mark_end(s);
